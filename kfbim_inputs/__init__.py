@@ -1,0 +1,144 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests/bench and by the oracle.
+
+This module holds no arithmetic of the method itself: only geometry
+descriptors (plain parameters of analytic surfaces), closed-form manufactured
+Stokes fields used as boundary data and forcing, and seeded random densities.
+Each consumer evaluates level sets, control points and everything else with
+its own code.
+
+Workloads (all in the bounding box [-1, 1]^3, viscosity 1):
+  * sphere: radius 0.5 centred at the origin, N = 32 (plain FP64 case);
+  * star:   r(theta, phi) = 0.5 + 0.1 sin(3 theta) cos(4 phi) (theta = polar
+            angle, phi = azimuth), N = 64 and N = 128 (headline case);
+  * ellipsoid: semi-axes (0.6, 0.45, 0.35) under a seeded rotation.
+Boundary data come from the divergence-free manufactured field
+u = (sin x cos y cos z, -cos x sin y cos z, 0), p = sin(x + y + z).
+"""
+import numpy as np
+
+BOX = (-1.0, 1.0)
+
+
+def sphere(radius=0.5, center=(0.0, 0.0, 0.0)):
+    return {"kind": "sphere", "center": [float(c) for c in center], "radius": float(radius)}
+
+
+def star(r0=0.5, eps=0.1, m=3, n=4, center=(0.0, 0.0, 0.0)):
+    """Star surface r(theta, phi) = r0 + eps sin(m theta) cos(n phi)."""
+    return {"kind": "star", "center": [float(c) for c in center], "r0": float(r0),
+            "eps": float(eps), "m": int(m), "n": int(n)}
+
+
+def seeded_rotation(seed):
+    """Rotation from the QR factorisation of a seeded Gaussian 3x3 matrix,
+    columns sign-fixed by diag(R) > 0 and det = +1."""
+    rng = np.random.default_rng(seed)
+    q, r = np.linalg.qr(rng.standard_normal((3, 3)))
+    q = q * np.sign(np.diag(r))[None, :]
+    if np.linalg.det(q) < 0:
+        q[:, 2] = -q[:, 2]
+    return q
+
+
+def ellipsoid(axes=(0.6, 0.45, 0.35), rotation=None, center=(0.0, 0.0, 0.0)):
+    rot = np.eye(3) if rotation is None else np.asarray(rotation, dtype=np.float64)
+    return {"kind": "ellipsoid", "center": [float(c) for c in center],
+            "axes": [float(a) for a in axes], "rotation": rot.reshape(-1).tolist()}
+
+
+def grid(N, lo=BOX[0], hi=BOX[1]):
+    return {"N": int(N), "lo": float(lo), "hi": float(hi)}
+
+
+# ---------------------------------------------------------------- workloads
+WORKLOADS = {
+    "sphere32": (sphere(), grid(32)),
+    "star64": (star(), grid(64)),
+    "star128": (star(), grid(128)),
+}
+
+
+# ------------------------------------------------- manufactured Stokes field
+def stokes_velocity(x):
+    """u = (sin x cos y cos z, -cos x sin y cos z, 0); x has shape (..., 3)."""
+    x = np.asarray(x, dtype=np.float64)
+    X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
+    u1 = np.sin(X) * np.cos(Y) * np.cos(Z)
+    u2 = -np.cos(X) * np.sin(Y) * np.cos(Z)
+    u3 = np.zeros_like(X)
+    return np.stack([u1, u2, u3], axis=-1)
+
+
+def stokes_pressure(x):
+    x = np.asarray(x, dtype=np.float64)
+    return np.sin(x[..., 0] + x[..., 1] + x[..., 2])
+
+
+def stokes_forcing(x, mu=1.0):
+    """f = -mu Lap u + grad p for the manufactured pair above."""
+    x = np.asarray(x, dtype=np.float64)
+    X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
+    c = np.cos(X + Y + Z)
+    f1 = 3.0 * mu * np.sin(X) * np.cos(Y) * np.cos(Z) + c
+    f2 = -3.0 * mu * np.cos(X) * np.sin(Y) * np.cos(Z) + c
+    f3 = c
+    return np.stack([f1, f2, f3], axis=-1)
+
+
+# --------------------------------------------------------- seeded densities
+def random_density(n, seed):
+    """Seeded N(0,1) values, one per control point (for linear-map parity)."""
+    return np.random.default_rng(seed).standard_normal(n)
+
+
+def smooth_field(seed, degree=3):
+    """Seeded smooth vector field x -> (3,) as a sum of low-frequency
+    trigonometric modes with N(0,1)/(1+l)^2 amplitudes (l = mode order)."""
+    rng = np.random.default_rng(seed)
+    modes = []
+    for comp in range(3):
+        for l in range(degree + 1):
+            for _ in range(3):
+                k = rng.standard_normal(3)
+                k = k / np.linalg.norm(k) * (l + 0.5)
+                amp = rng.standard_normal() / (1.0 + l) ** 2
+                ph = rng.uniform(0, 2 * np.pi)
+                modes.append((comp, k, amp, ph))
+
+    def field(x):
+        x = np.asarray(x, dtype=np.float64)
+        out = np.zeros(x.shape[:-1] + (3,))
+        for comp, k, amp, ph in modes:
+            out[..., comp] += amp * np.cos(x @ k + ph)
+        return out
+
+    return field
+
+
+# ------------------------------ paper Example 5.1 (sphere r = 1, box +-1.2)
+def example51_velocity(x):
+    """Example 5.1's velocity with u^(2)'s y^2(1 - y^2) read as y^2(2 - y^2):
+    the printed field has div u = -2y; this reading is divergence-free."""
+    x = np.asarray(x, dtype=np.float64)
+    X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
+    u1 = X**2 * (2 - X**2) + 4 * X * Y * (X**2 + Y**2 - 1) + Z**2 * (3 * Z**2 - 6 * X**2 - 2)
+    u2 = X**2 * (3 * X**2 - 6 * Y**2 - 1) + Y**2 * (2 - Y**2)
+    u3 = 4 * Z * X * (Z**2 + X**2 - 1)
+    return np.stack([u1, u2, u3], axis=-1)
+
+
+def example51_pressure(x):
+    x = np.asarray(x, dtype=np.float64)
+    X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
+    return 8 * Y * (3 * X**2 - Y**2) + 8 * X * (3 * Z**2 - X**2)
+
+
+def example51_forcing(x, mu=1.0):
+    """-mu Lap u + grad p for the field above (expanded by hand from the
+    polynomials): Lap u = (24z^2 - 24x^2 + 48xy, 24x^2 - 24y^2 + 2, 48xz) and
+    grad p = (24z^2 - 24x^2 + 48xy, 24x^2 - 24y^2, 48xz)."""
+    x = np.asarray(x, dtype=np.float64)
+    X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
+    lap = np.stack([24 * Z**2 - 24 * X**2 + 48 * X * Y, 24 * X**2 - 24 * Y**2 + 2, 48 * X * Z], -1)
+    gp = np.stack([24 * Z**2 - 24 * X**2 + 48 * X * Y, 24 * X**2 - 24 * Y**2, 48 * X * Z], -1)
+    return -mu * lap + gp

@@ -1,0 +1,203 @@
+/*
+ * kfbim.h - C ABI of the GB300 kernel-free boundary integral (KFBI) solver for
+ * the 3D Stokes interior Dirichlet problem (arXiv 2303.04992).
+ *
+ * Problem (Sec. 2, Eq. SP):  -mu Lap u + grad p = f,  div u = 0 in Omega,
+ * u = g on Gamma = dOmega.  Omega is embedded in the cube B = [lo, hi]^3 with
+ * an N^3 MAC grid (Sec. 4.2).  The solution is u = G_v f - M_v phi with the
+ * density phi solving the second-kind BIE 1/2 phi - M_v phi = g - G_v f
+ * (Eq. BIE-S), solved by GMRES from phi = 0 (Alg. 1 step 3).  Every integral is
+ * evaluated by solving the unified interface problem IUS-1..5 on the grid
+ * (Sec. 4): corrected MAC scheme (Eq. MAC), Schur-complement CG with an FFT
+ * Poisson solver (Eq. linearS1, items i-iii), and ten-node quadratic trace
+ * interpolation (Sec. 4.4).
+ *
+ * Conventions
+ *  - Every pointer named *_dev is CUDA device memory owned by the caller; every
+ *    *_host pointer is host memory owned by the caller.  The library owns its
+ *    context, tables and workspace (allocated in kfbim_setup, freed in
+ *    kfbim_destroy).
+ *  - Work is enqueued on the caller's `stream` (a cudaStream_t, NULL = legacy
+ *    default stream).  Calls that iterate to a tolerance synchronise that stream
+ *    to read one convergence scalar per iteration.
+ *  - Grid fields are N^3 doubles in C order [k][j][i] (i = x fastest).  Face
+ *    field u^(c) holds at (i,j,k) the value at face index i (c = 1), j (c = 2)
+ *    or k (c = 3) along its normal axis, at lo + index*h, and at cell-centre
+ *    coordinates lo + (index + 1/2) h across it; face index 0 is the wall and
+ *    is returned as 0.  The pressure field p holds cell centres.
+ *  - Control points: the intersections of Gamma with the grid lines of u^(c)'s
+ *    own grid (Sec. 3), ordered by component c, line axis, line, position.
+ *    The "primary" points (line most normal to Gamma) carry the density
+ *    unknowns and the BIE equations; density vectors are ordered like the
+ *    primary points.
+ *  - Return value: KFBIM_OK or a negative kfbim_status; kfbim_last_error()
+ *    returns the message of the last failure on that context.  Invalid inputs
+ *    are reported, never aborted on.  On KFBIM_E_NOCONV the outputs still hold
+ *    the last iterate.
+ */
+#ifndef KFBIM_H
+#define KFBIM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kfbim_ctx kfbim_ctx;
+
+typedef enum {
+  KFBIM_OK = 0,
+  KFBIM_E_INVALID = -1,   /* bad argument (null pointer, size, option) */
+  KFBIM_E_GEOMETRY = -2,  /* interface not resolved by the grid */
+  KFBIM_E_NOCONV = -3,    /* GMRES or CG iteration cap reached */
+  KFBIM_E_NONFINITE = -4, /* NaN/Inf in an input or a residual */
+  KFBIM_E_CUDA = -5,      /* CUDA runtime error */
+  KFBIM_E_OOM = -6        /* device or host allocation failed */
+} kfbim_status;
+
+typedef enum { KFBIM_SPHERE = 0, KFBIM_ELLIPSOID = 1, KFBIM_STAR = 2 } kfbim_geometry_kind;
+
+/* Analytic interface, Omega = {F <= 0}.
+ *   SPHERE:    params[0] = radius.
+ *   ELLIPSOID: params[0..2] = semi-axes; rot = row-major 3x3 rotation Q, the
+ *              body frame is xi = Q^T (x - center).
+ *   STAR:      r(theta, phi) = params[0] + params[1] sin(params[2] theta)
+ *              cos(params[3] phi), theta polar angle from +z, phi azimuth. */
+typedef struct {
+  int kind;
+  double center[3];
+  double rot[9];
+  double params[8];
+} kfbim_geometry;
+
+typedef struct {
+  int N;          /* cells per axis, a power of two, 16 <= N <= 256 */
+  double lo, hi;  /* box [lo, hi]^3 */
+} kfbim_grid;
+
+typedef enum {
+  KFBIM_FP64 = 0,  /* every step in FP64 */
+  KFBIM_MIXED = 1  /* FP32 transforms and Schur CG inside FP64 iterative
+                      refinement of the corrected MAC system; jumps,
+                      corrections, traces, residuals and GMRES stay FP64 */
+} kfbim_precision;
+
+typedef struct {
+  double mu;          /* viscosity (> 0) */
+  int precision;      /* kfbim_precision */
+  double gmres_tol;   /* relative l2 residual, e.g. 1e-10 */
+  int gmres_max;      /* <= 200 */
+  double cg_tol;      /* FP64 Schur CG relative residual, e.g. 1e-14 */
+  int cg_max;
+  double refine_tol;  /* MIXED: relative residual of the FP64 system */
+  int refine_max;     /* MIXED: refinement sweeps cap */
+  double inner_tol;   /* MIXED: FP32 CG relative residual per sweep */
+} kfbim_options;
+
+typedef struct {
+  int gmres_iters;
+  int interface_solves;
+  int cg_iters;        /* total over all interface solves */
+  int refine_sweeps;   /* total (MIXED) */
+  double gmres_residual;
+} kfbim_stats;
+
+/* Fills *opt with the defaults (mu 1, FP64, gmres 1e-10/200, cg 1e-14/2000,
+ * refine 1e-13/8, inner 1e-5). */
+void kfbim_default_options(kfbim_options* opt);
+
+/* Alg. 1 step 1: grids, sides, intersections, frames, control points and all
+ * jump / correction / interpolation tables; uploads them to the current CUDA
+ * device.  Host work only, plus device allocations.  Errors: E_INVALID,
+ * E_GEOMETRY (interface within 3h of the wall, double crossings, too few fit
+ * neighbours), E_OOM, E_CUDA.  On error *ctx is NULL. */
+int kfbim_setup(const kfbim_geometry* geom, const kfbim_grid* grid,
+                const kfbim_options* opt, kfbim_ctx** ctx);
+
+/* Host-only variant of kfbim_setup: builds the control points and every table
+ * on the host and touches no GPU (for inspection and host-side tests).  The
+ * returned context supports kfbim_sizes, kfbim_points, kfbim_sides,
+ * kfbim_table_sizes and kfbim_destroy; solver calls on it return
+ * KFBIM_E_INVALID. */
+int kfbim_setup_host(const kfbim_geometry* geom, const kfbim_grid* grid,
+                     const kfbim_options* opt, kfbim_ctx** ctx);
+
+/* Releases every device and host resource of ctx (synchronises the device
+ * when ctx owns device memory). */
+int kfbim_destroy(kfbim_ctx* ctx);
+const char* kfbim_last_error(const kfbim_ctx* ctx);
+
+/* Sizes: all control points, primary points (density unknowns), N. */
+int kfbim_sizes(const kfbim_ctx* ctx, int64_t* n_points, int64_t* n_primary, int* N);
+
+/* Sizes of the sparse tables: surface-fit entries, correction rows (RHS
+ * targets at irregular nodes) and correction entries; each nullable. */
+int kfbim_table_sizes(const kfbim_ctx* ctx, int64_t* fit_nnz, int64_t* corr_rows,
+                      int64_t* corr_nnz);
+
+/* Control-point data (host, each nullable): xyz [n_points*3], comp (1..3),
+ * axis (0..2), primary flag (0/1). */
+int kfbim_points(const kfbim_ctx* ctx, double* xyz_host, int32_t* comp_host,
+                 int32_t* axis_host, int32_t* primary_host);
+
+/* Side of every node of grid c (0 = cells, 1..3 = faces of u^(c)), 1 = Omega;
+ * N^3 bytes in field layout. */
+int kfbim_sides(const kfbim_ctx* ctx, int c, uint8_t* side_host);
+
+/* One GMRES matvec (Prop. DBI): out = (1/2 I - M_v) phi at the primary points.
+ * phi_dev, out_dev: n_primary doubles (may not alias). */
+int kfbim_apply(kfbim_ctx* ctx, const double* phi_dev, double* out_dev, void* stream);
+
+/* Full solve (Alg. 1 steps 2-3 and the final interior fields).
+ *   g_dev      [n_primary]     Dirichlet data at the primary points.
+ *   fpts_dev   [3*n_points]    f at every control point, component-blocked
+ *                              (f^(1) for all points, then f^(2), f^(3));
+ *                              nullable (then f = 0).
+ *   fgrid_dev  [3*N^3]         f^(c) at the nodes of face grid c; nullable.
+ *                              Values outside Omega are ignored (f~ = 0 there).
+ *   phi_dev    [n_primary]     out: density.
+ *   u_dev      [3*N^3]         out, nullable: interface-problem velocity; its
+ *                              values at Omega nodes are u_h.
+ *   p_dev      [N^3]           out, nullable: pressure (cells), gauge
+ *                              mean(p) = mu * mean(g_cells) of the augmented
+ *                              system with gamma = 1, alpha = mu N^3.
+ *   stats      nullable. */
+int kfbim_solve(kfbim_ctx* ctx, const double* g_dev, const double* fpts_dev,
+                const double* fgrid_dev, double* phi_dev, double* u_dev, double* p_dev,
+                kfbim_stats* stats, void* stream);
+
+/* kfbim_solve with host buffers: copies inputs to the device, solves and
+ * copies phi (and u, p when non-null) back; same shapes as kfbim_solve. */
+int kfbim_solve_host(kfbim_ctx* ctx, const double* g_host, const double* fpts_host,
+                     const double* fgrid_host, double* phi_host, double* u_host,
+                     double* p_host, kfbim_stats* stats, void* stream);
+
+/* Stage entry points (same kernels as the solve path, exposed for parity tests).
+ * kfbim_jumps: jump values at every control point (Sec. 4.3), layout
+ *   J_dev[12 * n_points] slot-major: slot s of point y at s*n_points + y with
+ *   slots [u^(c)], [grad u^(c)] (3), [Hess u^(c)] (11,22,33,23,13,12),
+ *   [p], [d_a p] (a = the point's line axis). fpts_dev nullable.
+ * kfbim_interface: the unified interface solve IUS-1..5 on the grid for
+ *   density phi and forcing (fpts, fgrid nullable); writes u (3 N^3), p (N^3).
+ * kfbim_trace: u^+ at the primary points from face fields u and jumps J. */
+int kfbim_jumps(kfbim_ctx* ctx, const double* phi_dev, const double* fpts_dev,
+                double* J_dev, void* stream);
+int kfbim_interface(kfbim_ctx* ctx, const double* phi_dev, const double* fpts_dev,
+                    const double* fgrid_dev, double* u_dev, double* p_dev, void* stream);
+int kfbim_trace(kfbim_ctx* ctx, const double* u_dev, const double* J_dev,
+                double* out_dev, void* stream);
+
+/* FFT Poisson solve -Delta_h u = r on face grid c (1..3) with the box
+ * conditions of Sec. 4.2 (DST-I across the normal axis, DST-II along the
+ * others): r_dev, u_dev N^3 doubles (wall face ignored / written 0). */
+int kfbim_poisson(kfbim_ctx* ctx, int c, const double* r_dev, double* u_dev, void* stream);
+
+/* Schur operator of item ii): q = (1/mu) G^T (-Delta_h)^{-1} G d + sum(d)/alpha,
+ * alpha = mu N^3; d_dev, q_dev N^3 doubles (cells). */
+int kfbim_schur_apply(kfbim_ctx* ctx, const double* d_dev, double* q_dev, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KFBIM_H */

@@ -1,0 +1,358 @@
+// Sparse and pointwise kernels of the KFBI matvec: jump evaluation (Sec. 4.3
+// jump conditions), right-hand-side corrections (Sec. 4.3 items 1-4), MAC
+// stencils and residual (Sec. 4.2), trace interpolation (Sec. 4.4) and the
+// reductions used by CG and GMRES.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace kfbim {
+
+constexpr int RED_THREADS = 256;
+constexpr int RED_BLOCKS = 304;   // 2 x 152 SMs
+
+// ------------------------------------------------------------------ jumps
+// One warp per control point: fitted value and five surface derivatives of
+// each density component (weighted sums over primary neighbours), then the
+// per-point 11 x 18 jump map.  J is slot-major: J[s * n + y].
+__global__ void k_jumps(const double* __restrict__ phi, const double* __restrict__ fpts,
+                        int64_t n, const int32_t* __restrict__ comp, const int32_t* __restrict__ pid,
+                        const int64_t* __restrict__ fit_ptr, const int32_t* __restrict__ fit_col,
+                        const double* __restrict__ fit_w, const double* __restrict__ jmap,
+                        double* __restrict__ J) {
+  const int lane = threadIdx.x & 31;
+  const int64_t y = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (y >= n) return;
+  const int c = comp[y] - 1;
+  double acc[3][6];
+#pragma unroll
+  for (int cc = 0; cc < 3; ++cc)
+#pragma unroll
+    for (int s = 0; s < 6; ++s) acc[cc][s] = 0.0;
+#pragma unroll
+  for (int cc = 0; cc < 3; ++cc) {
+    const int64_t b = fit_ptr[3 * y + cc], e = fit_ptr[3 * y + cc + 1];
+    for (int64_t q = b + lane; q < e; q += 32) {
+      const double v = phi[fit_col[q]];
+      const double* w = fit_w + 6 * q;
+#pragma unroll
+      for (int s = 0; s < 6; ++s) acc[cc][s] += w[s] * v;
+    }
+  }
+#pragma unroll
+  for (int cc = 0; cc < 3; ++cc)
+#pragma unroll
+    for (int s = 0; s < 6; ++s)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc[cc][s] += __shfl_xor_sync(0xffffffffu, acc[cc][s], o);
+  double in[18];
+#pragma unroll
+  for (int cc = 0; cc < 3; ++cc)
+#pragma unroll
+    for (int s = 0; s < 5; ++s) in[5 * cc + s] = acc[cc][s + 1];
+#pragma unroll
+  for (int cc = 0; cc < 3; ++cc) in[15 + cc] = fpts ? fpts[cc * n + y] : 0.0;
+  if (lane == 0) {
+    const int64_t p = pid[y];
+    double v0 = (p >= 0) ? phi[p] : 0.0;
+    if (p < 0) {
+      // secondary point: fitted value of its own component
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc)
+        if (cc == c) v0 = acc[cc][0];
+    }
+    J[y] = v0;
+  }
+  if (lane < 11) {
+    const double* M = jmap + ((size_t)y * 11 + lane) * 18;
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < 18; ++q) s += M[q] * in[q];
+    J[(int64_t)(lane + 1) * n + y] = s;
+  }
+}
+
+// ------------------------------------------------------------ RHS assembly
+// f~ on the face grids (f in Omega, 0 outside and on wall faces) and g = 0.
+__global__ void k_rhs_fill(const double* __restrict__ fgrid, const uint8_t* __restrict__ side1,
+                           const uint8_t* __restrict__ side2, const uint8_t* __restrict__ side3,
+                           int N, double* __restrict__ rhs) {
+  const int64_t N3 = (int64_t)N * N * N;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < 4 * N3;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int f = (int)(e / N3);
+    const int64_t x = e - f * N3;
+    double v = 0.0;
+    if (f < 3 && fgrid) {
+      const uint8_t* side = f == 0 ? side1 : (f == 1 ? side2 : side3);
+      const int i = (int)(x % N), j = (int)((x / N) % N), k = (int)(x / ((int64_t)N * N));
+      const int nrm = f == 0 ? i : (f == 1 ? j : k);
+      if (side[x] && nrm > 0) v = fgrid[e];
+    }
+    rhs[e] = v;
+  }
+}
+
+// Correction rows: rhs[row] += sum coef * J[src] (CSR keyed by target, no atomics).
+__global__ void k_corrections(const int64_t* __restrict__ row, const int64_t* __restrict__ ptr,
+                              const int64_t* __restrict__ src, const double* __restrict__ coef,
+                              int64_t nrows, const double* __restrict__ J, double* __restrict__ rhs) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nrows;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int64_t e = ptr[r]; e < ptr[r + 1]; ++e) s += coef[e] * J[src[e]];
+    rhs[row[r]] += s;
+  }
+}
+
+// ------------------------------------------------------------------ trace
+__global__ void k_trace(const double* __restrict__ u, const double* __restrict__ J, int64_t n_all,
+                        int64_t n_prim, const int64_t* __restrict__ prim_of, int N,
+                        const int32_t* __restrict__ tcomp, const int32_t* __restrict__ tnode,
+                        const double* __restrict__ tw, const double* __restrict__ tcj,
+                        double* __restrict__ out) {
+  const int64_t N3 = (int64_t)N * N * N;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n_prim;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const double* uc = u + (int64_t)(tcomp[q] - 1) * N3;
+    const int64_t y = prim_of[q];
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < 10; ++i) s += tw[10 * q + i] * uc[tnode[10 * q + i]];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) s += tcj[10 * q + k] * J[(int64_t)k * n_all + y];
+    out[q] = s;
+  }
+}
+
+// --------------------------------------------------------- MAC stencils
+__device__ __forceinline__ void unflat(int64_t x, int N, int& i, int& j, int& k) {
+  i = (int)(x % N);
+  j = (int)((x / N) % N);
+  k = (int)(x / ((int64_t)N * N));
+}
+
+// r^(c) = f^(c) - G_c p   (face grid c; wall faces 0)
+template <typename Tp, typename Tout>
+__global__ void k_f_minus_gp(const double* __restrict__ f, const Tp* __restrict__ p, int N, double h,
+                             Tout* __restrict__ r) {
+  const int64_t N3 = (int64_t)N * N * N;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < 3 * N3;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e / N3);
+    const int64_t x = e - c * N3;
+    int id[3];
+    unflat(x, N, id[0], id[1], id[2]);
+    double v = 0.0;
+    if (id[c] > 0) {
+      const int64_t st = c == 0 ? 1 : (c == 1 ? N : (int64_t)N * N);
+      v = f[e] - (double(p[x]) - double(p[x - st])) / h;
+    }
+    r[e] = Tout(v);
+  }
+}
+
+// FP64 residual of the corrected MAC system (Eq. MAC with the lambda_h
+// projection): rf = f - (-mu Lap u + G p), rg = g - mean(g) - D u.
+__global__ void k_mac_residual(const double* __restrict__ f, const double* __restrict__ g,
+                               const double* __restrict__ gmean, const double* __restrict__ u,
+                               const double* __restrict__ p, int N, double h, double mu,
+                               double* __restrict__ rf, double* __restrict__ rg) {
+  const int64_t N3 = (int64_t)N * N * N;
+  const double ih2 = 1.0 / (h * h), ih = 1.0 / h;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < 4 * N3;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e / N3);
+    const int64_t x = e - c * N3;
+    int id[3];
+    unflat(x, N, id[0], id[1], id[2]);
+    const int64_t st[3] = {1, N, (int64_t)N * N};
+    if (c < 3) {
+      if (id[c] == 0) { rf[e] = 0.0; continue; }
+      const double* uc = u + c * N3;
+      const double u0 = uc[x];
+      double lap = 0.0;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        double um, up;
+        if (b == c) {
+          um = (id[b] - 1 >= 1) ? uc[x - st[b]] : 0.0;
+          up = (id[b] + 1 <= N - 1) ? uc[x + st[b]] : 0.0;
+        } else {
+          um = (id[b] > 0) ? uc[x - st[b]] : -u0;
+          up = (id[b] < N - 1) ? uc[x + st[b]] : -u0;
+        }
+        lap += (up - 2.0 * u0 + um) * ih2;
+      }
+      const double gp = (p[x] - p[x - st[c]]) * ih;
+      rf[e] = f[e] - (-mu * lap + gp);
+    } else {
+      double d = 0.0;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const double* ub = u + b * N3;
+        const double lo = (id[b] >= 1) ? ub[x] : 0.0;
+        const double hi = (id[b] + 1 <= N - 1) ? ub[x + st[b]] : 0.0;
+        d += (hi - lo) * ih;
+      }
+      rg[x] = g[x] - gmean[0] - d;
+    }
+  }
+}
+
+// ------------------------------------------------------------ reductions
+template <typename Ta>
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  v = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+  if (w == 0) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  }
+  __syncthreads();
+  return v;
+}
+
+// partial[blockIdx.x] = sum x*y (y == nullptr: sum x; x == y allowed)
+template <typename Ta, typename Tb>
+__global__ void k_dot_partial(const Ta* __restrict__ x, const Tb* __restrict__ y, int64_t n,
+                              double* __restrict__ partial) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    s += y ? double(x[e]) * double(y[e]) : double(x[e]);
+  s = block_sum<double>(s, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// out[j] = scale * sum_b partial[j * nb + b]  (fixed order, one block per j)
+__global__ void k_sum_partials(const double* __restrict__ partial, int nb, double scale,
+                               double* __restrict__ out) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) s += partial[(int64_t)blockIdx.x * nb + b];
+  s = block_sum<double>(s, sh);
+  if (threadIdx.x == 0) out[blockIdx.x] = scale * s;
+}
+
+// ----------------------------------------------------------------- CG
+// Device scalars of one CG run.
+struct CGScalars {
+  double rr, bb, dq, alpha, beta, sumd, rank1;  // rank1 = 1/alpha_lambda
+};
+
+// After the dot d.q_S: alpha = rr / (d.q_S + sumd^2 * rank1)
+__global__ void k_cg_alpha(CGScalars* s, const double* dq) {
+  const double den = dq[0] + s->sumd * s->sumd * s->rank1;
+  s->dq = den;
+  s->alpha = (den != 0.0) ? s->rr / den : 0.0;
+}
+
+// x += alpha d; r -= alpha (q + sumd * rank1); partial sums of r^2
+template <typename T>
+__global__ void k_cg_update(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ d,
+                            const T* __restrict__ q, int64_t n, const CGScalars* __restrict__ s,
+                            double* __restrict__ partial) {
+  __shared__ double sh[32];
+  const double a = s->alpha;
+  const double c1 = s->sumd * s->rank1;
+  double acc = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const double rv = double(r[e]) - a * (double(q[e]) + c1);
+    x[e] = T(double(x[e]) + a * double(d[e]));
+    r[e] = T(rv);
+    acc += double(T(rv)) * double(T(rv));
+  }
+  acc = block_sum<double>(acc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+__global__ void k_cg_beta(CGScalars* s, const double* rr_new) {
+  const double rn = rr_new[0];
+  s->beta = (s->rr != 0.0) ? rn / s->rr : 0.0;
+  s->rr = rn;
+}
+
+// d = r + beta d; partial sums of d
+template <typename T>
+__global__ void k_cg_direction(T* __restrict__ d, const T* __restrict__ r, int64_t n,
+                               const CGScalars* __restrict__ s, double* __restrict__ partial) {
+  __shared__ double sh[32];
+  const double b = s->beta;
+  double acc = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const T v = T(double(r[e]) + b * double(d[e]));
+    d[e] = v;
+    acc += double(v);
+  }
+  acc = block_sum<double>(acc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+__global__ void k_set_sumd(CGScalars* s, const double* sumd) { s->sumd = sumd[0]; }
+
+// --------------------------------------------------------- vector helpers
+template <typename Ta, typename Tb>
+__global__ void k_convert(const Ta* __restrict__ a, Tb* __restrict__ b, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    b[e] = Tb(a[e]);
+}
+
+template <typename Ta>
+__global__ void k_add_to(const Ta* __restrict__ a, double* __restrict__ b, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    b[e] += double(a[e]);
+}
+
+// b[e] = a[e] + shift[0] * sc   (pressure gauge)
+__global__ void k_shift(double* __restrict__ b, const double* __restrict__ shift, double sc, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    b[e] += sc * shift[0];
+}
+
+// -------------------------------------------------------------- GMRES
+// partial[j * nb + b] = sum_e V[j][e] w[e]
+__global__ void k_multidot_partial(const double* __restrict__ V, int64_t ld, const double* __restrict__ w,
+                                   int64_t n, double* __restrict__ partial) {
+  __shared__ double sh[32];
+  const int j = blockIdx.y;
+  const double* v = V + (int64_t)j * ld;
+  double s = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    s += v[e] * w[e];
+  s = block_sum<double>(s, sh);
+  if (threadIdx.x == 0) partial[(int64_t)j * gridDim.x + blockIdx.x] = s;
+}
+
+// w -= sum_j h[j] V[j]   (sign = -1)  or  w = sum_j h[j] V[j] (sign = 0)
+__global__ void k_multi_axpy(const double* __restrict__ V, int64_t ld, const double* __restrict__ hcoef,
+                             int k, double* __restrict__ w, int64_t n, int assign) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int j = 0; j < k; ++j) s += hcoef[j] * V[(int64_t)j * ld + e];
+    w[e] = assign ? s : w[e] - s;
+  }
+}
+
+__global__ void k_scale_copy(const double* __restrict__ a, double sc_host, const double* __restrict__ sc_dev,
+                             double* __restrict__ b, int64_t n) {
+  const double sc = sc_dev ? sc_host / sc_dev[0] : sc_host;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    b[e] = sc * a[e];
+}
+
+}  // namespace kfbim

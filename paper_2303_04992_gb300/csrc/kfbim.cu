@@ -1,0 +1,828 @@
+// C-ABI and device orchestration of the KFBI Stokes solver (see include/kfbim.h).
+//
+// Interface solve (Sec. 4, Alg. 1 step 2), all on the GPU:
+//   jumps (k_jumps) -> RHS f~ + corrections (k_rhs_fill, k_corrections)
+//   -> Schur RHS b = g + (1/mu) sum_c G_c^T (-Delta_c)^{-1} f^(c)
+//   -> CG on (S + gamma gamma^T / alpha) p = b with
+//      S = (1/mu) sum_c B_c^{-1} Lambda_c B_c
+//   -> u^(c) = (1/mu) (-Delta_c)^{-1} (f^(c) - G_c p).
+// S is applied spectrally: G_c maps the cell basis cos(pi a (i+1/2)/N) to the
+// face basis -(2/h) sin(pi a / 2N) sin(pi a i / N), so each term
+// G_c^T (-Delta_c)^{-1} G_c is diagonal in B_c = DCT-II along axis c times
+// DST-II across, with eigenvalue sin^2(a_c) / sum_b sin^2(a_b).  This is the
+// same operator as the paper's (up to rounding) with only length-N transforms.
+// MIXED precision runs the transforms and CG in FP32 inside FP64 iterative
+// refinement of the corrected MAC system.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "kernels.cuh"
+#include "transforms.cuh"
+
+using namespace kfbim;
+
+struct kfbim_ctx {
+  kfbim_options opt{};
+  std::string err;
+  HostTables host;
+  int N = 0;
+  int64_t N3 = 0, n_all = 0, n_prim = 0, n_corr_rows = 0;
+  double h = 0, mu = 1;
+  std::vector<void*> allocs;
+  // tables
+  int32_t *d_comp = nullptr, *d_pid = nullptr, *d_fit_col = nullptr, *d_tr_comp = nullptr,
+          *d_tr_node = nullptr;
+  int64_t *d_fit_ptr = nullptr, *d_corr_row = nullptr, *d_corr_ptr = nullptr,
+          *d_corr_src = nullptr, *d_prim_of = nullptr;
+  double *d_fit_w = nullptr, *d_jmap = nullptr, *d_corr_coef = nullptr, *d_tr_w = nullptr,
+         *d_tr_cj = nullptr, *d_s2 = nullptr;
+  uint8_t* d_side[4] = {nullptr, nullptr, nullptr, nullptr};
+  C2<double>* d_tw64 = nullptr;
+  C2<double>* d_q64 = nullptr;
+  C2<float>* d_tw32 = nullptr;
+  C2<float>* d_q32 = nullptr;
+  // FP64 workspace
+  double *J = nullptr, *rhs = nullptr, *u = nullptr, *p = nullptr, *t1 = nullptr, *t2 = nullptr;
+  double *cr = nullptr, *cd = nullptr, *cq = nullptr, *rres = nullptr, *zero_phi = nullptr;
+  double *partial = nullptr, *scal = nullptr;   // reduction partials, scalars
+  CGScalars* cgs = nullptr;
+  // FP32 workspace (mixed)
+  float *f1 = nullptr, *f2 = nullptr, *fx = nullptr, *fr = nullptr, *fd = nullptr, *fq = nullptr,
+        *fu = nullptr;
+  // GMRES
+  int gm_max = 0;
+  double *V = nullptr, *gw = nullptr, *gh = nullptr, *grhs = nullptr, *gy = nullptr;
+  double* pinned = nullptr;  // host scalars
+  // staging buffers of kfbim_solve_host (allocated on first use)
+  double *hs_g = nullptr, *hs_phi = nullptr, *hs_fp = nullptr, *hs_fg = nullptr, *hs_u = nullptr,
+         *hs_p = nullptr;
+  bool device = false;        // false for kfbim_setup_host contexts
+  int64_t fit_nnz = 0, corr_nnz = 0;
+  // counters of the current call
+  int cg_iters = 0, refine_sweeps = 0, interface_solves = 0;
+};
+
+namespace {
+
+struct CudaError {
+  std::string msg;
+};
+
+#define CK(call)                                                                   \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) throw CudaError{std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+  } while (0)
+
+template <typename T>
+T* dalloc(kfbim_ctx* c, size_t count) {
+  void* p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+  if (e != cudaSuccess) throw CudaError{std::string("cudaMalloc: ") + cudaGetErrorString(e)};
+  c->allocs.push_back(p);
+  return static_cast<T*>(p);
+}
+
+template <typename T>
+T* upload(kfbim_ctx* c, const std::vector<T>& v) {
+  T* d = dalloc<T>(c, v.size());
+  if (!v.empty()) CK(cudaMemcpy(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return d;
+}
+
+inline int grid_for(int64_t n, int threads = 256) {
+  int64_t b = (n + threads - 1) / threads;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 16));
+}
+
+inline void check_launch() {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) throw CudaError{std::string("kernel launch: ") + cudaGetErrorString(e)};
+}
+
+// ------------------------------------------------------------ transforms
+template <typename T>
+struct Tw;
+template <>
+struct Tw<double> {
+  static const C2<double>* tw(kfbim_ctx* c) { return c->d_tw64; }
+  static const C2<double>* q(kfbim_ctx* c) { return c->d_q64; }
+};
+template <>
+struct Tw<float> {
+  static const C2<float>* tw(kfbim_ctx* c) { return c->d_tw32; }
+  static const C2<float>* q(kfbim_ctx* c) { return c->d_q32; }
+};
+
+template <typename Tin, typename T, typename Tout>
+void pass(kfbim_ctx* c, const Tin* in, Tout* out, int axis, int t0, int t1, int wmode, int wc,
+          int acc, double scale, cudaStream_t s) {
+  PassArgs a;
+  a.N = c->N;
+  a.axis = axis;
+  a.type0 = t0;
+  a.type1 = t1;
+  a.wmode = wmode;
+  a.wc = wc;
+  for (int b = 0; b < 3; ++b) a.kind[b] = (b == wc) ? 0 : 1;
+  a.mu = c->mu;
+  a.h = c->h;
+  a.accumulate = acc;
+  a.scale = scale;
+  const size_t smem = pass_smem_bytes(c->N, sizeof(T));
+  auto kern = k_axis_pass<Tin, T, Tout>;
+  static size_t configured = 0;  // per template instance
+  if (smem > configured) {
+    CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    configured = smem;
+  }
+  const int blocks = (int)((int64_t)c->N * c->N / LPC);
+  kern<<<blocks, PASS_THREADS, smem, s>>>(in, out, a, Tw<T>::tw(c), Tw<T>::q(c), c->d_s2);
+  check_launch();
+}
+
+inline void others(int cax, int& o1, int& o2) {
+  o1 = (cax == 0) ? 1 : 0;
+  o2 = (cax == 2) ? 1 : 2;
+}
+
+// u = (1/mu) (-Delta_c)^{-1} r on face grid c (cax = c - 1)
+template <typename Tin, typename T, typename Tout>
+void face_poisson(kfbim_ctx* c, int cax, const Tin* r, Tout* u, T* t1, T* t2, cudaStream_t s) {
+  int o1, o2;
+  others(cax, o1, o2);
+  pass<Tin, T, T>(c, r, t1, o2, X_DST2F, X_NONE, W_NONE, cax, 0, 1.0, s);
+  pass<T, T, T>(c, t1, t2, o1, X_DST2F, X_NONE, W_NONE, cax, 0, 1.0, s);
+  pass<T, T, T>(c, t2, t1, cax, X_DST1F, X_DST1I, W_POISSON, cax, 0, 1.0, s);
+  pass<T, T, T>(c, t1, t2, o1, X_DST2I, X_NONE, W_NONE, cax, 0, 1.0, s);
+  pass<T, T, Tout>(c, t2, u, o2, X_DST2I, X_NONE, W_NONE, cax, 0, 1.0, s);
+}
+
+// b += (1/mu) G_c^T (-Delta_c)^{-1} f^(c)
+template <typename Tin, typename T>
+void schur_rhs_add(kfbim_ctx* c, int cax, const Tin* f, T* b, T* t1, T* t2, cudaStream_t s) {
+  int o1, o2;
+  others(cax, o1, o2);
+  pass<Tin, T, T>(c, f, t1, o2, X_DST2F, X_NONE, W_NONE, cax, 0, 1.0, s);
+  pass<T, T, T>(c, t1, t2, o1, X_DST2F, X_NONE, W_NONE, cax, 0, 1.0, s);
+  pass<T, T, T>(c, t2, t1, cax, X_DST1F, X_DCT2I, W_RHS, cax, 0, 1.0, s);
+  pass<T, T, T>(c, t1, t2, o1, X_DST2I, X_NONE, W_NONE, cax, 0, 1.0, s);
+  pass<T, T, T>(c, t2, b, o2, X_DST2I, X_NONE, W_NONE, cax, 1, 1.0, s);
+}
+
+// q = (1/mu) sum_c G_c^T (-Delta_c)^{-1} G_c d   (rank-one term handled in CG)
+template <typename T>
+void schur_apply(kfbim_ctx* c, const T* d, T* q, T* t1, T* t2, cudaStream_t s) {
+  for (int cax = 0; cax < 3; ++cax) {
+    int o1, o2;
+    others(cax, o1, o2);
+    pass<T, T, T>(c, d, t1, o2, X_DST2F, X_NONE, W_NONE, cax, 0, 1.0, s);
+    pass<T, T, T>(c, t1, t2, o1, X_DST2F, X_NONE, W_NONE, cax, 0, 1.0, s);
+    pass<T, T, T>(c, t2, t1, cax, X_DCT2F, X_DCT2I, W_SCHUR, cax, 0, 1.0, s);
+    pass<T, T, T>(c, t1, t2, o1, X_DST2I, X_NONE, W_NONE, cax, 0, 1.0, s);
+    pass<T, T, T>(c, t2, q, o2, X_DST2I, X_NONE, W_NONE, cax, cax > 0 ? 1 : 0, 1.0, s);
+  }
+}
+
+double read_scalar(kfbim_ctx* c, const double* dptr, cudaStream_t s) {
+  CK(cudaMemcpyAsync(c->pinned, dptr, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return c->pinned[0];
+}
+
+template <typename Ta, typename Tb>
+void dot(kfbim_ctx* c, const Ta* x, const Tb* y, int64_t n, double* out, double scale, cudaStream_t s) {
+  k_dot_partial<Ta, Tb><<<RED_BLOCKS, RED_THREADS, 0, s>>>(x, y, n, c->partial);
+  check_launch();
+  k_sum_partials<<<1, RED_THREADS, 0, s>>>(c->partial, RED_BLOCKS, scale, out);
+  check_launch();
+}
+
+// CG on (S + 1 1^T / (mu N^3)) x = b from x = 0.  Vectors of type T.
+template <typename T>
+int cg(kfbim_ctx* c, const T* b, T* x, T* r, T* d, T* q, T* t1, T* t2, double tol, int maxit,
+       cudaStream_t s, int* iters) {
+  const int64_t n = c->N3;
+  CGScalars init{};
+  init.rank1 = 1.0 / (c->mu * (double)n);
+  CK(cudaMemcpyAsync(c->cgs, &init, sizeof(CGScalars), cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(x, 0, n * sizeof(T), s));
+  CK(cudaMemcpyAsync(r, b, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(d, b, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  double* sc = c->scal;
+  dot(c, r, r, n, &c->cgs->rr, 1.0, s);
+  dot(c, r, r, n, &c->cgs->bb, 1.0, s);
+  dot(c, d, (const T*)nullptr, n, &c->cgs->sumd, 1.0, s);
+  double bb = read_scalar(c, &c->cgs->bb, s);
+  int it = 0;
+  if (bb == 0.0) {
+    *iters = 0;
+    return KFBIM_OK;
+  }
+  if (!std::isfinite(bb)) return KFBIM_E_NONFINITE;
+  const double stop = tol * tol * bb;
+  double rr = bb;
+  while (true) {
+    if (rr <= stop) break;
+    if (it >= maxit) {
+      *iters = it;
+      return KFBIM_E_NOCONV;
+    }
+    schur_apply<T>(c, d, q, t1, t2, s);
+    dot(c, d, q, n, sc, 1.0, s);
+    k_cg_alpha<<<1, 1, 0, s>>>(c->cgs, sc);
+    k_cg_update<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(x, r, d, q, n, c->cgs, c->partial);
+    k_sum_partials<<<1, RED_THREADS, 0, s>>>(c->partial, RED_BLOCKS, 1.0, sc + 1);
+    k_cg_beta<<<1, 1, 0, s>>>(c->cgs, sc + 1);
+    k_cg_direction<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(d, r, n, c->cgs, c->partial);
+    k_sum_partials<<<1, RED_THREADS, 0, s>>>(c->partial, RED_BLOCKS, 1.0, sc + 2);
+    k_set_sumd<<<1, 1, 0, s>>>(c->cgs, sc + 2);
+    check_launch();
+    ++it;
+    rr = read_scalar(c, &c->cgs->rr, s);
+    if (!std::isfinite(rr)) return KFBIM_E_NONFINITE;
+  }
+  *iters = it;
+  return KFBIM_OK;
+}
+
+// Solve the corrected MAC system for rhs = [f1|f2|f3|g] (FP64) -> u, p (FP64).
+int grid_solve_fp64(kfbim_ctx* c, cudaStream_t s) {
+  const int64_t N3 = c->N3;
+  double* f = c->rhs;
+  double* g = c->rhs + 3 * N3;
+  double* b = c->cr;   // Schur RHS; CG copies it into its residual (r = cq below)
+  CK(cudaMemcpyAsync(b, g, N3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  for (int cax = 0; cax < 3; ++cax)
+    schur_rhs_add<double, double>(c, cax, f + cax * N3, b, c->t1, c->t2, s);
+  int it = 0;
+  int st = cg<double>(c, b, c->p, c->rres, c->cd, c->cq, c->t1, c->t2, c->opt.cg_tol, c->opt.cg_max,
+                      s, &it);
+  c->cg_iters += it;
+  if (st != KFBIM_OK && st != KFBIM_E_NOCONV) return st;
+  // u^(c) = (1/mu)(-Delta)^{-1} (f^(c) - G_c p)
+  k_f_minus_gp<double, double><<<grid_for(3 * N3), 256, 0, s>>>(f, c->p, c->N, c->h, c->u);
+  check_launch();
+  for (int cax = 0; cax < 3; ++cax)
+    face_poisson<double, double, double>(c, cax, c->u + cax * N3, c->u + cax * N3, c->t1, c->t2, s);
+  return st;
+}
+
+// MIXED: FP32 transforms and CG inside FP64 iterative refinement.
+int grid_solve_mixed(kfbim_ctx* c, cudaStream_t s) {
+  const int64_t N3 = c->N3;
+  double* f = c->rhs;
+  double* g = c->rhs + 3 * N3;
+  double* resf = c->t1;            // FP64 residual [rf (3 fields) | rg]
+  double* resg = c->t1 + 3 * N3;
+  double* gmean = c->scal + 4;
+  double* sc = c->scal + 5;
+  CK(cudaMemsetAsync(c->u, 0, 3 * N3 * sizeof(double), s));
+  CK(cudaMemsetAsync(c->p, 0, N3 * sizeof(double), s));
+  dot(c, g, (const double*)nullptr, N3, gmean, 1.0 / (double)N3, s);
+  // reference norm ||[f; g - mean g]||
+  k_mac_residual<<<grid_for(4 * N3), 256, 0, s>>>(f, g, gmean, c->u, c->p, c->N, c->h, c->mu, resf, resg);
+  check_launch();
+  dot(c, resf, resf, 4 * N3, sc, 1.0, s);
+  const double ref2 = read_scalar(c, sc, s);
+  if (!std::isfinite(ref2)) return KFBIM_E_NONFINITE;
+  int status = KFBIM_OK;
+  for (int sweep = 0;; ++sweep) {
+    if (sweep > 0) {
+      k_mac_residual<<<grid_for(4 * N3), 256, 0, s>>>(f, g, gmean, c->u, c->p, c->N, c->h, c->mu, resf, resg);
+      check_launch();
+      dot(c, resf, resf, 4 * N3, sc, 1.0, s);
+      const double r2 = read_scalar(c, sc, s);
+      if (!std::isfinite(r2)) return KFBIM_E_NONFINITE;
+      if (r2 <= c->opt.refine_tol * c->opt.refine_tol * ref2 || ref2 == 0.0) break;
+      if (sweep >= c->opt.refine_max) { status = KFBIM_E_NOCONV; break; }
+    }
+    ++c->refine_sweeps;
+    // FP32 correction solve: b = rg + (1/mu) sum G^T (-Delta)^{-1} rf
+    float* b32 = c->fu;  // N3 floats (fu holds 3*N3)
+    k_convert<double, float><<<grid_for(N3), 256, 0, s>>>(resg, b32, N3);
+    check_launch();
+    for (int cax = 0; cax < 3; ++cax)
+      schur_rhs_add<double, float>(c, cax, resf + cax * N3, b32, c->f1, c->f2, s);
+    int it = 0;
+    int st = cg<float>(c, b32, c->fx, c->fr, c->fd, c->fq, c->f1, c->f2, c->opt.inner_tol,
+                       c->opt.cg_max, s, &it);
+    c->cg_iters += it;
+    if (st == KFBIM_E_NONFINITE) return st;
+    // p += dp; u += (1/mu)(-Delta)^{-1}(rf - G dp)
+    k_add_to<float><<<grid_for(N3), 256, 0, s>>>(c->fx, c->p, N3);
+    k_f_minus_gp<float, float><<<grid_for(3 * N3), 256, 0, s>>>(resf, c->fx, c->N, c->h, c->fu);
+    check_launch();
+    for (int cax = 0; cax < 3; ++cax) {
+      face_poisson<float, float, float>(c, cax, c->fu + cax * N3, c->fu + cax * N3, c->f1, c->f2, s);
+    }
+    k_add_to<float><<<grid_for(3 * N3), 256, 0, s>>>(c->fu, c->u, 3 * N3);
+    check_launch();
+  }
+  // gauge: mean(p) = mu * mean(g)  (the lambda_h system with gamma = 1, alpha = mu N^3)
+  dot(c, c->p, (const double*)nullptr, N3, sc, 1.0 / (double)N3, s);
+  k_shift<<<grid_for(N3), 256, 0, s>>>(c->p, sc, -1.0, N3);
+  k_shift<<<grid_for(N3), 256, 0, s>>>(c->p, gmean, c->mu, N3);
+  check_launch();
+  return status;
+}
+
+// Full interface solve: jumps -> RHS -> grid solve.  Leaves J, u, p in ctx.
+int interface_solve(kfbim_ctx* c, const double* phi, const double* fpts, const double* fgrid,
+                    cudaStream_t s) {
+  const int64_t n = c->n_all;
+  const int wpb = 8;
+  k_jumps<<<(unsigned)((n + wpb - 1) / wpb), 32 * wpb, 0, s>>>(
+      phi, fpts, n, c->d_comp, c->d_pid, c->d_fit_ptr, c->d_fit_col, c->d_fit_w, c->d_jmap, c->J);
+  check_launch();
+  k_rhs_fill<<<grid_for(4 * c->N3), 256, 0, s>>>(fgrid, c->d_side[1], c->d_side[2], c->d_side[3],
+                                                  c->N, c->rhs);
+  check_launch();
+  if (c->n_corr_rows > 0) {
+    k_corrections<<<grid_for(c->n_corr_rows), 256, 0, s>>>(c->d_corr_row, c->d_corr_ptr, c->d_corr_src,
+                                                            c->d_corr_coef, c->n_corr_rows, c->J, c->rhs);
+    check_launch();
+  }
+  ++c->interface_solves;
+  return c->opt.precision == KFBIM_MIXED ? grid_solve_mixed(c, s) : grid_solve_fp64(c, s);
+}
+
+void trace(kfbim_ctx* c, const double* u, const double* J, double* out, cudaStream_t s) {
+  k_trace<<<grid_for(c->n_prim), 256, 0, s>>>(u, J, c->n_all, c->n_prim, c->d_prim_of, c->N,
+                                               c->d_tr_comp, c->d_tr_node, c->d_tr_w, c->d_tr_cj, out);
+  check_launch();
+}
+
+int apply_impl(kfbim_ctx* c, const double* phi, double* out, cudaStream_t s) {
+  int st = interface_solve(c, phi, nullptr, nullptr, s);
+  if (st != KFBIM_OK && st != KFBIM_E_NOCONV) return st;
+  trace(c, c->u, c->J, out, s);
+  return st;
+}
+
+// GMRES (Alg. 1 step 3): unrestarted, CGS2 on the device, Givens on the host.
+int gmres(kfbim_ctx* c, const double* rhs, double* x, cudaStream_t s, int* iters, double* res_out) {
+  const int64_t n = c->n_prim;
+  const int m = c->gm_max;
+  const int64_t ld = n;
+  double* sc = c->scal;
+  dot(c, rhs, rhs, n, sc, 1.0, s);
+  const double beta = std::sqrt(read_scalar(c, sc, s));
+  if (!std::isfinite(beta)) return KFBIM_E_NONFINITE;
+  if (beta == 0.0) {
+    CK(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+    *iters = 0;
+    *res_out = 0.0;
+    return KFBIM_OK;
+  }
+  k_scale_copy<<<grid_for(n), 256, 0, s>>>(rhs, 1.0 / beta, nullptr, c->V, n);
+  check_launch();
+  std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), gvec(m + 1, 0.0), hcol(m + 1);
+  gvec[0] = beta;
+  int k = 0;
+  int status = KFBIM_E_NOCONV;
+  double res = 1.0;
+  const int nb = 64;
+  for (k = 1; k <= m; ++k) {
+    int st = apply_impl(c, c->V + (int64_t)(k - 1) * ld, c->gw, s);
+    if (st != KFBIM_OK && st != KFBIM_E_NOCONV) return st;
+    std::fill(hcol.begin(), hcol.end(), 0.0);
+    for (int pass2 = 0; pass2 < 2; ++pass2) {
+      dim3 grid(nb, k);
+      k_multidot_partial<<<grid, RED_THREADS, 0, s>>>(c->V, ld, c->gw, n, c->partial);
+      k_sum_partials<<<k, RED_THREADS, 0, s>>>(c->partial, nb, 1.0, c->gh);
+      k_multi_axpy<<<grid_for(n), 256, 0, s>>>(c->V, ld, c->gh, k, c->gw, n, 0);
+      check_launch();
+      CK(cudaMemcpyAsync(c->pinned, c->gh, k * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      for (int j = 0; j < k; ++j) hcol[j] += c->pinned[j];
+    }
+    dot(c, c->gw, c->gw, n, sc, 1.0, s);
+    const double hn = std::sqrt(read_scalar(c, sc, s));
+    if (!std::isfinite(hn)) return KFBIM_E_NONFINITE;
+    hcol[k] = hn;
+    for (int j = 0; j < k - 1; ++j) {
+      const double a = hcol[j], b = hcol[j + 1];
+      hcol[j] = cs[j] * a + sn[j] * b;
+      hcol[j + 1] = -sn[j] * a + cs[j] * b;
+    }
+    const double a = hcol[k - 1], b = hcol[k];
+    const double r = std::hypot(a, b);
+    cs[k - 1] = (r == 0.0) ? 1.0 : a / r;
+    sn[k - 1] = (r == 0.0) ? 0.0 : b / r;
+    hcol[k - 1] = r;
+    hcol[k] = 0.0;
+    gvec[k] = -sn[k - 1] * gvec[k - 1];
+    gvec[k - 1] = cs[k - 1] * gvec[k - 1];
+    for (int j = 0; j < k; ++j) H[(size_t)j * m + (k - 1)] = hcol[j];
+    res = std::fabs(gvec[k]) / beta;
+    if (res < c->opt.gmres_tol || hn == 0.0) {
+      status = KFBIM_OK;
+      break;
+    }
+    if (k < m) {
+      k_scale_copy<<<grid_for(n), 256, 0, s>>>(c->gw, 1.0 / hn, nullptr, c->V + (int64_t)k * ld, n);
+      check_launch();
+    }
+  }
+  const int kk = std::min(k, m);
+  std::vector<double> y(kk, 0.0);
+  for (int i = kk - 1; i >= 0; --i) {
+    double acc = gvec[i];
+    for (int j = i + 1; j < kk; ++j) acc -= H[(size_t)i * m + j] * y[j];
+    y[i] = acc / H[(size_t)i * m + i];
+  }
+  CK(cudaMemcpyAsync(c->gy, y.data(), kk * sizeof(double), cudaMemcpyHostToDevice, s));
+  k_multi_axpy<<<grid_for(n), 256, 0, s>>>(c->V, ld, c->gy, kk, x, n, 1);
+  check_launch();
+  CK(cudaStreamSynchronize(s));
+  *iters = kk;
+  *res_out = res;
+  return status;
+}
+
+void fill_tables(kfbim_ctx* c) {
+  HostTables& t = c->host;
+  const int N = c->N;
+  c->d_comp = upload(c, t.comp);
+  c->d_pid = upload(c, t.pid);
+  c->d_fit_ptr = upload(c, t.fit_ptr);
+  c->d_fit_col = upload(c, t.fit_col);
+  c->d_fit_w = upload(c, t.fit_w);
+  c->d_jmap = upload(c, t.jmap);
+  c->d_corr_row = upload(c, t.corr_row);
+  c->d_corr_ptr = upload(c, t.corr_ptr);
+  c->d_corr_src = upload(c, t.corr_src);
+  c->d_corr_coef = upload(c, t.corr_coef);
+  c->n_corr_rows = (int64_t)t.corr_row.size();
+  c->d_tr_comp = upload(c, t.tr_comp);
+  c->d_tr_node = upload(c, t.tr_node);
+  c->d_tr_w = upload(c, t.tr_w);
+  c->d_tr_cj = upload(c, t.tr_cj);
+  std::vector<int64_t> prim_of;
+  for (int64_t y = 0; y < t.n_all; ++y)
+    if (t.primary[y]) prim_of.push_back(y);
+  c->d_prim_of = upload(c, prim_of);
+  for (int g = 0; g < 4; ++g) c->d_side[g] = upload(c, t.side[g]);
+  // twiddles exp(-2 pi i t / 2N), t < N; post twiddles exp(-i pi k / 2N), k < N
+  std::vector<C2<double>> tw(N), q(N);
+  std::vector<C2<float>> tw32(N), q32(N);
+  for (int k = 0; k < N; ++k) {
+    const double a = M_PI * (double)k / (double)N;
+    tw[k] = {std::cos(a), -std::sin(a)};
+    const double b = 0.5 * a;
+    q[k] = {std::cos(b), -std::sin(b)};
+    tw32[k] = {(float)tw[k].x, (float)tw[k].y};
+    q32[k] = {(float)q[k].x, (float)q[k].y};
+  }
+  c->d_tw64 = upload(c, tw);
+  c->d_q64 = upload(c, q);
+  c->d_tw32 = upload(c, tw32);
+  c->d_q32 = upload(c, q32);
+  std::vector<double> s2(2 * N);
+  for (int i = 0; i < N; ++i) {
+    const double a = std::sin(M_PI * i / (2.0 * N)), b = std::sin(M_PI * (i + 1) / (2.0 * N));
+    s2[i] = 4.0 * a * a;
+    s2[N + i] = 4.0 * b * b;
+  }
+  c->d_s2 = upload(c, s2);
+  // workspace
+  const int64_t N3 = c->N3;
+  c->J = dalloc<double>(c, kSlots * t.n_all);
+  c->rhs = dalloc<double>(c, 4 * N3);
+  c->u = dalloc<double>(c, 3 * N3);
+  c->p = dalloc<double>(c, N3);
+  c->t1 = dalloc<double>(c, 4 * N3);   // also the FP64 residual [rf | rg] of MIXED
+  c->t2 = dalloc<double>(c, N3);
+  c->cr = dalloc<double>(c, N3);
+  c->cd = dalloc<double>(c, N3);
+  c->cq = dalloc<double>(c, N3);
+  c->rres = dalloc<double>(c, N3);
+  c->zero_phi = dalloc<double>(c, std::max<int64_t>(1, t.n_prim));
+  CK(cudaMemset(c->zero_phi, 0, std::max<int64_t>(1, t.n_prim) * sizeof(double)));
+  c->partial = dalloc<double>(c, (size_t)RED_BLOCKS * 256);
+  c->scal = dalloc<double>(c, 64);
+  c->cgs = dalloc<CGScalars>(c, 1);
+  if (c->opt.precision == KFBIM_MIXED) {
+    c->f1 = dalloc<float>(c, N3);
+    c->f2 = dalloc<float>(c, N3);
+    c->fx = dalloc<float>(c, N3);
+    c->fr = dalloc<float>(c, N3);
+    c->fd = dalloc<float>(c, N3);
+    c->fq = dalloc<float>(c, N3);
+    c->fu = dalloc<float>(c, 3 * N3);
+  }
+  c->gm_max = c->opt.gmres_max;
+  c->V = dalloc<double>(c, (size_t)(c->gm_max + 1) * std::max<int64_t>(1, t.n_prim));
+  c->gw = dalloc<double>(c, std::max<int64_t>(1, t.n_prim));
+  c->gh = dalloc<double>(c, c->gm_max + 1);
+  c->grhs = dalloc<double>(c, std::max<int64_t>(1, t.n_prim));
+  c->gy = dalloc<double>(c, c->gm_max + 1);
+  void* ph = nullptr;
+  CK(cudaMallocHost(&ph, sizeof(double) * 256));
+  c->pinned = static_cast<double*>(ph);
+}
+
+int fail(kfbim_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+template <typename F>
+int guarded(kfbim_ctx* c, F&& f) {
+  if (!c) return KFBIM_E_INVALID;
+  if (!c->device) return fail(c, KFBIM_E_INVALID, "host-only context");
+  try {
+    return f();
+  } catch (const CudaError& e) {
+    return fail(c, KFBIM_E_CUDA, e.msg);
+  } catch (const std::bad_alloc&) {
+    return fail(c, KFBIM_E_OOM, "host allocation failed");
+  }
+}
+
+void reset_counters(kfbim_ctx* c) {
+  c->cg_iters = 0;
+  c->refine_sweeps = 0;
+  c->interface_solves = 0;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+void kfbim_default_options(kfbim_options* o) {
+  if (!o) return;
+  o->mu = 1.0;
+  o->precision = KFBIM_FP64;
+  o->gmres_tol = 1e-10;
+  o->gmres_max = 200;
+  o->cg_tol = 1e-14;
+  o->cg_max = 2000;
+  o->refine_tol = 1e-13;
+  o->refine_max = 8;
+  o->inner_tol = 1e-5;
+}
+
+static int setup_common(const kfbim_geometry* geom, const kfbim_grid* grid, const kfbim_options* opt,
+                        kfbim_ctx** out, bool device) {
+  if (!out) return KFBIM_E_INVALID;
+  *out = nullptr;
+  if (!geom || !grid || !opt) return KFBIM_E_INVALID;
+  const int N = grid->N;
+  if (N < 16 || N > 256 || (N & (N - 1)) != 0 || !(grid->hi > grid->lo)) return KFBIM_E_INVALID;
+  if (!(opt->mu > 0) || opt->gmres_max < 1 || opt->gmres_max > 200 || opt->cg_max < 1 ||
+      (opt->precision != KFBIM_FP64 && opt->precision != KFBIM_MIXED))
+    return KFBIM_E_INVALID;
+  if (geom->kind < 0 || geom->kind > 2) return KFBIM_E_INVALID;
+  std::unique_ptr<kfbim_ctx> c(new (std::nothrow) kfbim_ctx());
+  if (!c) return KFBIM_E_OOM;
+  c->opt = *opt;
+  c->N = N;
+  c->N3 = (int64_t)N * N * N;
+  c->h = (grid->hi - grid->lo) / N;
+  c->mu = opt->mu;
+  std::string err;
+  int st;
+  try {
+    st = build_tables(*geom, *grid, opt->mu, c->host, err);
+  } catch (const std::bad_alloc&) {
+    return KFBIM_E_OOM;
+  }
+  if (st != KFBIM_OK) {
+    std::fprintf(stderr, "kfbim_setup: %s\n", err.c_str());
+    return st;
+  }
+  c->n_all = c->host.n_all;
+  c->n_prim = c->host.n_prim;
+  c->fit_nnz = (int64_t)c->host.fit_col.size();
+  c->corr_nnz = (int64_t)c->host.corr_src.size();
+  c->n_corr_rows = (int64_t)c->host.corr_row.size();
+  if (device) {
+    try {
+      fill_tables(c.get());
+    } catch (const CudaError& e) {
+      std::fprintf(stderr, "kfbim_setup: %s\n", e.msg.c_str());
+      for (void* p : c->allocs) cudaFree(p);
+      if (c->pinned) cudaFreeHost(c->pinned);
+      return e.msg.find("out of memory") != std::string::npos ? KFBIM_E_OOM : KFBIM_E_CUDA;
+    }
+    c->device = true;
+  }
+  // the host tables are on the device now; keep only point data
+  HostTables& t = c->host;
+  std::vector<int64_t>().swap(t.fit_ptr);
+  std::vector<int32_t>().swap(t.fit_col);
+  std::vector<double>().swap(t.fit_w);
+  std::vector<double>().swap(t.jmap);
+  std::vector<int64_t>().swap(t.corr_row);
+  std::vector<int64_t>().swap(t.corr_ptr);
+  std::vector<int64_t>().swap(t.corr_src);
+  std::vector<double>().swap(t.corr_coef);
+  *out = c.release();
+  return KFBIM_OK;
+}
+
+int kfbim_setup(const kfbim_geometry* geom, const kfbim_grid* grid, const kfbim_options* opt,
+                kfbim_ctx** out) {
+  return setup_common(geom, grid, opt, out, true);
+}
+
+int kfbim_setup_host(const kfbim_geometry* geom, const kfbim_grid* grid, const kfbim_options* opt,
+                     kfbim_ctx** out) {
+  return setup_common(geom, grid, opt, out, false);
+}
+
+int kfbim_table_sizes(const kfbim_ctx* c, int64_t* fit_nnz, int64_t* corr_rows, int64_t* corr_nnz) {
+  if (!c) return KFBIM_E_INVALID;
+  if (fit_nnz) *fit_nnz = c->fit_nnz;
+  if (corr_rows) *corr_rows = c->n_corr_rows;
+  if (corr_nnz) *corr_nnz = c->corr_nnz;
+  return KFBIM_OK;
+}
+
+int kfbim_destroy(kfbim_ctx* c) {
+  if (!c) return KFBIM_E_INVALID;
+  if (c->device) cudaDeviceSynchronize();
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->pinned) cudaFreeHost(c->pinned);
+  delete c;
+  return KFBIM_OK;
+}
+
+const char* kfbim_last_error(const kfbim_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int kfbim_sizes(const kfbim_ctx* c, int64_t* n_points, int64_t* n_primary, int* N) {
+  if (!c) return KFBIM_E_INVALID;
+  if (n_points) *n_points = c->n_all;
+  if (n_primary) *n_primary = c->n_prim;
+  if (N) *N = c->N;
+  return KFBIM_OK;
+}
+
+int kfbim_points(const kfbim_ctx* c, double* xyz, int32_t* comp, int32_t* axis, int32_t* primary) {
+  if (!c) return KFBIM_E_INVALID;
+  const HostTables& t = c->host;
+  if (xyz) std::memcpy(xyz, t.xyz.data(), sizeof(double) * 3 * t.n_all);
+  if (comp) std::memcpy(comp, t.comp.data(), sizeof(int32_t) * t.n_all);
+  if (axis) std::memcpy(axis, t.axis.data(), sizeof(int32_t) * t.n_all);
+  if (primary) std::memcpy(primary, t.primary.data(), sizeof(int32_t) * t.n_all);
+  return KFBIM_OK;
+}
+
+int kfbim_sides(const kfbim_ctx* c, int g, uint8_t* side) {
+  if (!c || g < 0 || g > 3 || !side) return KFBIM_E_INVALID;
+  std::memcpy(side, c->host.side[g].data(), c->N3);
+  return KFBIM_OK;
+}
+
+int kfbim_apply(kfbim_ctx* c, const double* phi, double* out, void* stream) {
+  return guarded(c, [&]() -> int {
+    if (!phi || !out || phi == out) return fail(c, KFBIM_E_INVALID, "kfbim_apply: bad pointers");
+    reset_counters(c);
+    cudaStream_t s = (cudaStream_t)stream;
+    int st = apply_impl(c, phi, out, s);
+    if (st == KFBIM_E_NOCONV) c->err = "inner CG reached its iteration cap";
+    return st;
+  });
+}
+
+int kfbim_jumps(kfbim_ctx* c, const double* phi, const double* fpts, double* Jout, void* stream) {
+  return guarded(c, [&]() -> int {
+    if (!phi || !Jout) return fail(c, KFBIM_E_INVALID, "kfbim_jumps: bad pointers");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = c->n_all;
+    const int wpb = 8;
+    k_jumps<<<(unsigned)((n + wpb - 1) / wpb), 32 * wpb, 0, s>>>(
+        phi, fpts, n, c->d_comp, c->d_pid, c->d_fit_ptr, c->d_fit_col, c->d_fit_w, c->d_jmap, Jout);
+    check_launch();
+    return KFBIM_OK;
+  });
+}
+
+int kfbim_interface(kfbim_ctx* c, const double* phi, const double* fpts, const double* fgrid,
+                    double* u, double* p, void* stream) {
+  return guarded(c, [&]() -> int {
+    if (!phi || !u || !p) return fail(c, KFBIM_E_INVALID, "kfbim_interface: bad pointers");
+    reset_counters(c);
+    cudaStream_t s = (cudaStream_t)stream;
+    int st = interface_solve(c, phi, fpts, fgrid, s);
+    CK(cudaMemcpyAsync(u, c->u, 3 * c->N3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(p, c->p, c->N3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return st;
+  });
+}
+
+int kfbim_trace(kfbim_ctx* c, const double* u, const double* J, double* out, void* stream) {
+  return guarded(c, [&]() -> int {
+    if (!u || !J || !out) return fail(c, KFBIM_E_INVALID, "kfbim_trace: bad pointers");
+    trace(c, u, J, out, (cudaStream_t)stream);
+    return KFBIM_OK;
+  });
+}
+
+int kfbim_poisson(kfbim_ctx* c, int comp, const double* r, double* u, void* stream) {
+  return guarded(c, [&]() -> int {
+    if (comp < 1 || comp > 3 || !r || !u) return fail(c, KFBIM_E_INVALID, "kfbim_poisson: bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    // (1/mu) scaling is part of the weight: undo it so this is (-Delta_h)^{-1}
+    face_poisson<double, double, double>(c, comp - 1, r, c->cr, c->t1, c->t2, s);
+    k_scale_copy<<<grid_for(c->N3), 256, 0, s>>>(c->cr, c->mu, nullptr, u, c->N3);
+    check_launch();
+    return KFBIM_OK;
+  });
+}
+
+int kfbim_schur_apply(kfbim_ctx* c, const double* d, double* q, void* stream) {
+  return guarded(c, [&]() -> int {
+    if (!d || !q || d == q) return fail(c, KFBIM_E_INVALID, "kfbim_schur_apply: bad pointers");
+    cudaStream_t s = (cudaStream_t)stream;
+    schur_apply<double>(c, d, q, c->t1, c->t2, s);
+    dot(c, d, (const double*)nullptr, c->N3, c->scal, 1.0 / (c->mu * (double)c->N3), s);
+    k_shift<<<grid_for(c->N3), 256, 0, s>>>(q, c->scal, 1.0, c->N3);
+    check_launch();
+    return KFBIM_OK;
+  });
+}
+
+int kfbim_solve(kfbim_ctx* c, const double* g, const double* fpts, const double* fgrid, double* phi,
+                double* u, double* p, kfbim_stats* stats, void* stream) {
+  return guarded(c, [&]() -> int {
+    if (!g || !phi) return fail(c, KFBIM_E_INVALID, "kfbim_solve: bad pointers");
+    reset_counters(c);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = c->n_prim;
+    CK(cudaMemcpyAsync(c->grhs, g, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (fpts || fgrid) {
+      int st = interface_solve(c, c->zero_phi, fpts, fgrid, s);
+      if (st != KFBIM_OK && st != KFBIM_E_NOCONV) return st;
+      trace(c, c->u, c->J, c->gw, s);
+      k_scale_copy<<<grid_for(n), 256, 0, s>>>(c->gw, -1.0, nullptr, c->gw, n);
+      k_add_to<double><<<grid_for(n), 256, 0, s>>>(c->gw, c->grhs, n);
+      check_launch();
+    }
+    int its = 0;
+    double res = 0.0;
+    int st = gmres(c, c->grhs, phi, s, &its, &res);
+    if (st != KFBIM_OK && st != KFBIM_E_NOCONV) return st;
+    int st2 = interface_solve(c, phi, fpts, fgrid, s);
+    if (u) CK(cudaMemcpyAsync(u, c->u, 3 * c->N3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (p) CK(cudaMemcpyAsync(p, c->p, c->N3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    if (stats) {
+      stats->gmres_iters = its;
+      stats->interface_solves = c->interface_solves;
+      stats->cg_iters = c->cg_iters;
+      stats->refine_sweeps = c->refine_sweeps;
+      stats->gmres_residual = res;
+    }
+    if (st == KFBIM_E_NOCONV) {
+      c->err = "GMRES reached its iteration cap";
+      return st;
+    }
+    if (st2 == KFBIM_E_NOCONV) {
+      c->err = "inner CG or refinement reached its iteration cap";
+      return st2;
+    }
+    return st2;
+  });
+}
+
+int kfbim_solve_host(kfbim_ctx* c, const double* g, const double* fpts, const double* fgrid,
+                     double* phi, double* u, double* p, kfbim_stats* stats, void* stream) {
+  return guarded(c, [&]() -> int {
+    if (!g || !phi) return fail(c, KFBIM_E_INVALID, "kfbim_solve_host: bad pointers");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = c->n_prim, N3 = c->N3;
+    if (!c->hs_g) {
+      c->hs_g = dalloc<double>(c, n);
+      c->hs_phi = dalloc<double>(c, n);
+      c->hs_fp = dalloc<double>(c, 3 * c->n_all);
+      c->hs_fg = dalloc<double>(c, 3 * N3);
+      c->hs_u = dalloc<double>(c, 3 * N3);
+      c->hs_p = dalloc<double>(c, N3);
+    }
+    CK(cudaMemcpyAsync(c->hs_g, g, n * sizeof(double), cudaMemcpyHostToDevice, s));
+    if (fpts) CK(cudaMemcpyAsync(c->hs_fp, fpts, 3 * c->n_all * sizeof(double), cudaMemcpyHostToDevice, s));
+    if (fgrid) CK(cudaMemcpyAsync(c->hs_fg, fgrid, 3 * N3 * sizeof(double), cudaMemcpyHostToDevice, s));
+    int st = kfbim_solve(c, c->hs_g, fpts ? c->hs_fp : nullptr, fgrid ? c->hs_fg : nullptr, c->hs_phi,
+                         u ? c->hs_u : nullptr, p ? c->hs_p : nullptr, stats, stream);
+    CK(cudaMemcpyAsync(phi, c->hs_phi, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (u) CK(cudaMemcpyAsync(u, c->hs_u, 3 * N3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (p) CK(cudaMemcpyAsync(p, c->hs_p, N3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return st;
+  });
+}
+
+}  // extern "C"

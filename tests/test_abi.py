@@ -1,0 +1,62 @@
+"""The C-ABI library builds, loads and exports every symbol of include/kfbim.h
+(no GPU needed); its host setup reproduces the oracle's control points."""
+import os
+import re
+
+import numpy as np
+
+import kfbim_inputs as ki
+from oracle import kfbim as okfbim
+from paper_2303_04992_gb300 import build
+from paper_2303_04992_gb300.binding import SYMBOLS, KfbimError, Solver, load_library
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "kfbim.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(kfbim_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    build()
+    lib = load_library()
+    names = declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in SYMBOLS, n
+
+
+def test_host_setup_matches_oracle_points():
+    for geom, N in [(ki.sphere(), 32), (ki.star(), 32),
+                    (ki.ellipsoid((0.6, 0.45, 0.35), ki.seeded_rotation(3)), 32)]:
+        s = Solver(geom, ki.grid(N), device=False)
+        o = okfbim.Setup(geom, ki.grid(N))
+        xyz, comp, axis, prim = s.points()
+        assert s.n_points == o.cp.n and s.n_primary == o.n
+        assert np.array_equal(comp, o.cp.comp) and np.array_equal(axis, o.cp.axis)
+        assert np.array_equal(prim, o.primary)
+        assert np.abs(xyz - o.cp.xyz).max() < 1e-14
+        for c in range(4):
+            assert np.array_equal(s.sides(c), o.S[c])
+        s.close()
+
+
+def test_host_setup_rejects_bad_geometry():
+    import pytest
+    with pytest.raises(KfbimError) as e:
+        Solver(ki.sphere(0.95), ki.grid(16), device=False)
+    assert e.value.code == -2
+    with pytest.raises(KfbimError) as e:
+        Solver(ki.sphere(), ki.grid(24), device=False)      # not a power of two
+    assert e.value.code == -1
+
+
+def test_host_only_context_refuses_device_calls():
+    import pytest
+    s = Solver(ki.sphere(), ki.grid(16), device=False)
+    with pytest.raises(KfbimError) as e:
+        s._check(s._lib.kfbim_apply(s._ctx, None, None, None))
+    assert e.value.code == -1

@@ -25,7 +25,7 @@
 #include "internal.h"
 
 namespace kfbim {
-namespace {
+namespace {  // file-local helpers
 
 // ---------------------------------------------------------------- level sets
 struct Level {
@@ -137,10 +137,11 @@ bool lu_factor(double* A, int n, int* piv) {
 }
 
 void lu_solve(const double* LU, int n, const int* piv, double* b) {
-  for (int k = 0; k < n; ++k) {
+  // all row interchanges first (they were applied to whole rows of L too)
+  for (int k = 0; k < n; ++k)
     if (piv[k] != k) std::swap(b[k], b[piv[k]]);
+  for (int k = 0; k < n; ++k)
     for (int i = k + 1; i < n; ++i) b[i] -= LU[i * n + k] * b[k];
-  }
   for (int k = n - 1; k >= 0; --k) {
     double acc = b[k];
     for (int j = k + 1; j < n; ++j) acc -= LU[k * n + j] * b[j];

@@ -173,6 +173,16 @@ int kfbim_solve_host(kfbim_ctx* ctx, const double* g_host, const double* fpts_ho
                      const double* fgrid_host, double* phi_host, double* u_host,
                      double* p_host, kfbim_stats* stats, void* stream);
 
+/* Per-kernel timing of the FFT transform passes (the dominant kernels).
+ * enable = 1 starts (and zeroes) the counters, 0 stops them, -1 reads them:
+ * total device milliseconds between CUDA events recorded around each launch,
+ * the number of launches and the algorithmic bytes they move (N^3 values read
+ * and written per pass, read-modify-write when accumulating), split into the
+ * FP64 and the FP32 passes.  Output pointers are host memory, nullable.
+ * Reading synchronises the device. */
+int kfbim_profile(kfbim_ctx* ctx, int enable, double* ms64, int64_t* launches64,
+                  double* bytes64, double* ms32, int64_t* launches32, double* bytes32);
+
 /* Stage entry points (same kernels as the solve path, exposed for parity tests).
  * kfbim_jumps: jump values at every control point (Sec. 4.3), layout
  *   J_dev[12 * n_points] slot-major: slot s of point y at s*n_points + y with

@@ -63,6 +63,8 @@ SYMBOLS = {
     "kfbim_trace": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "kfbim_poisson": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     "kfbim_schur_apply": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "kfbim_profile": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                              c_void_p]),
 }
 
 _lib = None
@@ -222,6 +224,17 @@ class Solver:
     def poisson(self, c, r, u):
         self._check(self._lib.kfbim_poisson(self._ctx, c, _ptr(r), _ptr(u), self._stream()))
         return u
+
+    def profile(self, enable):
+        """enable True/False starts/stops kernel timing; None reads it:
+        {"fp64"|"fp32": (ms, launches, bytes)}."""
+        if enable is not None:
+            self._check(self._lib.kfbim_profile(self._ctx, 1 if enable else 0, *([None] * 6)))
+            return None
+        v = [c_double(), c_int64(), c_double(), c_double(), c_int64(), c_double()]
+        self._check(self._lib.kfbim_profile(self._ctx, -1, *[ctypes.byref(x) for x in v]))
+        return {"fp64": (v[0].value, v[1].value, v[2].value),
+                "fp32": (v[3].value, v[4].value, v[5].value)}
 
     def schur_apply(self, d, q):
         self._check(self._lib.kfbim_schur_apply(self._ctx, _ptr(d), _ptr(q), self._stream()))

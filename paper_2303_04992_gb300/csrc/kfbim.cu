@@ -65,6 +65,14 @@ struct kfbim_ctx {
   double *hs_g = nullptr, *hs_phi = nullptr, *hs_fp = nullptr, *hs_fg = nullptr, *hs_u = nullptr,
          *hs_p = nullptr;
   bool device = false;        // false for kfbim_setup_host contexts
+  // optional per-kernel timing of the transform passes (kfbim_profile)
+  bool prof = false;
+  std::vector<cudaEvent_t> prof_ev;    // pairs (start, stop)
+  int prof_used = 0;
+  double prof_ms[2] = {0, 0};          // total ms: FP64 passes, FP32 passes
+  int64_t prof_count[2] = {0, 0};
+  std::vector<int> prof_tag;           // precision slot of each event pair
+  double prof_bytes[2] = {0, 0};       // algorithmic bytes moved by those launches
   int64_t fit_nnz = 0, corr_nnz = 0;
   // counters of the current call
   int cg_iters = 0, refine_sweeps = 0, interface_solves = 0;
@@ -146,8 +154,28 @@ void pass(kfbim_ctx* c, const Tin* in, Tout* out, int axis, int t0, int t1, int 
     configured = smem;
   }
   const int blocks = (int)((int64_t)c->N * c->N / LPC);
+  const bool prof = c->prof && c->prof_used + 2 <= (int)c->prof_ev.size();
+  if (prof) CK(cudaEventRecord(c->prof_ev[c->prof_used], s));
   kern<<<blocks, PASS_THREADS, smem, s>>>(in, out, a, Tw<T>::tw(c), Tw<T>::q(c), c->d_s2);
   check_launch();
+  if (prof) {
+    CK(cudaEventRecord(c->prof_ev[c->prof_used + 1], s));
+    const int slot = sizeof(T) == 8 ? 0 : 1;
+    c->prof_tag[c->prof_used / 2] = slot;
+    c->prof_used += 2;
+    c->prof_count[slot] += 1;
+    c->prof_bytes[slot] += (double)c->N3 * (sizeof(Tin) + sizeof(Tout) * (acc ? 2 : 1));
+  }
+}
+
+// Fold recorded event pairs into the totals (the stream must be idle).
+void prof_collect(kfbim_ctx* c) {
+  for (int e = 0; e + 1 < c->prof_used; e += 2) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, c->prof_ev[e], c->prof_ev[e + 1]));
+    c->prof_ms[c->prof_tag[e / 2]] += ms;
+  }
+  c->prof_used = 0;
 }
 
 inline void others(int cax, int& o1, int& o2) {
@@ -193,9 +221,12 @@ void schur_apply(kfbim_ctx* c, const T* d, T* q, T* t1, T* t2, cudaStream_t s) {
   }
 }
 
+void prof_collect(kfbim_ctx* c);
+
 double read_scalar(kfbim_ctx* c, const double* dptr, cudaStream_t s) {
   CK(cudaMemcpyAsync(c->pinned, dptr, sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  if (c->prof_used) prof_collect(c);
   return c->pinned[0];
 }
 
@@ -654,6 +685,7 @@ int kfbim_table_sizes(const kfbim_ctx* c, int64_t* fit_nnz, int64_t* corr_rows, 
 int kfbim_destroy(kfbim_ctx* c) {
   if (!c) return KFBIM_E_INVALID;
   if (c->device) cudaDeviceSynchronize();
+  for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
   for (void* p : c->allocs) cudaFree(p);
   if (c->pinned) cudaFreeHost(c->pinned);
   delete c;
@@ -795,6 +827,34 @@ int kfbim_solve(kfbim_ctx* c, const double* g, const double* fpts, const double*
       return st2;
     }
     return st2;
+  });
+}
+
+int kfbim_profile(kfbim_ctx* c, int enable, double* ms64, int64_t* launches64, double* bytes64,
+                  double* ms32, int64_t* launches32, double* bytes32) {
+  return guarded(c, [&]() -> int {
+    if (enable >= 0) {
+      if (enable && c->prof_ev.empty()) {
+        c->prof_ev.resize(8192);
+        c->prof_tag.resize(4096);
+        for (auto& e : c->prof_ev) CK(cudaEventCreate(&e));
+      }
+      c->prof = enable != 0;
+      c->prof_used = 0;
+      c->prof_ms[0] = c->prof_ms[1] = 0;
+      c->prof_count[0] = c->prof_count[1] = 0;
+      c->prof_bytes[0] = c->prof_bytes[1] = 0;
+      return KFBIM_OK;
+    }
+    CK(cudaDeviceSynchronize());
+    if (c->prof_used) prof_collect(c);
+    if (ms64) *ms64 = c->prof_ms[0];
+    if (launches64) *launches64 = c->prof_count[0];
+    if (bytes64) *bytes64 = c->prof_bytes[0];
+    if (ms32) *ms32 = c->prof_ms[1];
+    if (launches32) *launches32 = c->prof_count[1];
+    if (bytes32) *bytes32 = c->prof_bytes[1];
+    return KFBIM_OK;
   });
 }
 

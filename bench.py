@@ -1,0 +1,370 @@
+#!/usr/bin/env python
+"""Benchmark of the KFBI Stokes solver on GB300.
+
+One step = one full kfbim_solve (Alg. 1): the volume interface solve for the
+right-hand side, GMRES to 1e-10 on the BIE (one interface solve per
+iteration) and the final interior-field interface solve, on the star
+workload r = 0.5 + 0.1 sin(3 theta) cos(4 phi) in [-1, 1]^3 at N = 128 with
+the manufactured Stokes data.  Inputs are resident in HBM when the timed
+region starts; the L2 is flushed (a 512 MiB write) before every step, outside
+the per-step CUDA events.
+
+Printed JSON line (rank 0): value = solves/s over all ranks (MIXED precision),
+the FP64 path's solves/s beside it, the relative difference of the MIXED
+density from the FP64 one, the roofline of the dominant kernel (the FP32
+transform passes, timed with CUDA events around each launch in a second run
+of the same steps), the oracle CPU baseline, e2e through kfbim_solve_host with
+host buffers, the kernel-launch count and the SM clocks sampled during the
+timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl kfbim|reference]
+Multi-GPU (torchrun): replicas only, every rank solves its own instance, no
+collective on the data path ("scaling": "weak").
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import kfbim_inputs as ki  # noqa: E402
+
+METRIC = "Stokes BIE solves/s at 128^3 (mixed vs FP64, rel err ≤1e-8); HBM GB/s"
+WORKLOAD = "star128"
+WORKLOAD_DESC = ("Stokes interior Dirichlet on the star r=0.5+0.1 sin(3theta) cos(4phi) in [-1,1]^3, "
+                 "MAC grid 128^3, mu=1, manufactured u=(sin x cos y cos z, -cos x sin y cos z, 0), "
+                 "p=sin(x+y+z), GMRES tol 1e-10")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="kfbim", choices=["kfbim", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--interface-solves", type=int, default=18, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------ oracle sample
+def oracle_sample(workload, reps, per_solve):
+    """Time the oracle (single thread) on `reps` matvecs of the workload."""
+    from oracle import kfbim as okfbim
+    geom, grid = ki.WORKLOADS[workload]
+    s = okfbim.Setup(geom, grid)
+    phi = ki.random_density(s.n, seed=0)
+    times = []
+    for _ in range(reps):
+        t = time.perf_counter()
+        s.apply(phi)
+        times.append(time.perf_counter() - t)
+    t_mv = statistics.median(times)
+    return {"matvec_s": t_mv, "times": times, "value": 1.0 / (t_mv * per_solve)}
+
+
+def run_oracle_subprocess(workload, reps, per_solve):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", "--workload",
+                        workload, "--steps", str(reps), "--interface-solves", str(per_solve)],
+                       capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed:\n" + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile(prefix="clocks", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.close()
+        rows = [l.split(",") for l in open(self.f.name).read().strip().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("transforms.cuh",):
+        h.update(open(os.path.join(ROOT, "paper_2303_04992_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def ncu_traffic(workload):
+    """DRAM bytes per launch of the FP32 transform pass from the committed ncu
+    summary, if it was taken on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "axis_pass_fp32_%s.md" % workload)
+    if not os.path.exists(p):
+        return None
+    txt = open(p).read()
+    m = re.search(r"kernel_source_sha256_12:\s*([0-9a-f]+)", txt)
+    t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not m or not t or m.group(1) != kernel_source_hash():
+        return None
+    return float(t.group(1))
+
+
+def inputs(solver, geom, grid):
+    """Manufactured Stokes data: g at the primary points, f at all points and
+    on the face grids (host numpy)."""
+    xyz, comp, _, prim = solver.points()
+    rows = np.arange(len(comp))
+    g = ki.stokes_velocity(xyz)[rows, comp - 1][prim]
+    fpts = ki.stokes_forcing(xyz).T.copy()
+    N, lo, h = solver.N, solver.lo, solver.h
+    idx = np.arange(N)
+    fg = []
+    for c in (1, 2, 3):
+        off = [0.5, 0.5, 0.5]
+        off[c - 1] = 0.0
+        Z, Y, X = np.meshgrid(lo + (idx + off[2]) * h, lo + (idx + off[1]) * h,
+                              lo + (idx + off[0]) * h, indexing="ij")      # [k, j, i]
+        fg.append(ki.stokes_forcing(np.stack([X, Y, Z], -1))[..., c - 1].ravel())
+    return g, fpts, np.concatenate(fg)
+
+
+# -------------------------------------------------------------- main arms
+def main_kfbim(args):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2303_04992_gb300 import FP64, MIXED, Solver, build
+    if rank == 0:
+        build()
+    if dist:
+        dist.barrier()
+    geom, grid = ki.WORKLOADS[args.workload]
+    dev = torch.device("cuda", local)
+    solver = Solver(geom, grid, precision=MIXED)
+    g_h, fpts_h, fgrid_h = inputs(solver, geom, grid)
+    g = torch.from_numpy(g_h).to(dev)
+    fpts = torch.from_numpy(fpts_h).to(dev)
+    fgrid = torch.from_numpy(fgrid_h).to(dev)
+    phi = torch.zeros(solver.n_primary, dtype=torch.float64, device=dev)
+    flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        solver.solve(g, phi, fpts, fgrid)
+    torch.cuda.synchronize()
+
+    def timed(steps, profile=False):
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        stats = []
+        if profile:
+            solver.profile(True)
+        for k in range(steps):
+            flush.zero_()
+            starts[k].record(stream)
+            solver.solve(g, phi, fpts, fgrid)
+            ends[k].record(stream)
+            stats.append(dict(solver.last_stats))
+        torch.cuda.synchronize()
+        prof = None
+        if profile:
+            prof = solver.profile(None)
+            solver.profile(False)
+        return sum(s.elapsed_time(e) for s, e in zip(starts, ends)), stats, prof
+
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    total_ms, stats, _ = timed(args.steps)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if dist:
+        dist.barrier()
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * args.steps / (total_ms / 1e3)
+    launches = int(sum(s["kernel_launches"] for s in stats))
+    phi_mixed = phi.cpu().numpy().copy()
+
+    # dominant kernel: FP32 transform passes, timed around each launch
+    _, _, prof = timed(args.steps, profile=True)
+    ms32, n32, bytes32 = prof["fp32"]
+    peak, peak_kind = measured_peaks()
+    achieved = (bytes32 / n32) / (ms32 / n32 * 1e-3) / 1e9 if n32 else 0.0
+    traffic = ncu_traffic(args.workload)
+    roofline = {"bound": "hbm", "kernel": "k_axis_pass<float> (FFT transform pass)",
+                "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+                "traffic": traffic, "algorithmic_bytes_per_launch": bytes32 / max(n32, 1),
+                "avg_launch_us": round(ms32 / max(n32, 1) * 1e3, 3),
+                "launches_per_step": n32 // args.steps,
+                "share_of_step": round(ms32 / args.steps / ms_per_step, 3)}
+
+    # e2e: host buffers through kfbim_solve_host (H2D of g, f; D2H of phi)
+    g_pin = torch.from_numpy(g_h).pin_memory().numpy()
+    fp_pin = torch.from_numpy(fpts_h).pin_memory().numpy()
+    fg_pin = torch.from_numpy(fgrid_h).pin_memory().numpy()
+    phi_pin = torch.zeros(solver.n_primary, dtype=torch.float64).pin_memory().numpy()
+    solver.solve_host(g_pin, phi_pin, fp_pin, fg_pin)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        solver.solve_host(g_pin, phi_pin, fp_pin, fg_pin)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": round(world * args.steps / e2e_s, 4), "unit": "solves/s",
+           "h2d_bytes_per_step": int(g_pin.nbytes + fp_pin.nbytes + fg_pin.nbytes),
+           "d2h_bytes_per_step": int(phi_pin.nbytes), "api": "kfbim_solve_host"}
+
+    # FP64 comparison leg (same inputs)
+    fp64 = None
+    rel = None
+    if not args.no_fp64:
+        s64 = Solver(geom, grid, precision=FP64)
+        phi64 = torch.zeros(s64.n_primary, dtype=torch.float64, device=dev)
+        s64.solve(g, phi64, fpts, fgrid)
+        torch.cuda.synchronize()
+        reps = 2
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * reps)]
+        ms = 0.0
+        for k in range(reps):
+            flush.zero_()
+            ev[2 * k].record(stream)
+            s64.solve(g, phi64, fpts, fgrid)
+            ev[2 * k + 1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(reps)) / reps
+        p64 = phi64.cpu().numpy()
+        rel = float(np.abs(phi_mixed - p64).max() / np.abs(p64).max())
+        fp64 = {"solves_per_s": round(1e3 / ms, 4), "ms_per_solve": round(ms, 2),
+                "gmres_iters": s64.last_stats["gmres_iters"], "cg_iters": s64.last_stats["cg_iters"],
+                "mixed_speedup": round((1e3 / ms_per_step) / (1e3 / ms), 2)}
+        s64.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        per_solve = stats[-1]["interface_solves"]
+        o = run_oracle_subprocess(args.workload, 1, per_solve)
+        cpu = {"value": round(o["value"], 6), "unit": "solves/s", "cores": 1, "kind": "oracle",
+               "sample": "one oracle matvec (interface solve + trace) on %s, single thread, "
+                         "%.1f s, scaled by the %d interface solves of one GPU solve"
+                         % (args.workload, o["matvec_s"], per_solve)}
+
+    if rank == 0:
+        st = stats[-1]
+        line = {"metric": METRIC, "value": round(value, 4), "unit": "solves/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32+f64 (mixed: FP32 transforms/CG, FP64 jumps/residuals/GMRES)",
+                "data": "synthetic",
+                "config": {"workload": args.workload, "description": WORKLOAD_DESC,
+                           "precision": "mixed", "l2_flush": "512 MiB write before each step",
+                           "n_points": solver.n_points, "n_unknowns": solver.n_primary,
+                           "gmres_iters": st["gmres_iters"], "interface_solves": st["interface_solves"],
+                           "cg_iters": st["cg_iters"], "refine_sweeps": st["refine_sweeps"],
+                           "parallelism": "replicas" if world > 1 else "single"},
+                "fp64": fp64, "rel_err_vs_fp64": rel, "roofline": roofline, "cpu_baseline": cpu,
+                "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main_reference(args):
+    """The oracle (single thread) on the same workload and metric: each step is
+    one oracle matvec, scaled by the interface solves of one solve."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    per_solve = args.interface_solves
+    o = run_oracle_subprocess(args.workload, args.warmup + args.steps, per_solve)
+    times = o["times"][args.warmup:]
+    t_mv = sum(times) / len(times)
+    value = 1.0 / (t_mv * per_solve)
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "solves/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(t_mv * per_solve * 1e3, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "description": WORKLOAD_DESC},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": round(value, 6),
+                             "sample": "each step: one oracle matvec on %s (single thread), scaled "
+                                       "by %d interface solves per solve" % (args.workload, per_solve)},
+            "e2e": {"value": round(value, 6), "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.oracle_sample:
+        print(json.dumps(oracle_sample(a.workload, a.steps, a.interface_solves)))
+    elif a.impl == "reference":
+        main_reference(a)
+    else:
+        main_kfbim(a)

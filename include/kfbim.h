@@ -101,6 +101,7 @@ typedef struct {
   int cg_iters;        /* total over all interface solves */
   int refine_sweeps;   /* total (MIXED) */
   double gmres_residual;
+  int64_t kernel_launches; /* CUDA kernels launched by the call */
 } kfbim_stats;
 
 /* Fills *opt with the defaults (mu 1, FP64, gmres 1e-10/200, cg 1e-14/2000,

@@ -36,7 +36,8 @@ class Options(ctypes.Structure):
 
 class Stats(ctypes.Structure):
     _fields_ = [("gmres_iters", c_int), ("interface_solves", c_int), ("cg_iters", c_int),
-                ("refine_sweeps", c_int), ("gmres_residual", c_double)]
+                ("refine_sweeps", c_int), ("gmres_residual", c_double),
+                ("kernel_launches", c_int64)]
 
 
 SYMBOLS = {

@@ -112,6 +112,8 @@ inline int grid_for(int64_t n, int threads = 256) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 16));
 }
 
+int64_t g_launches = 0;   // kernel launches issued through this library
+
 inline void check_launch() {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) throw CudaError{std::string("kernel launch: ") + cudaGetErrorString(e)};
@@ -156,7 +158,7 @@ void pass(kfbim_ctx* c, const Tin* in, Tout* out, int axis, int t0, int t1, int 
   const int blocks = (int)((int64_t)c->N * c->N / LPC);
   const bool prof = c->prof && c->prof_used + 2 <= (int)c->prof_ev.size();
   if (prof) CK(cudaEventRecord(c->prof_ev[c->prof_used], s));
-  kern<<<blocks, PASS_THREADS, smem, s>>>(in, out, a, Tw<T>::tw(c), Tw<T>::q(c), c->d_s2);
+  kern<<<blocks, PASS_THREADS, smem, s>>>(in, out, a, Tw<T>::tw(c), Tw<T>::q(c), c->d_s2); ++g_launches;
   check_launch();
   if (prof) {
     CK(cudaEventRecord(c->prof_ev[c->prof_used + 1], s));
@@ -232,9 +234,9 @@ double read_scalar(kfbim_ctx* c, const double* dptr, cudaStream_t s) {
 
 template <typename Ta, typename Tb>
 void dot(kfbim_ctx* c, const Ta* x, const Tb* y, int64_t n, double* out, double scale, cudaStream_t s) {
-  k_dot_partial<Ta, Tb><<<RED_BLOCKS, RED_THREADS, 0, s>>>(x, y, n, c->partial);
+  k_dot_partial<Ta, Tb><<<RED_BLOCKS, RED_THREADS, 0, s>>>(x, y, n, c->partial); ++g_launches;
   check_launch();
-  k_sum_partials<<<1, RED_THREADS, 0, s>>>(c->partial, RED_BLOCKS, scale, out);
+  k_sum_partials<<<1, RED_THREADS, 0, s>>>(c->partial, RED_BLOCKS, scale, out); ++g_launches;
   check_launch();
 }
 
@@ -270,13 +272,13 @@ int cg(kfbim_ctx* c, const T* b, T* x, T* r, T* d, T* q, T* t1, T* t2, double to
     }
     schur_apply<T>(c, d, q, t1, t2, s);
     dot(c, d, q, n, sc, 1.0, s);
-    k_cg_alpha<<<1, 1, 0, s>>>(c->cgs, sc);
-    k_cg_update<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(x, r, d, q, n, c->cgs, c->partial);
-    k_sum_partials<<<1, RED_THREADS, 0, s>>>(c->partial, RED_BLOCKS, 1.0, sc + 1);
-    k_cg_beta<<<1, 1, 0, s>>>(c->cgs, sc + 1);
-    k_cg_direction<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(d, r, n, c->cgs, c->partial);
-    k_sum_partials<<<1, RED_THREADS, 0, s>>>(c->partial, RED_BLOCKS, 1.0, sc + 2);
-    k_set_sumd<<<1, 1, 0, s>>>(c->cgs, sc + 2);
+    k_cg_alpha<<<1, 1, 0, s>>>(c->cgs, sc); ++g_launches;
+    k_cg_update<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(x, r, d, q, n, c->cgs, c->partial); ++g_launches;
+    k_sum_partials<<<1, RED_THREADS, 0, s>>>(c->partial, RED_BLOCKS, 1.0, sc + 1); ++g_launches;
+    k_cg_beta<<<1, 1, 0, s>>>(c->cgs, sc + 1); ++g_launches;
+    k_cg_direction<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(d, r, n, c->cgs, c->partial); ++g_launches;
+    k_sum_partials<<<1, RED_THREADS, 0, s>>>(c->partial, RED_BLOCKS, 1.0, sc + 2); ++g_launches;
+    k_set_sumd<<<1, 1, 0, s>>>(c->cgs, sc + 2); ++g_launches;
     check_launch();
     ++it;
     rr = read_scalar(c, &c->cgs->rr, s);
@@ -301,7 +303,7 @@ int grid_solve_fp64(kfbim_ctx* c, cudaStream_t s) {
   c->cg_iters += it;
   if (st != KFBIM_OK && st != KFBIM_E_NOCONV) return st;
   // u^(c) = (1/mu)(-Delta)^{-1} (f^(c) - G_c p)
-  k_f_minus_gp<double, double><<<grid_for(3 * N3), 256, 0, s>>>(f, c->p, c->N, c->h, c->u);
+  k_f_minus_gp<double, double><<<grid_for(3 * N3), 256, 0, s>>>(f, c->p, c->N, c->h, c->u); ++g_launches;
   check_launch();
   for (int cax = 0; cax < 3; ++cax)
     face_poisson<double, double, double>(c, cax, c->u + cax * N3, c->u + cax * N3, c->t1, c->t2, s);
@@ -321,7 +323,7 @@ int grid_solve_mixed(kfbim_ctx* c, cudaStream_t s) {
   CK(cudaMemsetAsync(c->p, 0, N3 * sizeof(double), s));
   dot(c, g, (const double*)nullptr, N3, gmean, 1.0 / (double)N3, s);
   // reference norm ||[f; g - mean g]||
-  k_mac_residual<<<grid_for(4 * N3), 256, 0, s>>>(f, g, gmean, c->u, c->p, c->N, c->h, c->mu, resf, resg);
+  k_mac_residual<<<grid_for(4 * N3), 256, 0, s>>>(f, g, gmean, c->u, c->p, c->N, c->h, c->mu, resf, resg); ++g_launches;
   check_launch();
   dot(c, resf, resf, 4 * N3, sc, 1.0, s);
   const double ref2 = read_scalar(c, sc, s);
@@ -329,7 +331,7 @@ int grid_solve_mixed(kfbim_ctx* c, cudaStream_t s) {
   int status = KFBIM_OK;
   for (int sweep = 0;; ++sweep) {
     if (sweep > 0) {
-      k_mac_residual<<<grid_for(4 * N3), 256, 0, s>>>(f, g, gmean, c->u, c->p, c->N, c->h, c->mu, resf, resg);
+      k_mac_residual<<<grid_for(4 * N3), 256, 0, s>>>(f, g, gmean, c->u, c->p, c->N, c->h, c->mu, resf, resg); ++g_launches;
       check_launch();
       dot(c, resf, resf, 4 * N3, sc, 1.0, s);
       const double r2 = read_scalar(c, sc, s);
@@ -340,7 +342,7 @@ int grid_solve_mixed(kfbim_ctx* c, cudaStream_t s) {
     ++c->refine_sweeps;
     // FP32 correction solve: b = rg + (1/mu) sum G^T (-Delta)^{-1} rf
     float* b32 = c->fu;  // N3 floats (fu holds 3*N3)
-    k_convert<double, float><<<grid_for(N3), 256, 0, s>>>(resg, b32, N3);
+    k_convert<double, float><<<grid_for(N3), 256, 0, s>>>(resg, b32, N3); ++g_launches;
     check_launch();
     for (int cax = 0; cax < 3; ++cax)
       schur_rhs_add<double, float>(c, cax, resf + cax * N3, b32, c->f1, c->f2, s);
@@ -350,19 +352,19 @@ int grid_solve_mixed(kfbim_ctx* c, cudaStream_t s) {
     c->cg_iters += it;
     if (st == KFBIM_E_NONFINITE) return st;
     // p += dp; u += (1/mu)(-Delta)^{-1}(rf - G dp)
-    k_add_to<float><<<grid_for(N3), 256, 0, s>>>(c->fx, c->p, N3);
-    k_f_minus_gp<float, float><<<grid_for(3 * N3), 256, 0, s>>>(resf, c->fx, c->N, c->h, c->fu);
+    k_add_to<float><<<grid_for(N3), 256, 0, s>>>(c->fx, c->p, N3); ++g_launches;
+    k_f_minus_gp<float, float><<<grid_for(3 * N3), 256, 0, s>>>(resf, c->fx, c->N, c->h, c->fu); ++g_launches;
     check_launch();
     for (int cax = 0; cax < 3; ++cax) {
       face_poisson<float, float, float>(c, cax, c->fu + cax * N3, c->fu + cax * N3, c->f1, c->f2, s);
     }
-    k_add_to<float><<<grid_for(3 * N3), 256, 0, s>>>(c->fu, c->u, 3 * N3);
+    k_add_to<float><<<grid_for(3 * N3), 256, 0, s>>>(c->fu, c->u, 3 * N3); ++g_launches;
     check_launch();
   }
   // gauge: mean(p) = mu * mean(g)  (the lambda_h system with gamma = 1, alpha = mu N^3)
   dot(c, c->p, (const double*)nullptr, N3, sc, 1.0 / (double)N3, s);
-  k_shift<<<grid_for(N3), 256, 0, s>>>(c->p, sc, -1.0, N3);
-  k_shift<<<grid_for(N3), 256, 0, s>>>(c->p, gmean, c->mu, N3);
+  k_shift<<<grid_for(N3), 256, 0, s>>>(c->p, sc, -1.0, N3); ++g_launches;
+  k_shift<<<grid_for(N3), 256, 0, s>>>(c->p, gmean, c->mu, N3); ++g_launches;
   check_launch();
   return status;
 }
@@ -373,14 +375,14 @@ int interface_solve(kfbim_ctx* c, const double* phi, const double* fpts, const d
   const int64_t n = c->n_all;
   const int wpb = 8;
   k_jumps<<<(unsigned)((n + wpb - 1) / wpb), 32 * wpb, 0, s>>>(
-      phi, fpts, n, c->d_comp, c->d_pid, c->d_fit_ptr, c->d_fit_col, c->d_fit_w, c->d_jmap, c->J);
+      phi, fpts, n, c->d_comp, c->d_pid, c->d_fit_ptr, c->d_fit_col, c->d_fit_w, c->d_jmap, c->J); ++g_launches;
   check_launch();
   k_rhs_fill<<<grid_for(4 * c->N3), 256, 0, s>>>(fgrid, c->d_side[1], c->d_side[2], c->d_side[3],
-                                                  c->N, c->rhs);
+                                                  c->N, c->rhs); ++g_launches;
   check_launch();
   if (c->n_corr_rows > 0) {
     k_corrections<<<grid_for(c->n_corr_rows), 256, 0, s>>>(c->d_corr_row, c->d_corr_ptr, c->d_corr_src,
-                                                            c->d_corr_coef, c->n_corr_rows, c->J, c->rhs);
+                                                            c->d_corr_coef, c->n_corr_rows, c->J, c->rhs); ++g_launches;
     check_launch();
   }
   ++c->interface_solves;
@@ -389,7 +391,7 @@ int interface_solve(kfbim_ctx* c, const double* phi, const double* fpts, const d
 
 void trace(kfbim_ctx* c, const double* u, const double* J, double* out, cudaStream_t s) {
   k_trace<<<grid_for(c->n_prim), 256, 0, s>>>(u, J, c->n_all, c->n_prim, c->d_prim_of, c->N,
-                                               c->d_tr_comp, c->d_tr_node, c->d_tr_w, c->d_tr_cj, out);
+                                               c->d_tr_comp, c->d_tr_node, c->d_tr_w, c->d_tr_cj, out); ++g_launches;
   check_launch();
 }
 
@@ -415,7 +417,7 @@ int gmres(kfbim_ctx* c, const double* rhs, double* x, cudaStream_t s, int* iters
     *res_out = 0.0;
     return KFBIM_OK;
   }
-  k_scale_copy<<<grid_for(n), 256, 0, s>>>(rhs, 1.0 / beta, nullptr, c->V, n);
+  k_scale_copy<<<grid_for(n), 256, 0, s>>>(rhs, 1.0 / beta, nullptr, c->V, n); ++g_launches;
   check_launch();
   std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), gvec(m + 1, 0.0), hcol(m + 1);
   gvec[0] = beta;
@@ -429,9 +431,9 @@ int gmres(kfbim_ctx* c, const double* rhs, double* x, cudaStream_t s, int* iters
     std::fill(hcol.begin(), hcol.end(), 0.0);
     for (int pass2 = 0; pass2 < 2; ++pass2) {
       dim3 grid(nb, k);
-      k_multidot_partial<<<grid, RED_THREADS, 0, s>>>(c->V, ld, c->gw, n, c->partial);
-      k_sum_partials<<<k, RED_THREADS, 0, s>>>(c->partial, nb, 1.0, c->gh);
-      k_multi_axpy<<<grid_for(n), 256, 0, s>>>(c->V, ld, c->gh, k, c->gw, n, 0);
+      k_multidot_partial<<<grid, RED_THREADS, 0, s>>>(c->V, ld, c->gw, n, c->partial); ++g_launches;
+      k_sum_partials<<<k, RED_THREADS, 0, s>>>(c->partial, nb, 1.0, c->gh); ++g_launches;
+      k_multi_axpy<<<grid_for(n), 256, 0, s>>>(c->V, ld, c->gh, k, c->gw, n, 0); ++g_launches;
       check_launch();
       CK(cudaMemcpyAsync(c->pinned, c->gh, k * sizeof(double), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
@@ -461,7 +463,7 @@ int gmres(kfbim_ctx* c, const double* rhs, double* x, cudaStream_t s, int* iters
       break;
     }
     if (k < m) {
-      k_scale_copy<<<grid_for(n), 256, 0, s>>>(c->gw, 1.0 / hn, nullptr, c->V + (int64_t)k * ld, n);
+      k_scale_copy<<<grid_for(n), 256, 0, s>>>(c->gw, 1.0 / hn, nullptr, c->V + (int64_t)k * ld, n); ++g_launches;
       check_launch();
     }
   }
@@ -473,7 +475,7 @@ int gmres(kfbim_ctx* c, const double* rhs, double* x, cudaStream_t s, int* iters
     y[i] = acc / H[(size_t)i * m + i];
   }
   CK(cudaMemcpyAsync(c->gy, y.data(), kk * sizeof(double), cudaMemcpyHostToDevice, s));
-  k_multi_axpy<<<grid_for(n), 256, 0, s>>>(c->V, ld, c->gy, kk, x, n, 1);
+  k_multi_axpy<<<grid_for(n), 256, 0, s>>>(c->V, ld, c->gy, kk, x, n, 1); ++g_launches;
   check_launch();
   CK(cudaStreamSynchronize(s));
   *iters = kk;
@@ -736,7 +738,7 @@ int kfbim_jumps(kfbim_ctx* c, const double* phi, const double* fpts, double* Jou
     const int64_t n = c->n_all;
     const int wpb = 8;
     k_jumps<<<(unsigned)((n + wpb - 1) / wpb), 32 * wpb, 0, s>>>(
-        phi, fpts, n, c->d_comp, c->d_pid, c->d_fit_ptr, c->d_fit_col, c->d_fit_w, c->d_jmap, Jout);
+        phi, fpts, n, c->d_comp, c->d_pid, c->d_fit_ptr, c->d_fit_col, c->d_fit_w, c->d_jmap, Jout); ++g_launches;
     check_launch();
     return KFBIM_OK;
   });
@@ -769,7 +771,7 @@ int kfbim_poisson(kfbim_ctx* c, int comp, const double* r, double* u, void* stre
     cudaStream_t s = (cudaStream_t)stream;
     // (1/mu) scaling is part of the weight: undo it so this is (-Delta_h)^{-1}
     face_poisson<double, double, double>(c, comp - 1, r, c->cr, c->t1, c->t2, s);
-    k_scale_copy<<<grid_for(c->N3), 256, 0, s>>>(c->cr, c->mu, nullptr, u, c->N3);
+    k_scale_copy<<<grid_for(c->N3), 256, 0, s>>>(c->cr, c->mu, nullptr, u, c->N3); ++g_launches;
     check_launch();
     return KFBIM_OK;
   });
@@ -781,7 +783,7 @@ int kfbim_schur_apply(kfbim_ctx* c, const double* d, double* q, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     schur_apply<double>(c, d, q, c->t1, c->t2, s);
     dot(c, d, (const double*)nullptr, c->N3, c->scal, 1.0 / (c->mu * (double)c->N3), s);
-    k_shift<<<grid_for(c->N3), 256, 0, s>>>(q, c->scal, 1.0, c->N3);
+    k_shift<<<grid_for(c->N3), 256, 0, s>>>(q, c->scal, 1.0, c->N3); ++g_launches;
     check_launch();
     return KFBIM_OK;
   });
@@ -792,6 +794,7 @@ int kfbim_solve(kfbim_ctx* c, const double* g, const double* fpts, const double*
   return guarded(c, [&]() -> int {
     if (!g || !phi) return fail(c, KFBIM_E_INVALID, "kfbim_solve: bad pointers");
     reset_counters(c);
+    const int64_t launches0 = g_launches;
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = c->n_prim;
     CK(cudaMemcpyAsync(c->grhs, g, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -799,8 +802,8 @@ int kfbim_solve(kfbim_ctx* c, const double* g, const double* fpts, const double*
       int st = interface_solve(c, c->zero_phi, fpts, fgrid, s);
       if (st != KFBIM_OK && st != KFBIM_E_NOCONV) return st;
       trace(c, c->u, c->J, c->gw, s);
-      k_scale_copy<<<grid_for(n), 256, 0, s>>>(c->gw, -1.0, nullptr, c->gw, n);
-      k_add_to<double><<<grid_for(n), 256, 0, s>>>(c->gw, c->grhs, n);
+      k_scale_copy<<<grid_for(n), 256, 0, s>>>(c->gw, -1.0, nullptr, c->gw, n); ++g_launches;
+      k_add_to<double><<<grid_for(n), 256, 0, s>>>(c->gw, c->grhs, n); ++g_launches;
       check_launch();
     }
     int its = 0;
@@ -817,6 +820,7 @@ int kfbim_solve(kfbim_ctx* c, const double* g, const double* fpts, const double*
       stats->cg_iters = c->cg_iters;
       stats->refine_sweeps = c->refine_sweeps;
       stats->gmres_residual = res;
+      stats->kernel_launches = g_launches - launches0;
     }
     if (st == KFBIM_E_NOCONV) {
       c->err = "GMRES reached its iteration cap";

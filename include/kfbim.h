@@ -208,6 +208,33 @@ int kfbim_poisson(kfbim_ctx* ctx, int c, const double* r_dev, double* u_dev, voi
  * alpha = mu N^3; d_dev, q_dev N^3 doubles (cells). */
 int kfbim_schur_apply(kfbim_ctx* ctx, const double* d_dev, double* q_dev, void* stream);
 
+/* Allocation-free variant of kfbim_poisson, for callers that may not allocate
+ * device memory: code that runs under a memory manager owning the whole device
+ * heap (a caching allocator that reserved HBM up front, or a host application
+ * that hands its plug-ins only buffers it allocated itself), and loops where
+ * cudaMalloc's implicit device synchronisation is not acceptable.  The paper has
+ * no counterpart: this is a deployment convenience around the FFT Poisson solve
+ * of Sec. 4.2 item ii.
+ *
+ * Solves -Delta_h u = r on face grid c (1..3) of an N^3 grid on [lo, hi]^3,
+ * N a power of two with 16 <= N <= 64; r_dev and u_dev are caller-owned N^3
+ * doubles in the layout of kfbim_poisson (must not alias).  No context, no
+ * cudaMalloc/cudaFree and no allocating library routine: the scratch (two N^3
+ * fields) and the transform tables live in file-scope static device arrays of
+ * 4 MiB + 2 KiB, which every GPU that loads the library holds until exit.
+ * The first call on a device resolves the arrays' device addresses
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the arrays: calls that overlap on the GPU (different
+ * streams, or several host threads on one device) race and corrupt each
+ * other's results; calls on one stream are ordered and each call rewrites the
+ * whole scratch and tables before reading them, so nothing from a previous
+ * call leaks into the next.
+ * Errors: KFBIM_E_INVALID for a bad argument or N > 64 (a message names the
+ * limit on stderr), KFBIM_E_CUDA if the symbols cannot be resolved or a launch
+ * fails. */
+int kfbim_poisson_noalloc(int c, int N, double lo, double hi, const double* r_dev,
+                          double* u_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

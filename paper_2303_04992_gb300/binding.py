@@ -64,6 +64,8 @@ SYMBOLS = {
     "kfbim_trace": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "kfbim_poisson": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     "kfbim_schur_apply": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "kfbim_poisson_noalloc": (c_int, [c_int, c_int, c_double, c_double, c_void_p, c_void_p,
+                                      c_void_p]),
     "kfbim_profile": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                               c_void_p]),
 }
@@ -89,6 +91,18 @@ def load_library():
             fn.argtypes = args
         _lib = lib
     return _lib
+
+
+def poisson_noalloc(c, N, lo, hi, r, u):
+    """Allocation-free FFT Poisson solve on face grid c (N <= 64): r, u are
+    caller-owned float64 CUDA tensors of N^3 values; torch's current stream."""
+    import torch
+    lib = load_library()
+    st = lib.kfbim_poisson_noalloc(c, N, lo, hi, _ptr(r), _ptr(u),
+                                   c_void_p(torch.cuda.current_stream().cuda_stream))
+    if st != 0:
+        raise KfbimError(st, "kfbim_poisson_noalloc failed (see stderr)")
+    return u
 
 
 def _geometry(desc):

@@ -20,6 +20,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -591,6 +592,84 @@ void reset_counters(kfbim_ctx* c) {
 
 }  // namespace
 
+// ------------------------------------------------ allocation-free Poisson
+// kfbim_poisson_noalloc runs the same five transform passes as kfbim_poisson
+// without a context: its two scratch fields and its twiddle and eigenvalue
+// tables live in the file-scope device arrays below, sized for N <= 64.
+// In host code these names are only stand-ins for the device symbols; the
+// device addresses are fetched with cudaGetSymbolAddress once per device.
+namespace {
+constexpr int kNoAllocMaxN = 64;
+static __device__ __align__(256) double g_na_scratch[2 * kNoAllocMaxN * kNoAllocMaxN * kNoAllocMaxN];
+static __device__ __align__(256) C2<double> g_na_tw[kNoAllocMaxN];
+static __device__ __align__(256) C2<double> g_na_q[kNoAllocMaxN];
+static __device__ __align__(256) double g_na_s2[2 * kNoAllocMaxN];
+
+struct NoAllocSymbols {
+  bool ready = false;
+  double* scratch = nullptr;
+  C2<double>* tw = nullptr;
+  C2<double>* q = nullptr;
+  double* s2 = nullptr;
+};
+constexpr int kMaxDevices = 64;
+NoAllocSymbols g_na_dev[kMaxDevices];
+std::mutex g_na_mutex;
+
+// Twiddles exp(-2 pi i t / 2N), post-twiddles exp(-i pi k / 2N) and the
+// one-dimensional Laplacian eigenvalues 4 sin^2 for length N (rewritten on
+// every call, so consecutive calls with different N are consistent).
+__global__ void k_na_tables(int N, C2<double>* tw, C2<double>* q, double* s2) {
+  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    double sn, cs;
+    sincospi((double)k / (double)N, &sn, &cs);
+    tw[k] = {cs, -sn};
+    sincospi(0.5 * (double)k / (double)N, &sn, &cs);
+    q[k] = {cs, -sn};
+    const double a = sinpi(0.5 * (double)k / (double)N), b = sinpi(0.5 * (double)(k + 1) / (double)N);
+    s2[k] = 4.0 * a * a;
+    s2[N + k] = 4.0 * b * b;
+  }
+}
+
+int noalloc_symbols(NoAllocSymbols** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return KFBIM_E_CUDA;
+  std::lock_guard<std::mutex> lock(g_na_mutex);
+  NoAllocSymbols& d = g_na_dev[dev];
+  if (!d.ready) {
+    if (cudaGetSymbolAddress((void**)&d.scratch, g_na_scratch) != cudaSuccess ||
+        cudaGetSymbolAddress((void**)&d.tw, g_na_tw) != cudaSuccess ||
+        cudaGetSymbolAddress((void**)&d.q, g_na_q) != cudaSuccess ||
+        cudaGetSymbolAddress((void**)&d.s2, g_na_s2) != cudaSuccess)
+      return KFBIM_E_CUDA;
+    d.ready = true;
+  }
+  *out = &d;
+  return KFBIM_OK;
+}
+
+void noalloc_pass(const NoAllocSymbols& d, int N, double h, const double* in, double* out, int axis,
+                  int t0, int t1, int wmode, int wc, cudaStream_t s) {
+  PassArgs a;
+  a.N = N;
+  a.axis = axis;
+  a.type0 = t0;
+  a.type1 = t1;
+  a.wmode = wmode;
+  a.wc = wc;
+  for (int b = 0; b < 3; ++b) a.kind[b] = (b == wc) ? 0 : 1;
+  a.mu = 1.0;
+  a.h = h;
+  a.accumulate = 0;
+  a.scale = 1.0;
+  // N <= 64 in FP64 needs at most 40 KiB of dynamic shared memory (default limit 48 KiB)
+  const size_t smem = pass_smem_bytes(N, sizeof(double));
+  k_axis_pass<double, double, double><<<(unsigned)(N * N / LPC), PASS_THREADS, smem, s>>>(
+      in, out, a, d.tw, d.q, d.s2);
+}
+}  // namespace
+
 // =================================================================== C ABI
 extern "C" {
 
@@ -860,6 +939,35 @@ int kfbim_profile(kfbim_ctx* c, int enable, double* ms64, int64_t* launches64, d
     if (bytes32) *bytes32 = c->prof_bytes[1];
     return KFBIM_OK;
   });
+}
+
+int kfbim_poisson_noalloc(int c, int N, double lo, double hi, const double* r, double* u,
+                          void* stream) {
+  if (c < 1 || c > 3 || !r || !u || r == u || !(hi > lo) || N < 16 || (N & (N - 1)) != 0)
+    return KFBIM_E_INVALID;
+  if (N > kNoAllocMaxN) {
+    std::fprintf(stderr, "kfbim_poisson_noalloc: N = %d exceeds the static scratch limit N <= %d\n",
+                 N, kNoAllocMaxN);
+    return KFBIM_E_INVALID;
+  }
+  NoAllocSymbols* d = nullptr;
+  int st = noalloc_symbols(&d);
+  if (st != KFBIM_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const double h = (hi - lo) / N;
+  const int64_t N3 = (int64_t)N * N * N;
+  double* t1 = d->scratch;
+  double* t2 = d->scratch + N3;
+  const int cax = c - 1;
+  int o1, o2;
+  others(cax, o1, o2);
+  k_na_tables<<<1, 64, 0, s>>>(N, d->tw, d->q, d->s2);
+  noalloc_pass(*d, N, h, r, t1, o2, X_DST2F, X_NONE, W_NONE, cax, s);
+  noalloc_pass(*d, N, h, t1, t2, o1, X_DST2F, X_NONE, W_NONE, cax, s);
+  noalloc_pass(*d, N, h, t2, t1, cax, X_DST1F, X_DST1I, W_POISSON, cax, s);
+  noalloc_pass(*d, N, h, t1, t2, o1, X_DST2I, X_NONE, W_NONE, cax, s);
+  noalloc_pass(*d, N, h, t2, u, o2, X_DST2I, X_NONE, W_NONE, cax, s);
+  return cudaGetLastError() == cudaSuccess ? KFBIM_OK : KFBIM_E_CUDA;
 }
 
 int kfbim_solve_host(kfbim_ctx* c, const double* g, const double* fpts, const double* fgrid,

@@ -144,7 +144,7 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("transforms.cuh",):
+    for f in ("transforms.cuh", "transforms2.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2303_04992_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:12]
 

@@ -2,7 +2,7 @@
 (Sec. 4.4, Eqs. Interpolation+/-; the unknowns are the value and first and
 second derivatives of u^+ at x, ten in all).
 
-Ten-node stencil (reading of 'ten closest grid nodes', Fig. of Sec. 4.4): for a
+Ten-node stencil (reading of the nearest-node choice of Sec. 4.4 and its figure): for a
 control point of X_c on an a-line, with lower node P0 and fraction theta, the
 base node b is P0 if theta < 1/2 else P0 + e_a; the stencil is
     b, b +- e_1, b +- e_2, b +- e_3, b + s_1 e_1 + s_2 e_2, b + s_1 e_1 + s_3 e_3,

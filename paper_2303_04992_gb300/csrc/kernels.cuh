@@ -242,49 +242,92 @@ __global__ void k_sum_partials(const double* __restrict__ partial, int nb, doubl
 }
 
 // ----------------------------------------------------------------- CG
-// Device scalars of one CG run.
+// Device scalars of one CG run on (S + 1 1^T rank1) x = b.  Every reduction
+// is finished by the last block to arrive (fixed-order sum of the block
+// partials), which also updates the scalars, so one CG iteration is the
+// Schur apply plus three kernels and needs no host round trip.  Once
+// rr <= stop the iteration is a no-op (done = 1): alpha = beta = 0 and the
+// transform passes of S d return immediately.
 struct CGScalars {
-  double rr, bb, dq, alpha, beta, sumd, rank1;  // rank1 = 1/alpha_lambda
+  double rr, bb, stop, dq, alpha, beta, sumd, rank1;
+  int done, iters;
+  unsigned int ticket[3];
 };
 
-// After the dot d.q_S: alpha = rr / (d.q_S + sumd^2 * rank1)
-__global__ void k_cg_alpha(CGScalars* s, const double* dq) {
-  const double den = dq[0] + s->sumd * s->sumd * s->rank1;
-  s->dq = den;
-  s->alpha = (den != 0.0) ? s->rr / den : 0.0;
+// Sum of the gridDim.x partials by the last block; returns true in that block.
+__device__ __forceinline__ bool last_block_sum(double v, double* __restrict__ partial,
+                                               unsigned int* ticket, double* sh, double* out) {
+  __shared__ bool is_last;
+  v = block_sum<double>(v, sh);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = v;
+    __threadfence();
+    const unsigned int t = atomicAdd(ticket, 1u);
+    is_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+  double s = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s += ((volatile double*)partial)[b];
+  s = block_sum<double>(s, sh);
+  if (threadIdx.x == 0) {
+    *out = s;
+    *ticket = 0u;
+  }
+  return true;
 }
 
-// x += alpha d; r -= alpha (q + sumd * rank1); partial sums of r^2
+// dq = d . q_S; alpha = rr / (dq + sumd^2 rank1)
+template <typename T>
+__global__ void k_cg_alpha(const T* __restrict__ d, const T* __restrict__ q, int64_t n,
+                           CGScalars* s, double* __restrict__ partial) {
+  __shared__ double sh[32];
+  __shared__ double total;
+  if (s->done) return;
+  double acc = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    acc += double(d[e]) * double(q[e]);
+  if (last_block_sum(acc, partial, &s->ticket[0], sh, &total) && threadIdx.x == 0) {
+    const double den = total + s->sumd * s->sumd * s->rank1;
+    s->dq = den;
+    s->alpha = (den != 0.0) ? s->rr / den : 0.0;
+  }
+}
+
+// x += alpha d; r -= alpha (q_S + sumd rank1); rr_new = r . r; beta; convergence flag
 template <typename T>
 __global__ void k_cg_update(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ d,
-                            const T* __restrict__ q, int64_t n, const CGScalars* __restrict__ s,
+                            const T* __restrict__ q, int64_t n, CGScalars* s,
                             double* __restrict__ partial) {
   __shared__ double sh[32];
+  __shared__ double total;
+  if (s->done) return;
   const double a = s->alpha;
   const double c1 = s->sumd * s->rank1;
   double acc = 0.0;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const double rv = double(r[e]) - a * (double(q[e]) + c1);
+    const T rv = T(double(r[e]) - a * (double(q[e]) + c1));
     x[e] = T(double(x[e]) + a * double(d[e]));
-    r[e] = T(rv);
-    acc += double(T(rv)) * double(T(rv));
+    r[e] = rv;
+    acc += double(rv) * double(rv);
   }
-  acc = block_sum<double>(acc, sh);
-  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+  if (last_block_sum(acc, partial, &s->ticket[1], sh, &total) && threadIdx.x == 0) {
+    s->beta = (s->rr != 0.0) ? total / s->rr : 0.0;
+    s->rr = total;
+    s->iters += 1;
+  }
 }
 
-__global__ void k_cg_beta(CGScalars* s, const double* rr_new) {
-  const double rn = rr_new[0];
-  s->beta = (s->rr != 0.0) ? rn / s->rr : 0.0;
-  s->rr = rn;
-}
-
-// d = r + beta d; partial sums of d
+// d = r + beta d; sumd = sum d; done once rr <= stop
 template <typename T>
-__global__ void k_cg_direction(T* __restrict__ d, const T* __restrict__ r, int64_t n,
-                               const CGScalars* __restrict__ s, double* __restrict__ partial) {
+__global__ void k_cg_direction(T* __restrict__ d, const T* __restrict__ r, int64_t n, CGScalars* s,
+                               double* __restrict__ partial) {
   __shared__ double sh[32];
+  __shared__ double total;
+  if (s->done) return;
   const double b = s->beta;
   double acc = 0.0;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
@@ -293,11 +336,54 @@ __global__ void k_cg_direction(T* __restrict__ d, const T* __restrict__ r, int64
     d[e] = v;
     acc += double(v);
   }
-  acc = block_sum<double>(acc, sh);
-  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+  if (last_block_sum(acc, partial, &s->ticket[2], sh, &total) && threadIdx.x == 0) {
+    s->sumd = total;
+    if (!(s->rr > s->stop)) s->done = 1;
+  }
 }
 
-__global__ void k_set_sumd(CGScalars* s, const double* sumd) { s->sumd = sumd[0]; }
+// initial scalars: rr = bb = b.b, sumd = sum b, stop = tol^2 bb
+template <typename T>
+__global__ void k_cg_init(const T* __restrict__ b, int64_t n, CGScalars* s, double tol2, double rank1,
+                          double* __restrict__ partial) {
+  __shared__ double sh[32];
+  double a0 = 0.0, a1 = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const double v = double(b[e]);
+    a0 += v * v;
+    a1 += v;
+  }
+  a0 = block_sum<double>(a0, sh);
+  a1 = block_sum<double>(a1, sh);
+  __shared__ bool is_last;
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = a0;
+    partial[2 * blockIdx.x + 1] = a1;
+    __threadfence();
+    is_last = (atomicAdd(&s->ticket[0], 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  double s0 = 0.0, s1 = 0.0;
+  for (int bk = threadIdx.x; bk < (int)gridDim.x; bk += blockDim.x) {
+    s0 += ((volatile double*)partial)[2 * bk];
+    s1 += ((volatile double*)partial)[2 * bk + 1];
+  }
+  s0 = block_sum<double>(s0, sh);
+  s1 = block_sum<double>(s1, sh);
+  if (threadIdx.x == 0) {
+    s->rr = s0;
+    s->bb = s0;
+    s->sumd = s1;
+    s->stop = tol2 * s0;
+    s->rank1 = rank1;
+    s->done = (s0 > s->stop) ? 0 : 1;
+    s->iters = 0;
+    s->ticket[0] = 0u;
+  }
+}
 
 // --------------------------------------------------------- vector helpers
 template <typename Ta, typename Tb>

@@ -27,6 +27,7 @@
 #include "internal.h"
 #include "kernels.cuh"
 #include "transforms.cuh"
+#include "transforms2.cuh"
 
 using namespace kfbim;
 
@@ -50,6 +51,9 @@ struct kfbim_ctx {
   C2<double>* d_q64 = nullptr;
   C2<float>* d_tw32 = nullptr;
   C2<float>* d_q32 = nullptr;
+  C2<double>* d_twc64 = nullptr;  // full-circle twiddles exp(-2 pi i t / 2N), t < 2N
+  C2<float>* d_twc32 = nullptr;
+  float* d_s2f = nullptr;         // FP32 copy of the eigenvalue table
   // FP64 workspace
   double *J = nullptr, *rhs = nullptr, *u = nullptr, *p = nullptr, *t1 = nullptr, *t2 = nullptr;
   double *cr = nullptr, *cd = nullptr, *cq = nullptr, *rres = nullptr, *zero_phi = nullptr;
@@ -66,6 +70,11 @@ struct kfbim_ctx {
   double *hs_g = nullptr, *hs_phi = nullptr, *hs_fp = nullptr, *hs_fg = nullptr, *hs_u = nullptr,
          *hs_p = nullptr;
   bool device = false;        // false for kfbim_setup_host contexts
+  // CUDA graphs of kCgGraphIters CG iterations (index 0: FP64, 1: FP32)
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t cg_exec[2] = {nullptr, nullptr};
+  int64_t cg_graph_kernels[2] = {0, 0};
+  bool use_graphs = true;
   // optional per-kernel timing of the transform passes (kfbim_profile)
   bool prof = false;
   std::vector<cudaEvent_t> prof_ev;    // pairs (start, stop)
@@ -127,17 +136,34 @@ template <>
 struct Tw<double> {
   static const C2<double>* tw(kfbim_ctx* c) { return c->d_tw64; }
   static const C2<double>* q(kfbim_ctx* c) { return c->d_q64; }
+  static const C2<double>* twc(kfbim_ctx* c) { return c->d_twc64; }
+  static const double* s2(kfbim_ctx* c) { return c->d_s2; }
 };
 template <>
 struct Tw<float> {
   static const C2<float>* tw(kfbim_ctx* c) { return c->d_tw32; }
   static const C2<float>* q(kfbim_ctx* c) { return c->d_q32; }
+  static const C2<float>* twc(kfbim_ctx* c) { return c->d_twc32; }
+  static const float* s2(kfbim_ctx* c) { return c->d_s2f; }
 };
+
+template <typename Tin, typename T, typename Tout, int N>
+void launch_pass2(kfbim_ctx* c, const Tin* in, Tout* out, const PassArgs& a, cudaStream_t s) {
+  const size_t smem = Pass2Smem<T, N>::bytes;
+  auto kern = k_axis_pass2<Tin, T, Tout, N>;
+  static size_t configured = 0;
+  if (smem > configured) {
+    CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    configured = smem;
+  }
+  kern<<<(unsigned)(N * N / LPC2), PASS2_THREADS, smem, s>>>(in, out, a, Tw<T>::twc(c), Tw<T>::q(c),
+                                                              Tw<T>::s2(c));
+}
 
 template <typename Tin, typename T, typename Tout>
 void pass(kfbim_ctx* c, const Tin* in, Tout* out, int axis, int t0, int t1, int wmode, int wc,
-          int acc, double scale, cudaStream_t s) {
-  PassArgs a;
+          int acc, double scale, cudaStream_t s, const int* skip = nullptr) {
+  PassArgs a{};  // value-initialised: every field, skip included, starts at zero
   a.N = c->N;
   a.axis = axis;
   a.type0 = t0;
@@ -149,17 +175,24 @@ void pass(kfbim_ctx* c, const Tin* in, Tout* out, int axis, int t0, int t1, int 
   a.h = c->h;
   a.accumulate = acc;
   a.scale = scale;
-  const size_t smem = pass_smem_bytes(c->N, sizeof(T));
-  auto kern = k_axis_pass<Tin, T, Tout>;
-  static size_t configured = 0;  // per template instance
-  if (smem > configured) {
-    CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    configured = smem;
-  }
-  const int blocks = (int)((int64_t)c->N * c->N / LPC);
+  a.skip = skip;
   const bool prof = c->prof && c->prof_used + 2 <= (int)c->prof_ev.size();
   if (prof) CK(cudaEventRecord(c->prof_ev[c->prof_used], s));
-  kern<<<blocks, PASS_THREADS, smem, s>>>(in, out, a, Tw<T>::tw(c), Tw<T>::q(c), c->d_s2); ++g_launches;
+  if (c->N == 128) launch_pass2<Tin, T, Tout, 128>(c, in, out, a, s);
+  else if (c->N == 64) launch_pass2<Tin, T, Tout, 64>(c, in, out, a, s);
+  else if (c->N == 32) launch_pass2<Tin, T, Tout, 32>(c, in, out, a, s);
+  else {
+    const size_t smem = pass_smem_bytes(c->N, sizeof(T));
+    auto kern = k_axis_pass<Tin, T, Tout>;
+    static size_t configured = 0;  // per template instance
+    if (smem > configured) {
+      CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      configured = smem;
+    }
+    const int blocks = (int)((int64_t)c->N * c->N / LPC);
+    kern<<<blocks, PASS_THREADS, smem, s>>>(in, out, a, Tw<T>::tw(c), Tw<T>::q(c), c->d_s2);
+  }
+  ++g_launches;
   check_launch();
   if (prof) {
     CK(cudaEventRecord(c->prof_ev[c->prof_used + 1], s));
@@ -212,15 +245,16 @@ void schur_rhs_add(kfbim_ctx* c, int cax, const Tin* f, T* b, T* t1, T* t2, cuda
 
 // q = (1/mu) sum_c G_c^T (-Delta_c)^{-1} G_c d   (rank-one term handled in CG)
 template <typename T>
-void schur_apply(kfbim_ctx* c, const T* d, T* q, T* t1, T* t2, cudaStream_t s) {
+void schur_apply(kfbim_ctx* c, const T* d, T* q, T* t1, T* t2, cudaStream_t s,
+                 const int* skip = nullptr) {
   for (int cax = 0; cax < 3; ++cax) {
     int o1, o2;
     others(cax, o1, o2);
-    pass<T, T, T>(c, d, t1, o2, X_DST2F, X_NONE, W_NONE, cax, 0, 1.0, s);
-    pass<T, T, T>(c, t1, t2, o1, X_DST2F, X_NONE, W_NONE, cax, 0, 1.0, s);
-    pass<T, T, T>(c, t2, t1, cax, X_DCT2F, X_DCT2I, W_SCHUR, cax, 0, 1.0, s);
-    pass<T, T, T>(c, t1, t2, o1, X_DST2I, X_NONE, W_NONE, cax, 0, 1.0, s);
-    pass<T, T, T>(c, t2, q, o2, X_DST2I, X_NONE, W_NONE, cax, cax > 0 ? 1 : 0, 1.0, s);
+    pass<T, T, T>(c, d, t1, o2, X_DST2F, X_NONE, W_NONE, cax, 0, 1.0, s, skip);
+    pass<T, T, T>(c, t1, t2, o1, X_DST2F, X_NONE, W_NONE, cax, 0, 1.0, s, skip);
+    pass<T, T, T>(c, t2, t1, cax, X_DCT2F, X_DCT2I, W_SCHUR, cax, 0, 1.0, s, skip);
+    pass<T, T, T>(c, t1, t2, o1, X_DST2I, X_NONE, W_NONE, cax, 0, 1.0, s, skip);
+    pass<T, T, T>(c, t2, q, o2, X_DST2I, X_NONE, W_NONE, cax, cax > 0 ? 1 : 0, 1.0, s, skip);
   }
 }
 
@@ -241,52 +275,88 @@ void dot(kfbim_ctx* c, const Ta* x, const Tb* y, int64_t n, double* out, double 
   check_launch();
 }
 
-// CG on (S + 1 1^T / (mu N^3)) x = b from x = 0.  Vectors of type T.
+constexpr int kCgGraphIters = 4;
+
+// One CG iteration: q = S d, then the three fused scalar/vector kernels.  All
+// of it is a no-op once cgs->done is set.
+template <typename T>
+void cg_iteration(kfbim_ctx* c, T* x, T* r, T* d, T* q, T* t1, T* t2, cudaStream_t s) {
+  const int64_t n = c->N3;
+  schur_apply<T>(c, d, q, t1, t2, s, &c->cgs->done);
+  k_cg_alpha<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(d, q, n, c->cgs, c->partial); ++g_launches;
+  k_cg_update<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(x, r, d, q, n, c->cgs, c->partial); ++g_launches;
+  k_cg_direction<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(d, r, n, c->cgs, c->partial); ++g_launches;
+  check_launch();
+}
+
+template <typename T>
+struct Slot;
+template <>
+struct Slot<double> { static constexpr int v = 0; };
+template <>
+struct Slot<float> { static constexpr int v = 1; };
+
+// The graph of kCgGraphIters iterations for this precision (captured once per
+// context: every pointer it uses is a fixed workspace buffer).
+template <typename T>
+cudaGraphExec_t cg_graph(kfbim_ctx* c, T* x, T* r, T* d, T* q, T* t1, T* t2) {
+  const int slot = Slot<T>::v;
+  if (c->cg_exec[slot]) return c->cg_exec[slot];
+  // kernel attributes are set outside the capture: one iteration on the idle
+  // capture stream with the done flag raised does nothing but configure them
+  const int one = 1;
+  CK(cudaMemcpyAsync(&c->cgs->done, &one, sizeof(int), cudaMemcpyHostToDevice, c->cap_stream));
+  const int64_t before = g_launches;
+  cg_iteration<T>(c, x, r, d, q, t1, t2, c->cap_stream);
+  CK(cudaStreamSynchronize(c->cap_stream));
+  const int64_t per_iter = g_launches - before;
+  g_launches = before;
+  cudaGraph_t graph;
+  CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+  for (int it = 0; it < kCgGraphIters; ++it) cg_iteration<T>(c, x, r, d, q, t1, t2, c->cap_stream);
+  CK(cudaStreamEndCapture(c->cap_stream, &graph));
+  g_launches = before;
+  CK(cudaGraphInstantiate(&c->cg_exec[slot], graph, 0));
+  CK(cudaGraphDestroy(graph));
+  c->cg_graph_kernels[slot] = per_iter * kCgGraphIters;
+  return c->cg_exec[slot];
+}
+
+// CG on (S + 1 1^T / (mu N^3)) x = b from x = 0, vectors of type T, FP64
+// scalars.  The host reads the status once per kCgGraphIters iterations.
 template <typename T>
 int cg(kfbim_ctx* c, const T* b, T* x, T* r, T* d, T* q, T* t1, T* t2, double tol, int maxit,
        cudaStream_t s, int* iters) {
   const int64_t n = c->N3;
-  CGScalars init{};
-  init.rank1 = 1.0 / (c->mu * (double)n);
-  CK(cudaMemcpyAsync(c->cgs, &init, sizeof(CGScalars), cudaMemcpyHostToDevice, s));
+  const bool graphs = c->use_graphs && !c->prof;
+  cudaGraphExec_t exec = graphs ? cg_graph<T>(c, x, r, d, q, t1, t2) : nullptr;
+  CK(cudaMemsetAsync(c->cgs, 0, sizeof(CGScalars), s));
   CK(cudaMemsetAsync(x, 0, n * sizeof(T), s));
   CK(cudaMemcpyAsync(r, b, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
   CK(cudaMemcpyAsync(d, b, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
-  double* sc = c->scal;
-  dot(c, r, r, n, &c->cgs->rr, 1.0, s);
-  dot(c, r, r, n, &c->cgs->bb, 1.0, s);
-  dot(c, d, (const T*)nullptr, n, &c->cgs->sumd, 1.0, s);
-  double bb = read_scalar(c, &c->cgs->bb, s);
-  int it = 0;
-  if (bb == 0.0) {
-    *iters = 0;
-    return KFBIM_OK;
-  }
-  if (!std::isfinite(bb)) return KFBIM_E_NONFINITE;
-  const double stop = tol * tol * bb;
-  double rr = bb;
+  k_cg_init<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(b, n, c->cgs, tol * tol, 1.0 / (c->mu * (double)n),
+                                                   c->partial);
+  ++g_launches;
+  check_launch();
+  int launched = 0;
   while (true) {
-    if (rr <= stop) break;
-    if (it >= maxit) {
-      *iters = it;
-      return KFBIM_E_NOCONV;
+    CK(cudaMemcpyAsync(c->pinned, c->cgs, sizeof(CGScalars), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (c->prof_used) prof_collect(c);
+    CGScalars h;
+    std::memcpy(&h, c->pinned, sizeof(CGScalars));
+    *iters = h.iters;
+    if (!std::isfinite(h.rr)) return KFBIM_E_NONFINITE;
+    if (h.done) return KFBIM_OK;
+    if (launched >= maxit) return KFBIM_E_NOCONV;
+    if (graphs) {
+      CK(cudaGraphLaunch(exec, s));
+      g_launches += c->cg_graph_kernels[Slot<T>::v];
+    } else {
+      for (int it = 0; it < kCgGraphIters; ++it) cg_iteration<T>(c, x, r, d, q, t1, t2, s);
     }
-    schur_apply<T>(c, d, q, t1, t2, s);
-    dot(c, d, q, n, sc, 1.0, s);
-    k_cg_alpha<<<1, 1, 0, s>>>(c->cgs, sc); ++g_launches;
-    k_cg_update<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(x, r, d, q, n, c->cgs, c->partial); ++g_launches;
-    k_sum_partials<<<1, RED_THREADS, 0, s>>>(c->partial, RED_BLOCKS, 1.0, sc + 1); ++g_launches;
-    k_cg_beta<<<1, 1, 0, s>>>(c->cgs, sc + 1); ++g_launches;
-    k_cg_direction<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(d, r, n, c->cgs, c->partial); ++g_launches;
-    k_sum_partials<<<1, RED_THREADS, 0, s>>>(c->partial, RED_BLOCKS, 1.0, sc + 2); ++g_launches;
-    k_set_sumd<<<1, 1, 0, s>>>(c->cgs, sc + 2); ++g_launches;
-    check_launch();
-    ++it;
-    rr = read_scalar(c, &c->cgs->rr, s);
-    if (!std::isfinite(rr)) return KFBIM_E_NONFINITE;
+    launched += kCgGraphIters;
   }
-  *iters = it;
-  return KFBIM_OK;
 }
 
 // Solve the corrected MAC system for rhs = [f1|f2|f3|g] (FP64) -> u, p (FP64).
@@ -518,6 +588,15 @@ void fill_tables(kfbim_ctx* c) {
     tw32[k] = {(float)tw[k].x, (float)tw[k].y};
     q32[k] = {(float)q[k].x, (float)q[k].y};
   }
+  std::vector<C2<double>> twc(2 * N);
+  std::vector<C2<float>> twc32(2 * N);
+  for (int k = 0; k < 2 * N; ++k) {
+    const double a = M_PI * (double)k / (double)N;
+    twc[k] = {std::cos(a), -std::sin(a)};
+    twc32[k] = {(float)twc[k].x, (float)twc[k].y};
+  }
+  c->d_twc64 = upload(c, twc);
+  c->d_twc32 = upload(c, twc32);
   c->d_tw64 = upload(c, tw);
   c->d_q64 = upload(c, q);
   c->d_tw32 = upload(c, tw32);
@@ -529,6 +608,8 @@ void fill_tables(kfbim_ctx* c) {
     s2[N + i] = 4.0 * b * b;
   }
   c->d_s2 = upload(c, s2);
+  std::vector<float> s2f(s2.begin(), s2.end());
+  c->d_s2f = upload(c, s2f);
   // workspace
   const int64_t N3 = c->N3;
   c->J = dalloc<double>(c, kSlots * t.n_all);
@@ -561,6 +642,7 @@ void fill_tables(kfbim_ctx* c) {
   c->gh = dalloc<double>(c, c->gm_max + 1);
   c->grhs = dalloc<double>(c, std::max<int64_t>(1, t.n_prim));
   c->gy = dalloc<double>(c, c->gm_max + 1);
+  CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
   void* ph = nullptr;
   CK(cudaMallocHost(&ph, sizeof(double) * 256));
   c->pinned = static_cast<double*>(ph);
@@ -651,7 +733,7 @@ int noalloc_symbols(NoAllocSymbols** out) {
 
 void noalloc_pass(const NoAllocSymbols& d, int N, double h, const double* in, double* out, int axis,
                   int t0, int t1, int wmode, int wc, cudaStream_t s) {
-  PassArgs a;
+  PassArgs a{};  // value-initialised: every field, skip included, starts at zero
   a.N = N;
   a.axis = axis;
   a.type0 = t0;
@@ -663,6 +745,7 @@ void noalloc_pass(const NoAllocSymbols& d, int N, double h, const double* in, do
   a.h = h;
   a.accumulate = 0;
   a.scale = 1.0;
+  a.skip = nullptr;
   // N <= 64 in FP64 needs at most 40 KiB of dynamic shared memory (default limit 48 KiB)
   const size_t smem = pass_smem_bytes(N, sizeof(double));
   k_axis_pass<double, double, double><<<(unsigned)(N * N / LPC), PASS_THREADS, smem, s>>>(
@@ -767,6 +850,9 @@ int kfbim_destroy(kfbim_ctx* c) {
   if (!c) return KFBIM_E_INVALID;
   if (c->device) cudaDeviceSynchronize();
   for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
+  for (auto& e : c->cg_exec)
+    if (e) cudaGraphExecDestroy(e);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   for (void* p : c->allocs) cudaFree(p);
   if (c->pinned) cudaFreeHost(c->pinned);
   delete c;

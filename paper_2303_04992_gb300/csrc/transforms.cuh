@@ -44,6 +44,7 @@ struct PassArgs {
   double mu, h;
   int accumulate;    // out += scale * result (else out = scale * result)
   double scale;
+  const int* skip;   // nullable: the pass does nothing when *skip != 0
 };
 
 template <typename T>
@@ -228,6 +229,7 @@ k_axis_pass(const Tin* __restrict__ in, Tout* __restrict__ out, PassArgs a,
             const C2<T>* __restrict__ tw, const C2<T>* __restrict__ qN,
             const double* __restrict__ s2) {
   extern __shared__ unsigned char smem_raw[];
+  if (a.skip && *a.skip) return;
   const int N = a.N;
   T* R = reinterpret_cast<T*>(smem_raw);
   C2<T>* CA = reinterpret_cast<C2<T>*>(smem_raw + sizeof(T) * LPC * N);

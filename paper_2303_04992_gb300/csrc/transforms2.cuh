@@ -1,0 +1,293 @@
+// Transform pass with compile-time N: the same real transforms as
+// transforms.cuh (DCT-II/III, DST-II/III via Makhoul's reordering, DST-I via
+// the odd extension, two real lines per complex FFT), but each complex FFT of
+// length L is a four-step FFT with a radix-16 DFT in registers, a twiddle, one
+// shared-memory exchange and a radix-(L/16) DFT in registers:
+//   z[m + M r] --DFT16 over r--> Y[m][s] * w_L^{m s} --DFT_M over m--> Z[s + 16 k],
+//   M = L / 16 threads per line pair.
+// Staging rows are padded (stride N + 1) so that column accesses of the
+// strided axes are free of bank conflicts.  One CTA holds LPC2 = 32 lines
+// (128 B coalesced rows for FP32 on the y and z axes).
+#pragma once
+
+#include "transforms.cuh"
+
+namespace kfbim {
+
+constexpr int LPC2 = 32;
+constexpr int PASS2_THREADS = 128;
+
+template <int R>
+__host__ __device__ constexpr int bitrev(int i) {
+  int r = 0;
+  for (int b = 1; b < R; b <<= 1) {
+    r = (r << 1) | (i & 1);
+    i >>= 1;
+  }
+  return r;
+}
+
+// cos and sin of 2 pi j / 16 for j in 0..15 (exact octant symmetry)
+__host__ __device__ constexpr double cos16(int j) {
+  constexpr double c1 = 0.92387953251128675613, c2 = 0.70710678118654752440, c3 = 0.38268343236508977173;
+  j &= 15;
+  return j == 0 ? 1.0 : j == 1 ? c1 : j == 2 ? c2 : j == 3 ? c3 : j == 4 ? 0.0 : j == 5 ? -c3
+       : j == 6 ? -c2 : j == 7 ? -c1 : j == 8 ? -1.0 : j == 9 ? -c1 : j == 10 ? -c2 : j == 11 ? -c3
+       : j == 12 ? 0.0 : j == 13 ? c3 : j == 14 ? c2 : c1;
+}
+__host__ __device__ constexpr double sin16(int j) { return cos16(j - 4); }
+
+// exp(-+ 2 pi i j / 16), sign + for the inverse transform (j a compile-time constant)
+template <typename T, bool INV>
+__device__ __forceinline__ C2<T> w16(int j) {
+  return {T(cos16(j)), INV ? T(sin16(j)) : T(-sin16(j))};
+}
+
+// In-register DFT of R <= 16 points, natural order in and out (radix-2 DIT).
+template <int R, bool INV, typename T>
+__device__ __forceinline__ void dft_reg(C2<T>* v) {
+  if constexpr (R > 1) {
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const int j = bitrev<R>(i);
+      if (j > i) {
+        const C2<T> t = v[i];
+        v[i] = v[j];
+        v[j] = t;
+      }
+    }
+#pragma unroll
+    for (int len = 2; len <= R; len <<= 1) {
+#pragma unroll
+      for (int i = 0; i < R; i += len) {
+#pragma unroll
+        for (int k = 0; k < len / 2; ++k) {
+          const C2<T> a = v[i + k];
+          C2<T> b = v[i + k + len / 2];
+          if (k != 0) b = cmul(b, w16<T, INV>(k * (16 / len)));
+          v[i + k] = {a.x + b.x, a.y + b.y};
+          v[i + k + len / 2] = {a.x - b.x, a.y - b.y};
+        }
+      }
+    }
+  }
+}
+
+template <int L>
+struct Fft2Shape {
+  static constexpr int M = L / 16;                                   // threads per pair
+  static constexpr int PPR = (PASS2_THREADS / M < LPC2 / 2) ? PASS2_THREADS / M : LPC2 / 2;
+  static constexpr int X = PPR * 16 * (M + 1);                       // exchange entries
+  static constexpr int Z = PPR * L;                                  // output entries
+};
+
+template <typename T, int N>
+struct Pass2Smem {
+  static constexpr int RS = N + 1;                 // padded staging row
+  using A = Fft2Shape<N>;
+  using B = Fft2Shape<2 * N>;
+  static constexpr size_t staging = sizeof(T) * LPC2 * RS;
+  static constexpr size_t stage_al = (staging + 15) / 16 * 16;
+  static constexpr size_t xbuf = sizeof(C2<T>) * (A::X > B::X ? A::X : B::X);
+  static constexpr size_t zbuf = sizeof(C2<T>) * (A::Z > B::Z ? A::Z : B::Z);
+  static constexpr size_t bytes = stage_al + xbuf + zbuf;
+};
+
+// One real transform of the LPC2 staged lines, in place in Rb.
+// KIND: 0 DCT-II family, 1 DST-II family, 2 DST-I.  INV: inverse.
+template <typename T, int N, int KIND, bool INV>
+__device__ void xform2(T* Rb, C2<T>* Xb, C2<T>* Zb, const C2<T>* __restrict__ tw,
+                       const C2<T>* __restrict__ qN) {
+  constexpr int RS = N + 1;
+  constexpr int L = (KIND == 2) ? 2 * N : N;
+  constexpr int R = 16;
+  constexpr int M = L / R;
+  constexpr int XS = M + 1;                       // padded exchange row
+  constexpr int PAIRS = LPC2 / 2;
+  constexpr int PPR = (PASS2_THREADS / M < PAIRS) ? PASS2_THREADS / M : PAIRS;  // pairs per round
+  constexpr int ROUNDS = PAIRS / PPR;
+  // DST-I is its own inverse up to the factor 2/N: both directions use the forward FFT
+  constexpr bool FINV = (KIND == 2) ? false : INV;
+  const int tid = threadIdx.x;
+  const int pl = tid / M, m = tid - pl * M;       // pair within round, thread within pair
+#pragma unroll 1
+  for (int round = 0; round < ROUNDS; ++round) {
+    const int p = round * PPR + pl;
+    const bool active = pl < PPR;
+    C2<T>* Xp = Xb + pl * (R * XS);
+    C2<T>* Zp = Zb + pl * L;
+    if (active) {
+      const T* RA = Rb + (2 * p) * RS;
+      const T* RB = RA + RS;
+      C2<T> v[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int n = m + M * r;
+        C2<T> z;
+        if constexpr (KIND == 2) {
+          T a = 0, b = 0;
+          if (n > 0 && n < N) { a = RA[n]; b = RB[n]; }
+          else if (n > N) { a = -RA[L - n]; b = -RB[L - n]; }
+          z = {a, b};
+        } else if constexpr (!INV) {
+          const int src = (n < N / 2) ? 2 * n : 2 * (N - 1 - n) + 1;
+          T a = RA[src], b = RB[src];
+          if (KIND == 1 && n >= N / 2) { a = -a; b = -b; }
+          z = {a, b};
+        } else {
+          const int k = n;
+          T xa, xna, xb, xnb;
+          if constexpr (KIND == 1) {
+            xa = RA[N - 1 - k]; xb = RB[N - 1 - k];
+            xna = k > 0 ? RA[k - 1] : T(0); xnb = k > 0 ? RB[k - 1] : T(0);
+          } else {
+            xa = RA[k]; xb = RB[k];
+            xna = k > 0 ? RA[N - k] : T(0); xnb = k > 0 ? RB[N - k] : T(0);
+          }
+          const C2<T> q = qN[k];                  // V = conj(q) (x_k - i x_{N-k})
+          const C2<T> VA = {q.x * xa - q.y * xna, -q.x * xna - q.y * xa};
+          const C2<T> VB = {q.x * xb - q.y * xnb, -q.x * xnb - q.y * xb};
+          z = {VA.x - VB.y, VA.y + VB.x};
+        }
+        v[r] = z;
+      }
+      dft_reg<R, FINV, T>(v);
+#pragma unroll
+      for (int s = 0; s < R; ++s) {
+        if (s != 0 && m != 0) {
+          // w_L^{m s} = exp(-2 pi i m s / L) = tw[(m s) * (2N / L)], table over the full circle
+          C2<T> w = tw[(m * s) * (2 * N / L)];
+          if (FINV) w.y = -w.y;
+          v[s] = cmul(v[s], w);
+        }
+        Xp[s * XS + m] = v[s];
+      }
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll
+      for (int s0 = 0; s0 < R; s0 += M) {
+        const int s = s0 + m;
+        C2<T> w[M];
+#pragma unroll
+        for (int k = 0; k < M; ++k) w[k] = Xp[s * XS + k];
+        dft_reg<M, FINV, T>(w);
+#pragma unroll
+        for (int k = 0; k < M; ++k) Zp[s + R * k] = w[k];
+      }
+    }
+    __syncthreads();
+    // post-processing: the PPR pairs of this round -> staged real lines
+    for (int e = tid; e < PPR * 2 * N; e += PASS2_THREADS) {
+      const int lr = e / N, o = e - lr * N;       // line within round, output index
+      const int pr = lr >> 1;
+      const C2<T>* Z = Zb + pr * L;
+      const bool lineB = lr & 1;
+      T val;
+      if constexpr (KIND == 2) {
+        const T sc = INV ? T(1) / T(N) : T(0.5);
+        val = (o == 0) ? T(0) : (lineB ? Z[o].x * sc : -Z[o].y * sc);
+      } else if constexpr (!INV) {
+        const int k = (KIND == 1) ? (N - 1 - o) : o;
+        const C2<T> zk = Z[k], zc = Z[(N - k) & (N - 1)];
+        C2<T> V;
+        if (!lineB) V = {T(0.5) * (zk.x + zc.x), T(0.5) * (zk.y - zc.y)};
+        else V = {T(0.5) * (zk.y + zc.y), T(-0.5) * (zk.x - zc.x)};
+        const C2<T> q = qN[k];
+        val = q.x * V.x - q.y * V.y;
+      } else {
+        const int n = (o & 1) ? (N - 1 - (o >> 1)) : (o >> 1);
+        const C2<T> z = Z[n];
+        val = (lineB ? z.y : z.x) * (T(1) / T(N));
+        if (KIND == 1 && (o & 1)) val = -val;
+      }
+      Rb[(round * 2 * PPR + lr) * RS + o] = val;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void xform2_dispatch(int type, T* Rb, C2<T>* Xb, C2<T>* Zb,
+                                                const C2<T>* tw, const C2<T>* qN) {
+  switch (type) {
+    case X_DCT2F: xform2<T, N, 0, false>(Rb, Xb, Zb, tw, qN); break;
+    case X_DCT2I: xform2<T, N, 0, true>(Rb, Xb, Zb, tw, qN); break;
+    case X_DST2F: xform2<T, N, 1, false>(Rb, Xb, Zb, tw, qN); break;
+    case X_DST2I: xform2<T, N, 1, true>(Rb, Xb, Zb, tw, qN); break;
+    case X_DST1F: xform2<T, N, 2, false>(Rb, Xb, Zb, tw, qN); break;
+    case X_DST1I: xform2<T, N, 2, true>(Rb, Xb, Zb, tw, qN); break;
+    default: break;
+  }
+}
+
+template <typename T, int N>
+__device__ __forceinline__ T spectral_weight2(const PassArgs& a, const T* __restrict__ s2, T inv_mu,
+                                              int i, int j, int k) {
+  const T sum = s2[a.kind[0] * N + i] + s2[a.kind[1] * N + j] + s2[a.kind[2] * N + k];
+  const int ac = a.wc == 0 ? i : (a.wc == 1 ? j : k);
+  const T isum = T(1) / sum;
+  if (a.wmode == W_SCHUR) return s2[ac] * isum * inv_mu;
+  if (ac == 0) return T(0);
+  const T h = T(a.h);
+  if (a.wmode == W_POISSON) return h * h * isum * inv_mu;
+  return T(-2) * h * sqrt(T(0.25) * s2[ac]) * isum * inv_mu;   // W_RHS
+}
+
+template <typename Tin, typename T, typename Tout, int N>
+__global__ void __launch_bounds__(PASS2_THREADS)
+k_axis_pass2(const Tin* __restrict__ in, Tout* __restrict__ out, PassArgs a,
+             const C2<T>* __restrict__ tw, const C2<T>* __restrict__ qN, const T* __restrict__ s2) {
+  using S = Pass2Smem<T, N>;
+  extern __shared__ __align__(16) unsigned char smem2[];
+  if (a.skip && *a.skip) return;
+  T* Rb = reinterpret_cast<T*>(smem2);
+  C2<T>* Xb = reinterpret_cast<C2<T>*>(smem2 + S::stage_al);
+  C2<T>* Zb = reinterpret_cast<C2<T>*>(smem2 + S::stage_al + S::xbuf);
+  constexpr int RS = S::RS;
+  const int line0 = blockIdx.x * LPC2;
+  const int axis = a.axis;
+  const int64_t NN = (int64_t)N * N;
+  // lines: x: line = k N + j (contiguous); y: (k, i), base k N^2 + i; z: (j, i), base j N + i
+  const int64_t stride = axis == 0 ? 1 : (axis == 1 ? N : NN);
+  const int64_t base0 = axis == 0 ? (int64_t)line0 * N
+                                  : (axis == 1 ? (int64_t)(line0 / N) * NN + (line0 % N) : (int64_t)line0);
+  // for y and z the LPC2 lines of a CTA are consecutive in x (LPC2 divides N)
+#pragma unroll 4
+  for (int e = threadIdx.x; e < LPC2 * N; e += PASS2_THREADS) {
+    int l, n;
+    int64_t g;
+    if (axis == 0) { l = e / N; n = e - l * N; g = base0 + (int64_t)l * N + n; }
+    else { n = e / LPC2; l = e - n * LPC2; g = base0 + l + n * stride; }
+    Rb[l * RS + n] = T(in[g]);
+  }
+  __syncthreads();
+  xform2_dispatch<T, N>(a.type0, Rb, Xb, Zb, tw, qN);
+  if (a.wmode != W_NONE) {
+    const T inv_mu = T(1.0 / a.mu);
+    for (int e = threadIdx.x; e < LPC2 * N; e += PASS2_THREADS) {
+      const int l = e / N, n = e - l * N;
+      const int line = line0 + l;
+      int i, j, k;
+      if (axis == 0) { i = n; j = line % N; k = line / N; }
+      else if (axis == 1) { i = line % N; j = n; k = line / N; }
+      else { i = line % N; j = line / N; k = n; }
+      Rb[l * RS + n] *= spectral_weight2<T, N>(a, s2, inv_mu, i, j, k);
+    }
+    __syncthreads();
+  }
+  xform2_dispatch<T, N>(a.type1, Rb, Xb, Zb, tw, qN);
+  const T sc = T(a.scale);
+#pragma unroll 4
+  for (int e = threadIdx.x; e < LPC2 * N; e += PASS2_THREADS) {
+    int l, n;
+    int64_t g;
+    if (axis == 0) { l = e / N; n = e - l * N; g = base0 + (int64_t)l * N + n; }
+    else { n = e / LPC2; l = e - n * LPC2; g = base0 + l + n * stride; }
+    const T v = sc * Rb[l * RS + n];
+    if (a.accumulate) out[g] = Tout(T(out[g]) + v);
+    else out[g] = Tout(v);
+  }
+}
+
+}  // namespace kfbim

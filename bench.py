@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--refine-tol", type=float, default=None, help="MIXED refinement tolerance")
+    ap.add_argument("--inner-tol", type=float, default=None, help="MIXED inner FP32 CG tolerance")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--interface-solves", type=int, default=18, help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -200,7 +202,12 @@ def main_kfbim(args):
         dist.barrier()
     geom, grid = ki.WORKLOADS[args.workload]
     dev = torch.device("cuda", local)
-    solver = Solver(geom, grid, precision=MIXED)
+    mixed_opts = {}
+    if args.refine_tol is not None:
+        mixed_opts["refine_tol"] = args.refine_tol
+    if args.inner_tol is not None:
+        mixed_opts["inner_tol"] = args.inner_tol
+    solver = Solver(geom, grid, precision=MIXED, **mixed_opts)
     g_h, fpts_h, fgrid_h = inputs(solver, geom, grid)
     g = torch.from_numpy(g_h).to(dev)
     fpts = torch.from_numpy(fpts_h).to(dev)
@@ -324,6 +331,7 @@ def main_kfbim(args):
                 "data": "synthetic",
                 "config": {"workload": args.workload, "description": WORKLOAD_DESC,
                            "precision": "mixed", "l2_flush": "512 MiB write before each step",
+                           "refine_tol": solver.options.refine_tol, "inner_tol": solver.options.inner_tol,
                            "n_points": solver.n_points, "n_unknowns": solver.n_primary,
                            "gmres_iters": st["gmres_iters"], "interface_solves": st["interface_solves"],
                            "cg_iters": st["cg_iters"], "refine_sweeps": st["refine_sweeps"],

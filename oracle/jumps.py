@@ -34,6 +34,7 @@ from scipy.spatial import cKDTree
 from . import geometry, grid as gridmod
 
 FIT_R2 = 36          # squared radius in (h/2)^2 units: 3h
+FIT_SIGMA2 = 1.0     # Gaussian weight exp(-|z - y|^2 / (FIT_SIGMA2 h^2))
 MIN_NEIGHBOURS = 12
 
 
@@ -76,7 +77,7 @@ def surface_derivatives(cp, frames, nbrs, phi, h):
         d = (cp.xyz[idx] - cp.xyz[:, None, :]) / h                 # (n, m, 3)
         s = np.einsum("nmk,nk->nm", d, T[:, 0, :])
         t = np.einsum("nmk,nk->nm", d, T[:, 1, :])
-        w = w * np.exp(-np.sum(d * d, axis=-1))
+        w = w * np.exp(-np.sum(d * d, axis=-1) / FIT_SIGMA2)
         V = np.stack([np.ones_like(s), s, t, s * s, s * t, t * t], axis=-1)   # (n, m, 6)
         A = np.einsum("nmi,nm,nmj->nij", V, w, V)
         b = np.einsum("nmi,nm,nm->ni", V, w, phi[idx])

@@ -12,6 +12,14 @@ namespace kfbim {
 constexpr int RED_THREADS = 256;
 constexpr int RED_BLOCKS = 304;   // 2 x 152 SMs
 
+// N is a power of two: flat index x = (k N + j) N + i, lg = log2 N.
+__device__ __forceinline__ void unflat(int64_t x, int lg, int& i, int& j, int& k) {
+  const int m = (1 << lg) - 1;
+  i = (int)(x & m);
+  j = (int)((x >> lg) & m);
+  k = (int)(x >> (2 * lg));
+}
+
 // ------------------------------------------------------------------ jumps
 // One warp per control point: fitted value and five surface derivatives of
 // each density component (weighted sums over primary neighbours), then the
@@ -77,16 +85,17 @@ __global__ void k_jumps(const double* __restrict__ phi, const double* __restrict
 // f~ on the face grids (f in Omega, 0 outside and on wall faces) and g = 0.
 __global__ void k_rhs_fill(const double* __restrict__ fgrid, const uint8_t* __restrict__ side1,
                            const uint8_t* __restrict__ side2, const uint8_t* __restrict__ side3,
-                           int N, double* __restrict__ rhs) {
-  const int64_t N3 = (int64_t)N * N * N;
+                           int lg, double* __restrict__ rhs) {
+  const int64_t N3 = (int64_t)1 << (3 * lg);
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < 4 * N3;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int f = (int)(e / N3);
-    const int64_t x = e - f * N3;
+    const int f = (int)(e >> (3 * lg));
+    const int64_t x = e - ((int64_t)f << (3 * lg));
     double v = 0.0;
     if (f < 3 && fgrid) {
       const uint8_t* side = f == 0 ? side1 : (f == 1 ? side2 : side3);
-      const int i = (int)(x % N), j = (int)((x / N) % N), k = (int)(x / ((int64_t)N * N));
+      int i, j, k;
+      unflat(x, lg, i, j, k);
       const int nrm = f == 0 ? i : (f == 1 ? j : k);
       if (side[x] && nrm > 0) v = fgrid[e];
     }
@@ -127,27 +136,24 @@ __global__ void k_trace(const double* __restrict__ u, const double* __restrict__
 }
 
 // --------------------------------------------------------- MAC stencils
-__device__ __forceinline__ void unflat(int64_t x, int N, int& i, int& j, int& k) {
-  i = (int)(x % N);
-  j = (int)((x / N) % N);
-  k = (int)(x / ((int64_t)N * N));
-}
 
 // r^(c) = f^(c) - G_c p   (face grid c; wall faces 0)
 template <typename Tp, typename Tout>
-__global__ void k_f_minus_gp(const double* __restrict__ f, const Tp* __restrict__ p, int N, double h,
+__global__ void k_f_minus_gp(const double* __restrict__ f, const Tp* __restrict__ p, int lg, double h,
                              Tout* __restrict__ r) {
-  const int64_t N3 = (int64_t)N * N * N;
+  const int64_t N3 = (int64_t)1 << (3 * lg);
+  const double ih = 1.0 / h;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < 3 * N3;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(e / N3);
-    const int64_t x = e - c * N3;
+    const int c = (int)(e >> (3 * lg));
+    const int64_t x = e - ((int64_t)c << (3 * lg));
     int id[3];
-    unflat(x, N, id[0], id[1], id[2]);
+    unflat(x, lg, id[0], id[1], id[2]);
+    const int nrm = c == 0 ? id[0] : (c == 1 ? id[1] : id[2]);
     double v = 0.0;
-    if (id[c] > 0) {
-      const int64_t st = c == 0 ? 1 : (c == 1 ? N : (int64_t)N * N);
-      v = f[e] - (double(p[x]) - double(p[x - st])) / h;
+    if (nrm > 0) {
+      const int64_t st = (int64_t)1 << (c * lg);
+      v = f[e] - (double(p[x]) - double(p[x - st])) * ih;
     }
     r[e] = Tout(v);
   }
@@ -157,46 +163,52 @@ __global__ void k_f_minus_gp(const double* __restrict__ f, const Tp* __restrict_
 // projection): rf = f - (-mu Lap u + G p), rg = g - mean(g) - D u.
 __global__ void k_mac_residual(const double* __restrict__ f, const double* __restrict__ g,
                                const double* __restrict__ gmean, const double* __restrict__ u,
-                               const double* __restrict__ p, int N, double h, double mu,
+                               const double* __restrict__ p, int lg, double h, double mu,
                                double* __restrict__ rf, double* __restrict__ rg) {
-  const int64_t N3 = (int64_t)N * N * N;
+  const int N = 1 << lg;
+  const int64_t N3 = (int64_t)1 << (3 * lg);
   const double ih2 = 1.0 / (h * h), ih = 1.0 / h;
+  const double gm = gmean[0];
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < 4 * N3;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(e / N3);
-    const int64_t x = e - c * N3;
+    const int c = (int)(e >> (3 * lg));
+    const int64_t x = e - ((int64_t)c << (3 * lg));
     int id[3];
-    unflat(x, N, id[0], id[1], id[2]);
-    const int64_t st[3] = {1, N, (int64_t)N * N};
+    unflat(x, lg, id[0], id[1], id[2]);
     if (c < 3) {
-      if (id[c] == 0) { rf[e] = 0.0; continue; }
-      const double* uc = u + c * N3;
+      const int nrm = c == 0 ? id[0] : (c == 1 ? id[1] : id[2]);
+      if (nrm == 0) { rf[e] = 0.0; continue; }
+      const double* uc = u + ((int64_t)c << (3 * lg));
       const double u0 = uc[x];
       double lap = 0.0;
 #pragma unroll
       for (int b = 0; b < 3; ++b) {
+        const int64_t st = (int64_t)1 << (b * lg);
+        const int ib = b == 0 ? id[0] : (b == 1 ? id[1] : id[2]);
         double um, up;
         if (b == c) {
-          um = (id[b] - 1 >= 1) ? uc[x - st[b]] : 0.0;
-          up = (id[b] + 1 <= N - 1) ? uc[x + st[b]] : 0.0;
+          um = (ib - 1 >= 1) ? uc[x - st] : 0.0;
+          up = (ib + 1 <= N - 1) ? uc[x + st] : 0.0;
         } else {
-          um = (id[b] > 0) ? uc[x - st[b]] : -u0;
-          up = (id[b] < N - 1) ? uc[x + st[b]] : -u0;
+          um = (ib > 0) ? uc[x - st] : -u0;
+          up = (ib < N - 1) ? uc[x + st] : -u0;
         }
         lap += (up - 2.0 * u0 + um) * ih2;
       }
-      const double gp = (p[x] - p[x - st[c]]) * ih;
+      const double gp = (p[x] - p[x - ((int64_t)1 << (c * lg))]) * ih;
       rf[e] = f[e] - (-mu * lap + gp);
     } else {
       double d = 0.0;
 #pragma unroll
       for (int b = 0; b < 3; ++b) {
-        const double* ub = u + b * N3;
-        const double lo = (id[b] >= 1) ? ub[x] : 0.0;
-        const double hi = (id[b] + 1 <= N - 1) ? ub[x + st[b]] : 0.0;
+        const int64_t st = (int64_t)1 << (b * lg);
+        const int ib = b == 0 ? id[0] : (b == 1 ? id[1] : id[2]);
+        const double* ub = u + ((int64_t)b << (3 * lg));
+        const double lo = (ib >= 1) ? ub[x] : 0.0;
+        const double hi = (ib + 1 <= N - 1) ? ub[x + st] : 0.0;
         d += (hi - lo) * ih;
       }
-      rg[x] = g[x] - gmean[0] - d;
+      rg[x] = g[x] - gm - d;
     }
   }
 }

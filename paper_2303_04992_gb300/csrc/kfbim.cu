@@ -35,7 +35,7 @@ struct kfbim_ctx {
   kfbim_options opt{};
   std::string err;
   HostTables host;
-  int N = 0;
+  int N = 0, lg = 0;   // lg = log2 N
   int64_t N3 = 0, n_all = 0, n_prim = 0, n_corr_rows = 0;
   double h = 0, mu = 1;
   std::vector<void*> allocs;
@@ -374,7 +374,7 @@ int grid_solve_fp64(kfbim_ctx* c, cudaStream_t s) {
   c->cg_iters += it;
   if (st != KFBIM_OK && st != KFBIM_E_NOCONV) return st;
   // u^(c) = (1/mu)(-Delta)^{-1} (f^(c) - G_c p)
-  k_f_minus_gp<double, double><<<grid_for(3 * N3), 256, 0, s>>>(f, c->p, c->N, c->h, c->u); ++g_launches;
+  k_f_minus_gp<double, double><<<grid_for(3 * N3), 256, 0, s>>>(f, c->p, c->lg, c->h, c->u); ++g_launches;
   check_launch();
   for (int cax = 0; cax < 3; ++cax)
     face_poisson<double, double, double>(c, cax, c->u + cax * N3, c->u + cax * N3, c->t1, c->t2, s);
@@ -394,7 +394,7 @@ int grid_solve_mixed(kfbim_ctx* c, cudaStream_t s) {
   CK(cudaMemsetAsync(c->p, 0, N3 * sizeof(double), s));
   dot(c, g, (const double*)nullptr, N3, gmean, 1.0 / (double)N3, s);
   // reference norm ||[f; g - mean g]||
-  k_mac_residual<<<grid_for(4 * N3), 256, 0, s>>>(f, g, gmean, c->u, c->p, c->N, c->h, c->mu, resf, resg); ++g_launches;
+  k_mac_residual<<<grid_for(4 * N3), 256, 0, s>>>(f, g, gmean, c->u, c->p, c->lg, c->h, c->mu, resf, resg); ++g_launches;
   check_launch();
   dot(c, resf, resf, 4 * N3, sc, 1.0, s);
   const double ref2 = read_scalar(c, sc, s);
@@ -402,7 +402,7 @@ int grid_solve_mixed(kfbim_ctx* c, cudaStream_t s) {
   int status = KFBIM_OK;
   for (int sweep = 0;; ++sweep) {
     if (sweep > 0) {
-      k_mac_residual<<<grid_for(4 * N3), 256, 0, s>>>(f, g, gmean, c->u, c->p, c->N, c->h, c->mu, resf, resg); ++g_launches;
+      k_mac_residual<<<grid_for(4 * N3), 256, 0, s>>>(f, g, gmean, c->u, c->p, c->lg, c->h, c->mu, resf, resg); ++g_launches;
       check_launch();
       dot(c, resf, resf, 4 * N3, sc, 1.0, s);
       const double r2 = read_scalar(c, sc, s);
@@ -424,7 +424,7 @@ int grid_solve_mixed(kfbim_ctx* c, cudaStream_t s) {
     if (st == KFBIM_E_NONFINITE) return st;
     // p += dp; u += (1/mu)(-Delta)^{-1}(rf - G dp)
     k_add_to<float><<<grid_for(N3), 256, 0, s>>>(c->fx, c->p, N3); ++g_launches;
-    k_f_minus_gp<float, float><<<grid_for(3 * N3), 256, 0, s>>>(resf, c->fx, c->N, c->h, c->fu); ++g_launches;
+    k_f_minus_gp<float, float><<<grid_for(3 * N3), 256, 0, s>>>(resf, c->fx, c->lg, c->h, c->fu); ++g_launches;
     check_launch();
     for (int cax = 0; cax < 3; ++cax) {
       face_poisson<float, float, float>(c, cax, c->fu + cax * N3, c->fu + cax * N3, c->f1, c->f2, s);
@@ -449,7 +449,7 @@ int interface_solve(kfbim_ctx* c, const double* phi, const double* fpts, const d
       phi, fpts, n, c->d_comp, c->d_pid, c->d_fit_ptr, c->d_fit_col, c->d_fit_w, c->d_jmap, c->J); ++g_launches;
   check_launch();
   k_rhs_fill<<<grid_for(4 * c->N3), 256, 0, s>>>(fgrid, c->d_side[1], c->d_side[2], c->d_side[3],
-                                                  c->N, c->rhs); ++g_launches;
+                                                  c->lg, c->rhs); ++g_launches;
   check_launch();
   if (c->n_corr_rows > 0) {
     k_corrections<<<grid_for(c->n_corr_rows), 256, 0, s>>>(c->d_corr_row, c->d_corr_ptr, c->d_corr_src,
@@ -784,6 +784,7 @@ static int setup_common(const kfbim_geometry* geom, const kfbim_grid* grid, cons
   if (!c) return KFBIM_E_OOM;
   c->opt = *opt;
   c->N = N;
+  while ((1 << c->lg) < N) ++c->lg;
   c->N3 = (int64_t)N * N * N;
   c->h = (grid->hi - grid->lo) / N;
   c->mu = opt->mu;

@@ -88,9 +88,11 @@ struct Pass2Smem {
   using B = Fft2Shape<2 * N>;
   static constexpr size_t staging = sizeof(T) * LPC2 * RS;
   static constexpr size_t stage_al = (staging + 15) / 16 * 16;
-  static constexpr size_t xbuf = sizeof(C2<T>) * (A::X > B::X ? A::X : B::X);
-  static constexpr size_t zbuf = sizeof(C2<T>) * (A::Z > B::Z ? A::Z : B::Z);
-  static constexpr size_t bytes = stage_al + xbuf + zbuf;
+  static constexpr int XA = A::X > A::Z ? A::X : A::Z;
+  static constexpr int XB = B::X > B::Z ? B::X : B::Z;
+  // the exchange buffer also receives the FFT output (after a barrier)
+  static constexpr size_t xbuf = sizeof(C2<T>) * (XA > XB ? XA : XB);
+  static constexpr size_t bytes = stage_al + xbuf;
 };
 
 // One real transform of the LPC2 staged lines, in place in Rb.
@@ -115,7 +117,7 @@ __device__ void xform2(T* Rb, C2<T>* Xb, C2<T>* Zb, const C2<T>* __restrict__ tw
     const int p = round * PPR + pl;
     const bool active = pl < PPR;
     C2<T>* Xp = Xb + pl * (R * XS);
-    C2<T>* Zp = Zb + pl * L;
+    C2<T>* Zp = Zb + pl * L;              // Zb aliases Xb
     if (active) {
       const T* RA = Rb + (2 * p) * RS;
       const T* RB = RA + RS;
@@ -164,16 +166,23 @@ __device__ void xform2(T* Rb, C2<T>* Xb, C2<T>* Zb, const C2<T>* __restrict__ tw
       }
     }
     __syncthreads();
+    // step C: R/M DFTs of length M per thread, all read before the output
+    // overwrites the exchange buffer
+    constexpr int NS = R / M;
+    C2<T> w[NS][M];
     if (active) {
 #pragma unroll
-      for (int s0 = 0; s0 < R; s0 += M) {
-        const int s = s0 + m;
-        C2<T> w[M];
+      for (int q = 0; q < NS; ++q)
 #pragma unroll
-        for (int k = 0; k < M; ++k) w[k] = Xp[s * XS + k];
-        dft_reg<M, FINV, T>(w);
+        for (int k = 0; k < M; ++k) w[q][k] = Xp[(q * M + m) * XS + k];
+    }
+    __syncthreads();
+    if (active) {
 #pragma unroll
-        for (int k = 0; k < M; ++k) Zp[s + R * k] = w[k];
+      for (int q = 0; q < NS; ++q) {
+        dft_reg<M, FINV, T>(w[q]);
+#pragma unroll
+        for (int k = 0; k < M; ++k) Zp[q * M + m + R * k] = w[q][k];
       }
     }
     __syncthreads();
@@ -243,7 +252,7 @@ k_axis_pass2(const Tin* __restrict__ in, Tout* __restrict__ out, PassArgs a,
   if (a.skip && *a.skip) return;
   T* Rb = reinterpret_cast<T*>(smem2);
   C2<T>* Xb = reinterpret_cast<C2<T>*>(smem2 + S::stage_al);
-  C2<T>* Zb = reinterpret_cast<C2<T>*>(smem2 + S::stage_al + S::xbuf);
+  C2<T>* Zb = Xb;
   constexpr int RS = S::RS;
   const int line0 = blockIdx.x * LPC2;
   const int axis = a.axis;
@@ -252,14 +261,27 @@ k_axis_pass2(const Tin* __restrict__ in, Tout* __restrict__ out, PassArgs a,
   const int64_t stride = axis == 0 ? 1 : (axis == 1 ? N : NN);
   const int64_t base0 = axis == 0 ? (int64_t)line0 * N
                                   : (axis == 1 ? (int64_t)(line0 / N) * NN + (line0 % N) : (int64_t)line0);
-  // for y and z the LPC2 lines of a CTA are consecutive in x (LPC2 divides N)
-#pragma unroll 4
-  for (int e = threadIdx.x; e < LPC2 * N; e += PASS2_THREADS) {
-    int l, n;
-    int64_t g;
-    if (axis == 0) { l = e / N; n = e - l * N; g = base0 + (int64_t)l * N + n; }
-    else { n = e / LPC2; l = e - n * LPC2; g = base0 + l + n * stride; }
-    Rb[l * RS + n] = T(in[g]);
+  // for y and z the LPC2 lines of a CTA are consecutive in x (LPC2 divides N);
+  // all loads of a thread are issued before any is used
+  constexpr int PER = LPC2 * N / PASS2_THREADS;
+  {
+    Tin vals[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = threadIdx.x + q * PASS2_THREADS;
+      int64_t g;
+      if (axis == 0) g = base0 + e;
+      else { const int n = e / LPC2, l = e - n * LPC2; g = base0 + l + n * stride; }
+      vals[q] = in[g];
+    }
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = threadIdx.x + q * PASS2_THREADS;
+      int l, n;
+      if (axis == 0) { l = e / N; n = e - l * N; }
+      else { n = e / LPC2; l = e - n * LPC2; }
+      Rb[l * RS + n] = T(vals[q]);
+    }
   }
   __syncthreads();
   xform2_dispatch<T, N>(a.type0, Rb, Xb, Zb, tw, qN);
@@ -278,15 +300,35 @@ k_axis_pass2(const Tin* __restrict__ in, Tout* __restrict__ out, PassArgs a,
   }
   xform2_dispatch<T, N>(a.type1, Rb, Xb, Zb, tw, qN);
   const T sc = T(a.scale);
-#pragma unroll 4
-  for (int e = threadIdx.x; e < LPC2 * N; e += PASS2_THREADS) {
-    int l, n;
-    int64_t g;
-    if (axis == 0) { l = e / N; n = e - l * N; g = base0 + (int64_t)l * N + n; }
-    else { n = e / LPC2; l = e - n * LPC2; g = base0 + l + n * stride; }
-    const T v = sc * Rb[l * RS + n];
-    if (a.accumulate) out[g] = Tout(T(out[g]) + v);
-    else out[g] = Tout(v);
+  if (a.accumulate) {
+    Tout prev[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = threadIdx.x + q * PASS2_THREADS;
+      int64_t g;
+      if (axis == 0) g = base0 + e;
+      else { const int n = e / LPC2, l = e - n * LPC2; g = base0 + l + n * stride; }
+      prev[q] = out[g];
+    }
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = threadIdx.x + q * PASS2_THREADS;
+      int l, n;
+      int64_t g;
+      if (axis == 0) { l = e / N; n = e - l * N; g = base0 + e; }
+      else { n = e / LPC2; l = e - n * LPC2; g = base0 + l + n * stride; }
+      out[g] = Tout(T(prev[q]) + sc * Rb[l * RS + n]);
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = threadIdx.x + q * PASS2_THREADS;
+      int l, n;
+      int64_t g;
+      if (axis == 0) { l = e / N; n = e - l * N; g = base0 + e; }
+      else { n = e / LPC2; l = e - n * LPC2; g = base0 + l + n * stride; }
+      out[g] = Tout(sc * Rb[l * RS + n]);
+    }
   }
 }
 

@@ -290,17 +290,22 @@ __device__ __forceinline__ bool last_block_sum(double v, double* __restrict__ pa
   return true;
 }
 
+// q_S = q + q2 + q3 (the three component terms, summed in place into q);
 // dq = d . q_S; alpha = rr / (dq + sumd^2 rank1)
 template <typename T>
-__global__ void k_cg_alpha(const T* __restrict__ d, const T* __restrict__ q, int64_t n,
-                           CGScalars* s, double* __restrict__ partial) {
+__global__ void k_cg_alpha(const T* __restrict__ d, T* __restrict__ q, const T* __restrict__ q2,
+                           const T* __restrict__ q3, int64_t n, CGScalars* s,
+                           double* __restrict__ partial) {
   __shared__ double sh[32];
   __shared__ double total;
   if (s->done) return;
   double acc = 0.0;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)gridDim.x * blockDim.x)
-    acc += double(d[e]) * double(q[e]);
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const T qs = q[e] + q2[e] + q3[e];
+    q[e] = qs;
+    acc += double(d[e]) * double(qs);
+  }
   if (last_block_sum(acc, partial, &s->ticket[0], sh, &total) && threadIdx.x == 0) {
     const double den = total + s->sumd * s->sumd * s->rank1;
     s->dq = den;
@@ -398,6 +403,24 @@ __global__ void k_cg_init(const T* __restrict__ b, int64_t n, CGScalars* s, doub
 }
 
 // --------------------------------------------------------- vector helpers
+// out = b1 + b2 + b3
+template <typename T>
+__global__ void k_sum3(const T* __restrict__ b1, const T* __restrict__ b2, const T* __restrict__ b3,
+                       T* __restrict__ out, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = b1[e] + b2[e] + b3[e];
+}
+
+// out = g + b1 + b2 + b3
+template <typename Ta, typename Tb>
+__global__ void k_sum4(const Ta* __restrict__ g, const Tb* __restrict__ b1, const Tb* __restrict__ b2,
+                       const Tb* __restrict__ b3, Tb* __restrict__ out, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = Tb(double(g[e]) + double(b1[e]) + double(b2[e]) + double(b3[e]));
+}
+
 template <typename Ta, typename Tb>
 __global__ void k_convert(const Ta* __restrict__ a, Tb* __restrict__ b, int64_t n) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;

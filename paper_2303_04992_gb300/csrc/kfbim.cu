@@ -62,6 +62,9 @@ struct kfbim_ctx {
   // FP32 workspace (mixed)
   float *f1 = nullptr, *f2 = nullptr, *fx = nullptr, *fr = nullptr, *fd = nullptr, *fq = nullptr,
         *fu = nullptr;
+  // second and third component outputs of the Schur apply, six stage temporaries
+  double *q2 = nullptr, *q3 = nullptr, *T6 = nullptr;
+  float *fq2 = nullptr, *fq3 = nullptr, *fT6 = nullptr;
   // GMRES
   int gm_max = 0;
   double *V = nullptr, *gw = nullptr, *gh = nullptr, *grhs = nullptr, *gy = nullptr;
@@ -148,7 +151,7 @@ struct Tw<float> {
 };
 
 template <typename Tin, typename T, typename Tout, int N>
-void launch_pass2(kfbim_ctx* c, const Tin* in, Tout* out, const PassArgs& a, cudaStream_t s) {
+void launch_pass2(kfbim_ctx* c, const PassJobs<Tin, Tout>& jobs, int njobs, cudaStream_t s) {
   const size_t smem = Pass2Smem<T, N>::bytes;
   auto kern = k_axis_pass2<Tin, T, Tout, N>;
   static size_t configured = 0;
@@ -156,32 +159,53 @@ void launch_pass2(kfbim_ctx* c, const Tin* in, Tout* out, const PassArgs& a, cud
     CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     configured = smem;
   }
-  kern<<<(unsigned)(N * N / LPC2), PASS2_THREADS, smem, s>>>(in, out, a, Tw<T>::twc(c), Tw<T>::q(c),
-                                                              Tw<T>::s2(c));
+  kern<<<dim3((unsigned)(N * N / LPC2), (unsigned)njobs), PASS2_THREADS, smem, s>>>(
+      jobs, Tw<T>::twc(c), Tw<T>::q(c), Tw<T>::s2(c));
 }
 
+// One transform pass of a stage: input, output, axis, first transform,
+// second transform, spectral weight, weight component, accumulate flag.
+struct Job {
+  const void* in;
+  void* out;
+  int axis, t0, t1, wmode, wc, acc;
+};
+
+void prof_collect(kfbim_ctx* c);
+
+// Launch up to three independent passes (one launch on the compile-time-N
+// kernel, one launch per job otherwise).
 template <typename Tin, typename T, typename Tout>
-void pass(kfbim_ctx* c, const Tin* in, Tout* out, int axis, int t0, int t1, int wmode, int wc,
-          int acc, double scale, cudaStream_t s, const int* skip = nullptr) {
-  PassArgs a{};  // value-initialised: every field, skip included, starts at zero
-  a.N = c->N;
-  a.axis = axis;
-  a.type0 = t0;
-  a.type1 = t1;
-  a.wmode = wmode;
-  a.wc = wc;
-  for (int b = 0; b < 3; ++b) a.kind[b] = (b == wc) ? 0 : 1;
-  a.mu = c->mu;
-  a.h = c->h;
-  a.accumulate = acc;
-  a.scale = scale;
-  a.skip = skip;
+void stage(kfbim_ctx* c, std::initializer_list<Job> list, cudaStream_t s, const int* skip = nullptr) {
+  PassJobs<Tin, Tout> jobs{};
+  int nj = 0;
+  double bytes = 0.0;
+  for (const Job& j : list) {
+    PassArgs a{};  // value-initialised: every field, skip included, starts at zero
+    a.N = c->N;
+    a.axis = j.axis;
+    a.type0 = j.t0;
+    a.type1 = j.t1;
+    a.wmode = j.wmode;
+    a.wc = j.wc;
+    for (int b = 0; b < 3; ++b) a.kind[b] = (b == j.wc) ? 0 : 1;
+    a.mu = c->mu;
+    a.h = c->h;
+    a.accumulate = j.acc;
+    a.scale = 1.0;
+    a.skip = skip;
+    jobs.j[nj] = {static_cast<const Tin*>(j.in), static_cast<Tout*>(j.out), a};
+    bytes += (double)c->N3 * (sizeof(Tin) + sizeof(Tout) * (j.acc ? 2 : 1));
+    ++nj;
+  }
   const bool prof = c->prof && c->prof_used + 2 <= (int)c->prof_ev.size();
   if (prof) CK(cudaEventRecord(c->prof_ev[c->prof_used], s));
-  if (c->N == 128) launch_pass2<Tin, T, Tout, 128>(c, in, out, a, s);
-  else if (c->N == 64) launch_pass2<Tin, T, Tout, 64>(c, in, out, a, s);
-  else if (c->N == 32) launch_pass2<Tin, T, Tout, 32>(c, in, out, a, s);
-  else {
+  if (c->N == 128 || c->N == 64 || c->N == 32) {
+    if (c->N == 128) launch_pass2<Tin, T, Tout, 128>(c, jobs, nj, s);
+    else if (c->N == 64) launch_pass2<Tin, T, Tout, 64>(c, jobs, nj, s);
+    else launch_pass2<Tin, T, Tout, 32>(c, jobs, nj, s);
+    ++g_launches;
+  } else {
     const size_t smem = pass_smem_bytes(c->N, sizeof(T));
     auto kern = k_axis_pass<Tin, T, Tout>;
     static size_t configured = 0;  // per template instance
@@ -190,9 +214,12 @@ void pass(kfbim_ctx* c, const Tin* in, Tout* out, int axis, int t0, int t1, int 
       configured = smem;
     }
     const int blocks = (int)((int64_t)c->N * c->N / LPC);
-    kern<<<blocks, PASS_THREADS, smem, s>>>(in, out, a, Tw<T>::tw(c), Tw<T>::q(c), c->d_s2);
+    for (int k = 0; k < nj; ++k) {
+      kern<<<blocks, PASS_THREADS, smem, s>>>(jobs.j[k].in, jobs.j[k].out, jobs.j[k].a, Tw<T>::tw(c),
+                                             Tw<T>::q(c), c->d_s2);
+      ++g_launches;
+    }
   }
-  ++g_launches;
   check_launch();
   if (prof) {
     CK(cudaEventRecord(c->prof_ev[c->prof_used + 1], s));
@@ -200,7 +227,7 @@ void pass(kfbim_ctx* c, const Tin* in, Tout* out, int axis, int t0, int t1, int 
     c->prof_tag[c->prof_used / 2] = slot;
     c->prof_used += 2;
     c->prof_count[slot] += 1;
-    c->prof_bytes[slot] += (double)c->N3 * (sizeof(Tin) + sizeof(Tout) * (acc ? 2 : 1));
+    c->prof_bytes[slot] += bytes;
   }
 }
 
@@ -219,46 +246,79 @@ inline void others(int cax, int& o1, int& o2) {
   o2 = (cax == 2) ? 1 : 2;
 }
 
-// u = (1/mu) (-Delta_c)^{-1} r on face grid c (cax = c - 1)
+// Stage tables.  Component c (axis cax = c - 1) is transformed along its two
+// other axes (o1 < o2) with DST-II, and along cax with DCT-II (cell basis) or
+// DST-I (face basis); the middle pass along cax is fused with the weight.
+
+// u = (1/mu) (-Delta_c)^{-1} r on face grid c (single component)
 template <typename Tin, typename T, typename Tout>
 void face_poisson(kfbim_ctx* c, int cax, const Tin* r, Tout* u, T* t1, T* t2, cudaStream_t s) {
   int o1, o2;
   others(cax, o1, o2);
-  pass<Tin, T, T>(c, r, t1, o2, X_DST2F, X_NONE, W_NONE, cax, 0, 1.0, s);
-  pass<T, T, T>(c, t1, t2, o1, X_DST2F, X_NONE, W_NONE, cax, 0, 1.0, s);
-  pass<T, T, T>(c, t2, t1, cax, X_DST1F, X_DST1I, W_POISSON, cax, 0, 1.0, s);
-  pass<T, T, T>(c, t1, t2, o1, X_DST2I, X_NONE, W_NONE, cax, 0, 1.0, s);
-  pass<T, T, Tout>(c, t2, u, o2, X_DST2I, X_NONE, W_NONE, cax, 0, 1.0, s);
+  stage<Tin, T, T>(c, {{r, t1, o2, X_DST2F, X_NONE, W_NONE, cax, 0}}, s);
+  stage<T, T, T>(c, {{t1, t2, o1, X_DST2F, X_NONE, W_NONE, cax, 0}}, s);
+  stage<T, T, T>(c, {{t2, t1, cax, X_DST1F, X_DST1I, W_POISSON, cax, 0}}, s);
+  stage<T, T, T>(c, {{t1, t2, o1, X_DST2I, X_NONE, W_NONE, cax, 0}}, s);
+  stage<T, T, Tout>(c, {{t2, u, o2, X_DST2I, X_NONE, W_NONE, cax, 0}}, s);
 }
 
-// b += (1/mu) G_c^T (-Delta_c)^{-1} f^(c)
-template <typename Tin, typename T>
-void schur_rhs_add(kfbim_ctx* c, int cax, const Tin* f, T* b, T* t1, T* t2, cudaStream_t s) {
-  int o1, o2;
-  others(cax, o1, o2);
-  pass<Tin, T, T>(c, f, t1, o2, X_DST2F, X_NONE, W_NONE, cax, 0, 1.0, s);
-  pass<T, T, T>(c, t1, t2, o1, X_DST2F, X_NONE, W_NONE, cax, 0, 1.0, s);
-  pass<T, T, T>(c, t2, t1, cax, X_DST1F, X_DCT2I, W_RHS, cax, 0, 1.0, s);
-  pass<T, T, T>(c, t1, t2, o1, X_DST2I, X_NONE, W_NONE, cax, 0, 1.0, s);
-  pass<T, T, T>(c, t2, b, o2, X_DST2I, X_NONE, W_NONE, cax, 1, 1.0, s);
-}
-
-// q = (1/mu) sum_c G_c^T (-Delta_c)^{-1} G_c d   (rank-one term handled in CG)
+// u^(c) = (1/mu) (-Delta_c)^{-1} r^(c) for c = 1..3 (r, u: 3 N^3, may alias);
+// T6 = six N^3 temporaries.
 template <typename T>
-void schur_apply(kfbim_ctx* c, const T* d, T* q, T* t1, T* t2, cudaStream_t s,
-                 const int* skip = nullptr) {
-  for (int cax = 0; cax < 3; ++cax) {
-    int o1, o2;
-    others(cax, o1, o2);
-    pass<T, T, T>(c, d, t1, o2, X_DST2F, X_NONE, W_NONE, cax, 0, 1.0, s, skip);
-    pass<T, T, T>(c, t1, t2, o1, X_DST2F, X_NONE, W_NONE, cax, 0, 1.0, s, skip);
-    pass<T, T, T>(c, t2, t1, cax, X_DCT2F, X_DCT2I, W_SCHUR, cax, 0, 1.0, s, skip);
-    pass<T, T, T>(c, t1, t2, o1, X_DST2I, X_NONE, W_NONE, cax, 0, 1.0, s, skip);
-    pass<T, T, T>(c, t2, q, o2, X_DST2I, X_NONE, W_NONE, cax, cax > 0 ? 1 : 0, 1.0, s, skip);
-  }
+void face_poisson3(kfbim_ctx* c, const T* r, T* u, T* T6, cudaStream_t s) {
+  const int64_t n = c->N3;
+  const T *r1 = r, *r2 = r + n, *r3 = r + 2 * n;
+  T *u1 = u, *u2 = u + n, *u3 = u + 2 * n;
+  T *A = T6, *B = T6 + n, *C = T6 + 2 * n, *D = T6 + 3 * n, *E = T6 + 4 * n, *F = T6 + 5 * n;
+  stage<T, T, T>(c, {{r1, A, 2, X_DST2F, X_NONE, W_NONE, 0, 0}, {r2, B, 2, X_DST2F, X_NONE, W_NONE, 1, 0},
+                     {r3, C, 1, X_DST2F, X_NONE, W_NONE, 2, 0}}, s);
+  stage<T, T, T>(c, {{A, D, 1, X_DST2F, X_NONE, W_NONE, 0, 0}, {B, E, 0, X_DST2F, X_NONE, W_NONE, 1, 0},
+                     {C, F, 0, X_DST2F, X_NONE, W_NONE, 2, 0}}, s);
+  stage<T, T, T>(c, {{D, A, 0, X_DST1F, X_DST1I, W_POISSON, 0, 0}, {E, B, 1, X_DST1F, X_DST1I, W_POISSON, 1, 0},
+                     {F, C, 2, X_DST1F, X_DST1I, W_POISSON, 2, 0}}, s);
+  stage<T, T, T>(c, {{A, D, 1, X_DST2I, X_NONE, W_NONE, 0, 0}, {B, E, 0, X_DST2I, X_NONE, W_NONE, 1, 0},
+                     {C, F, 0, X_DST2I, X_NONE, W_NONE, 2, 0}}, s);
+  stage<T, T, T>(c, {{D, u1, 2, X_DST2I, X_NONE, W_NONE, 0, 0}, {E, u2, 2, X_DST2I, X_NONE, W_NONE, 1, 0},
+                     {F, u3, 1, X_DST2I, X_NONE, W_NONE, 2, 0}}, s);
 }
 
-void prof_collect(kfbim_ctx* c);
+// b_c = (1/mu) G_c^T (-Delta_c)^{-1} f^(c) for c = 1..3 into b1, b2, b3
+// (f: 3 N^3 of type Tin); the caller adds g.
+template <typename Tin, typename T>
+void schur_rhs3(kfbim_ctx* c, const Tin* f, T* b1, T* b2, T* b3, T* T6, cudaStream_t s) {
+  const int64_t n = c->N3;
+  const Tin *f1 = f, *f2 = f + n, *f3 = f + 2 * n;
+  T *A = T6, *B = T6 + n, *C = T6 + 2 * n, *D = T6 + 3 * n, *E = T6 + 4 * n, *F = T6 + 5 * n;
+  stage<Tin, T, T>(c, {{f1, A, 2, X_DST2F, X_NONE, W_NONE, 0, 0}, {f2, B, 2, X_DST2F, X_NONE, W_NONE, 1, 0},
+                       {f3, C, 1, X_DST2F, X_NONE, W_NONE, 2, 0}}, s);
+  stage<T, T, T>(c, {{A, D, 1, X_DST2F, X_NONE, W_NONE, 0, 0}, {B, E, 0, X_DST2F, X_NONE, W_NONE, 1, 0},
+                     {C, F, 0, X_DST2F, X_NONE, W_NONE, 2, 0}}, s);
+  stage<T, T, T>(c, {{D, A, 0, X_DST1F, X_DCT2I, W_RHS, 0, 0}, {E, B, 1, X_DST1F, X_DCT2I, W_RHS, 1, 0},
+                     {F, C, 2, X_DST1F, X_DCT2I, W_RHS, 2, 0}}, s);
+  stage<T, T, T>(c, {{A, D, 1, X_DST2I, X_NONE, W_NONE, 0, 0}, {B, E, 0, X_DST2I, X_NONE, W_NONE, 1, 0},
+                     {C, F, 0, X_DST2I, X_NONE, W_NONE, 2, 0}}, s);
+  stage<T, T, T>(c, {{D, b1, 2, X_DST2I, X_NONE, W_NONE, 0, 0}, {E, b2, 2, X_DST2I, X_NONE, W_NONE, 1, 0},
+                     {F, b3, 1, X_DST2I, X_NONE, W_NONE, 2, 0}}, s);
+}
+
+// q_c = (1/mu) G_c^T (-Delta_c)^{-1} G_c d into q, q2, q3 (the CG kernel sums
+// them); the c = 1 and c = 2 terms share their first transform (DST-II along z).
+template <typename T>
+void schur_apply3(kfbim_ctx* c, const T* d, T* q, T* q2, T* q3, T* T6, cudaStream_t s,
+                  const int* skip = nullptr) {
+  const int64_t n = c->N3;
+  T *A = T6, *B = T6 + n, *C = T6 + 2 * n, *D = T6 + 3 * n, *E = T6 + 4 * n, *F = T6 + 5 * n;
+  stage<T, T, T>(c, {{d, A, 2, X_DST2F, X_NONE, W_NONE, 0, 0}, {d, B, 1, X_DST2F, X_NONE, W_NONE, 2, 0}},
+                 s, skip);
+  stage<T, T, T>(c, {{A, C, 1, X_DST2F, X_NONE, W_NONE, 0, 0}, {A, D, 0, X_DST2F, X_NONE, W_NONE, 1, 0},
+                     {B, E, 0, X_DST2F, X_NONE, W_NONE, 2, 0}}, s, skip);
+  stage<T, T, T>(c, {{C, A, 0, X_DCT2F, X_DCT2I, W_SCHUR, 0, 0}, {D, B, 1, X_DCT2F, X_DCT2I, W_SCHUR, 1, 0},
+                     {E, F, 2, X_DCT2F, X_DCT2I, W_SCHUR, 2, 0}}, s, skip);
+  stage<T, T, T>(c, {{A, C, 1, X_DST2I, X_NONE, W_NONE, 0, 0}, {B, D, 0, X_DST2I, X_NONE, W_NONE, 1, 0},
+                     {F, E, 0, X_DST2I, X_NONE, W_NONE, 2, 0}}, s, skip);
+  stage<T, T, T>(c, {{C, q, 2, X_DST2I, X_NONE, W_NONE, 0, 0}, {D, q2, 2, X_DST2I, X_NONE, W_NONE, 1, 0},
+                     {E, q3, 1, X_DST2I, X_NONE, W_NONE, 2, 0}}, s, skip);
+}
 
 double read_scalar(kfbim_ctx* c, const double* dptr, cudaStream_t s) {
   CK(cudaMemcpyAsync(c->pinned, dptr, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -277,15 +337,24 @@ void dot(kfbim_ctx* c, const Ta* x, const Tb* y, int64_t n, double* out, double 
 
 constexpr int kCgGraphIters = 4;
 
-// One CG iteration: q = S d, then the three fused scalar/vector kernels.  All
-// of it is a no-op once cgs->done is set.
+// CG vectors and stage temporaries of one precision (fixed workspace buffers).
 template <typename T>
-void cg_iteration(kfbim_ctx* c, T* x, T* r, T* d, T* q, T* t1, T* t2, cudaStream_t s) {
+struct CgWs {
+  T *x, *r, *d, *q, *q2, *q3, *T6;
+};
+
+CgWs<double> ws64(kfbim_ctx* c) { return {c->p, c->rres, c->cd, c->cq, c->q2, c->q3, c->T6}; }
+CgWs<float> ws32(kfbim_ctx* c) { return {c->fx, c->fr, c->fd, c->fq, c->fq2, c->fq3, c->fT6}; }
+
+// One CG iteration: q = S d (5 staged launches), then the three fused
+// scalar/vector kernels.  All of it is a no-op once cgs->done is set.
+template <typename T>
+void cg_iteration(kfbim_ctx* c, const CgWs<T>& w, cudaStream_t s) {
   const int64_t n = c->N3;
-  schur_apply<T>(c, d, q, t1, t2, s, &c->cgs->done);
-  k_cg_alpha<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(d, q, n, c->cgs, c->partial); ++g_launches;
-  k_cg_update<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(x, r, d, q, n, c->cgs, c->partial); ++g_launches;
-  k_cg_direction<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(d, r, n, c->cgs, c->partial); ++g_launches;
+  schur_apply3<T>(c, w.d, w.q, w.q2, w.q3, w.T6, s, &c->cgs->done);
+  k_cg_alpha<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(w.d, w.q, w.q2, w.q3, n, c->cgs, c->partial); ++g_launches;
+  k_cg_update<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(w.x, w.r, w.d, w.q, n, c->cgs, c->partial); ++g_launches;
+  k_cg_direction<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(w.d, w.r, n, c->cgs, c->partial); ++g_launches;
   check_launch();
 }
 
@@ -299,7 +368,7 @@ struct Slot<float> { static constexpr int v = 1; };
 // The graph of kCgGraphIters iterations for this precision (captured once per
 // context: every pointer it uses is a fixed workspace buffer).
 template <typename T>
-cudaGraphExec_t cg_graph(kfbim_ctx* c, T* x, T* r, T* d, T* q, T* t1, T* t2) {
+cudaGraphExec_t cg_graph(kfbim_ctx* c, const CgWs<T>& w) {
   const int slot = Slot<T>::v;
   if (c->cg_exec[slot]) return c->cg_exec[slot];
   // kernel attributes are set outside the capture: one iteration on the idle
@@ -307,13 +376,13 @@ cudaGraphExec_t cg_graph(kfbim_ctx* c, T* x, T* r, T* d, T* q, T* t1, T* t2) {
   const int one = 1;
   CK(cudaMemcpyAsync(&c->cgs->done, &one, sizeof(int), cudaMemcpyHostToDevice, c->cap_stream));
   const int64_t before = g_launches;
-  cg_iteration<T>(c, x, r, d, q, t1, t2, c->cap_stream);
+  cg_iteration<T>(c, w, c->cap_stream);
   CK(cudaStreamSynchronize(c->cap_stream));
   const int64_t per_iter = g_launches - before;
   g_launches = before;
   cudaGraph_t graph;
   CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-  for (int it = 0; it < kCgGraphIters; ++it) cg_iteration<T>(c, x, r, d, q, t1, t2, c->cap_stream);
+  for (int it = 0; it < kCgGraphIters; ++it) cg_iteration<T>(c, w, c->cap_stream);
   CK(cudaStreamEndCapture(c->cap_stream, &graph));
   g_launches = before;
   CK(cudaGraphInstantiate(&c->cg_exec[slot], graph, 0));
@@ -325,15 +394,14 @@ cudaGraphExec_t cg_graph(kfbim_ctx* c, T* x, T* r, T* d, T* q, T* t1, T* t2) {
 // CG on (S + 1 1^T / (mu N^3)) x = b from x = 0, vectors of type T, FP64
 // scalars.  The host reads the status once per kCgGraphIters iterations.
 template <typename T>
-int cg(kfbim_ctx* c, const T* b, T* x, T* r, T* d, T* q, T* t1, T* t2, double tol, int maxit,
-       cudaStream_t s, int* iters) {
+int cg(kfbim_ctx* c, const T* b, const CgWs<T>& w, double tol, int maxit, cudaStream_t s, int* iters) {
   const int64_t n = c->N3;
   const bool graphs = c->use_graphs && !c->prof;
-  cudaGraphExec_t exec = graphs ? cg_graph<T>(c, x, r, d, q, t1, t2) : nullptr;
+  cudaGraphExec_t exec = graphs ? cg_graph<T>(c, w) : nullptr;
   CK(cudaMemsetAsync(c->cgs, 0, sizeof(CGScalars), s));
-  CK(cudaMemsetAsync(x, 0, n * sizeof(T), s));
-  CK(cudaMemcpyAsync(r, b, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
-  CK(cudaMemcpyAsync(d, b, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemsetAsync(w.x, 0, n * sizeof(T), s));
+  CK(cudaMemcpyAsync(w.r, b, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(w.d, b, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
   k_cg_init<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(b, n, c->cgs, tol * tol, 1.0 / (c->mu * (double)n),
                                                    c->partial);
   ++g_launches;
@@ -353,7 +421,7 @@ int cg(kfbim_ctx* c, const T* b, T* x, T* r, T* d, T* q, T* t1, T* t2, double to
       CK(cudaGraphLaunch(exec, s));
       g_launches += c->cg_graph_kernels[Slot<T>::v];
     } else {
-      for (int it = 0; it < kCgGraphIters; ++it) cg_iteration<T>(c, x, r, d, q, t1, t2, s);
+      for (int it = 0; it < kCgGraphIters; ++it) cg_iteration<T>(c, w, s);
     }
     launched += kCgGraphIters;
   }
@@ -364,20 +432,19 @@ int grid_solve_fp64(kfbim_ctx* c, cudaStream_t s) {
   const int64_t N3 = c->N3;
   double* f = c->rhs;
   double* g = c->rhs + 3 * N3;
-  double* b = c->cr;   // Schur RHS; CG copies it into its residual (r = cq below)
-  CK(cudaMemcpyAsync(b, g, N3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  for (int cax = 0; cax < 3; ++cax)
-    schur_rhs_add<double, double>(c, cax, f + cax * N3, b, c->t1, c->t2, s);
+  double* b = c->cr;   // Schur RHS; CG copies it into its residual
+  const CgWs<double> w = ws64(c);
+  schur_rhs3<double, double>(c, f, w.q, w.q2, w.q3, w.T6, s);
+  k_sum4<double, double><<<grid_for(N3), 256, 0, s>>>(g, w.q, w.q2, w.q3, b, N3); ++g_launches;
+  check_launch();
   int it = 0;
-  int st = cg<double>(c, b, c->p, c->rres, c->cd, c->cq, c->t1, c->t2, c->opt.cg_tol, c->opt.cg_max,
-                      s, &it);
+  int st = cg<double>(c, b, w, c->opt.cg_tol, c->opt.cg_max, s, &it);
   c->cg_iters += it;
   if (st != KFBIM_OK && st != KFBIM_E_NOCONV) return st;
   // u^(c) = (1/mu)(-Delta)^{-1} (f^(c) - G_c p)
   k_f_minus_gp<double, double><<<grid_for(3 * N3), 256, 0, s>>>(f, c->p, c->lg, c->h, c->u); ++g_launches;
   check_launch();
-  for (int cax = 0; cax < 3; ++cax)
-    face_poisson<double, double, double>(c, cax, c->u + cax * N3, c->u + cax * N3, c->t1, c->t2, s);
+  face_poisson3<double>(c, c->u, c->u, w.T6, s);
   return st;
 }
 
@@ -412,23 +479,20 @@ int grid_solve_mixed(kfbim_ctx* c, cudaStream_t s) {
     }
     ++c->refine_sweeps;
     // FP32 correction solve: b = rg + (1/mu) sum G^T (-Delta)^{-1} rf
+    const CgWs<float> w = ws32(c);
     float* b32 = c->fu;  // N3 floats (fu holds 3*N3)
-    k_convert<double, float><<<grid_for(N3), 256, 0, s>>>(resg, b32, N3); ++g_launches;
+    schur_rhs3<double, float>(c, resf, w.q, w.q2, w.q3, w.T6, s);
+    k_sum4<double, float><<<grid_for(N3), 256, 0, s>>>(resg, w.q, w.q2, w.q3, b32, N3); ++g_launches;
     check_launch();
-    for (int cax = 0; cax < 3; ++cax)
-      schur_rhs_add<double, float>(c, cax, resf + cax * N3, b32, c->f1, c->f2, s);
     int it = 0;
-    int st = cg<float>(c, b32, c->fx, c->fr, c->fd, c->fq, c->f1, c->f2, c->opt.inner_tol,
-                       c->opt.cg_max, s, &it);
+    int st = cg<float>(c, b32, w, c->opt.inner_tol, c->opt.cg_max, s, &it);
     c->cg_iters += it;
     if (st == KFBIM_E_NONFINITE) return st;
     // p += dp; u += (1/mu)(-Delta)^{-1}(rf - G dp)
-    k_add_to<float><<<grid_for(N3), 256, 0, s>>>(c->fx, c->p, N3); ++g_launches;
-    k_f_minus_gp<float, float><<<grid_for(3 * N3), 256, 0, s>>>(resf, c->fx, c->lg, c->h, c->fu); ++g_launches;
+    k_add_to<float><<<grid_for(N3), 256, 0, s>>>(w.x, c->p, N3); ++g_launches;
+    k_f_minus_gp<float, float><<<grid_for(3 * N3), 256, 0, s>>>(resf, w.x, c->lg, c->h, c->fu); ++g_launches;
     check_launch();
-    for (int cax = 0; cax < 3; ++cax) {
-      face_poisson<float, float, float>(c, cax, c->fu + cax * N3, c->fu + cax * N3, c->f1, c->f2, s);
-    }
+    face_poisson3<float>(c, c->fu, c->fu, w.T6, s);
     k_add_to<float><<<grid_for(3 * N3), 256, 0, s>>>(c->fu, c->u, 3 * N3); ++g_launches;
     check_launch();
   }
@@ -627,7 +691,13 @@ void fill_tables(kfbim_ctx* c) {
   c->partial = dalloc<double>(c, (size_t)RED_BLOCKS * 256);
   c->scal = dalloc<double>(c, 64);
   c->cgs = dalloc<CGScalars>(c, 1);
+  c->q2 = dalloc<double>(c, N3);
+  c->q3 = dalloc<double>(c, N3);
+  c->T6 = dalloc<double>(c, 6 * N3);
   if (c->opt.precision == KFBIM_MIXED) {
+    c->fq2 = dalloc<float>(c, N3);
+    c->fq3 = dalloc<float>(c, N3);
+    c->fT6 = dalloc<float>(c, 6 * N3);
     c->f1 = dalloc<float>(c, N3);
     c->f2 = dalloc<float>(c, N3);
     c->fx = dalloc<float>(c, N3);
@@ -947,7 +1017,10 @@ int kfbim_schur_apply(kfbim_ctx* c, const double* d, double* q, void* stream) {
   return guarded(c, [&]() -> int {
     if (!d || !q || d == q) return fail(c, KFBIM_E_INVALID, "kfbim_schur_apply: bad pointers");
     cudaStream_t s = (cudaStream_t)stream;
-    schur_apply<double>(c, d, q, c->t1, c->t2, s);
+    const CgWs<double> w = ws64(c);
+    schur_apply3<double>(c, d, w.q, w.q2, w.q3, w.T6, s);
+    k_sum3<double><<<grid_for(c->N3), 256, 0, s>>>(w.q, w.q2, w.q3, q, c->N3);
+    ++g_launches;
     dot(c, d, (const double*)nullptr, c->N3, c->scal, 1.0 / (c->mu * (double)c->N3), s);
     k_shift<<<grid_for(c->N3), 256, 0, s>>>(q, c->scal, 1.0, c->N3); ++g_launches;
     check_launch();

@@ -243,13 +243,31 @@ __device__ __forceinline__ T spectral_weight2(const PassArgs& a, const T* __rest
   return T(-2) * h * sqrt(T(0.25) * s2[ac]) * isum * inv_mu;   // W_RHS
 }
 
+// Up to three independent passes in one launch (blockIdx.y selects the job):
+// the three components' transforms of one stage of the Schur apply, the
+// Schur right-hand side or the velocity recovery.
+template <typename Tin, typename Tout>
+struct PassJob {
+  const Tin* in;
+  Tout* out;
+  PassArgs a;
+};
+template <typename Tin, typename Tout>
+struct PassJobs {
+  PassJob<Tin, Tout> j[3];
+};
+
 template <typename Tin, typename T, typename Tout, int N>
 __global__ void __launch_bounds__(PASS2_THREADS)
-k_axis_pass2(const Tin* __restrict__ in, Tout* __restrict__ out, PassArgs a,
-             const C2<T>* __restrict__ tw, const C2<T>* __restrict__ qN, const T* __restrict__ s2) {
+k_axis_pass2(const __grid_constant__ PassJobs<Tin, Tout> jobs, const C2<T>* __restrict__ tw,
+             const C2<T>* __restrict__ qN, const T* __restrict__ s2) {
   using S = Pass2Smem<T, N>;
   extern __shared__ __align__(16) unsigned char smem2[];
+  const PassJob<Tin, Tout>& job = jobs.j[blockIdx.y];
+  const PassArgs& a = job.a;
   if (a.skip && *a.skip) return;
+  const Tin* __restrict__ in = job.in;
+  Tout* __restrict__ out = job.out;
   T* Rb = reinterpret_cast<T*>(smem2);
   C2<T>* Xb = reinterpret_cast<C2<T>*>(smem2 + S::stage_al);
   C2<T>* Zb = Xb;

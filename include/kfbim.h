@@ -105,7 +105,7 @@ typedef struct {
 } kfbim_stats;
 
 /* Fills *opt with the defaults (mu 1, FP64, gmres 1e-10/200, cg 1e-14/2000,
- * refine 1e-13/8, inner 1e-5). */
+ * refine 1e-11/8, inner 3e-6). */
 void kfbim_default_options(kfbim_options* opt);
 
 /* Alg. 1 step 1: grids, sides, intersections, frames, control points and all

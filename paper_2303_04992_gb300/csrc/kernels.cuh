@@ -10,7 +10,7 @@
 namespace kfbim {
 
 constexpr int RED_THREADS = 256;
-constexpr int RED_BLOCKS = 304;   // 2 x 152 SMs
+constexpr int RED_BLOCKS = 1216;  // 8 x 152 SMs
 
 // N is a power of two: flat index x = (k N + j) N + i, lg = log2 N.
 __device__ __forceinline__ void unflat(int64_t x, int lg, int& i, int& j, int& k) {
@@ -27,8 +27,8 @@ __device__ __forceinline__ void unflat(int64_t x, int lg, int& i, int& j, int& k
 __global__ void k_jumps(const double* __restrict__ phi, const double* __restrict__ fpts,
                         int64_t n, const int32_t* __restrict__ comp, const int32_t* __restrict__ pid,
                         const int64_t* __restrict__ fit_ptr, const int32_t* __restrict__ fit_col,
-                        const double* __restrict__ fit_w, const double* __restrict__ jmap,
-                        double* __restrict__ J) {
+                        const double* __restrict__ fit_w, int64_t fit_nnz,
+                        const double* __restrict__ jmap, double* __restrict__ J) {
   const int lane = threadIdx.x & 31;
   const int64_t y = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (y >= n) return;
@@ -38,14 +38,15 @@ __global__ void k_jumps(const double* __restrict__ phi, const double* __restrict
   for (int cc = 0; cc < 3; ++cc)
 #pragma unroll
     for (int s = 0; s < 6; ++s) acc[cc][s] = 0.0;
+  // fit weights are stored weight-major (fit_w[s * nnz + entry]): lanes read
+  // consecutive entries
 #pragma unroll
   for (int cc = 0; cc < 3; ++cc) {
     const int64_t b = fit_ptr[3 * y + cc], e = fit_ptr[3 * y + cc + 1];
     for (int64_t q = b + lane; q < e; q += 32) {
       const double v = phi[fit_col[q]];
-      const double* w = fit_w + 6 * q;
 #pragma unroll
-      for (int s = 0; s < 6; ++s) acc[cc][s] += w[s] * v;
+      for (int s = 0; s < 6; ++s) acc[cc][s] += fit_w[s * fit_nnz + q] * v;
     }
   }
 #pragma unroll
@@ -72,11 +73,13 @@ __global__ void k_jumps(const double* __restrict__ phi, const double* __restrict
     }
     J[y] = v0;
   }
+  // jump map stored input-major per point (jmap[(y * 18 + q) * 11 + row]): the
+  // 11 lanes read 11 consecutive values per input
   if (lane < 11) {
-    const double* M = jmap + ((size_t)y * 11 + lane) * 18;
+    const double* M = jmap + (size_t)y * 18 * 11 + lane;
     double s = 0.0;
 #pragma unroll
-    for (int q = 0; q < 18; ++q) s += M[q] * in[q];
+    for (int q = 0; q < 18; ++q) s += M[q * 11] * in[q];
     J[(int64_t)(lane + 1) * n + y] = s;
   }
 }
@@ -304,7 +307,7 @@ __global__ void k_cg_alpha(const T* __restrict__ d, T* __restrict__ q, const T* 
        e += (int64_t)gridDim.x * blockDim.x) {
     const T qs = q[e] + q2[e] + q3[e];
     q[e] = qs;
-    acc += double(d[e]) * double(qs);
+    acc += double(d[e] * qs);
   }
   if (last_block_sum(acc, partial, &s->ticket[0], sh, &total) && threadIdx.x == 0) {
     const double den = total + s->sumd * s->sumd * s->rank1;
@@ -321,15 +324,16 @@ __global__ void k_cg_update(T* __restrict__ x, T* __restrict__ r, const T* __res
   __shared__ double sh[32];
   __shared__ double total;
   if (s->done) return;
-  const double a = s->alpha;
-  const double c1 = s->sumd * s->rank1;
+  // element arithmetic in T (FP32 in MIXED), squared norm accumulated in FP64
+  const T a = T(s->alpha);
+  const T c1 = T(s->sumd * s->rank1);
   double acc = 0.0;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const T rv = T(double(r[e]) - a * (double(q[e]) + c1));
-    x[e] = T(double(x[e]) + a * double(d[e]));
+    const T rv = r[e] - a * (q[e] + c1);
+    x[e] = x[e] + a * d[e];
     r[e] = rv;
-    acc += double(rv) * double(rv);
+    acc += double(rv * rv);
   }
   if (last_block_sum(acc, partial, &s->ticket[1], sh, &total) && threadIdx.x == 0) {
     s->beta = (s->rr != 0.0) ? total / s->rr : 0.0;
@@ -345,11 +349,11 @@ __global__ void k_cg_direction(T* __restrict__ d, const T* __restrict__ r, int64
   __shared__ double sh[32];
   __shared__ double total;
   if (s->done) return;
-  const double b = s->beta;
+  const T b = T(s->beta);
   double acc = 0.0;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const T v = T(double(r[e]) + b * double(d[e]));
+    const T v = r[e] + b * d[e];
     d[e] = v;
     acc += double(v);
   }

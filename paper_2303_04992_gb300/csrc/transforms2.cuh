@@ -92,14 +92,15 @@ struct Pass2Smem {
   static constexpr int XB = B::X > B::Z ? B::X : B::Z;
   // the exchange buffer also receives the FFT output (after a barrier)
   static constexpr size_t xbuf = sizeof(C2<T>) * (XA > XB ? XA : XB);
-  static constexpr size_t bytes = stage_al + xbuf;
+  // twiddle tables staged per CTA: full-circle tw (2N) and post-twiddles qN (N)
+  static constexpr size_t tables = sizeof(C2<T>) * 3 * N;
+  static constexpr size_t bytes = stage_al + xbuf + tables;
 };
 
 // One real transform of the LPC2 staged lines, in place in Rb.
 // KIND: 0 DCT-II family, 1 DST-II family, 2 DST-I.  INV: inverse.
 template <typename T, int N, int KIND, bool INV>
-__device__ void xform2(T* Rb, C2<T>* Xb, C2<T>* Zb, const C2<T>* __restrict__ tw,
-                       const C2<T>* __restrict__ qN) {
+__device__ void xform2(T* Rb, C2<T>* Xb, C2<T>* Zb, const C2<T>* tw, const C2<T>* qN) {
   constexpr int RS = N + 1;
   constexpr int L = (KIND == 2) ? 2 * N : N;
   constexpr int R = 16;
@@ -258,7 +259,7 @@ struct PassJobs {
 };
 
 template <typename Tin, typename T, typename Tout, int N>
-__global__ void __launch_bounds__(PASS2_THREADS)
+__global__ void __launch_bounds__(PASS2_THREADS, (sizeof(T) == 4 ? 5 : 2))
 k_axis_pass2(const __grid_constant__ PassJobs<Tin, Tout> jobs, const C2<T>* __restrict__ tw,
              const C2<T>* __restrict__ qN, const T* __restrict__ s2) {
   using S = Pass2Smem<T, N>;
@@ -271,6 +272,12 @@ k_axis_pass2(const __grid_constant__ PassJobs<Tin, Tout> jobs, const C2<T>* __re
   T* Rb = reinterpret_cast<T*>(smem2);
   C2<T>* Xb = reinterpret_cast<C2<T>*>(smem2 + S::stage_al);
   C2<T>* Zb = Xb;
+  C2<T>* tws = reinterpret_cast<C2<T>*>(smem2 + S::stage_al + S::xbuf);
+  C2<T>* qs = tws + 2 * N;
+  for (int e = threadIdx.x; e < 3 * N; e += PASS2_THREADS) {
+    if (e < 2 * N) tws[e] = tw[e];
+    else qs[e - 2 * N] = qN[e - 2 * N];
+  }
   constexpr int RS = S::RS;
   const int line0 = blockIdx.x * LPC2;
   const int axis = a.axis;
@@ -302,7 +309,7 @@ k_axis_pass2(const __grid_constant__ PassJobs<Tin, Tout> jobs, const C2<T>* __re
     }
   }
   __syncthreads();
-  xform2_dispatch<T, N>(a.type0, Rb, Xb, Zb, tw, qN);
+  xform2_dispatch<T, N>(a.type0, Rb, Xb, Zb, tws, qs);
   if (a.wmode != W_NONE) {
     const T inv_mu = T(1.0 / a.mu);
     for (int e = threadIdx.x; e < LPC2 * N; e += PASS2_THREADS) {
@@ -316,7 +323,7 @@ k_axis_pass2(const __grid_constant__ PassJobs<Tin, Tout> jobs, const C2<T>* __re
     }
     __syncthreads();
   }
-  xform2_dispatch<T, N>(a.type1, Rb, Xb, Zb, tw, qN);
+  xform2_dispatch<T, N>(a.type1, Rb, Xb, Zb, tws, qs);
   const T sc = T(a.scale);
   if (a.accumulate) {
     Tout prev[PER];

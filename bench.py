@@ -184,6 +184,21 @@ def inputs(solver, geom, grid):
     return g, fpts, np.concatenate(fg)
 
 
+def job_throughput(total_ms, steps, dist=None, device="cpu"):
+    """Whole-job throughput of replicas: every rank solved `steps` instances
+    in total_ms of its own; the job time is the max over ranks (barrier first)
+    and the value counts the instances of all ranks.  Returns (value, max_ms)."""
+    import torch
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    world = 1
+    if dist is not None and dist.is_initialized():
+        dist.barrier()
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        world = dist.get_world_size()
+    total = float(t.item())
+    return world * steps / (total / 1e3), total
+
+
 # -------------------------------------------------------------- main arms
 def main_kfbim(args):
     import torch
@@ -247,13 +262,8 @@ def main_kfbim(args):
     total_ms, stats, _ = timed(args.steps)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if dist:
-        dist.barrier()
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    value, total_ms = job_throughput(total_ms, args.steps, dist, dev)
     ms_per_step = total_ms / args.steps
-    value = world * args.steps / (total_ms / 1e3)
     launches = int(sum(s["kernel_launches"] for s in stats))
     phi_mixed = phi.cpu().numpy().copy()
 

@@ -105,7 +105,6 @@ def test_gmres_cap_reports_noconv_with_last_iterate():
     with pytest.raises(KfbimError) as e:
         s.solve(cuda(g), phi, cuda(fpts), cuda(fg))
     assert e.value.code == -3
-    assert s.last_stats is None or True
     assert float(phi.abs().max()) > 0.0
 
 

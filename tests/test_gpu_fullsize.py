@@ -85,7 +85,8 @@ def test_mixed_solve_matches_fp64_solve_at_128(solvers):
         out[prec] = (phi.cpu().numpy(), p.cpu().numpy(), s.last_stats)
     assert rel(out[MIXED][0], out[FP64][0]) < 1e-8
     assert rel(out[MIXED][1], out[FP64][1]) < 1e-7
-    assert out[MIXED][2]["gmres_iters"] == out[FP64][2]["gmres_iters"]
+    # the inexact (refined FP32) matvec may take a few more GMRES steps near the tolerance
+    assert abs(out[MIXED][2]["gmres_iters"] - out[FP64][2]["gmres_iters"]) <= 3
 
 
 def test_nonfinite_data_is_reported(solvers):

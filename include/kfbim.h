@@ -83,8 +83,15 @@ typedef enum {
                       corrections, traces, residuals and GMRES stay FP64 */
 } kfbim_precision;
 
+typedef enum {
+  KFBIM_STOKES = 0,  /* -mu Lap u + grad p = f, div u = 0 (Eq. SP) */
+  KFBIM_NAVIER = 1   /* -mu Lap u - (lambda + mu) grad div u = f (Eq. Navier), solved
+                        in the unified form -mu Lap u + grad p = f, div u + c p = 0,
+                        c = 1/(lambda + mu), with the elastic interface traction */
+} kfbim_pde;
+
 typedef struct {
-  double mu;          /* viscosity (> 0) */
+  double mu;          /* viscosity, or Lame mu (> 0) */
   int precision;      /* kfbim_precision */
   double gmres_tol;   /* relative l2 residual, e.g. 1e-10 */
   int gmres_max;      /* <= 200 */
@@ -93,6 +100,8 @@ typedef struct {
   double refine_tol;  /* MIXED: relative residual of the FP64 system */
   int refine_max;     /* MIXED: refinement sweeps cap */
   double inner_tol;   /* MIXED: FP32 CG relative residual per sweep */
+  int pde;            /* kfbim_pde */
+  double lambda;      /* Lame lambda (NAVIER; lambda + mu > 0, lambda >= 0) */
 } kfbim_options;
 
 typedef struct {
@@ -104,8 +113,8 @@ typedef struct {
   int64_t kernel_launches; /* CUDA kernels launched by the call */
 } kfbim_stats;
 
-/* Fills *opt with the defaults (mu 1, FP64, gmres 1e-10/200, cg 1e-14/2000,
- * refine 1e-11/8, inner 3e-6). */
+/* Fills *opt with the defaults (Stokes, mu 1, FP64, gmres 1e-10/200,
+ * cg 1e-14/2000, refine 1e-11/8, inner 3e-6, lambda 0). */
 void kfbim_default_options(kfbim_options* opt);
 
 /* Alg. 1 step 1: grids, sides, intersections, frames, control points and all
@@ -160,9 +169,10 @@ int kfbim_apply(kfbim_ctx* ctx, const double* phi_dev, double* out_dev, void* st
  *   phi_dev    [n_primary]     out: density.
  *   u_dev      [3*N^3]         out, nullable: interface-problem velocity; its
  *                              values at Omega nodes are u_h.
- *   p_dev      [N^3]           out, nullable: pressure (cells), gauge
+ *   p_dev      [N^3]           out, nullable: pressure (cells).  Stokes: gauge
  *                              mean(p) = mu * mean(g_cells) of the augmented
- *                              system with gamma = 1, alpha = mu N^3.
+ *                              system with gamma = 1, alpha = mu N^3.  Navier:
+ *                              p = -(lambda + mu) div u, no gauge.
  *   stats      nullable. */
 int kfbim_solve(kfbim_ctx* ctx, const double* g_dev, const double* fpts_dev,
                 const double* fgrid_dev, double* phi_dev, double* u_dev, double* p_dev,
@@ -205,7 +215,7 @@ int kfbim_trace(kfbim_ctx* ctx, const double* u_dev, const double* J_dev,
 int kfbim_poisson(kfbim_ctx* ctx, int c, const double* r_dev, double* u_dev, void* stream);
 
 /* Schur operator of item ii): q = (1/mu) G^T (-Delta_h)^{-1} G d + sum(d)/alpha,
- * alpha = mu N^3; d_dev, q_dev N^3 doubles (cells). */
+ * alpha = mu N^3 (Stokes), or + c d (Navier); d_dev, q_dev N^3 doubles (cells). */
 int kfbim_schur_apply(kfbim_ctx* ctx, const double* d_dev, double* q_dev, void* stream);
 
 /* Allocation-free variant of kfbim_poisson, for callers that may not allocate

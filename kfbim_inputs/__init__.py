@@ -142,3 +142,50 @@ def example51_forcing(x, mu=1.0):
     lap = np.stack([24 * Z**2 - 24 * X**2 + 48 * X * Y, 24 * X**2 - 24 * Y**2 + 2, 48 * X * Z], -1)
     gp = np.stack([24 * Z**2 - 24 * X**2 + 48 * X * Y, 24 * X**2 - 24 * Y**2, 48 * X * Z], -1)
     return -mu * lap + gp
+
+
+# ------------------------------------ manufactured Lame displacement (Navier)
+LAME_MU, LAME_LAMBDA = 1.0, 2.0
+
+
+def lame_jets(x):
+    """u_i = exp(x + y + z) sin(i + x y), i = 1..3: values (n,3), gradients
+    (n,3,3) and Hessians (n,3,3,3) by the product rule."""
+    x = np.asarray(x, dtype=np.float64)
+    X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
+    E = np.exp(X + Y + Z)
+    u = np.zeros(x.shape[:-1] + (3,))
+    G = np.zeros(x.shape[:-1] + (3, 3))
+    H = np.zeros(x.shape[:-1] + (3, 3, 3))
+    for i in range(3):
+        S = np.sin(i + 1 + X * Y)
+        C = np.cos(i + 1 + X * Y)
+        u[..., i] = E * S
+        G[..., i, 0] = E * (S + Y * C)
+        G[..., i, 1] = E * (S + X * C)
+        G[..., i, 2] = E * S
+        H[..., i, 0, 0] = E * (S + 2 * Y * C - Y * Y * S)
+        H[..., i, 1, 1] = E * (S + 2 * X * C - X * X * S)
+        H[..., i, 2, 2] = E * S
+        H[..., i, 0, 1] = H[..., i, 1, 0] = E * (S + X * C + Y * C + C - X * Y * S)
+        H[..., i, 0, 2] = H[..., i, 2, 0] = E * (S + Y * C)
+        H[..., i, 1, 2] = H[..., i, 2, 1] = E * (S + X * C)
+    return u, G, H
+
+
+def lame_displacement(x):
+    return lame_jets(x)[0]
+
+
+def lame_forcing(x, mu=LAME_MU, lam=LAME_LAMBDA):
+    """f = -mu Lap u - (lambda + mu) grad(div u) (Eq. Navier)."""
+    _, _, H = lame_jets(x)
+    lap = np.einsum("...ijj->...i", H)
+    graddiv = np.einsum("...iij->...j", H)
+    return -mu * lap - (lam + mu) * graddiv
+
+
+def lame_pressure(x, mu=LAME_MU, lam=LAME_LAMBDA):
+    """The auxiliary unknown p = -(lambda + mu) div u of the unified form."""
+    _, G, _ = lame_jets(x)
+    return -(lam + mu) * np.einsum("...ii->...", G)

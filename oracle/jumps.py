@@ -22,6 +22,15 @@ Second order (21 equations for the 18 entries of H^(1..3) and the 3 of s):
   (iv)  tau_a . grad([sigma]) n + [sigma] d_a n = 0,  d_a n = sum_b K_ab tau_b
                                                                (6; d/ds_a of IUS-4)
 
+Navier (Lame) variant (Sec. 2 Eq. Navier, unified form I-E of the Sec. 4.1
+remark): p = -(lambda + mu) div u, div u + c p = 0 with c = 1/(lambda + mu), and
+the interface traction is the elastic one, sigma = lambda (div u) I +
+mu (grad u + grad u^T) = -kappa p I + mu (grad u + grad u^T), kappa = lambda c
+(reading: the traction of the Navier double layer, Sec. 3, is used in IUS-4).
+First order: A n = -(lambda / (lambda + 2 mu)) D n - sum_a (n . d_a phi) tau_a,
+q = -(lambda + mu) tr A.  Second order: (ii) gains + c s_j, (iv) uses kappa s
+and [sigma] = -kappa q I + mu (A + A^T).  Stokes is c = 0, kappa = 1.
+
 Surface derivatives of each density component (the paper defers this step to
 earlier work; our reading, parity unpinned): a weighted least-squares
 quadratic in the tangent-plane coordinates (s, t) = ((z - y).tau_1,
@@ -98,42 +107,47 @@ def _hidx(k, l):
     return SYM.index((min(k, l), max(k, l)))
 
 
-def first_order(n, T, dphi, mu):
-    """A (n,3,3) and q (n,) from the tangential derivatives dphi (n,3,2)."""
+def first_order(n, T, dphi, mu, lam=None):
+    """A (n,3,3) and q (n,) from the tangential derivatives dphi (n,3,2).
+    lam = None: Stokes; else the Navier (Lame) relations."""
     dphi_t = np.swapaxes(dphi, 1, 2)                             # (n, 2, 3): d_a phi
     D = np.einsum("nai,nai->n", T, dphi_t)
     nd = np.einsum("ni,nai->na", n, dphi_t)
-    An = -D[:, None] * n - np.einsum("na,nai->ni", nd, T)
+    Ann = -D if lam is None else -D * lam / (lam + 2.0 * mu)
+    An = Ann[:, None] * n - np.einsum("na,nai->ni", nd, T)
     A = np.einsum("nai,naj->nij", dphi_t, T) + An[:, :, None] * n[:, None, :]
-    q = -2.0 * mu * D
+    q = -2.0 * mu * D if lam is None else -(lam + mu) * (Ann + D)
     return A, q
 
 
-def second_order_system(n, T, K, mu):
+def second_order_system(n, T, K, mu, lam=None):
     """Matrix L (n, 21, 21) of equations (i)-(iv) acting on
-    x = (H^(1) (6), H^(2) (6), H^(3) (6), s (3))."""
+    x = (H^(1) (6), H^(2) (6), H^(3) (6), s (3)); lam = None for Stokes."""
+    c = 0.0 if lam is None else 1.0 / (lam + mu)
+    kap = 1.0 if lam is None else lam / (lam + mu)
     npt = len(n)
     L = np.zeros((npt, 21, 21))
     row = 0
-    for c in range(3):                                   # (i)
+    for cc in range(3):                                  # (i)
         for (a, b) in [(0, 0), (0, 1), (1, 1)]:
             for k in range(3):
                 for l in range(3):
-                    L[:, row, 6 * c + _hidx(k, l)] += T[:, a, k] * T[:, b, l]
+                    L[:, row, 6 * cc + _hidx(k, l)] += T[:, a, k] * T[:, b, l]
             row += 1
     for j in range(3):                                   # (ii)
-        for c in range(3):
-            L[:, row, 6 * c + _hidx(c, j)] += 1.0
+        for cc in range(3):
+            L[:, row, 6 * cc + _hidx(cc, j)] += 1.0
+        L[:, row, 18 + j] += c
         row += 1
-    for c in range(3):                                   # (iii)
+    for cc in range(3):                                  # (iii)
         for k in range(3):
-            L[:, row, 6 * c + _hidx(k, k)] += -mu
-        L[:, row, 18 + c] += 1.0
+            L[:, row, 6 * cc + _hidx(k, k)] += -mu
+        L[:, row, 18 + cc] += 1.0
         row += 1
     for a in range(2):                                   # (iv)
         for i in range(3):
             for j in range(3):
-                L[:, row, 18 + j] += -T[:, a, j] * n[:, i]
+                L[:, row, 18 + j] += -kap * T[:, a, j] * n[:, i]
                 for k in range(3):
                     L[:, row, 6 * i + _hidx(k, j)] += mu * T[:, a, j] * n[:, k]
                     L[:, row, 6 * k + _hidx(i, j)] += mu * T[:, a, j] * n[:, k]
@@ -141,9 +155,10 @@ def second_order_system(n, T, K, mu):
     return L
 
 
-def second_order_rhs(n, T, K, A, q, d2phi, fy, mu):
+def second_order_rhs(n, T, K, A, q, d2phi, fy, mu, lam=None):
     """Right-hand side (n, 21) of (i)-(iv); d2phi (n, 3, 3) = (d_11, d_12, d_22)
-    per component, fy (n, 3) = [f~] at the point."""
+    per component, fy (n, 3) = [f~] at the point; lam = None for Stokes."""
+    kap = 1.0 if lam is None else lam / (lam + mu)
     npt = len(n)
     rhs = np.zeros((npt, 21))
     An = np.einsum("nij,nj->ni", A, n)
@@ -156,7 +171,7 @@ def second_order_rhs(n, T, K, A, q, d2phi, fy, mu):
     for c in range(3):
         rhs[:, row] = fy[:, c]
         row += 1
-    sig = -q[:, None, None] * np.eye(3) + mu * (A + np.swapaxes(A, 1, 2))
+    sig = -kap * q[:, None, None] * np.eye(3) + mu * (A + np.swapaxes(A, 1, 2))
     dn = np.einsum("nab,nbk->nak", K, T)                 # d_a n
     for a in range(2):
         v = np.einsum("nik,nk->ni", sig, dn[:, a, :])
@@ -189,7 +204,7 @@ class JumpData:
         self.nbrs = neighbour_lists(cp, self.primary)
 
 
-def jumps(jd, phi_p, fy, mu):
+def jumps(jd, phi_p, fy, mu, lam=None):
     """Jump values at every control point y in X_c on an a-line:
     column 0 [u^(c)], 1-3 [grad u^(c)], 4-9 [Hess u^(c)] (order 11,22,33,23,13,12),
     10 [p], 11 [d_a p].  phi_p: density at the primary points (canonical
@@ -203,9 +218,9 @@ def jumps(jd, phi_p, fy, mu):
     der = surface_derivatives(cp, jd.frames, jd.nbrs, phi, jd.h)   # (n, 3, 6)
     rows = np.arange(cp.n)
     phi = np.where(jd.primary, phi, der[rows, cp.comp - 1, 0])
-    A, q = first_order(n, T, der[:, :, 1:3], mu)
-    L = second_order_system(n, T, K, mu)
-    rhs = second_order_rhs(n, T, K, A, q, der[:, :, 3:6], fy, mu)
+    A, q = first_order(n, T, der[:, :, 1:3], mu, lam)
+    L = second_order_system(n, T, K, mu, lam)
+    rhs = second_order_rhs(n, T, K, A, q, der[:, :, 3:6], fy, mu, lam)
     x = np.linalg.solve(L, rhs[..., None])[..., 0]
     out = np.zeros((cp.n, 12))
     rows = np.arange(cp.n)

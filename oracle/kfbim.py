@@ -13,10 +13,15 @@ from . import grid as gridmod, jumps as jumpmod, correct, interp, mac
 
 
 class Setup:
-    def __init__(self, geom, grid_desc, mu=1.0, cg_tol=1e-14):
+    """lam = None: Stokes (Eq. SP, unified IUS); lam = Lame lambda: Navier
+    (Eq. Navier, unified I-E with c = 1/(lambda + mu))."""
+
+    def __init__(self, geom, grid_desc, mu=1.0, cg_tol=1e-14, lam=None):
         self.geom = geom
         self.grid = gridmod.Grid(grid_desc["N"], grid_desc["lo"], grid_desc["hi"])
         self.mu = float(mu)
+        self.lam = None if lam is None else float(lam)
+        self.cpen = None if lam is None else 1.0 / (self.lam + self.mu)
         self.cg_tol = cg_tol
         self.cp, self.S = gridmod.control_points(self.grid, geom)
         gridmod.check_geometry(self.grid, geom, self.cp, self.S)
@@ -38,7 +43,7 @@ class Setup:
 
     def interface(self, phi, fy, f_faces):
         """Unified interface solve (IUS-1..5) on the grid: returns (u, p, J)."""
-        J = jumpmod.jumps(self.jd, phi, fy, self.mu)
+        J = jumpmod.jumps(self.jd, phi, fy, self.mu, self.lam)
         Cf, Cg = correct.corrections(self.grid, self.cp, self.S, J, self.mu)
         if f_faces is None:
             f = Cf
@@ -46,7 +51,7 @@ class Setup:
             ft = self.masked_forcing(f_faces)
             f = [ft[c] + Cf[c] for c in range(3)]
         f = [mac.zero_walls(f[c - 1], c) for c in (1, 2, 3)]
-        u, p, it = mac.interface_solve(f, Cg, self.mu, self.grid.h, tol=self.cg_tol)
+        u, p, it = mac.interface_solve(f, Cg, self.mu, self.grid.h, tol=self.cg_tol, cpen=self.cpen)
         self.cg_iters.append(it)
         return u, p, J
 

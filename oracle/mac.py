@@ -95,8 +95,8 @@ def _eig1(n_modes, N, first):
 
 
 def poisson(rc, c, h):
-    """Solve -Delta_h u^(c) = r^(c) (Sec. 4.2 item ii, 'FFT-based Poisson
-    solver') with scipy's DST: type I along axis c-1 on faces 1..N-1, type II
+    """Solve -Delta_h u^(c) = r^(c) (the FFT Poisson solver of Sec. 4.2 item
+    ii) with scipy's DST: type I along axis c-1 on faces 1..N-1, type II
     along the other axes; eigenvalues (4/h^2) sum sin^2(pi m / 2N)."""
     N = rc.shape[0]
     axc = _ax(c - 1)
@@ -123,14 +123,18 @@ def poisson(rc, c, h):
     return out
 
 
-def schur_apply(d, mu, h, alpha):
+def schur_apply(d, mu, h, alpha, cpen=None):
     """(1/mu) G^T (-Delta_h)^{-1} G d + (1/alpha) gamma gamma^T d, gamma = 1.
 
     Reading of the sign in item ii): the '+' printed with the rank-one term
     gives an SPD operator for CG; both signs give the same velocity and the
-    same mean-free pressure.  G^T = -D."""
+    same mean-free pressure.  G^T = -D.
+    Navier (cpen = c = 1/(lambda + mu), continuity row div u + c p = g):
+    (1/mu) G^T (-Delta_h)^{-1} G d + c d, no rank-one term."""
     g = grad(d, h)
     w = [poisson(g[c - 1], c, h) for c in (1, 2, 3)]
+    if cpen is not None:
+        return -div(w, h) / mu + cpen * d
     return -div(w, h) / mu + np.sum(d) / alpha
 
 
@@ -164,15 +168,16 @@ def cg(apply, b, tol=1e-14, maxit=2000):
     return x, it
 
 
-def interface_solve(f, g, mu, h, tol=1e-14):
+def interface_solve(f, g, mu, h, tol=1e-14, cpen=None):
     """Solve the (corrected) MAC system [-mu Lap, G; D, 0][u; p] = [f; g]
     through the augmented system with lambda_h (gamma = 1, alpha = mu N^3):
     Schur CG for p (item ii), then u = (1/mu)(-Delta_h)^{-1}(f - G p)
-    (item iii).  Returns (u (3 face fields), p, CG iterations)."""
+    (item iii).  Navier (cpen = c): [-mu Lap, G; D, c I], Schur operator
+    S + c I.  Returns (u (3 face fields), p, CG iterations)."""
     N = g.shape[0]
     alpha = mu * N ** 3
     b = schur_rhs(f, g, mu, h)
-    p, it = cg(lambda d: schur_apply(d, mu, h, alpha), b, tol=tol)
+    p, it = cg(lambda d: schur_apply(d, mu, h, alpha, cpen), b, tol=tol)
     Gp = grad(p, h)
     u = [poisson(f[c - 1] - Gp[c - 1], c, h) / mu for c in (1, 2, 3)]
     return u, p, it

@@ -31,7 +31,8 @@ class Grid(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("mu", c_double), ("precision", c_int), ("gmres_tol", c_double),
                 ("gmres_max", c_int), ("cg_tol", c_double), ("cg_max", c_int),
-                ("refine_tol", c_double), ("refine_max", c_int), ("inner_tol", c_double)]
+                ("refine_tol", c_double), ("refine_max", c_int), ("inner_tol", c_double),
+                ("pde", c_int), ("lam", c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -136,12 +137,16 @@ class Solver:
     """One geometry + grid.  Device arguments are torch float64 CUDA tensors
     (contiguous); work goes on torch's current CUDA stream."""
 
-    def __init__(self, geom, grid, mu=1.0, precision=0, device=True, **opts):
+    def __init__(self, geom, grid, mu=1.0, precision=0, device=True, lam=None, **opts):
+        """lam = None: Stokes; lam = Lame lambda: Navier (Lame) problem."""
         lib = load_library()
         o = Options()
         lib.kfbim_default_options(ctypes.byref(o))
         o.mu = mu
         o.precision = precision
+        if lam is not None:
+            o.pde = 1
+            o.lam = lam
         for k, v in opts.items():
             setattr(o, k, v)
         self.options = o
@@ -158,6 +163,7 @@ class Solver:
         self.lo, self.hi = float(grid["lo"]), float(grid["hi"])
         self.h = (self.hi - self.lo) / self.N
         self.mu = mu
+        self.lam = lam
         self.last_stats = None
 
     def close(self):

@@ -48,8 +48,9 @@ struct HostTables {
   std::vector<double> tr_w, tr_cj;                 // kStencil each
 };
 
-// Alg. 1 step 1 and every table of the matvec.  Returns a kfbim_status.
-int build_tables(const kfbim_geometry& geom, const kfbim_grid& grid, double mu,
+// Alg. 1 step 1 and every table of the matvec.  lam < 0: Stokes; otherwise
+// the Navier (Lame) jump relations with Lame lambda.  Returns a kfbim_status.
+int build_tables(const kfbim_geometry& geom, const kfbim_grid& grid, double mu, double lam,
                  HostTables& t, std::string& err);
 
 }  // namespace kfbim

@@ -163,10 +163,11 @@ __global__ void k_f_minus_gp(const double* __restrict__ f, const Tp* __restrict_
 }
 
 // FP64 residual of the corrected MAC system (Eq. MAC with the lambda_h
-// projection): rf = f - (-mu Lap u + G p), rg = g - mean(g) - D u.
+// projection): rf = f - (-mu Lap u + G p), rg = g - mean(g) - D u - c p
+// (Stokes: c = 0; Navier: the mean is 0 and c = 1/(lambda + mu)).
 __global__ void k_mac_residual(const double* __restrict__ f, const double* __restrict__ g,
                                const double* __restrict__ gmean, const double* __restrict__ u,
-                               const double* __restrict__ p, int lg, double h, double mu,
+                               const double* __restrict__ p, int lg, double h, double mu, double cpen,
                                double* __restrict__ rf, double* __restrict__ rg) {
   const int N = 1 << lg;
   const int64_t N3 = (int64_t)1 << (3 * lg);
@@ -211,7 +212,7 @@ __global__ void k_mac_residual(const double* __restrict__ f, const double* __res
         const double hi = (ib + 1 <= N - 1) ? ub[x + st] : 0.0;
         d += (hi - lo) * ih;
       }
-      rg[x] = g[x] - gm - d;
+      rg[x] = g[x] - gm - d - cpen * p[x];
     }
   }
 }
@@ -264,7 +265,7 @@ __global__ void k_sum_partials(const double* __restrict__ partial, int nb, doubl
 // rr <= stop the iteration is a no-op (done = 1): alpha = beta = 0 and the
 // transform passes of S d return immediately.
 struct CGScalars {
-  double rr, bb, stop, dq, alpha, beta, sumd, rank1;
+  double rr, bb, stop, dq, alpha, beta, sumd, rank1, cdiag;
   int done, iters;
   unsigned int ticket[3];
 };
@@ -293,7 +294,8 @@ __device__ __forceinline__ bool last_block_sum(double v, double* __restrict__ pa
   return true;
 }
 
-// q_S = q + q2 + q3 (the three component terms, summed in place into q);
+// q_S = q + q2 + q3 + cdiag d (the three component terms and, for the
+// Navier system, the c p block; summed in place into q);
 // dq = d . q_S; alpha = rr / (dq + sumd^2 rank1)
 template <typename T>
 __global__ void k_cg_alpha(const T* __restrict__ d, T* __restrict__ q, const T* __restrict__ q2,
@@ -302,10 +304,11 @@ __global__ void k_cg_alpha(const T* __restrict__ d, T* __restrict__ q, const T* 
   __shared__ double sh[32];
   __shared__ double total;
   if (s->done) return;
+  const T cd = T(s->cdiag);
   double acc = 0.0;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const T qs = q[e] + q2[e] + q3[e];
+    const T qs = q[e] + q2[e] + q3[e] + cd * d[e];
     q[e] = qs;
     acc += double(d[e] * qs);
   }
@@ -366,7 +369,7 @@ __global__ void k_cg_direction(T* __restrict__ d, const T* __restrict__ r, int64
 // initial scalars: rr = bb = b.b, sumd = sum b, stop = tol^2 bb
 template <typename T>
 __global__ void k_cg_init(const T* __restrict__ b, int64_t n, CGScalars* s, double tol2, double rank1,
-                          double* __restrict__ partial) {
+                          double cdiag, double* __restrict__ partial) {
   __shared__ double sh[32];
   double a0 = 0.0, a1 = 0.0;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
@@ -400,6 +403,7 @@ __global__ void k_cg_init(const T* __restrict__ b, int64_t n, CGScalars* s, doub
     s->sumd = s1;
     s->stop = tol2 * s0;
     s->rank1 = rank1;
+    s->cdiag = cdiag;
     s->done = (s0 > s->stop) ? 0 : 1;
     s->iters = 0;
     s->ticket[0] = 0u;
@@ -407,6 +411,13 @@ __global__ void k_cg_init(const T* __restrict__ b, int64_t n, CGScalars* s, doub
 }
 
 // --------------------------------------------------------- vector helpers
+// y += a x
+__global__ void k_axpy(const double* __restrict__ x, double a, double* __restrict__ y, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    y[e] += a * x[e];
+}
+
 // out = b1 + b2 + b3
 template <typename T>
 __global__ void k_sum3(const T* __restrict__ b1, const T* __restrict__ b2, const T* __restrict__ b3,

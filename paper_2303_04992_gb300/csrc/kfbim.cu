@@ -38,6 +38,8 @@ struct kfbim_ctx {
   int N = 0, lg = 0;   // lg = log2 N
   int64_t N3 = 0, n_all = 0, n_prim = 0, n_corr_rows = 0;
   double h = 0, mu = 1;
+  bool navier = false;
+  double cpen = 0.0;   // c = 1/(lambda + mu) of the Navier continuity row, 0 for Stokes
   std::vector<void*> allocs;
   // tables
   int32_t *d_comp = nullptr, *d_pid = nullptr, *d_fit_col = nullptr, *d_tr_comp = nullptr,
@@ -402,7 +404,8 @@ int cg(kfbim_ctx* c, const T* b, const CgWs<T>& w, double tol, int maxit, cudaSt
   CK(cudaMemsetAsync(w.x, 0, n * sizeof(T), s));
   CK(cudaMemcpyAsync(w.r, b, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
   CK(cudaMemcpyAsync(w.d, b, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
-  k_cg_init<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(b, n, c->cgs, tol * tol, 1.0 / (c->mu * (double)n),
+  const double rank1 = c->navier ? 0.0 : 1.0 / (c->mu * (double)n);
+  k_cg_init<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(b, n, c->cgs, tol * tol, rank1, c->cpen,
                                                    c->partial);
   ++g_launches;
   check_launch();
@@ -459,7 +462,8 @@ int grid_solve_mixed(kfbim_ctx* c, cudaStream_t s) {
   double* sc = c->scal + 5;
   CK(cudaMemsetAsync(c->u, 0, 3 * N3 * sizeof(double), s));
   CK(cudaMemsetAsync(c->p, 0, N3 * sizeof(double), s));
-  dot(c, g, (const double*)nullptr, N3, gmean, 1.0 / (double)N3, s);
+  if (c->navier) CK(cudaMemsetAsync(gmean, 0, sizeof(double), s));
+  else dot(c, g, (const double*)nullptr, N3, gmean, 1.0 / (double)N3, s);
   // u = p = 0: the first residual is [f; g - mean g] (no stencil needed)
   CK(cudaMemcpyAsync(resf, f, 3 * N3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
   CK(cudaMemcpyAsync(resg, g, N3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -471,7 +475,7 @@ int grid_solve_mixed(kfbim_ctx* c, cudaStream_t s) {
   int status = KFBIM_OK;
   for (int sweep = 0;; ++sweep) {
     if (sweep > 0) {
-      k_mac_residual<<<grid_for(4 * N3), 256, 0, s>>>(f, g, gmean, c->u, c->p, c->lg, c->h, c->mu, resf, resg); ++g_launches;
+      k_mac_residual<<<grid_for(4 * N3), 256, 0, s>>>(f, g, gmean, c->u, c->p, c->lg, c->h, c->mu, c->cpen, resf, resg); ++g_launches;
       check_launch();
       dot(c, resf, resf, 4 * N3, sc, 1.0, s);
       const double r2 = read_scalar(c, sc, s);
@@ -498,6 +502,7 @@ int grid_solve_mixed(kfbim_ctx* c, cudaStream_t s) {
     k_add_to<float><<<grid_for(3 * N3), 256, 0, s>>>(c->fu, c->u, 3 * N3); ++g_launches;
     check_launch();
   }
+  if (c->navier) return status;
   // gauge: mean(p) = mu * mean(g)  (the lambda_h system with gamma = 1, alpha = mu N^3)
   dot(c, c->p, (const double*)nullptr, N3, sc, 1.0 / (double)N3, s);
   k_shift<<<grid_for(N3), 256, 0, s>>>(c->p, sc, -1.0, N3); ++g_launches;
@@ -852,6 +857,8 @@ void kfbim_default_options(kfbim_options* o) {
   o->refine_tol = 1e-11;
   o->refine_max = 8;
   o->inner_tol = 3e-6;
+  o->pde = KFBIM_STOKES;
+  o->lambda = 0.0;
 }
 
 static int setup_common(const kfbim_geometry* geom, const kfbim_grid* grid, const kfbim_options* opt,
@@ -865,6 +872,9 @@ static int setup_common(const kfbim_geometry* geom, const kfbim_grid* grid, cons
       (opt->precision != KFBIM_FP64 && opt->precision != KFBIM_MIXED))
     return KFBIM_E_INVALID;
   if (geom->kind < 0 || geom->kind > 2) return KFBIM_E_INVALID;
+  if (opt->pde != KFBIM_STOKES && opt->pde != KFBIM_NAVIER) return KFBIM_E_INVALID;
+  if (opt->pde == KFBIM_NAVIER && !(opt->lambda >= 0.0 && opt->lambda + opt->mu > 0.0))
+    return KFBIM_E_INVALID;
   std::unique_ptr<kfbim_ctx> c(new (std::nothrow) kfbim_ctx());
   if (!c) return KFBIM_E_OOM;
   c->opt = *opt;
@@ -873,10 +883,12 @@ static int setup_common(const kfbim_geometry* geom, const kfbim_grid* grid, cons
   c->N3 = (int64_t)N * N * N;
   c->h = (grid->hi - grid->lo) / N;
   c->mu = opt->mu;
+  c->navier = opt->pde == KFBIM_NAVIER;
+  c->cpen = c->navier ? 1.0 / (opt->lambda + opt->mu) : 0.0;
   std::string err;
   int st;
   try {
-    st = build_tables(*geom, *grid, opt->mu, c->host, err);
+    st = build_tables(*geom, *grid, opt->mu, c->navier ? opt->lambda : -1.0, c->host, err);
   } catch (const std::bad_alloc&) {
     return KFBIM_E_OOM;
   }
@@ -1037,6 +1049,12 @@ int kfbim_schur_apply(kfbim_ctx* c, const double* d, double* q, void* stream) {
     schur_apply3<double>(c, d, w.q, w.q2, w.q3, w.T6, s);
     k_sum3<double><<<grid_for(c->N3), 256, 0, s>>>(w.q, w.q2, w.q3, q, c->N3);
     ++g_launches;
+    if (c->navier) {
+      k_axpy<<<grid_for(c->N3), 256, 0, s>>>(d, c->cpen, q, c->N3);
+      ++g_launches;
+      check_launch();
+      return KFBIM_OK;
+    }
     dot(c, d, (const double*)nullptr, c->N3, c->scal, 1.0 / (c->mu * (double)c->N3), s);
     k_shift<<<grid_for(c->N3), 256, 0, s>>>(q, c->scal, 1.0, c->N3); ++g_launches;
     check_launch();

@@ -13,6 +13,9 @@
 //     [sigma n] = 0 and the 21 second-order relations (tangential second
 //     derivatives of [u] = phi on the curved surface, grad [div u] = 0,
 //     the momentum jump IUS-1 and the tangential derivative of IUS-4);
+//   * Navier (Lame): c = 1/(lambda + mu) enters grad [div u + c p] = 0 and the
+//     elastic traction -kappa p I + mu (grad u + grad u^T), kappa = lambda c;
+//     first order A n = -(lambda/(lambda + 2 mu)) D n - ..., q = -(lambda + mu) tr A;
 //   * the right-hand-side correction matrix (Sec. 4.3 items 1-4, one rule
 //     C_P += a_PQ chi_Q J(Q) for every stencil neighbour Q across Gamma);
 //   * the ten-node quadratic interpolation rows of the trace (Sec. 4.4).
@@ -192,25 +195,29 @@ Frame make_frame(const Level& lev, const double* x) {
 }
 
 // First-order jumps A (3x3, A[c][j] = [d_j u^(c)]) and q = [p] from the
-// tangential derivatives dphi[c][a] of the density components.
-void first_order(const Frame& f, const double dphi[3][2], double mu, double A[3][3], double* q) {
+// tangential derivatives dphi[c][a] of the density components (lam < 0: Stokes).
+void first_order(const Frame& f, const double dphi[3][2], double mu, double lam, double A[3][3],
+                 double* q) {
   double D = 0;
   for (int a = 0; a < 2; ++a)
     for (int c = 0; c < 3; ++c) D += f.t[a][c] * dphi[c][a];
   double nd[2] = {0, 0};
   for (int a = 0; a < 2; ++a)
     for (int c = 0; c < 3; ++c) nd[a] += f.n[c] * dphi[c][a];
+  const double Ann = lam < 0 ? -D : -D * lam / (lam + 2.0 * mu);
   double An[3];
-  for (int c = 0; c < 3; ++c) An[c] = -D * f.n[c] - nd[0] * f.t[0][c] - nd[1] * f.t[1][c];
+  for (int c = 0; c < 3; ++c) An[c] = Ann * f.n[c] - nd[0] * f.t[0][c] - nd[1] * f.t[1][c];
   for (int c = 0; c < 3; ++c)
     for (int j = 0; j < 3; ++j)
       A[c][j] = dphi[c][0] * f.t[0][j] + dphi[c][1] * f.t[1][j] + An[c] * f.n[j];
-  *q = -2.0 * mu * D;
+  *q = lam < 0 ? -2.0 * mu * D : -(lam + mu) * (Ann + D);
 }
 
 // The 21 x 21 second-order system on x = (H^(1), H^(2), H^(3), s).
-void second_order_matrix(const Frame& f, double mu, double* L) {
+void second_order_matrix(const Frame& f, double mu, double lam, double* L) {
   std::memset(L, 0, sizeof(double) * 21 * 21);
+  const double cpen = lam < 0 ? 0.0 : 1.0 / (lam + mu);
+  const double kap = lam < 0 ? 1.0 : lam / (lam + mu);
   int row = 0;
   const int ab[3][2] = {{0, 0}, {0, 1}, {1, 1}};
   for (int c = 0; c < 3; ++c)
@@ -218,8 +225,10 @@ void second_order_matrix(const Frame& f, double mu, double* L) {
       for (int k = 0; k < 3; ++k)
         for (int l = 0; l < 3; ++l)
           L[row * 21 + 6 * c + hidx(k, l)] += f.t[ab[q][0]][k] * f.t[ab[q][1]][l];
-  for (int j = 0; j < 3; ++j, ++row)
+  for (int j = 0; j < 3; ++j, ++row) {
     for (int c = 0; c < 3; ++c) L[row * 21 + 6 * c + hidx(c, j)] += 1.0;
+    L[row * 21 + 18 + j] += cpen;
+  }
   for (int c = 0; c < 3; ++c, ++row) {
     for (int k = 0; k < 3; ++k) L[row * 21 + 6 * c + hidx(k, k)] += -mu;
     L[row * 21 + 18 + c] += 1.0;
@@ -227,7 +236,7 @@ void second_order_matrix(const Frame& f, double mu, double* L) {
   for (int a = 0; a < 2; ++a)
     for (int i = 0; i < 3; ++i, ++row)
       for (int j = 0; j < 3; ++j) {
-        L[row * 21 + 18 + j] += -f.t[a][j] * f.n[i];
+        L[row * 21 + 18 + j] += -kap * f.t[a][j] * f.n[i];
         for (int k = 0; k < 3; ++k) {
           L[row * 21 + 6 * i + hidx(k, j)] += mu * f.t[a][j] * f.n[k];
           L[row * 21 + 6 * k + hidx(i, j)] += mu * f.t[a][j] * f.n[k];
@@ -236,7 +245,8 @@ void second_order_matrix(const Frame& f, double mu, double* L) {
 }
 
 void second_order_rhs(const Frame& f, const double A[3][3], double q, const double d2[3][3],
-                      const double* fy, double mu, double* rhs) {
+                      const double* fy, double mu, double lam, double* rhs) {
+  const double kap = lam < 0 ? 1.0 : lam / (lam + mu);
   double An[3];
   for (int c = 0; c < 3; ++c) An[c] = A[c][0] * f.n[0] + A[c][1] * f.n[1] + A[c][2] * f.n[2];
   int row = 0;
@@ -247,7 +257,7 @@ void second_order_rhs(const Frame& f, const double A[3][3], double q, const doub
   for (int c = 0; c < 3; ++c) rhs[row++] = fy[c];
   double sig[3][3];
   for (int i = 0; i < 3; ++i)
-    for (int k = 0; k < 3; ++k) sig[i][k] = (i == k ? -q : 0.0) + mu * (A[i][k] + A[k][i]);
+    for (int k = 0; k < 3; ++k) sig[i][k] = (i == k ? -kap * q : 0.0) + mu * (A[i][k] + A[k][i]);
   for (int a = 0; a < 2; ++a) {
     double dn[3];
     for (int k = 0; k < 3; ++k) dn[k] = f.K[a][0] * f.t[0][k] + f.K[a][1] * f.t[1][k];
@@ -263,8 +273,8 @@ inline int64_t flat(int N, int i, int j, int k) { return ((int64_t)k * N + j) * 
 
 }  // namespace
 
-int build_tables(const kfbim_geometry& geom, const kfbim_grid& grid, double mu, HostTables& t,
-                 std::string& err) {
+int build_tables(const kfbim_geometry& geom, const kfbim_grid& grid, double mu, double lam,
+                 HostTables& t, std::string& err) {
   const int N = grid.N;
   t.N = N;
   t.lo = grid.lo;
@@ -468,7 +478,7 @@ int build_tables(const kfbim_geometry& geom, const kfbim_grid& grid, double mu, 
     const Frame& f = fr[y];
     double L[21 * 21];
     int piv[21];
-    second_order_matrix(f, mu, L);
+    second_order_matrix(f, mu, lam, L);
     if (!lu_factor(L, 21, piv)) {
       err = "singular jump system";
       return KFBIM_E_GEOMETRY;
@@ -485,9 +495,9 @@ int build_tables(const kfbim_geometry& geom, const kfbim_grid& grid, double mu, 
         fy[cc] = in[15 + cc];
       }
       double A[3][3], q;
-      first_order(f, dphi, mu, A, &q);
+      first_order(f, dphi, mu, lam, A, &q);
       double x[21];
-      second_order_rhs(f, A, q, d2, fy, mu, x);
+      second_order_rhs(f, A, q, d2, fy, mu, lam, x);
       lu_solve(L, 21, piv, x);
       double out[kMapOut];
       for (int k = 0; k < 3; ++k) out[k] = A[c][k];

@@ -187,31 +187,33 @@ __device__ void xform2(T* Rb, C2<T>* Xb, C2<T>* Zb, const C2<T>* tw, const C2<T>
       }
     }
     __syncthreads();
-    // post-processing: the PPR pairs of this round -> staged real lines
-    for (int e = tid; e < PPR * 2 * N; e += PASS2_THREADS) {
-      const int lr = e / N, o = e - lr * N;       // line within round, output index
-      const int pr = lr >> 1;
+    // post-processing: the PPR pairs of this round -> staged real lines; one
+    // pass over (pair, index) yields the outputs of both lines of the pair
+    for (int e = tid; e < PPR * N; e += PASS2_THREADS) {
+      const int pr = e / N, o = e - pr * N;       // pair within round, output index
       const C2<T>* Z = Zb + pr * L;
-      const bool lineB = lr & 1;
-      T val;
+      T* RA = Rb + (round * 2 * PPR + 2 * pr) * RS;
+      T* RB = RA + RS;
       if constexpr (KIND == 2) {
         const T sc = INV ? T(1) / T(N) : T(0.5);
-        val = (o == 0) ? T(0) : (lineB ? Z[o].x * sc : -Z[o].y * sc);
+        const C2<T> z = Z[o];
+        RA[o] = (o == 0) ? T(0) : -z.y * sc;
+        RB[o] = (o == 0) ? T(0) : z.x * sc;
       } else if constexpr (!INV) {
         const int k = (KIND == 1) ? (N - 1 - o) : o;
         const C2<T> zk = Z[k], zc = Z[(N - k) & (N - 1)];
-        C2<T> V;
-        if (!lineB) V = {T(0.5) * (zk.x + zc.x), T(0.5) * (zk.y - zc.y)};
-        else V = {T(0.5) * (zk.y + zc.y), T(-0.5) * (zk.x - zc.x)};
+        const C2<T> VA = {T(0.5) * (zk.x + zc.x), T(0.5) * (zk.y - zc.y)};
+        const C2<T> VB = {T(0.5) * (zk.y + zc.y), T(-0.5) * (zk.x - zc.x)};
         const C2<T> q = qN[k];
-        val = q.x * V.x - q.y * V.y;
+        RA[o] = q.x * VA.x - q.y * VA.y;
+        RB[o] = q.x * VB.x - q.y * VB.y;
       } else {
         const int n = (o & 1) ? (N - 1 - (o >> 1)) : (o >> 1);
         const C2<T> z = Z[n];
-        val = (lineB ? z.y : z.x) * (T(1) / T(N));
-        if (KIND == 1 && (o & 1)) val = -val;
+        const T sc = (KIND == 1 && (o & 1)) ? -T(1) / T(N) : T(1) / T(N);
+        RA[o] = z.x * sc;
+        RB[o] = z.y * sc;
       }
-      Rb[(round * 2 * PPR + lr) * RS + o] = val;
     }
     __syncthreads();
   }

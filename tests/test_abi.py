@@ -44,6 +44,17 @@ def test_host_setup_matches_oracle_points():
         s.close()
 
 
+def test_host_setup_navier_matches_oracle_points():
+    geom = ki.ellipsoid((0.6, 0.45, 0.35), ki.seeded_rotation(3))
+    s = Solver(geom, ki.grid(32), device=False, lam=2.0)
+    o = okfbim.Setup(geom, ki.grid(32), lam=2.0)
+    _, comp, _, prim = s.points()
+    assert np.array_equal(prim, o.primary) and np.array_equal(comp, o.cp.comp)
+    with __import__("pytest").raises(KfbimError):
+        Solver(geom, ki.grid(32), device=False, lam=-3.0)   # lambda + mu <= 0
+    s.close()
+
+
 def test_host_setup_rejects_bad_geometry():
     import pytest
     with pytest.raises(KfbimError) as e:

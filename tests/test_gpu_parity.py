@@ -175,3 +175,74 @@ def test_solve_mixed_sphere32():
     for c in range(3):
         assert rel(ug[c], want["u"][c]) < 1e-8
     assert rel(p.cpu().numpy().reshape(N, N, N), want["p"]) < 1e-8
+
+
+# ------------------------------------------------------------------ Navier
+ELL = ki.ellipsoid((0.6, 0.45, 0.35), ki.seeded_rotation(3))
+
+
+def _navier_pair(N=32):
+    key = "navier_ell%d" % N
+    if key not in _ORACLE:
+        _ORACLE[key] = okfbim.Setup(ELL, ki.grid(N), mu=ki.LAME_MU, lam=ki.LAME_LAMBDA)
+    return _ORACLE[key]
+
+
+def _lame_inputs(o):
+    x = o.cp.xyz
+    rows = np.arange(o.cp.n)
+    g = ki.lame_displacement(x)[rows, o.cp.comp - 1][o.primary]
+    fy = ki.lame_forcing(x)
+    ff = [ki.lame_forcing(o.grid.node_xyz(c, o.grid.all_idx()))[..., c - 1] for c in (1, 2, 3)]
+    return g, fy, ff
+
+
+def test_navier_jumps_and_apply():
+    o = _navier_pair()
+    rng = np.random.default_rng(21)
+    phi = rng.standard_normal(o.n)
+    fy = rng.standard_normal((o.cp.n, 3))
+    want_J = ojumps.jumps(o.jd, phi, fy, ki.LAME_MU, ki.LAME_LAMBDA)
+    want = o.apply(phi)
+    for prec, tol in ((0, 1e-10), (MIXED, 1e-8)):
+        s = Solver(ELL, ki.grid(32), mu=ki.LAME_MU, lam=ki.LAME_LAMBDA, precision=prec)
+        J = torch.zeros(12 * s.n_points, dtype=torch.float64, device="cuda")
+        s.jumps(cuda(phi), J, cuda(fy.T.copy()))
+        got = J.cpu().numpy().reshape(12, s.n_points).T
+        for k in range(12):
+            assert rel(got[:, k], want_J[:, k]) < 1e-11, k
+        out = torch.zeros(s.n_primary, dtype=torch.float64, device="cuda")
+        s.apply(cuda(phi), out)
+        assert rel(out.cpu().numpy(), want) < tol, prec
+        s.close()
+
+
+def test_navier_schur_apply():
+    o = _navier_pair()
+    N = 32
+    d = np.random.default_rng(22).standard_normal((N, N, N))
+    want = mac.schur_apply(d, ki.LAME_MU, o.grid.h, ki.LAME_MU * N ** 3, o.cpen)
+    s = Solver(ELL, ki.grid(N), mu=ki.LAME_MU, lam=ki.LAME_LAMBDA)
+    got = s.schur_apply(cuda(d), torch.zeros(N ** 3, dtype=torch.float64, device="cuda"))
+    assert rel(got.cpu().numpy().reshape(N, N, N), want) < 1e-12
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (MIXED, 1e-8)])
+def test_navier_solve(prec, tol):
+    o = _navier_pair()
+    g, fy, ff = _lame_inputs(o)
+    key = "navier_solution"
+    if key not in _ORACLE:
+        _ORACLE[key] = o.solve(g, fy, ff)
+    want = _ORACLE[key]
+    N = 32
+    s = Solver(ELL, ki.grid(N), mu=ki.LAME_MU, lam=ki.LAME_LAMBDA, precision=prec)
+    phi = torch.zeros(s.n_primary, dtype=torch.float64, device="cuda")
+    u = torch.zeros(3 * N ** 3, dtype=torch.float64, device="cuda")
+    p = torch.zeros(N ** 3, dtype=torch.float64, device="cuda")
+    s.solve(cuda(g), phi, cuda(fy.T.copy()), cuda(np.concatenate([f.ravel() for f in ff])), u, p)
+    assert rel(phi.cpu().numpy(), want["phi"]) < tol
+    ug = u.cpu().numpy().reshape(3, N, N, N)
+    for c in range(3):
+        assert rel(ug[c], want["u"][c]) < tol
+    assert rel(p.cpu().numpy().reshape(N, N, N), want["p"]) < 10 * tol

@@ -167,3 +167,70 @@ def test_primary_points_cover_each_direction_once():
         assert prim[m] == (np.argmax(np.abs(n[m])) == cp.axis[m]) or \
             abs(abs(n[m, cp.axis[m]]) - np.abs(n[m]).max()) < 1e-12
     assert 0.3 < prim.mean() < 0.8
+
+
+# ---- Navier (Lame): traction-free polynomial displacements on the sphere ----
+LAM = 2.0
+
+
+def navier_traction_free_family():
+    """Null space of {(lambda div w I + mu (grad w + grad w^T)) n = 0 on |x| = R}
+    over cubic displacements w (the auxiliary p = -(lambda + mu) div w)."""
+    rng = np.random.default_rng(1)
+    nw = len(MW)
+    S = rng.standard_normal((240, 3))
+    S = R * S / np.linalg.norm(S, axis=1)[:, None]
+    n = S / R
+    rows = []
+    for i in range(3):
+        T = np.zeros((len(S), 3 * nw))
+        for c in range(3):     # lambda div w n_i
+            T[:, c * nw:(c + 1) * nw] += LAM * _mono_vals(MW, S, tuple(int(k == c) for k in range(3))) * n[:, i:i + 1]
+        for k in range(3):
+            T[:, i * nw:(i + 1) * nw] += MU * _mono_vals(MW, S, tuple(int(m == k) for m in range(3))) * n[:, k:k + 1]
+            T[:, k * nw:(k + 1) * nw] += MU * _mono_vals(MW, S, tuple(int(m == i) for m in range(3))) * n[:, k:k + 1]
+        rows.append(T)
+    M = np.vstack(rows)
+    _, s, vt = np.linalg.svd(M)
+    return vt[np.sum(s > 1e-10 * s[0]):]
+
+
+@pytest.mark.parametrize("member", [0, 5])
+def test_navier_jump_relations_exact_on_traction_free_pairs(member):
+    null = navier_traction_free_family()
+    assert null.shape[0] >= 6
+    rng = np.random.default_rng(member)
+    coefw = rng.standard_normal(null.shape[0]) @ null
+    coef = np.concatenate([coefw, np.zeros(len(MP))])
+    d = rng.standard_normal((25, 3))
+    y = R * d / np.linalg.norm(d, axis=1)[:, None]
+    n, T, K = geometry.frames(ki.sphere(R), y)
+    w, gw, hw, _, _, _ = jets(coef, y)
+    pi = -(LAM + MU) * np.einsum("ncc->n", gw)
+    gpi = -(LAM + MU) * np.einsum("ncjc->nj", hw)
+    f = -MU * np.einsum("ncjj->nc", hw) + gpi
+    d1 = np.einsum("ncj,naj->nca", gw, T)
+    gn = np.einsum("ncj,nj->nc", gw, n)
+    d2 = np.zeros((len(y), 3, 3))
+    for m, (a, b) in enumerate([(0, 0), (0, 1), (1, 1)]):
+        d2[:, :, m] = np.einsum("ncjl,nj,nl->nc", hw, T[:, a], T[:, b]) - K[:, a, b][:, None] * gn
+    A, q = jumps.first_order(n, T, d1, MU, LAM)
+    assert np.abs(A - gw).max() < 1e-10 * max(1.0, np.abs(gw).max())
+    assert np.abs(q - pi).max() < 1e-10 * max(1.0, np.abs(pi).max())
+    L = jumps.second_order_system(n, T, K, MU, LAM)
+    rhs = jumps.second_order_rhs(n, T, K, A, q, d2, f, MU, LAM)
+    x = np.linalg.solve(L, rhs[..., None])[..., 0]
+    for c in range(3):
+        for m, (k, l) in enumerate(jumps.SYM):
+            assert np.abs(x[:, 6 * c + m] - hw[:, c, k, l]).max() < 1e-9 * max(1.0, np.abs(hw).max())
+    assert np.abs(x[:, 18:] - gpi).max() < 1e-9 * max(1.0, np.abs(gpi).max())
+
+
+def test_navier_second_order_system_full_rank():
+    rng = np.random.default_rng(2)
+    for _ in range(4):
+        Q, _ = np.linalg.qr(rng.standard_normal((3, 3)))
+        K = rng.standard_normal((1, 2, 2))
+        K = K + np.swapaxes(K, 1, 2)
+        L = jumps.second_order_system(Q[:, 0][None], np.stack([Q[:, 1], Q[:, 2]])[None], K, MU, LAM)[0]
+        assert np.linalg.matrix_rank(L) == 21

@@ -84,3 +84,29 @@ def test_gmres_on_random_matrix():
     x, it, hist = kfbim.gmres(lambda v: A @ v, b, tol=1e-13)
     assert np.abs(A @ x - b).max() < 1e-11
     assert hist[-1] < 1e-13
+
+
+def test_navier_constant_density_and_convergence():
+    """Navier (Lame, mu = 1, lambda = 2): constant densities are reproduced
+    exactly; the manufactured displacement exp(x+y+z) sin(i+xy) converges at
+    second order with bounded GMRES counts."""
+    errs, its = [], []
+    for N in (16, 32):
+        s = kfbim.Setup(ki.sphere(), ki.grid(N), mu=ki.LAME_MU, lam=ki.LAME_LAMBDA)
+        phi = _const_density(s)
+        assert np.abs(s.apply(phi) - phi).max() < 1e-12
+        rows = np.arange(s.cp.n)
+        g = ki.lame_displacement(s.cp.xyz)[rows, s.cp.comp - 1][s.primary]
+        fy = ki.lame_forcing(s.cp.xyz)
+        ff = [ki.lame_forcing(s.grid.node_xyz(c, s.grid.all_idx()))[..., c - 1] for c in (1, 2, 3)]
+        r = s.solve(g, fy, ff)
+        e = 0.0
+        for c in (1, 2, 3):
+            X = s.grid.node_xyz(c, s.grid.all_idx())
+            m = s.S[c] & s.grid.unknown_mask(c)
+            ue = ki.lame_displacement(X)[..., c - 1]
+            e = max(e, np.abs(r["u"][c - 1] - ue)[m].max() / np.abs(ue[m]).max())
+        errs.append(e)
+        its.append(r["iters"])
+    assert errs[0] / errs[1] > 3.5
+    assert max(its) <= 25

@@ -165,13 +165,16 @@ def ncu_traffic(workload):
     return float(t.group(1))
 
 
-def inputs(solver, geom, grid):
-    """Manufactured Stokes data: g at the primary points, f at all points and
-    on the face grids (host numpy)."""
+def inputs(solver, geom, grid, navier=False):
+    """Manufactured data (Stokes velocity, or the Lame displacement for the
+    Navier workload): g at the primary points, f at all points and on the face
+    grids (host numpy)."""
+    vel = ki.lame_displacement if navier else ki.stokes_velocity
+    frc = ki.lame_forcing if navier else ki.stokes_forcing
     xyz, comp, _, prim = solver.points()
     rows = np.arange(len(comp))
-    g = ki.stokes_velocity(xyz)[rows, comp - 1][prim]
-    fpts = ki.stokes_forcing(xyz).T.copy()
+    g = vel(xyz)[rows, comp - 1][prim]
+    fpts = frc(xyz).T.copy()
     N, lo, h = solver.N, solver.lo, solver.h
     idx = np.arange(N)
     fg = []
@@ -180,7 +183,7 @@ def inputs(solver, geom, grid):
         off[c - 1] = 0.0
         Z, Y, X = np.meshgrid(lo + (idx + off[2]) * h, lo + (idx + off[1]) * h,
                               lo + (idx + off[0]) * h, indexing="ij")      # [k, j, i]
-        fg.append(ki.stokes_forcing(np.stack([X, Y, Z], -1))[..., c - 1].ravel())
+        fg.append(frc(np.stack([X, Y, Z], -1))[..., c - 1].ravel())
     return g, fpts, np.concatenate(fg)
 
 
@@ -216,14 +219,16 @@ def main_kfbim(args):
     if dist:
         dist.barrier()
     geom, grid = ki.WORKLOADS[args.workload]
+    navier = args.workload in ki.NAVIER_WORKLOADS
+    pde = {"mu": ki.LAME_MU, "lam": ki.LAME_LAMBDA} if navier else {}
     dev = torch.device("cuda", local)
     mixed_opts = {}
     if args.refine_tol is not None:
         mixed_opts["refine_tol"] = args.refine_tol
     if args.inner_tol is not None:
         mixed_opts["inner_tol"] = args.inner_tol
-    solver = Solver(geom, grid, precision=MIXED, **mixed_opts)
-    g_h, fpts_h, fgrid_h = inputs(solver, geom, grid)
+    solver = Solver(geom, grid, precision=MIXED, **mixed_opts, **pde)
+    g_h, fpts_h, fgrid_h = inputs(solver, geom, grid, navier)
     g = torch.from_numpy(g_h).to(dev)
     fpts = torch.from_numpy(fpts_h).to(dev)
     fgrid = torch.from_numpy(fgrid_h).to(dev)
@@ -302,7 +307,7 @@ def main_kfbim(args):
     fp64 = None
     rel = None
     if not args.no_fp64:
-        s64 = Solver(geom, grid, precision=FP64)
+        s64 = Solver(geom, grid, precision=FP64, **pde)
         phi64 = torch.zeros(s64.n_primary, dtype=torch.float64, device=dev)
         s64.solve(g, phi64, fpts, fgrid)
         torch.cuda.synchronize()
@@ -334,12 +339,16 @@ def main_kfbim(args):
 
     if rank == 0:
         st = stats[-1]
+        desc = WORKLOAD_DESC if not navier else (
+            "Navier (Lame mu=1, lambda=2) interior Dirichlet on the ellipsoid semi-axes "
+            "(0.6,0.45,0.35) under a seeded rotation in [-1,1]^3, MAC grid 128^3, manufactured "
+            "u_i=exp(x+y+z) sin(i+xy), GMRES tol 1e-10")
         line = {"metric": METRIC, "value": round(value, 4), "unit": "solves/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32+f64 (mixed: FP32 transforms/CG, FP64 jumps/residuals/GMRES)",
                 "data": "synthetic",
-                "config": {"workload": args.workload, "description": WORKLOAD_DESC,
+                "config": {"workload": args.workload, "description": desc,
                            "precision": "mixed", "l2_flush": "512 MiB write before each step",
                            "refine_tol": solver.options.refine_tol, "inner_tol": solver.options.inner_tol,
                            "n_points": solver.n_points, "n_unknowns": solver.n_primary,

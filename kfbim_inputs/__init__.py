@@ -55,7 +55,10 @@ WORKLOADS = {
     "sphere32": (sphere(), grid(32)),
     "star64": (star(), grid(64)),
     "star128": (star(), grid(128)),
+    # Navier (Lame mu = 1, lambda = 2) on the rotated ellipsoid; data: lame_*
+    "ell128_navier": (ellipsoid((0.6, 0.45, 0.35), seeded_rotation(3)), grid(128)),
 }
+NAVIER_WORKLOADS = {"ell128_navier"}
 
 
 # ------------------------------------------------- manufactured Stokes field

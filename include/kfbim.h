@@ -184,6 +184,32 @@ int kfbim_solve_host(kfbim_ctx* ctx, const double* g_host, const double* fpts_ho
                      const double* fgrid_host, double* phi_host, double* u_host,
                      double* p_host, kfbim_stats* stats, void* stream);
 
+/* Largest batch accepted by kfbim_solve_batch. */
+#define KFBIM_BATCH_MAX 64
+
+/* B independent solves (Alg. 1 steps 2-3) on the geometry and grid of ctx,
+ * for B sets of boundary data and forcing.  The paper solves one problem at
+ * a time; this is the many-right-hand-side form of the same solve.  Every
+ * array holds the B instances back to back, each with the shape kfbim_solve
+ * gives it: g_dev [B*n_primary], fpts_dev [B*3*n_points] (nullable),
+ * fgrid_dev [B*3*N^3] (nullable), phi_dev [B*n_primary], u_dev [B*3*N^3]
+ * (nullable), p_dev [B*N^3] (nullable), stats [B] (nullable; kernel_launches
+ * is the count of the whole call).  Instance b's result equals that of
+ * kfbim_solve on instance b up to rounding order (the same GMRES, refinement
+ * and CG iteration per instance).
+ * MIXED contexts run the instances in lockstep: every FFT stage is one launch
+ * for all instances still iterating, and GMRES reads its host scalars once
+ * per iteration for the whole batch.  FP64 contexts solve the instances one
+ * after another.  The first call with a larger B than before allocates the
+ * per-instance workspace (about 20 N^3 doubles-worth plus the Krylov basis of
+ * gmres_max + 1 vectors per instance); it is kept until kfbim_destroy.
+ * Errors: KFBIM_E_INVALID for B outside 1..KFBIM_BATCH_MAX or a null g/phi;
+ * KFBIM_E_NONFINITE if any instance meets NaN/Inf; KFBIM_E_NOCONV if any
+ * instance hit the GMRES cap (its stats entry says which). */
+int kfbim_solve_batch(kfbim_ctx* ctx, int B, const double* g_dev, const double* fpts_dev,
+                      const double* fgrid_dev, double* phi_dev, double* u_dev, double* p_dev,
+                      kfbim_stats* stats, void* stream);
+
 /* Per-kernel timing of the FFT transform passes (the dominant kernels).
  * enable = 1 starts (and zeroes) the counters, 0 stops them, -1 reads them:
  * total device milliseconds between CUDA events recorded around each launch,

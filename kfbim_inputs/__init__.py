@@ -118,6 +118,38 @@ def smooth_field(seed, degree=3):
     return field
 
 
+def harmonic_curl_field(seed, degree=6, scale=0.5):
+    """Seeded divergence-free boundary-data field u = curl A, A^(c) a random
+    solid-harmonic expansion of degree <= `degree` in x / scale.  Degree l
+    contributes 2l + 1 terms Re (v . x/scale)^l with isotropic null vectors
+    v = e1 + i e2 (e1, e2 orthonormal, seeded), each with an N(0,1)/(1+l)^2
+    coefficient; such powers span the degree-l solid harmonics.  The curl
+    makes the net flux through any closed surface zero, the solvability
+    condition of interior Stokes Dirichlet data.  Returns x -> (..., 3)."""
+    rng = np.random.default_rng(seed)
+    terms = []                                   # (component, l, v, coefficient)
+    for comp in range(3):
+        for l in range(1, degree + 1):           # l = 0 is constant: no curl
+            for _ in range(2 * l + 1):
+                q, _r = np.linalg.qr(rng.standard_normal((3, 3)))
+                v = q[:, 0] + 1j * q[:, 1]
+                terms.append((comp, l, v, rng.standard_normal() / (1.0 + l) ** 2))
+
+    def field(x):
+        x = np.asarray(x, dtype=np.float64) / scale
+        dA = np.zeros(x.shape[:-1] + (3, 3))      # dA[..., c, j] = d_j A^(c) (per unit x/scale)
+        for comp, l, v, a in terms:
+            w = (x @ v) ** (l - 1)
+            dA[..., comp, :] += a * l * np.real(w[..., None] * v)
+        out = np.empty(x.shape[:-1] + (3,))
+        out[..., 0] = dA[..., 2, 1] - dA[..., 1, 2]
+        out[..., 1] = dA[..., 0, 2] - dA[..., 2, 0]
+        out[..., 2] = dA[..., 1, 0] - dA[..., 0, 1]
+        return out / scale
+
+    return field
+
+
 # ------------------------------ paper Example 5.1 (sphere r = 1, box +-1.2)
 def example51_velocity(x):
     """Example 5.1's velocity with u^(2)'s y^2(1 - y^2) read as y^2(2 - y^2):

@@ -60,6 +60,8 @@ SYMBOLS = {
                             ctypes.POINTER(Stats), c_void_p]),
     "kfbim_solve_host": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                  c_void_p, ctypes.POINTER(Stats), c_void_p]),
+    "kfbim_solve_batch": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                  c_void_p, ctypes.POINTER(Stats), c_void_p]),
     "kfbim_jumps": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "kfbim_interface": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "kfbim_trace": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
@@ -227,6 +229,17 @@ class Solver:
                                                _np_ptr(phi), _np_ptr(u), _np_ptr(p), ctypes.byref(st),
                                                self._stream()))
         self.last_stats = {k: getattr(st, k) for k, _ in Stats._fields_}
+        return phi
+
+    def solve_batch(self, g, phi, fpts=None, fgrid=None, u=None, p=None):
+        """B solves in one call: g, phi are (B, n_primary) device tensors, fpts
+        (B, 3 n_points), fgrid (B, 3 N^3), u (B, 3 N^3), p (B, N^3); each
+        contiguous.  last_stats becomes a list of B dicts."""
+        B = int(g.shape[0])
+        st = (Stats * B)()
+        self._check(self._lib.kfbim_solve_batch(self._ctx, B, _ptr(g), _ptr(fpts), _ptr(fgrid), _ptr(phi),
+                                                _ptr(u), _ptr(p), st, self._stream()))
+        self.last_stats = [{k: getattr(st[b], k) for k, _ in Stats._fields_} for b in range(B)]
         return phi
 
     def jumps(self, phi, J, fpts=None):

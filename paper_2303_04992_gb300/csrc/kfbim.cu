@@ -89,6 +89,18 @@ struct kfbim_ctx {
   std::vector<int> prof_tag;           // precision slot of each event pair
   double prof_bytes[2] = {0, 0};       // algorithmic bytes moved by those launches
   int64_t fit_nnz = 0, corr_nnz = 0;
+  // batch of instances on this geometry (kfbim_solve_batch), allocated on demand
+  struct Slot {
+    double *J, *rhs, *u, *p, *res, *grhs, *V, *gw, *gh, *gy;
+    float *x, *r, *d, *q, *q2, *q3, *T6, *fu;
+  };
+  std::vector<Slot> bs;
+  CGScalars* bcgs = nullptr;   // one per slot, contiguous
+  double* bscal = nullptr;     // 8 per slot, contiguous
+  double* bgh = nullptr;       // (bm + 1) per slot, contiguous (slot.gh points into it)
+  void* bpinned = nullptr;     // host staging of bcgs / bscal / bgh
+  int bcap = 0, bm = 0;
+  std::vector<int> b_cg, b_sweeps, b_isolves;   // per-slot counters of the current call
   // counters of the current call
   int cg_iters = 0, refine_sweeps = 0, interface_solves = 0;
 };
@@ -97,6 +109,7 @@ namespace {
 
 struct CudaError {
   std::string msg;
+  int code = KFBIM_E_CUDA;
 };
 
 #define CK(call)                                                                   \
@@ -152,10 +165,12 @@ struct Tw<float> {
   static const float* s2(kfbim_ctx* c) { return c->d_s2f; }
 };
 
-template <typename Tin, typename T, typename Tout, int N>
-void launch_pass2(kfbim_ctx* c, const PassJobs<Tin, Tout>& jobs, int njobs, cudaStream_t s) {
+constexpr int kMaxJobs = 48;   // jobs per batched launch: 3 per instance, 16 instances
+
+template <typename Tin, typename T, typename Tout, int N, int MAXJ>
+void launch_pass2(kfbim_ctx* c, const PassJobs<Tin, Tout, MAXJ>& jobs, int njobs, cudaStream_t s) {
   const size_t smem = Pass2Smem<T, N>::bytes;
-  auto kern = k_axis_pass2<Tin, T, Tout, N>;
+  auto kern = k_axis_pass2<Tin, T, Tout, N, MAXJ>;
   static size_t configured = 0;
   if (smem > configured) {
     CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -166,47 +181,62 @@ void launch_pass2(kfbim_ctx* c, const PassJobs<Tin, Tout>& jobs, int njobs, cuda
 }
 
 // One transform pass of a stage: input, output, axis, first transform,
-// second transform, spectral weight, weight component, accumulate flag.
+// second transform, spectral weight, weight component, accumulate flag, and
+// the done flag of the CG run the pass belongs to (nullable).
 struct Job {
   const void* in;
   void* out;
   int axis, t0, t1, wmode, wc, acc;
+  const int* skip = nullptr;
 };
 
 void prof_collect(kfbim_ctx* c);
 
-// Launch up to three independent passes (one launch on the compile-time-N
-// kernel, one launch per job otherwise).
+template <typename Tin, typename Tout>
+PassJob<Tin, Tout> make_job(kfbim_ctx* c, const Job& j, const int* skip) {
+  PassArgs a{};  // value-initialised: every field, skip included, starts at zero
+  a.N = c->N;
+  a.axis = j.axis;
+  a.type0 = j.t0;
+  a.type1 = j.t1;
+  a.wmode = j.wmode;
+  a.wc = j.wc;
+  for (int b = 0; b < 3; ++b) a.kind[b] = (b == j.wc) ? 0 : 1;
+  a.mu = c->mu;
+  a.h = c->h;
+  a.accumulate = j.acc;
+  a.scale = 1.0;
+  a.skip = j.skip ? j.skip : skip;
+  return {static_cast<const Tin*>(j.in), static_cast<Tout*>(j.out), a};
+}
+
+template <typename Tin, typename T, typename Tout, int MAXJ>
+void launch_jobs(kfbim_ctx* c, const Job* list, int nj, cudaStream_t s, const int* skip) {
+  PassJobs<Tin, Tout, MAXJ> jobs{};
+  for (int k = 0; k < nj; ++k) jobs.j[k] = make_job<Tin, Tout>(c, list[k], skip);
+  if (c->N == 128) launch_pass2<Tin, T, Tout, 128, MAXJ>(c, jobs, nj, s);
+  else if (c->N == 64) launch_pass2<Tin, T, Tout, 64, MAXJ>(c, jobs, nj, s);
+  else launch_pass2<Tin, T, Tout, 32, MAXJ>(c, jobs, nj, s);
+  ++g_launches;
+}
+
+// Launch a list of independent passes: up to 3 jobs per launch on the
+// compile-time-N kernel (48 for longer, batched lists), one launch per job on
+// the runtime-N kernel.
 template <typename Tin, typename T, typename Tout>
-void stage(kfbim_ctx* c, std::initializer_list<Job> list, cudaStream_t s, const int* skip = nullptr) {
-  PassJobs<Tin, Tout> jobs{};
-  int nj = 0;
+void stage_list(kfbim_ctx* c, const std::vector<Job>& list, cudaStream_t s, const int* skip = nullptr) {
   double bytes = 0.0;
-  for (const Job& j : list) {
-    PassArgs a{};  // value-initialised: every field, skip included, starts at zero
-    a.N = c->N;
-    a.axis = j.axis;
-    a.type0 = j.t0;
-    a.type1 = j.t1;
-    a.wmode = j.wmode;
-    a.wc = j.wc;
-    for (int b = 0; b < 3; ++b) a.kind[b] = (b == j.wc) ? 0 : 1;
-    a.mu = c->mu;
-    a.h = c->h;
-    a.accumulate = j.acc;
-    a.scale = 1.0;
-    a.skip = skip;
-    jobs.j[nj] = {static_cast<const Tin*>(j.in), static_cast<Tout*>(j.out), a};
-    bytes += (double)c->N3 * (sizeof(Tin) + sizeof(Tout) * (j.acc ? 2 : 1));
-    ++nj;
-  }
+  for (const Job& j : list) bytes += (double)c->N3 * (sizeof(Tin) + sizeof(Tout) * (j.acc ? 2 : 1));
   const bool prof = c->prof && c->prof_used + 2 <= (int)c->prof_ev.size();
   if (prof) CK(cudaEventRecord(c->prof_ev[c->prof_used], s));
+  const int nj = (int)list.size();
   if (c->N == 128 || c->N == 64 || c->N == 32) {
-    if (c->N == 128) launch_pass2<Tin, T, Tout, 128>(c, jobs, nj, s);
-    else if (c->N == 64) launch_pass2<Tin, T, Tout, 64>(c, jobs, nj, s);
-    else launch_pass2<Tin, T, Tout, 32>(c, jobs, nj, s);
-    ++g_launches;
+    if (nj <= 3) {
+      launch_jobs<Tin, T, Tout, 3>(c, list.data(), nj, s, skip);
+    } else {
+      for (int k0 = 0; k0 < nj; k0 += kMaxJobs)
+        launch_jobs<Tin, T, Tout, kMaxJobs>(c, list.data() + k0, std::min(kMaxJobs, nj - k0), s, skip);
+    }
   } else {
     const size_t smem = pass_smem_bytes(c->N, sizeof(T));
     auto kern = k_axis_pass<Tin, T, Tout>;
@@ -216,9 +246,9 @@ void stage(kfbim_ctx* c, std::initializer_list<Job> list, cudaStream_t s, const 
       configured = smem;
     }
     const int blocks = (int)((int64_t)c->N * c->N / LPC);
-    for (int k = 0; k < nj; ++k) {
-      kern<<<blocks, PASS_THREADS, smem, s>>>(jobs.j[k].in, jobs.j[k].out, jobs.j[k].a, Tw<T>::tw(c),
-                                             Tw<T>::q(c), c->d_s2);
+    for (const Job& j : list) {
+      const PassJob<Tin, Tout> pj = make_job<Tin, Tout>(c, j, skip);
+      kern<<<blocks, PASS_THREADS, smem, s>>>(pj.in, pj.out, pj.a, Tw<T>::tw(c), Tw<T>::q(c), c->d_s2);
       ++g_launches;
     }
   }
@@ -231,6 +261,11 @@ void stage(kfbim_ctx* c, std::initializer_list<Job> list, cudaStream_t s, const 
     c->prof_count[slot] += 1;
     c->prof_bytes[slot] += bytes;
   }
+}
+
+template <typename Tin, typename T, typename Tout>
+void stage(kfbim_ctx* c, std::initializer_list<Job> list, cudaStream_t s, const int* skip = nullptr) {
+  stage_list<Tin, T, Tout>(c, std::vector<Job>(list), s, skip);
 }
 
 // Fold recorded event pairs into the totals (the stream must be idle).
@@ -750,7 +785,7 @@ int guarded(kfbim_ctx* c, F&& f) {
   try {
     return f();
   } catch (const CudaError& e) {
-    return fail(c, KFBIM_E_CUDA, e.msg);
+    return fail(c, e.code, e.msg);
   } catch (const std::bad_alloc&) {
     return fail(c, KFBIM_E_OOM, "host allocation failed");
   }
@@ -841,6 +876,419 @@ void noalloc_pass(const NoAllocSymbols& d, int N, double h, const double* in, do
   k_axis_pass<double, double, double><<<(unsigned)(N * N / LPC), PASS_THREADS, smem, s>>>(
       in, out, a, d.tw, d.q, d.s2);
 }
+}  // namespace
+
+// ------------------------------------------------------------------ batch
+// Several boundary-data instances on one geometry (MIXED precision), solved in
+// lockstep: every transform stage is one launch for all active instances (three
+// jobs per instance, each with its instance's CG done flag), the CG and
+// refinement loops stop per instance, and GMRES advances all unconverged
+// instances with one batched matvec per iteration.
+namespace {
+
+void batch_alloc(kfbim_ctx* c, int B) {
+  if (B <= c->bcap) return;
+  const int64_t N3 = c->N3, np = std::max<int64_t>(1, c->n_prim);
+  c->bm = c->opt.gmres_max;
+  c->bgh = dalloc<double>(c, (size_t)B * (c->bm + 1));
+  for (int b = 0; b < c->bcap; ++b) c->bs[b].gh = c->bgh + (size_t)b * (c->bm + 1);
+  for (int b = c->bcap; b < B; ++b) {
+    kfbim_ctx::Slot sl{};
+    sl.J = dalloc<double>(c, kSlots * c->n_all);
+    sl.rhs = dalloc<double>(c, 4 * N3);
+    sl.u = dalloc<double>(c, 3 * N3);
+    sl.p = dalloc<double>(c, N3);
+    sl.res = dalloc<double>(c, 4 * N3);
+    sl.grhs = dalloc<double>(c, np);
+    sl.V = dalloc<double>(c, (size_t)(c->bm + 1) * np);
+    sl.gw = dalloc<double>(c, np);
+    sl.gh = c->bgh + (size_t)b * (c->bm + 1);
+    sl.gy = dalloc<double>(c, c->bm + 1);
+    sl.x = dalloc<float>(c, N3);
+    sl.r = dalloc<float>(c, N3);
+    sl.d = dalloc<float>(c, N3);
+    sl.q = dalloc<float>(c, N3);
+    sl.q2 = dalloc<float>(c, N3);
+    sl.q3 = dalloc<float>(c, N3);
+    sl.T6 = dalloc<float>(c, 6 * N3);
+    sl.fu = dalloc<float>(c, 3 * N3);
+    c->bs.push_back(sl);
+  }
+  c->bcgs = dalloc<CGScalars>(c, B);
+  c->bscal = dalloc<double>(c, 8 * (size_t)B);
+  if (c->bpinned) CK(cudaFreeHost(c->bpinned));
+  c->bpinned = nullptr;
+  const size_t pin = std::max({sizeof(CGScalars) * B, sizeof(double) * 8 * B,
+                               sizeof(double) * (size_t)B * (c->bm + 1)});
+  CK(cudaMallocHost(&c->bpinned, pin));
+  c->bcap = B;
+}
+
+// Stage lists for the instances in `act` (3 jobs each, skip = instance done flag).
+void schur_apply_batch(kfbim_ctx* c, const std::vector<int>& act, cudaStream_t s) {
+  const int64_t n = c->N3;
+  std::vector<Job> L[5];
+  for (int b : act) {
+    const kfbim_ctx::Slot& w = c->bs[b];
+    const int* sk = &c->bcgs[b].done;
+    float *A = w.T6, *B = w.T6 + n, *C = w.T6 + 2 * n, *D = w.T6 + 3 * n, *E = w.T6 + 4 * n,
+          *F = w.T6 + 5 * n;
+    L[0].push_back({w.d, A, 2, X_DST2F, X_NONE, W_NONE, 0, 0, sk});
+    L[0].push_back({w.d, B, 1, X_DST2F, X_NONE, W_NONE, 2, 0, sk});
+    L[1].push_back({A, C, 1, X_DST2F, X_NONE, W_NONE, 0, 0, sk});
+    L[1].push_back({A, D, 0, X_DST2F, X_NONE, W_NONE, 1, 0, sk});
+    L[1].push_back({B, E, 0, X_DST2F, X_NONE, W_NONE, 2, 0, sk});
+    L[2].push_back({C, A, 0, X_DCT2F, X_DCT2I, W_SCHUR, 0, 0, sk});
+    L[2].push_back({D, B, 1, X_DCT2F, X_DCT2I, W_SCHUR, 1, 0, sk});
+    L[2].push_back({E, F, 2, X_DCT2F, X_DCT2I, W_SCHUR, 2, 0, sk});
+    L[3].push_back({A, C, 1, X_DST2I, X_NONE, W_NONE, 0, 0, sk});
+    L[3].push_back({B, D, 0, X_DST2I, X_NONE, W_NONE, 1, 0, sk});
+    L[3].push_back({F, E, 0, X_DST2I, X_NONE, W_NONE, 2, 0, sk});
+    L[4].push_back({C, w.q, 2, X_DST2I, X_NONE, W_NONE, 0, 0, sk});
+    L[4].push_back({D, w.q2, 2, X_DST2I, X_NONE, W_NONE, 1, 0, sk});
+    L[4].push_back({E, w.q3, 1, X_DST2I, X_NONE, W_NONE, 2, 0, sk});
+  }
+  for (int k = 0; k < 5; ++k) stage_list<float, float, float>(c, L[k], s);
+}
+
+// face-to-cell (W_RHS) or face-to-face (W_POISSON) transform of three face
+// fields per instance: src(b) -> dst(b) (component outputs at stride N^3)
+template <typename Tin>
+void face3_batch(kfbim_ctx* c, const std::vector<int>& act, const std::vector<const Tin*>& src,
+                 const std::vector<float*>& dst1, const std::vector<float*>& dst2,
+                 const std::vector<float*>& dst3, int wmode, cudaStream_t s) {
+  const int64_t n = c->N3;
+  const int t1 = wmode == W_RHS ? X_DCT2I : X_DST1I;
+  std::vector<Job> L[5];
+  for (size_t q = 0; q < act.size(); ++q) {
+    const kfbim_ctx::Slot& w = c->bs[act[q]];
+    const Tin* f = src[q];
+    float *A = w.T6, *B = w.T6 + n, *C = w.T6 + 2 * n, *D = w.T6 + 3 * n, *E = w.T6 + 4 * n,
+          *F = w.T6 + 5 * n;
+    L[0].push_back({f, A, 2, X_DST2F, X_NONE, W_NONE, 0, 0});
+    L[0].push_back({f + n, B, 2, X_DST2F, X_NONE, W_NONE, 1, 0});
+    L[0].push_back({f + 2 * n, C, 1, X_DST2F, X_NONE, W_NONE, 2, 0});
+    L[1].push_back({A, D, 1, X_DST2F, X_NONE, W_NONE, 0, 0});
+    L[1].push_back({B, E, 0, X_DST2F, X_NONE, W_NONE, 1, 0});
+    L[1].push_back({C, F, 0, X_DST2F, X_NONE, W_NONE, 2, 0});
+    L[2].push_back({D, A, 0, X_DST1F, t1, wmode, 0, 0});
+    L[2].push_back({E, B, 1, X_DST1F, t1, wmode, 1, 0});
+    L[2].push_back({F, C, 2, X_DST1F, t1, wmode, 2, 0});
+    L[3].push_back({A, D, 1, X_DST2I, X_NONE, W_NONE, 0, 0});
+    L[3].push_back({B, E, 0, X_DST2I, X_NONE, W_NONE, 1, 0});
+    L[3].push_back({C, F, 0, X_DST2I, X_NONE, W_NONE, 2, 0});
+    L[4].push_back({D, dst1[q], 2, X_DST2I, X_NONE, W_NONE, 0, 0});
+    L[4].push_back({E, dst2[q], 2, X_DST2I, X_NONE, W_NONE, 1, 0});
+    L[4].push_back({F, dst3[q], 1, X_DST2I, X_NONE, W_NONE, 2, 0});
+  }
+  stage_list<Tin, float, float>(c, L[0], s);
+  for (int k = 1; k < 5; ++k) stage_list<float, float, float>(c, L[k], s);
+}
+
+// Lockstep FP32 CG of the instances in `act` on (S + ...) x = b (b in fu[0:N3]).
+void cg_batch(kfbim_ctx* c, const std::vector<int>& act, double tol, cudaStream_t s) {
+  const int64_t n = c->N3;
+  const double rank1 = c->navier ? 0.0 : 1.0 / (c->mu * (double)n);
+  for (int b : act) {
+    const kfbim_ctx::Slot& w = c->bs[b];
+    CK(cudaMemsetAsync(&c->bcgs[b], 0, sizeof(CGScalars), s));
+    CK(cudaMemsetAsync(w.x, 0, n * sizeof(float), s));
+    CK(cudaMemcpyAsync(w.r, w.fu, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(w.d, w.fu, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    k_cg_init<float><<<RED_BLOCKS, RED_THREADS, 0, s>>>(w.fu, n, &c->bcgs[b], tol * tol, rank1, c->cpen,
+                                                         c->partial);
+    ++g_launches;
+  }
+  check_launch();
+  std::vector<CGScalars> h(c->bcap);
+  int launched = 0;
+  while (true) {
+    CK(cudaMemcpyAsync(c->bpinned, c->bcgs, sizeof(CGScalars) * c->bcap, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (c->prof_used) prof_collect(c);
+    std::memcpy(h.data(), c->bpinned, sizeof(CGScalars) * c->bcap);
+    std::vector<int> run;
+    for (int b : act) {
+      if (!std::isfinite(h[b].rr)) throw CudaError{"non-finite CG residual in a batched solve", KFBIM_E_NONFINITE};
+      if (!h[b].done) run.push_back(b);
+    }
+    if (run.empty() || launched >= c->opt.cg_max) break;
+    for (int it = 0; it < kCgGraphIters; ++it) {
+      schur_apply_batch(c, run, s);
+      for (int b : run) {
+        const kfbim_ctx::Slot& w = c->bs[b];
+        k_cg_alpha<float><<<RED_BLOCKS, RED_THREADS, 0, s>>>(w.d, w.q, w.q2, w.q3, n, &c->bcgs[b], c->partial);
+        k_cg_update<float><<<RED_BLOCKS, RED_THREADS, 0, s>>>(w.x, w.r, w.d, w.q, n, &c->bcgs[b], c->partial);
+        k_cg_direction<float><<<RED_BLOCKS, RED_THREADS, 0, s>>>(w.d, w.r, n, &c->bcgs[b], c->partial);
+        g_launches += 3;
+      }
+      check_launch();
+    }
+    launched += kCgGraphIters;
+  }
+  for (int b : act) {
+    c->cg_iters += h[b].iters;
+    c->b_cg[b] += h[b].iters;
+  }
+}
+
+// Read one double per slot of `act` from bscal[8 b + k].
+std::vector<double> read_slots(kfbim_ctx* c, const std::vector<int>& act, int k, cudaStream_t s) {
+  CK(cudaMemcpyAsync(c->bpinned, c->bscal, sizeof(double) * 8 * c->bcap, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (c->prof_used) prof_collect(c);
+  const double* h = static_cast<const double*>(c->bpinned);
+  std::vector<double> v;
+  for (int b : act) {
+    if (!std::isfinite(h[8 * b + k])) throw CudaError{"non-finite residual in a batched solve", KFBIM_E_NONFINITE};
+    v.push_back(h[8 * b + k]);
+  }
+  return v;
+}
+
+// MIXED grid solve of the instances in `act` (rhs in slot.rhs -> slot.u, slot.p).
+void grid_solve_batch(kfbim_ctx* c, const std::vector<int>& act, cudaStream_t s) {
+  const int64_t N3 = c->N3;
+  for (int b : act) {
+    const kfbim_ctx::Slot& w = c->bs[b];
+    double* g = w.rhs + 3 * N3;
+    double* gmean = c->bscal + 8 * b;
+    CK(cudaMemsetAsync(w.u, 0, 3 * N3 * sizeof(double), s));
+    CK(cudaMemsetAsync(w.p, 0, N3 * sizeof(double), s));
+    if (c->navier) CK(cudaMemsetAsync(gmean, 0, sizeof(double), s));
+    else dot(c, g, (const double*)nullptr, N3, gmean, 1.0 / (double)N3, s);
+    CK(cudaMemcpyAsync(w.res, w.rhs, 4 * N3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    k_shift<<<grid_for(N3), 256, 0, s>>>(w.res + 3 * N3, gmean, -1.0, N3); ++g_launches;
+    dot(c, w.res, w.res, 4 * N3, c->bscal + 8 * b + 1, 1.0, s);
+  }
+  const std::vector<double> ref2 = read_slots(c, act, 1, s);
+  std::vector<int> live;
+  for (size_t q = 0; q < act.size(); ++q)
+    if (ref2[q] > 0.0) live.push_back(act[q]);
+  for (int sweep = 0; !live.empty(); ++sweep) {
+    if (sweep > 0) {
+      for (int b : live) {
+        const kfbim_ctx::Slot& w = c->bs[b];
+        k_mac_residual<<<grid_for(4 * N3), 256, 0, s>>>(w.rhs, w.rhs + 3 * N3, c->bscal + 8 * b, w.u, w.p,
+                                                        c->lg, c->h, c->mu, c->cpen, w.res, w.res + 3 * N3);
+        ++g_launches;
+        dot(c, w.res, w.res, 4 * N3, c->bscal + 8 * b + 2, 1.0, s);
+      }
+      check_launch();
+      const std::vector<double> r2 = read_slots(c, live, 2, s);
+      std::vector<int> keep;
+      for (size_t q = 0; q < live.size(); ++q) {
+        const double ref = ref2[std::find(act.begin(), act.end(), live[q]) - act.begin()];
+        if (!(r2[q] <= c->opt.refine_tol * c->opt.refine_tol * ref)) keep.push_back(live[q]);
+      }
+      live.swap(keep);
+      if (live.empty() || sweep >= c->opt.refine_max) break;
+    }
+    c->refine_sweeps += (int)live.size();
+    for (int b : live) ++c->b_sweeps[b];
+    std::vector<const double*> src;
+    std::vector<float*> d1, d2, d3;
+    for (int b : live) {
+      const kfbim_ctx::Slot& w = c->bs[b];
+      src.push_back(w.res);
+      d1.push_back(w.q);
+      d2.push_back(w.q2);
+      d3.push_back(w.q3);
+    }
+    face3_batch<double>(c, live, src, d1, d2, d3, W_RHS, s);
+    for (int b : live) {
+      const kfbim_ctx::Slot& w = c->bs[b];
+      k_sum4<double, float><<<grid_for(N3), 256, 0, s>>>(w.res + 3 * N3, w.q, w.q2, w.q3, w.fu, N3);
+      ++g_launches;
+    }
+    check_launch();
+    cg_batch(c, live, c->opt.inner_tol, s);
+    std::vector<const float*> fsrc;
+    std::vector<float*> u1, u2, u3;
+    for (int b : live) {
+      const kfbim_ctx::Slot& w = c->bs[b];
+      k_add_to<float><<<grid_for(N3), 256, 0, s>>>(w.x, w.p, N3);
+      k_f_minus_gp<float, float><<<grid_for(3 * N3), 256, 0, s>>>(w.res, w.x, c->lg, c->h, w.fu);
+      g_launches += 2;
+      fsrc.push_back(w.fu);
+      u1.push_back(w.fu);
+      u2.push_back(w.fu + N3);
+      u3.push_back(w.fu + 2 * N3);
+    }
+    check_launch();
+    face3_batch<float>(c, live, fsrc, u1, u2, u3, W_POISSON, s);
+    for (int b : live) {
+      const kfbim_ctx::Slot& w = c->bs[b];
+      k_add_to<float><<<grid_for(3 * N3), 256, 0, s>>>(w.fu, w.u, 3 * N3);
+      ++g_launches;
+    }
+    check_launch();
+  }
+  if (c->navier) return;
+  for (int b : act) {   // gauge mean(p) = mu mean(g)
+    const kfbim_ctx::Slot& w = c->bs[b];
+    double* sc = c->bscal + 8 * b + 3;
+    dot(c, w.p, (const double*)nullptr, N3, sc, 1.0 / (double)N3, s);
+    k_shift<<<grid_for(N3), 256, 0, s>>>(w.p, sc, -1.0, N3);
+    k_shift<<<grid_for(N3), 256, 0, s>>>(w.p, c->bscal + 8 * b, c->mu, N3);
+    g_launches += 2;
+  }
+  check_launch();
+}
+
+// Jumps, RHS and grid solve for the instances in `act`; phi/fpts/fgrid per instance.
+void interface_batch(kfbim_ctx* c, const std::vector<int>& act, const std::vector<const double*>& phi,
+                     const std::vector<const double*>& fpts, const std::vector<const double*>& fgrid,
+                     cudaStream_t s) {
+  const int64_t n = c->n_all;
+  const int wpb = 8;
+  for (size_t q = 0; q < act.size(); ++q) {
+    const kfbim_ctx::Slot& w = c->bs[act[q]];
+    k_jumps<<<(unsigned)((n + wpb - 1) / wpb), 32 * wpb, 0, s>>>(
+        phi[q], fpts[q], n, c->d_comp, c->d_pid, c->d_fit_ptr, c->d_fit_col, c->d_fit_w, c->fit_nnz,
+        c->d_jmap, w.J);
+    k_rhs_fill<<<grid_for(4 * c->N3), 256, 0, s>>>(fgrid[q], c->d_side[1], c->d_side[2], c->d_side[3],
+                                                    c->lg, w.rhs);
+    g_launches += 2;
+    if (c->n_corr_rows > 0) {
+      k_corrections<<<grid_for(c->n_corr_rows), 256, 0, s>>>(c->d_corr_row, c->d_corr_ptr, c->d_corr_src,
+                                                              c->d_corr_coef, c->n_corr_rows, w.J, w.rhs);
+      ++g_launches;
+    }
+  }
+  check_launch();
+  c->interface_solves += (int)act.size();
+  for (int b : act) ++c->b_isolves[b];
+  grid_solve_batch(c, act, s);
+}
+
+// Lockstep GMRES (Alg. 1 step 3) of the instances in `act` with right-hand
+// sides slot.grhs; solutions to x[b].  Per instance the arithmetic is the
+// single-instance GMRES; the batch shares the matvec launches and the host
+// reads (three per iteration for the whole batch).
+void gmres_batch(kfbim_ctx* c, const std::vector<int>& act, const std::vector<double*>& x,
+                 std::vector<int>& iters, std::vector<double>& resid, std::vector<int>& status,
+                 cudaStream_t s) {
+  const int64_t n = c->n_prim, ld = n;
+  const int m = c->bm, nb = 64;
+  const int B = c->bcap;
+  for (int b : act) dot(c, c->bs[b].grhs, c->bs[b].grhs, n, c->bscal + 8 * b + 4, 1.0, s);
+  const std::vector<double> b2 = read_slots(c, act, 4, s);
+  struct Gm {
+    std::vector<double> H, cs, sn, g;
+    double beta = 0.0;
+  };
+  std::vector<Gm> G(B);
+  std::vector<int> live;
+  for (size_t q = 0; q < act.size(); ++q) {
+    const int b = act[q];
+    Gm& z = G[b];
+    z.beta = std::sqrt(b2[q]);
+    iters[b] = 0;
+    resid[b] = 0.0;
+    status[b] = KFBIM_OK;
+    if (z.beta == 0.0) {
+      CK(cudaMemsetAsync(x[b], 0, n * sizeof(double), s));
+      continue;
+    }
+    z.H.assign((size_t)(m + 1) * m, 0.0);
+    z.cs.assign(m, 0.0);
+    z.sn.assign(m, 0.0);
+    z.g.assign(m + 1, 0.0);
+    z.g[0] = z.beta;
+    status[b] = KFBIM_E_NOCONV;
+    resid[b] = 1.0;
+    k_scale_copy<<<grid_for(n), 256, 0, s>>>(c->bs[b].grhs, 1.0 / z.beta, nullptr, c->bs[b].V, n);
+    ++g_launches;
+    live.push_back(b);
+  }
+  check_launch();
+  std::vector<int> done_at(B, 0);
+  const double* hp = static_cast<const double*>(c->bpinned);
+  for (int k = 1; k <= m && !live.empty(); ++k) {
+    std::vector<const double*> phi, nul(live.size(), nullptr);
+    for (int b : live) phi.push_back(c->bs[b].V + (int64_t)(k - 1) * ld);
+    interface_batch(c, live, phi, nul, nul, s);
+    for (int b : live) {
+      const kfbim_ctx::Slot& w = c->bs[b];
+      k_trace<<<grid_for(c->n_prim), 256, 0, s>>>(w.u, w.J, c->n_all, c->n_prim, c->d_prim_of, c->N,
+                                                   c->d_tr_comp, c->d_tr_node, c->d_tr_w, c->d_tr_cj, w.gw);
+      ++g_launches;
+    }
+    check_launch();
+    std::vector<std::vector<double>> hcol(B);
+    for (int b : live) hcol[b].assign(m + 1, 0.0);
+    for (int pass2 = 0; pass2 < 2; ++pass2) {
+      for (int b : live) {
+        const kfbim_ctx::Slot& w = c->bs[b];
+        k_multidot_partial<<<dim3(nb, k), RED_THREADS, 0, s>>>(w.V, ld, w.gw, n, c->partial);
+        k_sum_partials<<<k, RED_THREADS, 0, s>>>(c->partial, nb, 1.0, w.gh);
+        k_multi_axpy<<<grid_for(n), 256, 0, s>>>(w.V, ld, w.gh, k, w.gw, n, 0);
+        g_launches += 3;
+      }
+      check_launch();
+      CK(cudaMemcpyAsync(c->bpinned, c->bgh, sizeof(double) * (size_t)B * (m + 1), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      for (int b : live)
+        for (int j = 0; j < k; ++j) hcol[b][j] += hp[(size_t)b * (m + 1) + j];
+    }
+    for (int b : live) dot(c, c->bs[b].gw, c->bs[b].gw, n, c->bscal + 8 * b + 5, 1.0, s);
+    const std::vector<double> hn2 = read_slots(c, live, 5, s);
+    std::vector<int> keep;
+    for (size_t q = 0; q < live.size(); ++q) {
+      const int b = live[q];
+      Gm& z = G[b];
+      std::vector<double>& h = hcol[b];
+      const double hn = std::sqrt(hn2[q]);
+      h[k] = hn;
+      for (int j = 0; j < k - 1; ++j) {
+        const double a = h[j], bb = h[j + 1];
+        h[j] = z.cs[j] * a + z.sn[j] * bb;
+        h[j + 1] = -z.sn[j] * a + z.cs[j] * bb;
+      }
+      const double a = h[k - 1], bb = h[k];
+      const double r = std::hypot(a, bb);
+      z.cs[k - 1] = (r == 0.0) ? 1.0 : a / r;
+      z.sn[k - 1] = (r == 0.0) ? 0.0 : bb / r;
+      h[k - 1] = r;
+      h[k] = 0.0;
+      z.g[k] = -z.sn[k - 1] * z.g[k - 1];
+      z.g[k - 1] = z.cs[k - 1] * z.g[k - 1];
+      for (int j = 0; j < k; ++j) z.H[(size_t)j * m + (k - 1)] = h[j];
+      resid[b] = std::fabs(z.g[k]) / z.beta;
+      done_at[b] = k;
+      if (resid[b] < c->opt.gmres_tol || hn == 0.0) {
+        status[b] = KFBIM_OK;
+        continue;
+      }
+      if (k < m) {
+        k_scale_copy<<<grid_for(n), 256, 0, s>>>(c->bs[b].gw, 1.0 / hn, nullptr, c->bs[b].V + (int64_t)k * ld, n);
+        ++g_launches;
+      }
+      keep.push_back(b);
+    }
+    check_launch();
+    live.swap(keep);
+  }
+  for (int b : act) {
+    Gm& z = G[b];
+    if (z.beta == 0.0) continue;
+    const int kk = done_at[b];
+    std::vector<double> y(kk, 0.0);
+    for (int i = kk - 1; i >= 0; --i) {
+      double acc = z.g[i];
+      for (int j = i + 1; j < kk; ++j) acc -= z.H[(size_t)i * m + j] * y[j];
+      y[i] = acc / z.H[(size_t)i * m + i];
+    }
+    CK(cudaMemcpyAsync(c->bs[b].gy, y.data(), kk * sizeof(double), cudaMemcpyHostToDevice, s));
+    k_multi_axpy<<<grid_for(n), 256, 0, s>>>(c->bs[b].V, ld, c->bs[b].gy, kk, x[b], n, 1);
+    ++g_launches;
+    CK(cudaStreamSynchronize(s));   // y lives on the host stack
+    iters[b] = kk;
+  }
+  check_launch();
+}
+
 }  // namespace
 
 // =================================================================== C ABI
@@ -953,6 +1401,7 @@ int kfbim_destroy(kfbim_ctx* c) {
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   for (void* p : c->allocs) cudaFree(p);
   if (c->pinned) cudaFreeHost(c->pinned);
+  if (c->bpinned) cudaFreeHost(c->bpinned);
   delete c;
   return KFBIM_OK;
 }
@@ -1104,6 +1553,82 @@ int kfbim_solve(kfbim_ctx* c, const double* g, const double* fpts, const double*
       return st2;
     }
     return st2;
+  });
+}
+
+int kfbim_solve_batch(kfbim_ctx* c, int B, const double* g, const double* fpts, const double* fgrid,
+                      double* phi, double* u, double* p, kfbim_stats* stats, void* stream) {
+  return guarded(c, [&]() -> int {
+    if (B < 1 || B > KFBIM_BATCH_MAX || !g || !phi)
+      return fail(c, KFBIM_E_INVALID, "kfbim_solve_batch: bad batch size or pointers");
+    const int64_t n = c->n_prim, N3 = c->N3, na = c->n_all;
+    if (c->opt.precision != KFBIM_MIXED) {
+      // FP64 contexts solve the instances one after another
+      int worst = KFBIM_OK;
+      for (int b = 0; b < B; ++b) {
+        int st = kfbim_solve(c, g + b * n, fpts ? fpts + b * 3 * na : nullptr,
+                             fgrid ? fgrid + b * 3 * N3 : nullptr, phi + b * n, u ? u + b * 3 * N3 : nullptr,
+                             p ? p + b * N3 : nullptr, stats ? stats + b : nullptr, stream);
+        if (st != KFBIM_OK && st != KFBIM_E_NOCONV) return st;
+        if (st != KFBIM_OK) worst = st;
+      }
+      return worst;
+    }
+    batch_alloc(c, B);
+    reset_counters(c);
+    c->b_cg.assign(c->bcap, 0);
+    c->b_sweeps.assign(c->bcap, 0);
+    c->b_isolves.assign(c->bcap, 0);
+    const int64_t launches0 = g_launches;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<int> all(B);
+    std::vector<const double*> fp(B, nullptr), fg(B, nullptr), zero(B, c->zero_phi), ph(B);
+    std::vector<double*> x(c->bcap, nullptr);
+    for (int b = 0; b < B; ++b) {
+      all[b] = b;
+      if (fpts) fp[b] = fpts + b * 3 * na;
+      if (fgrid) fg[b] = fgrid + b * 3 * N3;
+      ph[b] = phi + b * n;
+      x[b] = phi + b * n;
+      CK(cudaMemcpyAsync(c->bs[b].grhs, g + b * n, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+    if (fpts || fgrid) {
+      // g - G_v f: the interface solve with zero density and the forcing
+      interface_batch(c, all, zero, fp, fg, s);
+      for (int b = 0; b < B; ++b) {
+        const kfbim_ctx::Slot& w = c->bs[b];
+        k_trace<<<grid_for(n), 256, 0, s>>>(w.u, w.J, na, n, c->d_prim_of, c->N, c->d_tr_comp, c->d_tr_node,
+                                            c->d_tr_w, c->d_tr_cj, w.gw);
+        k_scale_copy<<<grid_for(n), 256, 0, s>>>(w.gw, -1.0, nullptr, w.gw, n);
+        k_add_to<double><<<grid_for(n), 256, 0, s>>>(w.gw, w.grhs, n);
+        g_launches += 3;
+      }
+      check_launch();
+    }
+    std::vector<int> its(c->bcap, 0), st(c->bcap, KFBIM_OK);
+    std::vector<double> res(c->bcap, 0.0);
+    gmres_batch(c, all, x, its, res, st, s);
+    interface_batch(c, all, ph, fp, fg, s);
+    for (int b = 0; b < B; ++b) {
+      const kfbim_ctx::Slot& w = c->bs[b];
+      if (u) CK(cudaMemcpyAsync(u + b * 3 * N3, w.u, 3 * N3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      if (p) CK(cudaMemcpyAsync(p + b * N3, w.p, N3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    int worst = KFBIM_OK;
+    for (int b = 0; b < B; ++b) {
+      if (st[b] != KFBIM_OK) worst = st[b];
+      if (stats) {
+        stats[b].gmres_iters = its[b];
+        stats[b].interface_solves = c->b_isolves[b];
+        stats[b].cg_iters = c->b_cg[b];
+        stats[b].refine_sweeps = c->b_sweeps[b];
+        stats[b].gmres_residual = res[b];
+        stats[b].kernel_launches = g_launches - launches0;
+      }
+    }
+    if (worst == KFBIM_E_NOCONV) c->err = "GMRES reached its iteration cap for an instance of the batch";
+    return worst;
   });
 }
 

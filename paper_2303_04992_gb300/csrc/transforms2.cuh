@@ -255,14 +255,16 @@ struct PassJob {
   Tout* out;
   PassArgs a;
 };
-template <typename Tin, typename Tout>
+// Up to MAXJ jobs per launch: 3 for one instance, 48 for a batch of 16
+// instances (kernel parameters of up to ~5 KB).
+template <typename Tin, typename Tout, int MAXJ>
 struct PassJobs {
-  PassJob<Tin, Tout> j[3];
+  PassJob<Tin, Tout> j[MAXJ];
 };
 
-template <typename Tin, typename T, typename Tout, int N>
+template <typename Tin, typename T, typename Tout, int N, int MAXJ>
 __global__ void __launch_bounds__(PASS2_THREADS, (sizeof(T) == 4 ? 5 : 2))
-k_axis_pass2(const __grid_constant__ PassJobs<Tin, Tout> jobs, const C2<T>* __restrict__ tw,
+k_axis_pass2(const __grid_constant__ PassJobs<Tin, Tout, MAXJ> jobs, const C2<T>* __restrict__ tw,
              const C2<T>* __restrict__ qN, const T* __restrict__ s2) {
   using S = Pass2Smem<T, N>;
   extern __shared__ __align__(16) unsigned char smem2[];

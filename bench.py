@@ -410,6 +410,7 @@ def main_kfbim(args):
                            "gmres_iters": st["gmres_iters"], "interface_solves": st["interface_solves"],
                            "cg_iters": st["cg_iters"], "refine_sweeps": st["refine_sweeps"],
                            "parallelism": "replicas" if world > 1 else "single"},
+                "transforms": solver.transforms_info(),
                 "fp64": fp64, "rel_err_vs_fp64": rel, "batched": batched,
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": e2e, "gpu_launches": launches, "clocks": clk}

@@ -102,7 +102,17 @@ typedef struct {
   double inner_tol;   /* MIXED: FP32 CG relative residual per sweep */
   int pde;            /* kfbim_pde */
   double lambda;      /* Lame lambda (NAVIER; lambda + mu > 0, lambda >= 0) */
+  int transforms;     /* kfbim_transforms: kernels of the FP32 (MIXED) axis passes */
 } kfbim_options;
+
+/* Kernels of the FP32 axis passes of MIXED contexts.  The tensor-core form
+ * (a dense 3xTF32 transform-matrix GEMM on tcgen05) exists for N = 128 only;
+ * elsewhere, and for every FP64 pass, the FFT pass runs. */
+typedef enum {
+  KFBIM_XF_AUTO = 0,    /* timed at setup: the faster of the two per stage kind */
+  KFBIM_XF_FFT = 1,     /* four-step FFT passes (CUDA cores) */
+  KFBIM_XF_TENSOR = 2   /* tensor-core GEMM passes where N = 128 */
+} kfbim_transforms;
 
 typedef struct {
   int gmres_iters;
@@ -114,7 +124,7 @@ typedef struct {
 } kfbim_stats;
 
 /* Fills *opt with the defaults (Stokes, mu 1, FP64, gmres 1e-10/200,
- * cg 1e-14/2000, refine 1e-11/8, inner 3e-6, lambda 0). */
+ * cg 1e-14/2000, refine 1e-11/8, inner 3e-6, lambda 0, transforms AUTO). */
 void kfbim_default_options(kfbim_options* opt);
 
 /* Alg. 1 step 1: grids, sides, intersections, frames, control points and all
@@ -234,6 +244,23 @@ int kfbim_interface(kfbim_ctx* ctx, const double* phi_dev, const double* fpts_de
                     const double* fgrid_dev, double* u_dev, double* p_dev, void* stream);
 int kfbim_trace(kfbim_ctx* ctx, const double* u_dev, const double* J_dev,
                 double* out_dev, void* stream);
+
+/* One FP32 axis pass (test entry point of the transform kernels): out = W . T in
+ * along axis (0 x, 1 y, 2 z) of an N^3 field, T = transform `type` (1 DCT-II,
+ * 2 its inverse, 3 DST-II, 4 its inverse, 5 DST-I, 6 its inverse; conventions
+ * in transforms.cuh), W the spectral weight `wmode` (0 none, 1 Schur, 2 Poisson,
+ * 3 Schur RHS; component wc = 0..2) or 1.  backend: KFBIM_XF_FFT or
+ * KFBIM_XF_TENSOR (E_INVALID unless N = 128 and MIXED).  in_dev, out_dev: N^3
+ * floats (may alias). */
+int kfbim_transform_f32(kfbim_ctx* ctx, int type, int axis, int wmode, int wc,
+                        const float* in_dev, float* out_dev, int backend, void* stream);
+
+/* The kernel each kind of FP32 stage runs on (0 FFT, 1 tensor core) for a
+ * plain stage (one transform per job) and a fused stage (transform, weight,
+ * transform), and the autotuner's timings in ms per three-job stage: plain
+ * FFT, plain tensor core, fused FFT, fused tensor core (zeros when the
+ * autotuner did not run).  Host pointers, nullable. */
+int kfbim_transforms_info(const kfbim_ctx* ctx, int* plain, int* fused, float* tune_ms4);
 
 /* FFT Poisson solve -Delta_h u = r on face grid c (1..3) with the box
  * conditions of Sec. 4.2 (DST-I across the normal axis, DST-II along the

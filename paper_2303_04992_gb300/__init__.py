@@ -12,3 +12,6 @@ from .build import build  # noqa: F401
 
 FP64 = 0
 MIXED = 1
+XF_AUTO = 0      # FP32 axis passes: timed choice per stage kind
+XF_FFT = 1       # four-step FFT passes
+XF_TENSOR = 2    # tcgen05 transform-matrix GEMM passes (N = 128)

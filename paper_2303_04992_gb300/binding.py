@@ -32,7 +32,7 @@ class Options(ctypes.Structure):
     _fields_ = [("mu", c_double), ("precision", c_int), ("gmres_tol", c_double),
                 ("gmres_max", c_int), ("cg_tol", c_double), ("cg_max", c_int),
                 ("refine_tol", c_double), ("refine_max", c_int), ("inner_tol", c_double),
-                ("pde", c_int), ("lam", c_double)]
+                ("pde", c_int), ("lam", c_double), ("transforms", c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -62,6 +62,9 @@ SYMBOLS = {
                                  c_void_p, ctypes.POINTER(Stats), c_void_p]),
     "kfbim_solve_batch": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                   c_void_p, ctypes.POINTER(Stats), c_void_p]),
+    "kfbim_transform_f32": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_int,
+                                    c_void_p]),
+    "kfbim_transforms_info": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "kfbim_jumps": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "kfbim_interface": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "kfbim_trace": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
@@ -254,6 +257,18 @@ class Solver:
     def trace(self, u, J, out):
         self._check(self._lib.kfbim_trace(self._ctx, _ptr(u), _ptr(J), _ptr(out), self._stream()))
         return out
+
+    def transform_f32(self, xform, axis, inp, out, backend, wmode=0, wc=0):
+        self._check(self._lib.kfbim_transform_f32(self._ctx, xform, axis, wmode, wc, _ptr(inp), _ptr(out),
+                                                  backend, self._stream()))
+        return out
+
+    def transforms_info(self):
+        """{"plain": 0|1, "fused": 0|1 (1 = tensor core), "tune_ms": [4 floats]}."""
+        pl, fu = c_int(), c_int()
+        ms = (ctypes.c_float * 4)()
+        self._check(self._lib.kfbim_transforms_info(self._ctx, ctypes.byref(pl), ctypes.byref(fu), ms))
+        return {"plain": pl.value, "fused": fu.value, "tune_ms": [round(float(x), 4) for x in ms]}
 
     def poisson(self, c, r, u):
         self._check(self._lib.kfbim_poisson(self._ctx, c, _ptr(r), _ptr(u), self._stream()))

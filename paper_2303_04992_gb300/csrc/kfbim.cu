@@ -28,6 +28,7 @@
 #include "kernels.cuh"
 #include "transforms.cuh"
 #include "transforms2.cuh"
+#include "tc_pass.cuh"
 
 using namespace kfbim;
 
@@ -56,6 +57,13 @@ struct kfbim_ctx {
   C2<double>* d_twc64 = nullptr;  // full-circle twiddles exp(-2 pi i t / 2N), t < 2N
   C2<float>* d_twc32 = nullptr;
   float* d_s2f = nullptr;         // FP32 copy of the eigenvalue table
+  // tensor-core passes (N = 128, MIXED): transform matrices [type 1..6][hi|lo][n][m],
+  // the kernels' timeout flag, and the kernel chosen per stage kind (0 FFT, 1 GEMM)
+  float* d_tc_mats = nullptr;
+  int* d_tc_err = nullptr;
+  int xf_plain = 0, xf_fused = 0;
+  int num_sms = 152;
+  float tune_ms[4] = {0, 0, 0, 0};   // plain FFT, plain GEMM, fused FFT, fused GEMM (ms per stage)
   // FP64 workspace
   double *J = nullptr, *rhs = nullptr, *u = nullptr, *p = nullptr, *t1 = nullptr, *t2 = nullptr;
   double *cr = nullptr, *cd = nullptr, *cq = nullptr, *rres = nullptr, *zero_phi = nullptr;
@@ -223,20 +231,83 @@ void launch_jobs(kfbim_ctx* c, const Job* list, int nj, cudaStream_t s, const in
 // Launch a list of independent passes: up to 3 jobs per launch on the
 // compile-time-N kernel (48 for longer, batched lists), one launch per job on
 // the runtime-N kernel.
+// Tensor-core passes of one stage: all jobs share the first transform; a
+// fused job (second transform) becomes a weighted pass into its output and an
+// in-place pass of the second transform.  Returns the kernel launches.
+template <typename Tin>
+int tc_passes(kfbim_ctx* c, const std::vector<Job>& list, cudaStream_t s, const int* skip, double* bytes) {
+  const int nj = (int)list.size();
+  auto launch = [&](const auto* jl, int n, auto tag) {
+    using TI = decltype(tag);
+    const int type = jl[0].t0;
+    PassJobs<TI, float, TC_MAXJ> jobs{};
+    for (int k = 0; k < n; ++k) {
+      Job j = jl[k];
+      j.t1 = X_NONE;
+      jobs.j[k] = make_job<TI, float>(c, j, skip);
+      *bytes += (double)c->N3 * (sizeof(TI) + sizeof(float) * (j.acc ? 2 : 1));
+    }
+    const int grid = std::min(c->num_sms, n * TC_TILES_PER_JOB);
+    static bool configured = false;   // per template instance
+    if (!configured) {
+      CK(cudaFuncSetAttribute(k_tc_pass<TI>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+      configured = true;
+    }
+    k_tc_pass<TI><<<grid, TC_THREADS, TC_SMEM, s>>>(jobs, n, c->d_tc_mats + (size_t)(type - 1) * 2 * TC_N * TC_N,
+                                                     c->d_s2f, c->d_tc_err);
+    ++g_launches;
+  };
+  int launches = 0;
+  for (int k0 = 0; k0 < nj; k0 += TC_MAXJ) {
+    const int n = std::min(TC_MAXJ, nj - k0);
+    launch(list.data() + k0, n, Tin{});
+    ++launches;
+  }
+  if (list[0].t1 != X_NONE) {
+    std::vector<Job> second;
+    for (const Job& j : list) second.push_back({j.out, j.out, j.axis, j.t1, X_NONE, W_NONE, j.wc, j.acc, j.skip});
+    for (int k0 = 0; k0 < nj; k0 += TC_MAXJ) {
+      const int n = std::min(TC_MAXJ, nj - k0);
+      launch(second.data() + k0, n, float{});
+      ++launches;
+    }
+  }
+  check_launch();
+  return launches;
+}
+
+// Whether a stage of FP32 passes goes to the tensor-core kernel.
+template <typename T, typename Tout>
+bool use_tc(const kfbim_ctx* c, const std::vector<Job>& list) {
+  if (!std::is_same<T, float>::value || !std::is_same<Tout, float>::value) return false;
+  if (!c->d_tc_mats || list.empty()) return false;
+  const bool fused = list[0].t1 != X_NONE;
+  if (!(fused ? c->xf_fused : c->xf_plain)) return false;
+  for (const Job& j : list) {
+    if (j.t0 != list[0].t0 || j.t1 != list[0].t1) return false;
+    if (fused && j.acc) return false;   // the split passes cannot accumulate through a temporary
+  }
+  return true;
+}
+
 template <typename Tin, typename T, typename Tout>
 void stage_list(kfbim_ctx* c, const std::vector<Job>& list, cudaStream_t s, const int* skip = nullptr) {
   double bytes = 0.0;
-  for (const Job& j : list) bytes += (double)c->N3 * (sizeof(Tin) + sizeof(Tout) * (j.acc ? 2 : 1));
   const bool prof = c->prof && c->prof_used + 2 <= (int)c->prof_ev.size();
   if (prof) CK(cudaEventRecord(c->prof_ev[c->prof_used], s));
   const int nj = (int)list.size();
-  if (c->N == 128 || c->N == 64 || c->N == 32) {
+  int launches = 1;
+  if (use_tc<T, Tout>(c, list)) {
+    launches = tc_passes<Tin>(c, list, s, skip, &bytes);
+  } else if (c->N == 128 || c->N == 64 || c->N == 32) {
+    for (const Job& j : list) bytes += (double)c->N3 * (sizeof(Tin) + sizeof(Tout) * (j.acc ? 2 : 1));
     if (nj <= 3) {
       launch_jobs<Tin, T, Tout, 3>(c, list.data(), nj, s, skip);
     } else {
       for (int k0 = 0; k0 < nj; k0 += kMaxJobs)
         launch_jobs<Tin, T, Tout, kMaxJobs>(c, list.data() + k0, std::min(kMaxJobs, nj - k0), s, skip);
     }
+    launches = nj <= 3 ? 1 : (nj + kMaxJobs - 1) / kMaxJobs;
   } else {
     const size_t smem = pass_smem_bytes(c->N, sizeof(T));
     auto kern = k_axis_pass<Tin, T, Tout>;
@@ -247,10 +318,12 @@ void stage_list(kfbim_ctx* c, const std::vector<Job>& list, cudaStream_t s, cons
     }
     const int blocks = (int)((int64_t)c->N * c->N / LPC);
     for (const Job& j : list) {
+      bytes += (double)c->N3 * (sizeof(Tin) + sizeof(Tout) * (j.acc ? 2 : 1));
       const PassJob<Tin, Tout> pj = make_job<Tin, Tout>(c, j, skip);
       kern<<<blocks, PASS_THREADS, smem, s>>>(pj.in, pj.out, pj.a, Tw<T>::tw(c), Tw<T>::q(c), c->d_s2);
       ++g_launches;
     }
+    launches = nj;
   }
   check_launch();
   if (prof) {
@@ -258,7 +331,7 @@ void stage_list(kfbim_ctx* c, const std::vector<Job>& list, cudaStream_t s, cons
     const int slot = sizeof(T) == 8 ? 0 : 1;
     c->prof_tag[c->prof_used / 2] = slot;
     c->prof_used += 2;
-    c->prof_count[slot] += 1;
+    c->prof_count[slot] += launches;
     c->prof_bytes[slot] += bytes;
   }
 }
@@ -661,6 +734,99 @@ int gmres(kfbim_ctx* c, const double* rhs, double* x, cudaStream_t s, int* iters
   return status;
 }
 
+// Transform matrices of the tensor-core passes, M[a][n] (output a, input n),
+// for the six transforms of transforms.cuh at N = 128, split into TF32 hi/lo
+// parts and stored column-major ([type][hi|lo][n][a]) so that lane a of a warp
+// reads row a.  TF32 rounding: round to nearest, ties away from zero, on the
+// 13 low mantissa bits.
+std::vector<float> tc_matrices(int N) {
+  auto tf32 = [](float x) {
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    u = (u + 0x1000u) & 0xFFFFE000u;
+    float r;
+    std::memcpy(&r, &u, 4);
+    return r;
+  };
+  std::vector<float> out((size_t)6 * 2 * N * N);
+  const double pi = M_PI;
+  for (int type = 1; type <= 6; ++type) {
+    for (int a = 0; a < N; ++a)
+      for (int n = 0; n < N; ++n) {
+        double m = 0.0;
+        switch (type) {
+          case X_DCT2F: m = std::cos(pi * a * (n + 0.5) / N); break;
+          case X_DCT2I: m = (n == 0 ? 1.0 : 2.0) / N * std::cos(pi * n * (a + 0.5) / N); break;
+          case X_DST2F: m = std::sin(pi * (a + 1) * (n + 0.5) / N); break;
+          case X_DST2I: m = (n == N - 1 ? 1.0 : 2.0) / N * std::sin(pi * (n + 1) * (a + 0.5) / N); break;
+          case X_DST1F: m = (a > 0 && n > 0) ? std::sin(pi * (double)a * n / N) : 0.0; break;
+          case X_DST1I: m = (a > 0 && n > 0) ? 2.0 / N * std::sin(pi * (double)a * n / N) : 0.0; break;
+        }
+        const float hi = tf32((float)m);
+        const float lo = tf32((float)(m - (double)hi));
+        const size_t base = (size_t)(type - 1) * 2 * N * N;
+        out[base + (size_t)n * N + a] = hi;
+        out[base + (size_t)N * N + (size_t)n * N + a] = lo;
+      }
+  }
+  return out;
+}
+
+void check_tc(kfbim_ctx* c, cudaStream_t s) {
+  if (!c->d_tc_err) return;
+  int e = 0;
+  CK(cudaMemcpyAsync(&e, c->d_tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (e) throw CudaError{"tensor-core transform pass: an mbarrier wait timed out"};
+}
+
+// Autotuner of the FP32 axis passes (N = 128): times a plain three-job stage
+// (DST-II along z/z/y) and a fused three-job stage (DCT-II, Schur weight,
+// DCT-III along each component's axis) with the FFT kernel and with the
+// tensor-core kernel on the FP32 stage temporaries, and keeps the faster
+// kernel for each stage kind.
+void autotune(kfbim_ctx* c) {
+  const int64_t n = c->N3;
+  float* X = c->fT6;
+  cudaStream_t s = c->cap_stream;
+  CK(cudaMemsetAsync(X, 0, 6 * n * sizeof(float), s));
+  const std::vector<Job> plain = {{X, X + 3 * n, 2, X_DST2F, X_NONE, W_NONE, 0, 0},
+                                  {X + n, X + 4 * n, 2, X_DST2F, X_NONE, W_NONE, 1, 0},
+                                  {X + 2 * n, X + 5 * n, 1, X_DST2F, X_NONE, W_NONE, 2, 0}};
+  const std::vector<Job> fused = {{X + 3 * n, X, 0, X_DCT2F, X_DCT2I, W_SCHUR, 0, 0},
+                                  {X + 4 * n, X + n, 1, X_DCT2F, X_DCT2I, W_SCHUR, 1, 0},
+                                  {X + 5 * n, X + 2 * n, 2, X_DCT2F, X_DCT2I, W_SCHUR, 2, 0}};
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const int64_t launches0 = g_launches;
+  auto time_stage = [&](const std::vector<Job>& list) {
+    for (int w = 0; w < 2; ++w) stage_list<float, float, float>(c, list, s);
+    const int reps = 10;
+    CK(cudaEventRecord(e0, s));
+    for (int r = 0; r < reps; ++r) stage_list<float, float, float>(c, list, s);
+    CK(cudaEventRecord(e1, s));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    return ms / reps;
+  };
+  c->xf_plain = 0;
+  c->tune_ms[0] = time_stage(plain);
+  c->xf_plain = 1;
+  c->tune_ms[1] = time_stage(plain);
+  c->xf_fused = 0;
+  c->tune_ms[2] = time_stage(fused);
+  c->xf_fused = 1;
+  c->tune_ms[3] = time_stage(fused);
+  CK(cudaEventDestroy(e0));
+  CK(cudaEventDestroy(e1));
+  g_launches = launches0;
+  check_tc(c, s);
+  c->xf_plain = c->tune_ms[1] < c->tune_ms[0];
+  c->xf_fused = c->tune_ms[3] < c->tune_ms[2];
+}
+
 void fill_tables(kfbim_ctx* c) {
   HostTables& t = c->host;
   const int N = c->N;
@@ -771,6 +937,19 @@ void fill_tables(kfbim_ctx* c) {
   void* ph = nullptr;
   CK(cudaMallocHost(&ph, sizeof(double) * 256));
   c->pinned = static_cast<double*>(ph);
+  if (c->opt.precision == KFBIM_MIXED && N == TC_N && c->opt.transforms != KFBIM_XF_FFT) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev));
+    c->d_tc_mats = upload(c, tc_matrices(N));
+    c->d_tc_err = dalloc<int>(c, 1);
+    CK(cudaMemset(c->d_tc_err, 0, sizeof(int)));
+    if (c->opt.transforms == KFBIM_XF_TENSOR) {
+      c->xf_plain = c->xf_fused = 1;
+    } else {
+      autotune(c);
+    }
+  }
 }
 
 int fail(kfbim_ctx* c, int code, const std::string& msg) {
@@ -1307,6 +1486,7 @@ void kfbim_default_options(kfbim_options* o) {
   o->inner_tol = 3e-6;
   o->pde = KFBIM_STOKES;
   o->lambda = 0.0;
+  o->transforms = KFBIM_XF_AUTO;
 }
 
 static int setup_common(const kfbim_geometry* geom, const kfbim_grid* grid, const kfbim_options* opt,
@@ -1321,6 +1501,7 @@ static int setup_common(const kfbim_geometry* geom, const kfbim_grid* grid, cons
     return KFBIM_E_INVALID;
   if (geom->kind < 0 || geom->kind > 2) return KFBIM_E_INVALID;
   if (opt->pde != KFBIM_STOKES && opt->pde != KFBIM_NAVIER) return KFBIM_E_INVALID;
+  if (opt->transforms < KFBIM_XF_AUTO || opt->transforms > KFBIM_XF_TENSOR) return KFBIM_E_INVALID;
   if (opt->pde == KFBIM_NAVIER && !(opt->lambda >= 0.0 && opt->lambda + opt->mu > 0.0))
     return KFBIM_E_INVALID;
   std::unique_ptr<kfbim_ctx> c(new (std::nothrow) kfbim_ctx());
@@ -1438,6 +1619,7 @@ int kfbim_apply(kfbim_ctx* c, const double* phi, double* out, void* stream) {
     reset_counters(c);
     cudaStream_t s = (cudaStream_t)stream;
     int st = apply_impl(c, phi, out, s);
+    check_tc(c, s);
     if (st == KFBIM_E_NOCONV) c->err = "inner CG reached its iteration cap";
     return st;
   });
@@ -1466,6 +1648,7 @@ int kfbim_interface(kfbim_ctx* c, const double* phi, const double* fpts, const d
     int st = interface_solve(c, phi, fpts, fgrid, s);
     CK(cudaMemcpyAsync(u, c->u, 3 * c->N3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(p, c->p, c->N3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    check_tc(c, s);
     return st;
   });
 }
@@ -1476,6 +1659,39 @@ int kfbim_trace(kfbim_ctx* c, const double* u, const double* J, double* out, voi
     trace(c, u, J, out, (cudaStream_t)stream);
     return KFBIM_OK;
   });
+}
+
+int kfbim_transform_f32(kfbim_ctx* c, int type, int axis, int wmode, int wc, const float* in, float* out,
+                        int backend, void* stream) {
+  return guarded(c, [&]() -> int {
+    if (type < X_DCT2F || type > X_DST1I || axis < 0 || axis > 2 || wmode < W_NONE || wmode > W_RHS || wc < 0 ||
+        wc > 2 || !in || !out || (backend != KFBIM_XF_FFT && backend != KFBIM_XF_TENSOR))
+      return fail(c, KFBIM_E_INVALID, "kfbim_transform_f32: bad arguments");
+    if (c->opt.precision != KFBIM_MIXED) return fail(c, KFBIM_E_INVALID, "kfbim_transform_f32: needs a MIXED context");
+    if (backend == KFBIM_XF_TENSOR && !c->d_tc_mats)
+      return fail(c, KFBIM_E_INVALID, "kfbim_transform_f32: tensor-core passes need N = 128 and transforms != FFT");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int keep = c->xf_plain;
+    c->xf_plain = backend == KFBIM_XF_TENSOR;
+    try {
+      stage<float, float, float>(c, {{in, out, axis, type, X_NONE, wmode, wc, 0}}, s);
+    } catch (...) {
+      c->xf_plain = keep;
+      throw;
+    }
+    c->xf_plain = keep;
+    check_tc(c, s);
+    return KFBIM_OK;
+  });
+}
+
+int kfbim_transforms_info(const kfbim_ctx* c, int* plain, int* fused, float* tune_ms4) {
+  if (!c) return KFBIM_E_INVALID;
+  if (plain) *plain = c->xf_plain;
+  if (fused) *fused = c->xf_fused;
+  if (tune_ms4)
+    for (int k = 0; k < 4; ++k) tune_ms4[k] = c->tune_ms[k];
+  return KFBIM_OK;
 }
 
 int kfbim_poisson(kfbim_ctx* c, int comp, const double* r, double* u, void* stream) {
@@ -1536,6 +1752,7 @@ int kfbim_solve(kfbim_ctx* c, const double* g, const double* fpts, const double*
     if (u) CK(cudaMemcpyAsync(u, c->u, 3 * c->N3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
     if (p) CK(cudaMemcpyAsync(p, c->p, c->N3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
     CK(cudaStreamSynchronize(s));
+    check_tc(c, s);
     if (stats) {
       stats->gmres_iters = its;
       stats->interface_solves = c->interface_solves;
@@ -1615,6 +1832,7 @@ int kfbim_solve_batch(kfbim_ctx* c, int B, const double* g, const double* fpts, 
       if (p) CK(cudaMemcpyAsync(p + b * N3, w.p, N3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
     }
     CK(cudaStreamSynchronize(s));
+    check_tc(c, s);
     int worst = KFBIM_OK;
     for (int b = 0; b < B; ++b) {
       if (st[b] != KFBIM_OK) worst = st[b];

@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--refine-tol", type=float, default=None, help="MIXED refinement tolerance")
     ap.add_argument("--inner-tol", type=float, default=None, help="MIXED inner FP32 CG tolerance")
+    ap.add_argument("--transforms", default="auto", choices=["auto", "fft", "tensor"],
+                    help="kernels of the FP32 axis passes (auto: the setup-time autotuner's choice)")
     ap.add_argument("--batch", type=int, default=16,
                     help="instances of the batched leg (kfbim_solve_batch); 0 skips it")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
@@ -146,23 +148,29 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_hash():
+PASS_SOURCES = {"fft": ("transforms.cuh", "transforms2.cuh"),
+                 "tensor": ("transforms.cuh", "transforms2.cuh", "tc_pass.cuh")}
+
+
+def kernel_source_hash(kind="fft"):
     h = hashlib.sha256()
-    for f in ("transforms.cuh", "transforms2.cuh"):
+    for f in PASS_SOURCES[kind]:
         h.update(open(os.path.join(ROOT, "paper_2303_04992_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:12]
 
 
-def ncu_traffic(workload):
-    """DRAM bytes per launch of the FP32 transform pass from the committed ncu
-    summary, if it was taken on the current kernel source (else None)."""
-    p = os.path.join(ROOT, "profiles", "axis_pass_fp32_%s.md" % workload)
+def ncu_traffic(workload, kind="fft"):
+    """DRAM bytes per launch of the FP32 transform pass (FFT or tensor-core
+    kernel) from the committed ncu summary, if it was taken on the current
+    kernel source (else None)."""
+    name = "axis_pass_fp32_%s.md" if kind == "fft" else "tc_pass_fp32_%s.md"
+    p = os.path.join(ROOT, "profiles", name % workload)
     if not os.path.exists(p):
         return None
     txt = open(p).read()
     m = re.search(r"kernel_source_sha256_12:\s*([0-9a-f]+)", txt)
     t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
-    if not m or not t or m.group(1) != kernel_source_hash():
+    if not m or not t or m.group(1) != kernel_source_hash(kind):
         return None
     return float(t.group(1))
 
@@ -278,6 +286,7 @@ def main_kfbim(args):
         mixed_opts["refine_tol"] = args.refine_tol
     if args.inner_tol is not None:
         mixed_opts["inner_tol"] = args.inner_tol
+    mixed_opts["transforms"] = {"auto": 0, "fft": 1, "tensor": 2}[args.transforms]
     solver = Solver(geom, grid, precision=MIXED, **mixed_opts, **pde)
     g_h, fpts_h, fgrid_h = inputs(solver, geom, grid, navier)
     g = torch.from_numpy(g_h).to(dev)
@@ -328,8 +337,12 @@ def main_kfbim(args):
     ms32, n32, bytes32 = prof["fp32"]
     peak, peak_kind = measured_peaks()
     achieved = (bytes32 / n32) / (ms32 / n32 * 1e-3) / 1e9 if n32 else 0.0
-    traffic = ncu_traffic(args.workload)
-    roofline = {"bound": "hbm", "kernel": "k_axis_pass<float> (FFT transform pass)",
+    tinfo = solver.transforms_info()
+    kind = "tensor" if tinfo["plain"] else "fft"
+    traffic = ncu_traffic(args.workload, kind)
+    kname = ("k_tc_pass (tcgen05 3xTF32 transform-matrix GEMM pass)" if kind == "tensor"
+             else "k_axis_pass2<float> (four-step FFT transform pass)")
+    roofline = {"bound": "hbm", "kernel": kname,
                 "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_source": peak_kind,
                 "traffic": traffic, "algorithmic_bytes_per_launch": bytes32 / max(n32, 1),
@@ -410,7 +423,7 @@ def main_kfbim(args):
                            "gmres_iters": st["gmres_iters"], "interface_solves": st["interface_solves"],
                            "cg_iters": st["cg_iters"], "refine_sweeps": st["refine_sweeps"],
                            "parallelism": "replicas" if world > 1 else "single"},
-                "transforms": solver.transforms_info(),
+                "transforms": dict(tinfo, requested=args.transforms),
                 "fp64": fp64, "rel_err_vs_fp64": rel, "batched": batched,
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": e2e, "gpu_launches": launches, "clocks": clk}

@@ -234,41 +234,37 @@ void launch_jobs(kfbim_ctx* c, const Job* list, int nj, cudaStream_t s, const in
 // Tensor-core passes of one stage: all jobs share the first transform; a
 // fused job (second transform) becomes a weighted pass into its output and an
 // in-place pass of the second transform.  Returns the kernel launches.
-template <typename Tin>
 int tc_passes(kfbim_ctx* c, const std::vector<Job>& list, cudaStream_t s, const int* skip, double* bytes) {
   const int nj = (int)list.size();
-  auto launch = [&](const auto* jl, int n, auto tag) {
-    using TI = decltype(tag);
+  auto launch = [&](const Job* jl, int n) {
     const int type = jl[0].t0;
-    PassJobs<TI, float, TC_MAXJ> jobs{};
+    PassJobs<float, float, TC_MAXJ> jobs{};
     for (int k = 0; k < n; ++k) {
       Job j = jl[k];
       j.t1 = X_NONE;
-      jobs.j[k] = make_job<TI, float>(c, j, skip);
-      *bytes += (double)c->N3 * (sizeof(TI) + sizeof(float) * (j.acc ? 2 : 1));
+      jobs.j[k] = make_job<float, float>(c, j, skip);
+      *bytes += (double)c->N3 * sizeof(float) * (j.acc ? 3 : 2);
     }
     const int grid = std::min(c->num_sms, n * TC_TILES_PER_JOB);
-    static bool configured = false;   // per template instance
+    static bool configured = false;
     if (!configured) {
-      CK(cudaFuncSetAttribute(k_tc_pass<TI>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+      CK(cudaFuncSetAttribute(k_tc_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
       configured = true;
     }
-    k_tc_pass<TI><<<grid, TC_THREADS, TC_SMEM, s>>>(jobs, n, c->d_tc_mats + (size_t)(type - 1) * 2 * TC_N * TC_N,
-                                                     c->d_s2f, c->d_tc_err);
+    k_tc_pass<<<grid, TC_THREADS, TC_SMEM, s>>>(jobs, n, c->d_tc_mats + (size_t)(type - 1) * 2 * TC_N * TC_N,
+                                                c->d_s2f, c->d_tc_err);
     ++g_launches;
   };
   int launches = 0;
   for (int k0 = 0; k0 < nj; k0 += TC_MAXJ) {
-    const int n = std::min(TC_MAXJ, nj - k0);
-    launch(list.data() + k0, n, Tin{});
+    launch(list.data() + k0, std::min(TC_MAXJ, nj - k0));
     ++launches;
   }
   if (list[0].t1 != X_NONE) {
     std::vector<Job> second;
     for (const Job& j : list) second.push_back({j.out, j.out, j.axis, j.t1, X_NONE, W_NONE, j.wc, j.acc, j.skip});
     for (int k0 = 0; k0 < nj; k0 += TC_MAXJ) {
-      const int n = std::min(TC_MAXJ, nj - k0);
-      launch(second.data() + k0, n, float{});
+      launch(second.data() + k0, std::min(TC_MAXJ, nj - k0));
       ++launches;
     }
   }
@@ -276,10 +272,12 @@ int tc_passes(kfbim_ctx* c, const std::vector<Job>& list, cudaStream_t s, const 
   return launches;
 }
 
-// Whether a stage of FP32 passes goes to the tensor-core kernel.
-template <typename T, typename Tout>
+// Whether a stage of FP32 passes goes to the tensor-core kernel (FP32 input
+// and output; FP64-input stages stay on the FFT kernel).
+template <typename Tin, typename T, typename Tout>
 bool use_tc(const kfbim_ctx* c, const std::vector<Job>& list) {
-  if (!std::is_same<T, float>::value || !std::is_same<Tout, float>::value) return false;
+  if (!std::is_same<Tin, float>::value || !std::is_same<T, float>::value || !std::is_same<Tout, float>::value)
+    return false;
   if (!c->d_tc_mats || list.empty()) return false;
   const bool fused = list[0].t1 != X_NONE;
   if (!(fused ? c->xf_fused : c->xf_plain)) return false;
@@ -297,8 +295,8 @@ void stage_list(kfbim_ctx* c, const std::vector<Job>& list, cudaStream_t s, cons
   if (prof) CK(cudaEventRecord(c->prof_ev[c->prof_used], s));
   const int nj = (int)list.size();
   int launches = 1;
-  if (use_tc<T, Tout>(c, list)) {
-    launches = tc_passes<Tin>(c, list, s, skip, &bytes);
+  if (use_tc<Tin, T, Tout>(c, list)) {
+    launches = tc_passes(c, list, s, skip, &bytes);
   } else if (c->N == 128 || c->N == 64 || c->N == 32) {
     for (const Job& j : list) bytes += (double)c->N3 * (sizeof(Tin) + sizeof(Tout) * (j.acc ? 2 : 1));
     if (nj <= 3) {

@@ -15,10 +15,11 @@
 //
 // CTA: 256 threads, persistent over a contiguous range of tiles of the
 // launch's (non-skipped) jobs, which all use the same transform.  Pipeline per
-// tile: global loads (issued one tile ahead into registers) -> TF32 split ->
-// shared memory stage s (two stages) -> 48 MMAs by one thread into
-// accumulator s (two buffers) -> commit to mbarrier s; the epilogue of the
-// previous tile (tcgen05.ld, weight, coalesced store) overlaps the MMAs.
+// tile: cp.async copies straight into the operand layout (a ring of three
+// stages, two tiles ahead) -> in-place TF32 hi/lo split -> 48 MMAs issued by
+// one thread into accumulator buffer it % 2 -> commit to mbarrier it % 2; the
+// epilogue of the previous tile (tcgen05.ld, weight, coalesced store) and the
+// copies of the tile after next overlap the MMAs.
 // Every mbarrier wait is bounded (about one second of clock cycles); a
 // timeout sets *err, the CTA stops waiting and issuing, and later launches
 // return at once while *err is set (results are then invalid; the host
@@ -35,9 +36,9 @@ constexpr int TC_THREADS = 256;
 constexpr int TC_MAXJ = 48;
 constexpr int TC_TILES_PER_JOB = TC_N * TC_N / TC_COLS;
 constexpr int TC_B_BYTES = TC_COLS * TC_N * 4;     // one operand copy (hi or lo) of a tile
-constexpr int TC_STAGE_BYTES = 2 * TC_B_BYTES;     // hi + lo
+constexpr int TC_STAGES = 3;                       // cp.async ring depth
 constexpr int TC_OUT_BYTES = TC_N * TC_COLS * 4;   // output staging
-constexpr int TC_SMEM = 1024 + 2 * TC_STAGE_BYTES + TC_OUT_BYTES + 256;
+constexpr int TC_SMEM = 1024 + 2 * TC_STAGES * TC_B_BYTES + TC_OUT_BYTES + 256;
 constexpr uint32_t TC_TMEM_COLS = 512;             // T_hi [0,128) T_lo [128,256) D0, D1 [256,384)
 // tcgen05 instruction descriptor: D F32, A and B TF32, both K-major, N = 64, M = 128
 constexpr uint32_t TC_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_COLS >> 3) << 17) |
@@ -142,74 +143,66 @@ __device__ __forceinline__ int64_t tc_col_offset(int axis, int c) {
   return axis == 0 ? (int64_t)c * N : (axis == 1 ? (int64_t)(c / N) * N * N + (c % N) : (int64_t)c);
 }
 
-template <typename Tin>
-struct TcLoad {
-  Tin v[8][4];
-};
-
-// Issue the loads of one tile: 64 lines x 32 chunks of 4 consecutive n.
-// x: lanes run along the chunks of one line (coalesced 512 B rows);
-// y, z: lanes run along the lines for one chunk (coalesced across lines).
-template <typename Tin>
-__device__ __forceinline__ void tc_load_tile(const Tin* __restrict__ in, int axis, int colbase, TcLoad<Tin>& L) {
+// Asynchronous copies (cp.async) of one tile into a stage, already in the
+// K-major 128-byte-swizzled operand layout: element (line p, n) of K-block
+// n/32 sits at block + p*128 + ((chunk ^ (p % 8)) * 16) + (n % 4) * 4, chunk =
+// (n % 32) / 4.  x: 16-byte copies of 4 consecutive n, lanes along the chunks
+// of a line; y, z: 4-byte copies, lanes along the lines (coalesced reads).
+__device__ __forceinline__ void tc_issue_tile(const float* __restrict__ in, int axis, int colbase,
+                                              uint32_t stage) {
   constexpr int64_t N = TC_N;
-  const int64_t estride = axis == 0 ? 1 : (axis == 1 ? N : N * N);
+  if (axis == 0) {
 #pragma unroll
-  for (int r = 0; r < 8; ++r) {
-    const int t = threadIdx.x + TC_THREADS * r;
-    int p, ch;
-    if (axis == 0) { p = t >> 5; ch = t & 31; }
-    else { ch = t >> 6; p = t & 63; }
-    const Tin* src = in + tc_col_offset(axis, colbase + p) + (int64_t)(4 * ch) * estride;
-    if (axis == 0) {
-      if constexpr (sizeof(Tin) == 4) {
-        const float4 q = *reinterpret_cast<const float4*>(src);
-        L.v[r][0] = q.x; L.v[r][1] = q.y; L.v[r][2] = q.z; L.v[r][3] = q.w;
-      } else {
-        const double2 q0 = *reinterpret_cast<const double2*>(src);
-        const double2 q1 = *reinterpret_cast<const double2*>(src + 2);
-        L.v[r][0] = q0.x; L.v[r][1] = q0.y; L.v[r][2] = q1.x; L.v[r][3] = q1.y;
-      }
-    } else {
-#pragma unroll
-      for (int w = 0; w < 4; ++w) L.v[r][w] = src[w * estride];
+    for (int r = 0; r < 8; ++r) {
+      const int t = threadIdx.x + TC_THREADS * r;
+      const int p = t >> 5, ch = t & 31;
+      const float* src = in + (int64_t)(colbase + p) * N + 4 * ch;
+      const uint32_t dst = stage + (ch >> 3) * (TC_COLS * 128) + p * 128 + (((ch & 7) ^ (p & 7)) << 4);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+    }
+  } else {
+    const int64_t estride = axis == 1 ? N : N * N;
+    const int p = threadIdx.x & 63;
+    const float* base = in + tc_col_offset(axis, colbase + p);
+#pragma unroll 8
+    for (int r = 0; r < 32; ++r) {
+      const int n = (threadIdx.x >> 6) + 4 * r;
+      const uint32_t dst = stage + (n >> 5) * (TC_COLS * 128) + p * 128 + ((((n & 31) >> 2) ^ (p & 7)) << 4) +
+                           ((n & 3) << 2);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(base + n * estride) : "memory");
     }
   }
 }
 
-// Split the loaded tile into TF32 hi/lo parts and write the two K-major,
-// 128-byte-swizzled B operands: element (line p, n) of K-block n/32 sits at
-// block + p*128 + ((chunk ^ (p % 8)) * 16) + (n % 4) * 4, chunk = (n % 32) / 4.
-template <typename Tin>
-__device__ __forceinline__ void tc_store_tile(uint8_t* bhi, uint8_t* blo, int axis, const TcLoad<Tin>& L) {
+__device__ __forceinline__ void tc_commit_group() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+// Split a landed stage in place into its TF32 high part and, in the matching
+// low stage, the remainder x - hi.
+__device__ __forceinline__ void tc_split_stage(float* hi, float* lo) {
 #pragma unroll
-  for (int r = 0; r < 8; ++r) {
-    const int t = threadIdx.x + TC_THREADS * r;
-    int p, ch;
-    if (axis == 0) { p = t >> 5; ch = t & 31; }
-    else { ch = t >> 6; p = t & 63; }
-    const int off = (ch >> 3) * (TC_COLS * 128) + p * 128 + (((ch & 7) ^ (p & 7)) << 4);
+  for (int r = 0; r < TC_B_BYTES / 16 / TC_THREADS; ++r) {
+    const int e = 4 * (threadIdx.x + TC_THREADS * r);
+    float4 x = *reinterpret_cast<const float4*>(hi + e);
     float4 h, l;
-    float x;
-    x = (float)L.v[r][0]; h.x = tf32_rna(x); l.x = x - h.x;
-    x = (float)L.v[r][1]; h.y = tf32_rna(x); l.y = x - h.y;
-    x = (float)L.v[r][2]; h.z = tf32_rna(x); l.z = x - h.z;
-    x = (float)L.v[r][3]; h.w = tf32_rna(x); l.w = x - h.w;
-    *reinterpret_cast<float4*>(bhi + off) = h;
-    *reinterpret_cast<float4*>(blo + off) = l;
+    h.x = tf32_rna(x.x); l.x = x.x - h.x;
+    h.y = tf32_rna(x.y); l.y = x.y - h.y;
+    h.z = tf32_rna(x.z); l.z = x.z - h.z;
+    h.w = tf32_rna(x.w); l.w = x.w - h.w;
+    *reinterpret_cast<float4*>(hi + e) = h;
+    *reinterpret_cast<float4*>(lo + e) = l;
   }
 }
 
-template <typename Tin>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-k_tc_pass(const __grid_constant__ PassJobs<Tin, float, TC_MAXJ> jobs, int njobs,
+k_tc_pass(const __grid_constant__ PassJobs<float, float, TC_MAXJ> jobs, int njobs,
           const float* __restrict__ Tm, const float* __restrict__ s2, int* __restrict__ err) {
   extern __shared__ __align__(16) uint8_t tc_smem_raw[];
   const uint32_t raw = smem_u32(tc_smem_raw);
   uint8_t* smem = tc_smem_raw + (((raw + 1023u) & ~1023u) - raw);
-  uint8_t* bst = smem;                                           // [stage][hi|lo][B tile]
-  float* ost = reinterpret_cast<float*>(smem + 2 * TC_STAGE_BYTES);
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * TC_STAGE_BYTES + TC_OUT_BYTES);
+  uint8_t* hi_st = smem;                                     // TC_STAGES x B tile (hi)
+  uint8_t* lo_st = smem + TC_STAGES * TC_B_BYTES;            // TC_STAGES x B tile (lo)
+  float* ost = reinterpret_cast<float*>(smem + 2 * TC_STAGES * TC_B_BYTES);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * TC_STAGES * TC_B_BYTES + TC_OUT_BYTES);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 2);
   int* nact_s = reinterpret_cast<int*>(tmem_slot + 1);
   int* act = nact_s + 1;
@@ -229,6 +222,18 @@ k_tc_pass(const __grid_constant__ PassJobs<Tin, float, TC_MAXJ> jobs, int njobs,
   const int t_begin = (int)((int64_t)blockIdx.x * ntiles / gridDim.x);
   const int t_end = (int)((int64_t)(blockIdx.x + 1) * ntiles / gridDim.x);
   if (t_begin >= t_end) return;
+  auto job_of = [&](int t) -> const PassJob<float, float>& { return jobs.j[act[t / TC_TILES_PER_JOB]]; };
+  auto issue = [&](int t) {
+    const PassJob<float, float>& jb = job_of(t);
+    const int it = t - t_begin;
+    tc_issue_tile(jb.in, jb.a.axis, (t % TC_TILES_PER_JOB) * TC_COLS,
+                  smem_u32(hi_st + (it % TC_STAGES) * TC_B_BYTES));
+  };
+  // the first two tiles are in flight while the CTA sets up
+  issue(t_begin);
+  tc_commit_group();
+  if (t_begin + 1 < t_end) issue(t_begin + 1);
+  tc_commit_group();
 
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
@@ -261,28 +266,24 @@ k_tc_pass(const __grid_constant__ PassJobs<Tin, float, TC_MAXJ> jobs, int njobs,
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
   }
 
-  TcLoad<Tin> L;
-  auto job_of = [&](int t) -> const PassJob<Tin, float>& { return jobs.j[act[t / TC_TILES_PER_JOB]]; };
-  {
-    const PassJob<Tin, float>& jb = job_of(t_begin);
-    tc_load_tile<Tin>(jb.in, jb.a.axis, (t_begin % TC_TILES_PER_JOB) * TC_COLS, L);
-  }
   bool ok = true;
-
-  auto epilogue = [&](int t, int s, uint32_t parity) {
-    if (ok && !tc_wait(smem_u32(&mbar[s]), parity)) {
+  auto wait_mma = [&](int it) {
+    if (ok && !tc_wait(smem_u32(&mbar[it & 1]), (uint32_t)((it >> 1) & 1))) {
       ok = false;
       atomicExch(err, 1);
     }
     tc_fence_after();
-    const PassJob<Tin, float>& jb = job_of(t);
+  };
+
+  auto epilogue = [&](int t, int dbuf) {
+    const PassJob<float, float>& jb = job_of(t);
     const PassArgs& a = jb.a;
     const int axis = a.axis;
     const int colbase = (t % TC_TILES_PER_JOB) * TC_COLS;
     const int m = 32 * (warp & 3) + lane;      // output index along the axis
     const int p0 = 32 * (warp >> 2);            // first of this thread's 32 lines
     float v[32];
-    tc_ld32(tmem + lane_base + (uint32_t)(2 * TC_N + TC_COLS * s + p0), v);
+    tc_ld32(tmem + lane_base + (uint32_t)(2 * TC_N + TC_COLS * dbuf + p0), v);
     const float sc = (float)a.scale;
     if (a.wmode != W_NONE) {
       const float inv_mu = (float)(1.0 / a.mu);
@@ -335,17 +336,19 @@ k_tc_pass(const __grid_constant__ PassJobs<Tin, float, TC_MAXJ> jobs, int njobs,
 #pragma unroll 1
   for (int t = t_begin; t < t_end; ++t) {
     const int it = t - t_begin;
-    const int s = it & 1;
-    uint8_t* bhi = bst + s * TC_STAGE_BYTES;
-    uint8_t* blo = bhi + TC_B_BYTES;
-    tc_store_tile<Tin>(bhi, blo, job_of(t).a.axis, L);
+    const int st = it % TC_STAGES;
+    float* hi = reinterpret_cast<float*>(hi_st + st * TC_B_BYTES);
+    float* lo = reinterpret_cast<float*>(lo_st + st * TC_B_BYTES);
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+    __syncthreads();
+    tc_split_stage(hi, lo);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_fence_before();
     __syncthreads();
     if (tid == 0 && ok) {
       tc_fence_after();
-      const uint32_t d = tmem + (uint32_t)(2 * TC_N + TC_COLS * s);
-      const uint32_t bh = smem_u32(bhi), bl = smem_u32(blo);
+      const uint32_t d = tmem + (uint32_t)(2 * TC_N + TC_COLS * (it & 1));
+      const uint32_t bh = smem_u32(hi), bl = smem_u32(lo);
 #pragma unroll 1
       for (int ks = 0; ks < TC_N / 8; ++ks) {
         const uint32_t koff = (uint32_t)((ks >> 2) * (TC_COLS * 128) + (ks & 3) * 32);
@@ -355,18 +358,21 @@ k_tc_pass(const __grid_constant__ PassJobs<Tin, float, TC_MAXJ> jobs, int njobs,
         tc_mma(d, ahi, dl, 1);
         tc_mma(d, ahi, dh, 1);
       }
-      tc_commit(smem_u32(&mbar[s]));
+      tc_commit(smem_u32(&mbar[it & 1]));
     }
-    if (t + 1 < t_end) {
-      const PassJob<Tin, float>& jb = job_of(t + 1);
-      tc_load_tile<Tin>(jb.in, jb.a.axis, ((t + 1) % TC_TILES_PER_JOB) * TC_COLS, L);
-    }
-    if (it >= 1) epilogue(t - 1, s ^ 1, (uint32_t)(((it - 1) >> 1) & 1));
+    // stage (it + 2) % 3 was read by the MMAs of tile it - 1: wait for them,
+    // then refill it with tile it + 2 and run the epilogue of tile it - 1
+    if (it >= 1) wait_mma(it - 1);
+    if (t + 2 < t_end) issue(t + 2);
+    tc_commit_group();
+    if (it >= 1) epilogue(t - 1, (it - 1) & 1);
   }
   {
     const int it = t_end - 1 - t_begin;
-    epilogue(t_end - 1, it & 1, (uint32_t)((it >> 1) & 1));
+    wait_mma(it);
+    epilogue(t_end - 1, it & 1);
   }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();

@@ -782,7 +782,13 @@ void check_tc(kfbim_ctx* c, cudaStream_t s) {
 // (DST-II along z/z/y) and a fused three-job stage (DCT-II, Schur weight,
 // DCT-III along each component's axis) with the FFT kernel and with the
 // tensor-core kernel on the FP32 stage temporaries, and keeps the faster
-// kernel for each stage kind.
+// kernel for each stage kind.  The tensor-core passes are less accurate (TF32
+// products accumulate in the tensor core's FP32 adder, about 2e-6 relative
+// against about 2e-7 for the FFT), which costs the MIXED refinement a third
+// sweep per interface solve: on star128 the Schur CG iterations per solve grew
+// from 1642 to 2489.  A tensor-core stage is therefore chosen only when it is
+// faster than the FFT stage by that factor.
+constexpr float kTcIterationFactor = 1.5f;
 void autotune(kfbim_ctx* c) {
   const int64_t n = c->N3;
   float* X = c->fT6;
@@ -821,8 +827,8 @@ void autotune(kfbim_ctx* c) {
   CK(cudaEventDestroy(e1));
   g_launches = launches0;
   check_tc(c, s);
-  c->xf_plain = c->tune_ms[1] < c->tune_ms[0];
-  c->xf_fused = c->tune_ms[3] < c->tune_ms[2];
+  c->xf_plain = c->tune_ms[1] * kTcIterationFactor < c->tune_ms[0];
+  c->xf_fused = c->tune_ms[3] * kTcIterationFactor < c->tune_ms[2];
 }
 
 void fill_tables(kfbim_ctx* c) {

@@ -109,7 +109,7 @@ def test_tc_solve_matches_fp64(star_pair):
     torch.cuda.synchronize()
     assert float((phi - phi64).abs().max() / phi64.abs().max()) < 1e-8
     assert abs(st["gmres_iters"] - s64.last_stats["gmres_iters"]) <= 3
-    # the refinement keeps about two sweeps per interface solve
+    # the coarser accumulation costs at most a third refinement sweep per interface solve
     assert st["refine_sweeps"] <= 3 * st["interface_solves"]
 
 
@@ -119,5 +119,6 @@ def test_autotuner_record():
     info = s.transforms_info()
     ms = info["tune_ms"]
     assert all(m > 0 for m in ms)
-    assert info["plain"] == int(ms[1] < ms[0])
-    assert info["fused"] == int(ms[3] < ms[2])
+    # a tensor-core stage must beat the FFT stage by the iteration factor 1.5
+    assert info["plain"] == int(ms[1] * 1.5 < ms[0])
+    assert info["fused"] == int(ms[3] * 1.5 < ms[2])

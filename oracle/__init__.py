@@ -16,9 +16,11 @@ no fusion or reordering:
   correct.py   right-hand-side corrections                  (Sec. 4.3 items 1-4)
   interp.py    ten-node quadratic trace interpolation       (Sec. 4.4)
   kfbim.py     interface solve, matvec, GMRES, final fields (Alg. 1 steps 2-3)
+  adjoint.py   gradient of a velocity loss w.r.t. the boundary data, by the
+               dense transpose of the forward maps (small grids)
 
-Readings of the paper where it is silent, ambiguous or self-contradictory are
-listed in the design doc; each function repeats the reading it relies on.
+Where the paper is silent, ambiguous or self-contradictory, each function
+states the reading it relies on.
 Parity status: every function is pinned by a `-m "not gpu"` test except the
 control-point surface fit (the paper defers that design to earlier work), whose
 choice of neighbourhood and weights is parity unpinned; it is covered only

@@ -55,10 +55,14 @@ class Setup:
         self.cg_iters.append(it)
         return u, p, J
 
+    def trace(self, u, J):
+        """u^+ at the primary control points from face fields u and jumps J."""
+        return interp.trace(self.grid, self.cp, self.S, u, J)[self.primary]
+
     def apply(self, phi):
         """(1/2 I - M_v) phi at the primary control points."""
         u, _, J = self.interface(phi, np.zeros((self.cp.n, 3)), None)
-        return interp.trace(self.grid, self.cp, self.S, u, J)[self.primary]
+        return self.trace(u, J)
 
     def volume_trace(self, fy, f_faces):
         """(G_v f) on Gamma at the primary control points."""

@@ -194,6 +194,26 @@ int kfbim_solve_host(kfbim_ctx* ctx, const double* g_host, const double* fpts_ho
                      const double* fgrid_host, double* phi_host, double* u_host,
                      double* p_host, kfbim_stats* stats, void* stream);
 
+/* Adjoint (gradients with respect to the boundary data; not in the paper,
+ * which solves forward problems only).  With A the GMRES matvec of
+ * kfbim_apply and U the linear map from the density to the interface-solve
+ * velocity (the u_dev of kfbim_solve), a solve computes u = U A^-1 (g - G_v f)
+ * + (terms in f), so for a loss L(u) the gradient with respect to g is
+ * dL/dg = A^-T U^T dL/du.
+ * kfbim_apply_adjoint: out = A^T lam, lam_dev and out_dev n_primary doubles
+ *   (may not alias): the transposed trace, transposed grid solve (the forward
+ *   corrected MAC solve of (w, 0) with the pressure negated: K^T = S K S for
+ *   S = diag(I, -I)), transposed corrections and transposed jump map.
+ * kfbim_solve_adjoint: gbar = A^-T U^T ubar by GMRES on A^T (same tolerance
+ *   and cap as kfbim_solve).  ubar_dev [3*N^3]: dL/du on the three face grids
+ *   (wall-face entries ignored); gbar_dev [n_primary]: dL/dg at the primary
+ *   points.  stats nullable.  Errors as kfbim_solve.  The transposed tables
+ *   are built on the first call (host work plus device memory, about the
+ *   size of the forward tables). */
+int kfbim_apply_adjoint(kfbim_ctx* ctx, const double* lam_dev, double* out_dev, void* stream);
+int kfbim_solve_adjoint(kfbim_ctx* ctx, const double* ubar_dev, double* gbar_dev,
+                        kfbim_stats* stats, void* stream);
+
 /* Largest batch accepted by kfbim_solve_batch. */
 #define KFBIM_BATCH_MAX 64
 

@@ -9,6 +9,7 @@ loudly when it has not been built.
 """
 from .binding import Solver, KfbimError, load_library, library_path  # noqa: F401
 from .build import build  # noqa: F401
+from .autograd import solve_velocity  # noqa: F401
 
 FP64 = 0
 MIXED = 1

@@ -65,6 +65,8 @@ SYMBOLS = {
     "kfbim_transform_f32": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_int,
                                     c_void_p]),
     "kfbim_transforms_info": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "kfbim_apply_adjoint": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "kfbim_solve_adjoint": (c_int, [c_void_p, c_void_p, c_void_p, ctypes.POINTER(Stats), c_void_p]),
     "kfbim_jumps": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "kfbim_interface": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "kfbim_trace": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
@@ -244,6 +246,18 @@ class Solver:
                                                 _ptr(u), _ptr(p), st, self._stream()))
         self.last_stats = [{k: getattr(st[b], k) for k, _ in Stats._fields_} for b in range(B)]
         return phi
+
+    def apply_adjoint(self, lam, out):
+        self._check(self._lib.kfbim_apply_adjoint(self._ctx, _ptr(lam), _ptr(out), self._stream()))
+        return out
+
+    def solve_adjoint(self, ubar, gbar):
+        """gbar = dL/dg for ubar = dL/du (3 N^3 face-grid values)."""
+        st = Stats()
+        self._check(self._lib.kfbim_solve_adjoint(self._ctx, _ptr(ubar), _ptr(gbar), ctypes.byref(st),
+                                                  self._stream()))
+        self.last_stats = {k: getattr(st, k) for k, _ in Stats._fields_}
+        return gbar
 
     def jumps(self, phi, J, fpts=None):
         self._check(self._lib.kfbim_jumps(self._ctx, _ptr(phi), _ptr(fpts), _ptr(J), self._stream()))

@@ -492,3 +492,118 @@ __global__ void k_scale_copy(const double* __restrict__ a, double sc_host, const
 }
 
 }  // namespace kfbim
+
+namespace kfbim {
+
+// ------------------------------------------------------------- adjoint
+// Transposes of the linear maps phi -> J (jumps), J -> rhs (corrections) and
+// (u, J) -> trace, each a gather over a transposed CSR built once on the
+// host (fixed summation order, no atomics).
+
+// rhs[0 : 3 N^3] = ubar with the wall faces (normal index 0) zeroed, rhs[3 N^3 :] = 0.
+__global__ void k_adjoint_rhs(const double* __restrict__ ubar, int lg, double* __restrict__ rhs) {
+  const int64_t N3 = (int64_t)1 << (3 * lg);
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < 4 * N3;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int f = (int)(e >> (3 * lg));
+    double v = 0.0;
+    if (f < 3) {
+      int i, j, k;
+      unflat(e - ((int64_t)f << (3 * lg)), lg, i, j, k);
+      const int nrm = f == 0 ? i : (f == 1 ? j : k);
+      if (nrm > 0) v = ubar[e];
+    }
+    rhs[e] = v;
+  }
+}
+
+// ubar[key[r]] = sum_e w[e] lam[q[e]]: the trace rows transposed onto the
+// face-grid nodes they read (ubar zeroed by the caller).
+__global__ void k_trace_T_u(const int64_t* __restrict__ key, const int64_t* __restrict__ ptr,
+                            const int32_t* __restrict__ q, const double* __restrict__ w, int64_t nkeys,
+                            const double* __restrict__ lam, double* __restrict__ ubar) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nkeys;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int64_t e = ptr[r]; e < ptr[r + 1]; ++e) s += w[e] * lam[q[e]];
+    ubar[key[r]] = s;
+  }
+}
+
+// Jbar[k][y] = tcj[q][k] lam[q] for the primary point y of trace row q
+// (each point has at most one trace row; Jbar zeroed by the caller).
+__global__ void k_trace_T_J(const double* __restrict__ lam, int64_t n_all, int64_t n_prim,
+                            const int64_t* __restrict__ prim_of, const double* __restrict__ tcj,
+                            double* __restrict__ Jbar) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n_prim;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t y = prim_of[q];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) Jbar[(int64_t)k * n_all + y] = tcj[10 * q + k] * lam[q];
+  }
+}
+
+// Jbar[key[r]] += sum_e coef[e] rbar[row[e]]: the correction rows transposed
+// (key = slot * n_all + point).
+__global__ void k_corrections_T(const int64_t* __restrict__ key, const int64_t* __restrict__ ptr,
+                                const int64_t* __restrict__ row, const double* __restrict__ coef,
+                                int64_t nkeys, const double* __restrict__ rbar, double* __restrict__ Jbar) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nkeys;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int64_t e = ptr[r]; e < ptr[r + 1]; ++e) s += coef[e] * rbar[row[e]];
+    Jbar[key[r]] += s;
+  }
+}
+
+// Per point y: the jump map transposed, Dbar[(3y + c')][s] (s = 0 value, 1..5
+// the fitted derivatives d_1, d_2, d_11, d_12, d_22 of phi^(c')).  Slot 0 of a
+// secondary point is its fitted value; of a primary point, phi itself (added
+// in k_fit_T).
+__global__ void k_jumps_T(const double* __restrict__ Jbar, int64_t n, const int32_t* __restrict__ comp,
+                          const int32_t* __restrict__ pid, const double* __restrict__ jmap,
+                          double* __restrict__ Dbar) {
+  for (int64_t y = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; y < n;
+       y += (int64_t)gridDim.x * blockDim.x) {
+    double jb[11];
+#pragma unroll
+    for (int r = 0; r < 11; ++r) jb[r] = Jbar[(int64_t)(r + 1) * n + y];
+    const double* M = jmap + (size_t)y * 18 * 11;
+    const int c = comp[y] - 1;
+    const double j0 = (pid[y] < 0) ? Jbar[y] : 0.0;
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc) {
+      double* D = Dbar + (size_t)(3 * y + cc) * 6;
+      D[0] = (cc == c) ? j0 : 0.0;
+#pragma unroll
+      for (int s = 0; s < 5; ++s) {
+        const double* m = M + (5 * cc + s) * 11;
+        double acc = 0.0;
+#pragma unroll
+        for (int r = 0; r < 11; ++r) acc += m[r] * jb[r];
+        D[s + 1] = acc;
+      }
+    }
+  }
+}
+
+// phibar[col] = Jbar[0][point of col] + sum over the fit entries reading col
+// of sum_s fit_w[s][q] Dbar[row][s]  (the surface fit transposed).
+__global__ void k_fit_T(const int64_t* __restrict__ ptr, const int64_t* __restrict__ q,
+                        const int64_t* __restrict__ rr, const double* __restrict__ fit_w, int64_t fit_nnz,
+                        const double* __restrict__ Dbar, const double* __restrict__ Jbar,
+                        const int64_t* __restrict__ prim_of, int64_t n_prim, double* __restrict__ out) {
+  for (int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; col < n_prim;
+       col += (int64_t)gridDim.x * blockDim.x) {
+    double s = Jbar[prim_of[col]];
+    for (int64_t e = ptr[col]; e < ptr[col + 1]; ++e) {
+      const int64_t qe = q[e];
+      const double* D = Dbar + (size_t)rr[e] * 6;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) s += fit_w[k * fit_nnz + qe] * D[k];
+    }
+    out[col] = s;
+  }
+}
+
+}  // namespace kfbim

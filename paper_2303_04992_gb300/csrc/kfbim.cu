@@ -109,6 +109,14 @@ struct kfbim_ctx {
   void* bpinned = nullptr;     // host staging of bcgs / bscal / bgh
   int bcap = 0, bm = 0;
   std::vector<int> b_cg, b_sweeps, b_isolves;   // per-slot counters of the current call
+  // adjoint: transposed trace (by node), corrections (by jump slot) and fit
+  // (by primary column) tables, built on first use; Jbar, Dbar work arrays
+  bool adj_ready = false;
+  int64_t ta_n = 0, ca_n = 0;
+  int64_t *d_ta_key = nullptr, *d_ta_ptr = nullptr, *d_ca_key = nullptr, *d_ca_ptr = nullptr,
+          *d_ca_row = nullptr, *d_fa_ptr = nullptr, *d_fa_q = nullptr, *d_fa_rr = nullptr;
+  int32_t* d_ta_q = nullptr;
+  double *d_ta_w = nullptr, *d_ca_coef = nullptr, *d_Jbar = nullptr, *d_Dbar = nullptr;
   // counters of the current call
   int cg_iters = 0, refine_sweeps = 0, interface_solves = 0;
 };
@@ -651,8 +659,12 @@ int apply_impl(kfbim_ctx* c, const double* phi, double* out, cudaStream_t s) {
   return st;
 }
 
-// GMRES (Alg. 1 step 3): unrestarted, CGS2 on the device, Givens on the host.
-int gmres(kfbim_ctx* c, const double* rhs, double* x, cudaStream_t s, int* iters, double* res_out) {
+// GMRES (Alg. 1 step 3): unrestarted, CGS2 on the device, Givens on the host;
+// with `adjoint`, GMRES on the transposed matvec.
+int adjoint_apply(kfbim_ctx* c, const double* lam, double* out, cudaStream_t s);
+
+int gmres(kfbim_ctx* c, const double* rhs, double* x, cudaStream_t s, int* iters, double* res_out,
+          bool adjoint = false) {
   const int64_t n = c->n_prim;
   const int m = c->gm_max;
   const int64_t ld = n;
@@ -675,7 +687,8 @@ int gmres(kfbim_ctx* c, const double* rhs, double* x, cudaStream_t s, int* iters
   double res = 1.0;
   const int nb = 64;
   for (k = 1; k <= m; ++k) {
-    int st = apply_impl(c, c->V + (int64_t)(k - 1) * ld, c->gw, s);
+    int st = adjoint ? adjoint_apply(c, c->V + (int64_t)(k - 1) * ld, c->gw, s)
+                     : apply_impl(c, c->V + (int64_t)(k - 1) * ld, c->gw, s);
     if (st != KFBIM_OK && st != KFBIM_E_NOCONV) return st;
     std::fill(hcol.begin(), hcol.end(), 0.0);
     for (int pass2 = 0; pass2 < 2; ++pass2) {
@@ -730,6 +743,139 @@ int gmres(kfbim_ctx* c, const double* rhs, double* x, cudaStream_t s, int* iters
   *iters = kk;
   *res_out = res;
   return status;
+}
+
+// ------------------------------------------------------------ adjoint
+// A phi = T_u K^-1 C J(phi) + T_J J(phi) (trace of the interface solve), so
+// A^T lam = J^T (C^T K^-T (T_u^T lam, 0) + T_J^T lam).  K is the corrected MAC
+// operator [mu L, G; D, c I] with D = -G^T (c = 0, plus the lambda_h
+// projection and gauge, for Stokes): with S = diag(I, -I), K^T = S K S, so
+// K^-T (w, 0) = (u', -p') where (u', p') is the forward grid solve of (w, 0).
+template <typename V>
+void csr_by_key(std::vector<std::pair<int64_t, V>>& e, std::vector<int64_t>& key, std::vector<int64_t>& ptr,
+                std::vector<V>& val) {
+  std::stable_sort(e.begin(), e.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+  ptr.assign(1, 0);
+  for (size_t k = 0; k < e.size(); ++k) {
+    if (k == 0 || e[k].first != e[k - 1].first) {
+      if (k > 0) ptr.push_back((int64_t)k);
+      key.push_back(e[k].first);
+    }
+    val.push_back(e[k].second);
+  }
+  ptr.push_back((int64_t)e.size());
+}
+
+void adjoint_tables(kfbim_ctx* c) {
+  if (c->adj_ready) return;
+  const HostTables& t = c->host;
+  const int64_t N3 = c->N3;
+  {  // trace rows by face-grid node
+    std::vector<std::pair<int64_t, std::pair<int32_t, double>>> e;
+    for (int64_t q = 0; q < t.n_prim; ++q)
+      for (int i = 0; i < kStencil; ++i)
+        e.push_back({(int64_t)(t.tr_comp[q] - 1) * N3 + t.tr_node[kStencil * q + i],
+                     {(int32_t)q, t.tr_w[kStencil * q + i]}});
+    std::vector<int64_t> key, ptr;
+    std::vector<std::pair<int32_t, double>> val;
+    csr_by_key(e, key, ptr, val);
+    std::vector<int32_t> qv;
+    std::vector<double> wv;
+    for (const auto& v : val) {
+      qv.push_back(v.first);
+      wv.push_back(v.second);
+    }
+    c->ta_n = (int64_t)key.size();
+    c->d_ta_key = upload(c, key);
+    c->d_ta_ptr = upload(c, ptr);
+    c->d_ta_q = upload(c, qv);
+    c->d_ta_w = upload(c, wv);
+  }
+  {  // correction rows by jump slot
+    std::vector<std::pair<int64_t, std::pair<int64_t, double>>> e;
+    for (size_t r = 0; r + 1 < t.corr_ptr.size(); ++r)
+      for (int64_t k = t.corr_ptr[r]; k < t.corr_ptr[r + 1]; ++k)
+        e.push_back({t.corr_src[k], {t.corr_row[r], t.corr_coef[k]}});
+    std::vector<int64_t> key, ptr;
+    std::vector<std::pair<int64_t, double>> val;
+    csr_by_key(e, key, ptr, val);
+    std::vector<int64_t> row;
+    std::vector<double> coef;
+    for (const auto& v : val) {
+      row.push_back(v.first);
+      coef.push_back(v.second);
+    }
+    c->ca_n = (int64_t)key.size();
+    c->d_ca_key = upload(c, key);
+    c->d_ca_ptr = upload(c, ptr);
+    c->d_ca_row = upload(c, row);
+    c->d_ca_coef = upload(c, coef);
+  }
+  {  // fit entries by primary column
+    std::vector<std::vector<std::pair<int64_t, int64_t>>> bycol(std::max<int64_t>(1, t.n_prim));
+    for (int64_t rr = 0; rr + 1 < (int64_t)t.fit_ptr.size(); ++rr)
+      for (int64_t q = t.fit_ptr[rr]; q < t.fit_ptr[rr + 1]; ++q) bycol[t.fit_col[q]].emplace_back(q, rr);
+    std::vector<int64_t> ptr{0}, qv, rv;
+    for (int64_t col = 0; col < t.n_prim; ++col) {
+      for (const auto& pr : bycol[col]) {
+        qv.push_back(pr.first);
+        rv.push_back(pr.second);
+      }
+      ptr.push_back((int64_t)qv.size());
+    }
+    c->d_fa_ptr = upload(c, ptr);
+    c->d_fa_q = upload(c, qv);
+    c->d_fa_rr = upload(c, rv);
+  }
+  c->d_Jbar = dalloc<double>(c, kSlots * c->n_all);
+  c->d_Dbar = dalloc<double>(c, 18 * c->n_all);
+  c->adj_ready = true;
+}
+
+// rhs = [ubar | 0] and Jbar hold the adjoint inputs of the interface solve:
+// out = J^T (C^T K^-T rhs + Jbar).
+int adjoint_tail(kfbim_ctx* c, double* out, cudaStream_t s) {
+  const int64_t N3 = c->N3, n = c->n_all;
+  ++c->interface_solves;
+  int st = c->opt.precision == KFBIM_MIXED ? grid_solve_mixed(c, s) : grid_solve_fp64(c, s);
+  if (st != KFBIM_OK && st != KFBIM_E_NOCONV) return st;
+  double* rbar = c->t1;   // [u' | -p'] (4 N^3)
+  CK(cudaMemcpyAsync(rbar, c->u, 3 * N3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  k_scale_copy<<<grid_for(N3), 256, 0, s>>>(c->p, -1.0, nullptr, rbar + 3 * N3, N3); ++g_launches;
+  if (c->ca_n > 0) {
+    k_corrections_T<<<grid_for(c->ca_n), 256, 0, s>>>(c->d_ca_key, c->d_ca_ptr, c->d_ca_row, c->d_ca_coef, c->ca_n,
+                                                       rbar, c->d_Jbar); ++g_launches;
+  }
+  k_jumps_T<<<grid_for(n), 256, 0, s>>>(c->d_Jbar, n, c->d_comp, c->d_pid, c->d_jmap, c->d_Dbar); ++g_launches;
+  k_fit_T<<<grid_for(c->n_prim), 256, 0, s>>>(c->d_fa_ptr, c->d_fa_q, c->d_fa_rr, c->d_fit_w, c->fit_nnz, c->d_Dbar,
+                                               c->d_Jbar, c->d_prim_of, c->n_prim, out); ++g_launches;
+  check_launch();
+  return st;
+}
+
+// out = A^T lam (primary points).
+int adjoint_apply(kfbim_ctx* c, const double* lam, double* out, cudaStream_t s) {
+  adjoint_tables(c);
+  const int64_t N3 = c->N3;
+  CK(cudaMemsetAsync(c->rhs, 0, 4 * N3 * sizeof(double), s));
+  CK(cudaMemsetAsync(c->d_Jbar, 0, kSlots * c->n_all * sizeof(double), s));
+  if (c->ta_n > 0) {
+    k_trace_T_u<<<grid_for(c->ta_n), 256, 0, s>>>(c->d_ta_key, c->d_ta_ptr, c->d_ta_q, c->d_ta_w, c->ta_n, lam,
+                                                   c->rhs); ++g_launches;
+  }
+  k_trace_T_J<<<grid_for(c->n_prim), 256, 0, s>>>(lam, c->n_all, c->n_prim, c->d_prim_of, c->d_tr_cj, c->d_Jbar);
+  ++g_launches;
+  check_launch();
+  return adjoint_tail(c, out, s);
+}
+
+// out = U^T ubar, U: phi -> interface-solve velocity (3 face fields).
+int adjoint_from_u(kfbim_ctx* c, const double* ubar, double* out, cudaStream_t s) {
+  adjoint_tables(c);
+  k_adjoint_rhs<<<grid_for(4 * c->N3), 256, 0, s>>>(ubar, c->lg, c->rhs); ++g_launches;
+  CK(cudaMemsetAsync(c->d_Jbar, 0, kSlots * c->n_all * sizeof(double), s));
+  check_launch();
+  return adjoint_tail(c, out, s);
 }
 
 // Transform matrices of the tensor-core passes, M[a][n] (output a, input n),
@@ -1851,6 +1997,45 @@ int kfbim_solve_batch(kfbim_ctx* c, int B, const double* g, const double* fpts, 
     }
     if (worst == KFBIM_E_NOCONV) c->err = "GMRES reached its iteration cap for an instance of the batch";
     return worst;
+  });
+}
+
+int kfbim_apply_adjoint(kfbim_ctx* c, const double* lam, double* out, void* stream) {
+  return guarded(c, [&]() -> int {
+    if (!lam || !out || lam == out) return fail(c, KFBIM_E_INVALID, "kfbim_apply_adjoint: bad pointers");
+    reset_counters(c);
+    cudaStream_t s = (cudaStream_t)stream;
+    int st = adjoint_apply(c, lam, out, s);
+    CK(cudaStreamSynchronize(s));
+    check_tc(c, s);
+    if (st == KFBIM_E_NOCONV) c->err = "inner CG reached its iteration cap";
+    return st;
+  });
+}
+
+int kfbim_solve_adjoint(kfbim_ctx* c, const double* ubar, double* gbar, kfbim_stats* stats, void* stream) {
+  return guarded(c, [&]() -> int {
+    if (!ubar || !gbar) return fail(c, KFBIM_E_INVALID, "kfbim_solve_adjoint: bad pointers");
+    reset_counters(c);
+    const int64_t launches0 = g_launches;
+    cudaStream_t s = (cudaStream_t)stream;
+    int st0 = adjoint_from_u(c, ubar, c->grhs, s);
+    if (st0 != KFBIM_OK && st0 != KFBIM_E_NOCONV) return st0;
+    int its = 0;
+    double res = 0.0;
+    int st = gmres(c, c->grhs, gbar, s, &its, &res, true);
+    CK(cudaStreamSynchronize(s));
+    check_tc(c, s);
+    if (stats) {
+      stats->gmres_iters = its;
+      stats->interface_solves = c->interface_solves;
+      stats->cg_iters = c->cg_iters;
+      stats->refine_sweeps = c->refine_sweeps;
+      stats->gmres_residual = res;
+      stats->kernel_launches = g_launches - launches0;
+    }
+    if (st == KFBIM_E_NOCONV) c->err = "adjoint GMRES reached its iteration cap";
+    return st;
   });
 }
 

@@ -208,8 +208,8 @@ int kfbim_solve_host(kfbim_ctx* ctx, const double* g_host, const double* fpts_ho
  *   and cap as kfbim_solve).  ubar_dev [3*N^3]: dL/du on the three face grids
  *   (wall-face entries ignored); gbar_dev [n_primary]: dL/dg at the primary
  *   points.  stats nullable.  Errors as kfbim_solve.  The transposed tables
- *   are built on the first call (host work plus device memory, about the
- *   size of the forward tables). */
+ *   are built by kfbim_setup (device memory about a third of the forward
+ *   tables). */
 int kfbim_apply_adjoint(kfbim_ctx* ctx, const double* lam_dev, double* out_dev, void* stream);
 int kfbim_solve_adjoint(kfbim_ctx* ctx, const double* ubar_dev, double* gbar_dev,
                         kfbim_stats* stats, void* stream);

@@ -589,8 +589,8 @@ __global__ void k_jumps_T(const double* __restrict__ Jbar, int64_t n, const int3
 
 // phibar[col] = Jbar[0][point of col] + sum over the fit entries reading col
 // of sum_s fit_w[s][q] Dbar[row][s]  (the surface fit transposed).
-__global__ void k_fit_T(const int64_t* __restrict__ ptr, const int64_t* __restrict__ q,
-                        const int64_t* __restrict__ rr, const double* __restrict__ fit_w, int64_t fit_nnz,
+__global__ void k_fit_T(const int64_t* __restrict__ ptr, const int32_t* __restrict__ q,
+                        const int32_t* __restrict__ rr, const double* __restrict__ fit_w, int64_t fit_nnz,
                         const double* __restrict__ Dbar, const double* __restrict__ Jbar,
                         const int64_t* __restrict__ prim_of, int64_t n_prim, double* __restrict__ out) {
   for (int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; col < n_prim;

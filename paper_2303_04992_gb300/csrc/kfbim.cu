@@ -110,12 +110,12 @@ struct kfbim_ctx {
   int bcap = 0, bm = 0;
   std::vector<int> b_cg, b_sweeps, b_isolves;   // per-slot counters of the current call
   // adjoint: transposed trace (by node), corrections (by jump slot) and fit
-  // (by primary column) tables, built on first use; Jbar, Dbar work arrays
+  // (by primary column) tables, built at setup; Jbar, Dbar work arrays
   bool adj_ready = false;
   int64_t ta_n = 0, ca_n = 0;
   int64_t *d_ta_key = nullptr, *d_ta_ptr = nullptr, *d_ca_key = nullptr, *d_ca_ptr = nullptr,
-          *d_ca_row = nullptr, *d_fa_ptr = nullptr, *d_fa_q = nullptr, *d_fa_rr = nullptr;
-  int32_t* d_ta_q = nullptr;
+          *d_ca_row = nullptr, *d_fa_ptr = nullptr;
+  int32_t *d_ta_q = nullptr, *d_fa_q = nullptr, *d_fa_rr = nullptr;
   double *d_ta_w = nullptr, *d_ca_coef = nullptr, *d_Jbar = nullptr, *d_Dbar = nullptr;
   // counters of the current call
   int cg_iters = 0, refine_sweeps = 0, interface_solves = 0;
@@ -815,11 +815,12 @@ void adjoint_tables(kfbim_ctx* c) {
     std::vector<std::vector<std::pair<int64_t, int64_t>>> bycol(std::max<int64_t>(1, t.n_prim));
     for (int64_t rr = 0; rr + 1 < (int64_t)t.fit_ptr.size(); ++rr)
       for (int64_t q = t.fit_ptr[rr]; q < t.fit_ptr[rr + 1]; ++q) bycol[t.fit_col[q]].emplace_back(q, rr);
-    std::vector<int64_t> ptr{0}, qv, rv;
+    std::vector<int64_t> ptr{0};
+    std::vector<int32_t> qv, rv;
     for (int64_t col = 0; col < t.n_prim; ++col) {
       for (const auto& pr : bycol[col]) {
-        qv.push_back(pr.first);
-        rv.push_back(pr.second);
+        qv.push_back((int32_t)pr.first);
+        rv.push_back((int32_t)pr.second);
       }
       ptr.push_back((int64_t)qv.size());
     }
@@ -1683,6 +1684,7 @@ static int setup_common(const kfbim_geometry* geom, const kfbim_grid* grid, cons
   if (device) {
     try {
       fill_tables(c.get());
+      adjoint_tables(c.get());   // before the host fit and correction tables are released
     } catch (const CudaError& e) {
       std::fprintf(stderr, "kfbim_setup: %s\n", e.msg.c_str());
       for (void* p : c->allocs) cudaFree(p);

@@ -163,6 +163,27 @@ inline void check_launch() {
   if (e != cudaSuccess) throw CudaError{std::string("kernel launch: ") + cudaGetErrorString(e)};
 }
 
+// Raise, never lower, the dynamic shared-memory limit of a kernel that is
+// launched with several sizes (the runtime-N pass): setting the attribute to a
+// small size would also lower it below the 48 KiB default for every later
+// launch of that kernel, from any path of this library.
+cudaError_t raise_dynamic_smem(const void* kern, size_t bytes) {
+  static std::mutex m;
+  static std::vector<std::pair<const void*, size_t>> limit;
+  std::lock_guard<std::mutex> lock(m);
+  size_t* cur = nullptr;
+  for (auto& e : limit)
+    if (e.first == kern) cur = &e.second;
+  if (!cur) {
+    limit.push_back({kern, (size_t)48 * 1024});
+    cur = &limit.back().second;
+  }
+  if (bytes <= *cur) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) *cur = bytes;
+  return e;
+}
+
 // ------------------------------------------------------------ transforms
 template <typename T>
 struct Tw;
@@ -317,11 +338,7 @@ void stage_list(kfbim_ctx* c, const std::vector<Job>& list, cudaStream_t s, cons
   } else {
     const size_t smem = pass_smem_bytes(c->N, sizeof(T));
     auto kern = k_axis_pass<Tin, T, Tout>;
-    static size_t configured = 0;  // per template instance
-    if (smem > configured) {
-      CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      configured = smem;
-    }
+    CK(raise_dynamic_smem((const void*)kern, smem));
     const int blocks = (int)((int64_t)c->N * c->N / LPC);
     for (const Job& j : list) {
       bytes += (double)c->N3 * (sizeof(Tin) + sizeof(Tout) * (j.acc ? 2 : 1));
@@ -1175,11 +1192,15 @@ int noalloc_symbols(NoAllocSymbols** out) {
   std::lock_guard<std::mutex> lock(g_na_mutex);
   NoAllocSymbols& d = g_na_dev[dev];
   if (!d.ready) {
-    if (cudaGetSymbolAddress((void**)&d.scratch, g_na_scratch) != cudaSuccess ||
-        cudaGetSymbolAddress((void**)&d.tw, g_na_tw) != cudaSuccess ||
-        cudaGetSymbolAddress((void**)&d.q, g_na_q) != cudaSuccess ||
-        cudaGetSymbolAddress((void**)&d.s2, g_na_s2) != cudaSuccess)
+    cudaError_t e = cudaGetSymbolAddress((void**)&d.scratch, g_na_scratch);
+    if (e == cudaSuccess) e = cudaGetSymbolAddress((void**)&d.tw, g_na_tw);
+    if (e == cudaSuccess) e = cudaGetSymbolAddress((void**)&d.q, g_na_q);
+    if (e == cudaSuccess) e = cudaGetSymbolAddress((void**)&d.s2, g_na_s2);
+    if (e != cudaSuccess) {
+      std::fprintf(stderr, "kfbim_poisson_noalloc: resolving the static scratch failed: %s\n",
+                   cudaGetErrorString(e));
       return KFBIM_E_CUDA;
+    }
     d.ready = true;
   }
   *out = &d;
@@ -1201,7 +1222,9 @@ void noalloc_pass(const NoAllocSymbols& d, int N, double h, const double* in, do
   a.accumulate = 0;
   a.scale = 1.0;
   a.skip = nullptr;
-  // N <= 64 in FP64 needs at most 40 KiB of dynamic shared memory (default limit 48 KiB)
+  // N <= 64 in FP64 needs at most 40 KiB of dynamic shared memory, within the
+  // 48 KiB default; the kernel's limit may only have been raised by other
+  // paths of this library (raise_dynamic_smem never lowers it)
   const size_t smem = pass_smem_bytes(N, sizeof(double));
   k_axis_pass<double, double, double><<<(unsigned)(N * N / LPC), PASS_THREADS, smem, s>>>(
       in, out, a, d.tw, d.q, d.s2);
@@ -2095,7 +2118,12 @@ int kfbim_poisson_noalloc(int c, int N, double lo, double hi, const double* r, d
   noalloc_pass(*d, N, h, t2, t1, cax, X_DST1F, X_DST1I, W_POISSON, cax, s);
   noalloc_pass(*d, N, h, t1, t2, o1, X_DST2I, X_NONE, W_NONE, cax, s);
   noalloc_pass(*d, N, h, t2, u, o2, X_DST2I, X_NONE, W_NONE, cax, s);
-  return cudaGetLastError() == cudaSuccess ? KFBIM_OK : KFBIM_E_CUDA;
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    std::fprintf(stderr, "kfbim_poisson_noalloc: launch failed: %s\n", cudaGetErrorString(e));
+    return KFBIM_E_CUDA;
+  }
+  return KFBIM_OK;
 }
 
 int kfbim_solve_host(kfbim_ctx* c, const double* g, const double* fpts, const double* fgrid,

@@ -15,7 +15,9 @@ density from the FP64 one, the roofline of the dominant kernel (the FP32
 transform passes, timed with CUDA events around each launch in a second run
 of the same steps), the oracle CPU baseline, e2e through kfbim_solve_host with
 host buffers, the kernel-launch count and the SM clocks sampled during the
-timed region.
+timed region; beside them, the autotuner's choice of transform kernels, one
+adjoint (gradient) solve on the same data, and a batch of 16 instances in one
+kfbim_solve_batch call against the same instances solved one at a time.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl kfbim|reference]
 Multi-GPU (torchrun): replicas only, every rank solves its own instance, no
@@ -59,6 +61,7 @@ def parse():
     ap.add_argument("--inner-tol", type=float, default=None, help="MIXED inner FP32 CG tolerance")
     ap.add_argument("--transforms", default="auto", choices=["auto", "fft", "tensor"],
                     help="kernels of the FP32 axis passes (auto: the setup-time autotuner's choice)")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (gradient) leg")
     ap.add_argument("--batch", type=int, default=16,
                     help="instances of the batched leg (kfbim_solve_batch); 0 skips it")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
@@ -210,6 +213,49 @@ def job_throughput(total_ms, steps, dist=None, device="cpu"):
         world = dist.get_world_size()
     total = float(t.item())
     return world * steps / (total / 1e3), total
+
+
+def adjoint_leg(solver, args, flush, stream, dev):
+    """dL/dg by kfbim_solve_adjoint for L = 1/2 |u - u_t|^2 over the Omega face
+    nodes (u from the bench's forward solve, u_t = 0.8 x the manufactured
+    velocity), timed like the forward steps."""
+    import torch
+    N, lo, h = solver.N, solver.lo, solver.h
+    idx = np.arange(N)
+    mask, tgt = [], []
+    for c in (1, 2, 3):
+        off = [0.5, 0.5, 0.5]
+        off[c - 1] = 0.0
+        Z, Y, X = np.meshgrid(lo + (idx + off[2]) * h, lo + (idx + off[1]) * h,
+                              lo + (idx + off[0]) * h, indexing="ij")
+        tgt.append(0.8 * ki.stokes_velocity(np.stack([X, Y, Z], -1))[..., c - 1].ravel())
+        mask.append(solver.sides(c).ravel().astype(np.float64))
+    mask = torch.from_numpy(np.concatenate(mask)).to(dev)
+    tgt = torch.from_numpy(np.concatenate(tgt)).to(dev)
+    g_h, fpts_h, fgrid_h = inputs(solver, None, None)
+    phi = torch.zeros(solver.n_primary, dtype=torch.float64, device=dev)
+    u = torch.zeros(3 * N ** 3, dtype=torch.float64, device=dev)
+    p = torch.zeros(N ** 3, dtype=torch.float64, device=dev)
+    solver.solve(torch.from_numpy(g_h).to(dev), phi, torch.from_numpy(fpts_h).to(dev),
+                 torch.from_numpy(fgrid_h).to(dev), u, p)
+    ubar = mask * (u - tgt)
+    gbar = torch.zeros_like(phi)
+    solver.solve_adjoint(ubar, gbar)
+    torch.cuda.synchronize()
+    steps = max(1, min(args.steps, 2))
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * steps)]
+    for k in range(steps):
+        flush.zero_()
+        ev[2 * k].record(stream)
+        solver.solve_adjoint(ubar, gbar)
+        ev[2 * k + 1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(steps)) / steps
+    st = solver.last_stats
+    return {"gradient_solves_per_s": round(1e3 / ms, 4), "ms_per_gradient": round(ms, 2),
+            "gmres_iters": st["gmres_iters"], "interface_solves": st["interface_solves"],
+            "gmres_residual": st["gmres_residual"], "api": "kfbim_solve_adjoint",
+            "loss": "1/2 |u - 0.8 u_exact|^2 over the Omega face nodes", "steps": steps}
 
 
 def batch_inputs(solver, B):
@@ -392,6 +438,10 @@ def main_kfbim(args):
                 "mixed_speedup": round((1e3 / ms_per_step) / (1e3 / ms), 2)}
         s64.close()
 
+    adjoint = None
+    if not args.no_adjoint and not navier:
+        adjoint = adjoint_leg(solver, args, flush, stream, dev)
+
     batched = None
     if args.batch > 0:
         batched = batch_leg(solver, args, flush, stream, dev)
@@ -423,7 +473,7 @@ def main_kfbim(args):
                            "gmres_iters": st["gmres_iters"], "interface_solves": st["interface_solves"],
                            "cg_iters": st["cg_iters"], "refine_sweeps": st["refine_sweeps"],
                            "parallelism": "replicas" if world > 1 else "single"},
-                "transforms": dict(tinfo, requested=args.transforms),
+                "transforms": dict(tinfo, requested=args.transforms), "adjoint": adjoint,
                 "fp64": fp64, "rel_err_vs_fp64": rel, "batched": batched,
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": e2e, "gpu_launches": launches, "clocks": clk}

@@ -56,14 +56,17 @@ typedef enum {
   KFBIM_E_OOM = -6        /* device or host allocation failed */
 } kfbim_status;
 
-typedef enum { KFBIM_SPHERE = 0, KFBIM_ELLIPSOID = 1, KFBIM_STAR = 2 } kfbim_geometry_kind;
+typedef enum { KFBIM_SPHERE = 0, KFBIM_ELLIPSOID = 1, KFBIM_STAR = 2, KFBIM_TORUS = 3 } kfbim_geometry_kind;
 
 /* Analytic interface, Omega = {F <= 0}.
  *   SPHERE:    params[0] = radius.
  *   ELLIPSOID: params[0..2] = semi-axes; rot = row-major 3x3 rotation Q, the
  *              body frame is xi = Q^T (x - center).
  *   STAR:      r(theta, phi) = params[0] + params[1] sin(params[2] theta)
- *              cos(params[3] phi), theta polar angle from +z, phi azimuth. */
+ *              cos(params[3] phi), theta polar angle from +z, phi azimuth.
+ *   TORUS:     (params[1] - sqrt(x^2 + y^2))^2 + z^2 = params[0]^2 about the
+ *              z axis through center: tube radius params[0] < axis distance
+ *              params[1] (Example 5.3). */
 typedef struct {
   int kind;
   double center[3];

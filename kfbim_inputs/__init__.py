@@ -29,6 +29,11 @@ def star(r0=0.5, eps=0.1, m=3, n=4, center=(0.0, 0.0, 0.0)):
             "eps": float(eps), "m": int(m), "n": int(n)}
 
 
+def torus(a=0.35, c=0.7, center=(0.0, 0.0, 0.0)):
+    """Torus (c - sqrt(x^2 + y^2))^2 + z^2 = a^2 about the z axis."""
+    return {"kind": "torus", "center": [float(v) for v in center], "a": float(a), "c": float(c)}
+
+
 def seeded_rotation(seed):
     """Rotation from the QR factorisation of a seeded Gaussian 3x3 matrix,
     columns sign-fixed by diag(R) > 0 and det = +1."""
@@ -176,6 +181,83 @@ def example51_forcing(x, mu=1.0):
     X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
     lap = np.stack([24 * Z**2 - 24 * X**2 + 48 * X * Y, 24 * X**2 - 24 * Y**2 + 2, 48 * X * Z], -1)
     gp = np.stack([24 * Z**2 - 24 * X**2 + 48 * X * Y, 24 * X**2 - 24 * Y**2, 48 * X * Z], -1)
+    return -mu * lap + gp
+
+
+# ---------------- paper Example 5.2 (ellipsoid x^2 + y^2/0.64 + z^2/0.36 = 1)
+def example52_geometry():
+    return ellipsoid(axes=(1.0, 0.8, 0.6))
+
+
+def example52_velocity(x):
+    x = np.asarray(x, dtype=np.float64)
+    X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
+    u1 = 2 * X**3 * Y / 3 - Z**2 * X**2 + np.exp(Z) + np.sin(np.pi * Z)
+    u2 = -X**2 * Y**2 + np.cos(np.pi * X)
+    u3 = 2 * Z**3 * X / 3 + np.exp(X) + np.sin(np.pi * X)
+    return np.stack([u1, u2, u3], axis=-1)
+
+
+def example52_pressure(x):
+    x = np.asarray(x, dtype=np.float64)
+    X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
+    return (X - 1) ** 3 * (Y - 1) ** 3 * (Z - 1) ** 3
+
+
+def example52_forcing(x, mu=1.0):
+    """-mu Lap u + grad p, with
+    Lap u = (4xy - 2x^2 - 2z^2 + e^z - pi^2 sin(pi z), -2x^2 - 2y^2 - pi^2 cos(pi x),
+             4xz + e^x - pi^2 sin(pi x))."""
+    x = np.asarray(x, dtype=np.float64)
+    X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
+    pi2 = np.pi ** 2
+    lap = np.stack([4 * X * Y - 2 * X**2 - 2 * Z**2 + np.exp(Z) - pi2 * np.sin(np.pi * Z),
+                    -2 * X**2 - 2 * Y**2 - pi2 * np.cos(np.pi * X),
+                    4 * X * Z + np.exp(X) - pi2 * np.sin(np.pi * X)], -1)
+    a, b, c = X - 1, Y - 1, Z - 1
+    gp = np.stack([3 * a**2 * b**3 * c**3, 3 * a**3 * b**2 * c**3, 3 * a**3 * b**3 * c**2], -1)
+    return -mu * lap + gp
+
+
+# ------------------------------- paper Example 5.3 (torus a = 0.35, c = 0.7)
+def example53_geometry():
+    return torus(0.35, 0.7)
+
+
+def example53_velocity(x):
+    x = np.asarray(x, dtype=np.float64)
+    X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
+    u1 = (-4 * X * Y * (1 - X**2 - Y**2) - X**2 * (X**2 + 6 * Z**2 - 2) + Z**2 * (3 * Z**2 - 2)
+          + np.exp(np.cos(Y)) + np.exp(np.sin(Z)))
+    u2 = X**2 * (3 * X**2 - 6 * Y**2 - 2) - Y**2 * (Y**2 - 2) + np.exp(np.sin(X))
+    u3 = -4 * (1 - X**2 - Z**2) * X * Z + np.exp(np.cos(X))
+    return np.stack([u1, u2, u3], axis=-1)
+
+
+def example53_pressure(x):
+    x = np.asarray(x, dtype=np.float64)
+    X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
+    return np.exp(1 - Y**2 - Z**3) * np.sin(X**2 + 1)
+
+
+def example53_forcing(x, mu=1.0):
+    """-mu Lap u + grad p; the exponential terms of Lap u come from
+    (e^{cos t})'' = e^{cos t} (sin^2 t - cos t), (e^{sin t})'' = e^{sin t} (cos^2 t - sin t)."""
+    x = np.asarray(x, dtype=np.float64)
+    X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
+
+    def ecos2(t):
+        return np.exp(np.cos(t)) * (np.sin(t) ** 2 - np.cos(t))
+
+    def esin2(t):
+        return np.exp(np.sin(t)) * (np.cos(t) ** 2 - np.sin(t))
+
+    lap = np.stack([-24 * X**2 + 48 * X * Y + 24 * Z**2 + ecos2(Y) + esin2(Z),
+                    24 * X**2 - 24 * Y**2 + esin2(X),
+                    48 * X * Z + ecos2(X)], -1)
+    E = np.exp(1 - Y**2 - Z**3)
+    gp = np.stack([2 * X * E * np.cos(X**2 + 1), -2 * Y * E * np.sin(X**2 + 1),
+                   -3 * Z**2 * E * np.sin(X**2 + 1)], -1)
     return -mu * lap + gp
 
 

@@ -82,7 +82,25 @@ def _star(geom, X):
     return F, G, H
 
 
-_KINDS = {"sphere": _sphere, "ellipsoid": _ellipsoid, "star": _star}
+def _torus(geom, X):
+    """F = (c - s)^2 + z^2 - a^2 with s the distance from the z axis
+    (Example 5.3's domain is F < 0); derivatives written out in x, y, z."""
+    cen = np.asarray(geom["center"])
+    a, c = geom["a"], geom["c"]
+    d = X - cen
+    x, y, z = d[..., 0], d[..., 1], d[..., 2]
+    s = np.sqrt(x * x + y * y)
+    F = (c - s) ** 2 + z * z - a * a
+    G = np.stack([-2.0 * (c - s) * x / s, -2.0 * (c - s) * y / s, 2.0 * z], axis=-1)
+    H = np.zeros(X.shape[:-1] + (3, 3))
+    H[..., 0, 0] = 2.0 * x * x / (s * s) - 2.0 * (c - s) * y * y / s ** 3
+    H[..., 1, 1] = 2.0 * y * y / (s * s) - 2.0 * (c - s) * x * x / s ** 3
+    H[..., 0, 1] = H[..., 1, 0] = 2.0 * x * y / (s * s) + 2.0 * (c - s) * x * y / s ** 3
+    H[..., 2, 2] = 2.0
+    return F, G, H
+
+
+_KINDS = {"sphere": _sphere, "ellipsoid": _ellipsoid, "star": _star, "torus": _torus}
 
 
 def level_set(geom, X):

@@ -10,7 +10,7 @@ c_int, c_double, c_int64, c_void_p = ctypes.c_int, ctypes.c_double, ctypes.c_int
 
 STATUS = {0: "OK", -1: "E_INVALID", -2: "E_GEOMETRY", -3: "E_NOCONV", -4: "E_NONFINITE",
           -5: "E_CUDA", -6: "E_OOM"}
-KINDS = {"sphere": 0, "ellipsoid": 1, "star": 2}
+KINDS = {"sphere": 0, "ellipsoid": 1, "star": 2, "torus": 3}
 
 
 class KfbimError(RuntimeError):
@@ -125,6 +125,8 @@ def _geometry(desc):
         params = [desc["radius"]]
     elif desc["kind"] == "ellipsoid":
         params = list(desc["axes"])
+    elif desc["kind"] == "torus":
+        params = [desc["a"], desc["c"]]
     else:
         params = [desc["r0"], desc["eps"], desc["m"], desc["n"]]
     for i, v in enumerate(params):

@@ -74,6 +74,28 @@ struct Level {
           }
       return;
     }
+    if (g.kind == KFBIM_TORUS) {
+      // F = (c - s)^2 + z^2 - a^2, s = distance from the z axis (Example 5.3);
+      // with e = (x, y) / s: grad F = (-2 (c - s) e, 2 z),
+      // Hess F on the (x, y) block = 2 e e^T - 2 (c - s) / s (I - e e^T), zz = 2.
+      const double a = g.params[0], c = g.params[1];
+      const double s = std::sqrt(d0 * d0 + d1 * d1);
+      *F = (c - s) * (c - s) + d2 * d2 - a * a;
+      const double e[2] = {d0 / s, d1 / s};
+      if (G) {
+        G[0] = -2.0 * (c - s) * e[0];
+        G[1] = -2.0 * (c - s) * e[1];
+        G[2] = 2.0 * d2;
+      }
+      if (H) {
+        for (int i = 0; i < 9; ++i) H[i] = 0.0;
+        for (int i = 0; i < 2; ++i)
+          for (int j = 0; j < 2; ++j)
+            H[3 * i + j] = 2.0 * e[i] * e[j] - 2.0 * (c - s) / s * ((i == j) - e[i] * e[j]);
+        H[8] = 2.0;
+      }
+      return;
+    }
     // STAR: F = rho - R(theta, phi), chain rule through spherical coordinates.
     const double r0 = g.params[0], eps = g.params[1], m = g.params[2], n = g.params[3];
     const double s = std::sqrt(d0 * d0 + d1 * d1);

@@ -30,10 +30,11 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_host_setup_matches_oracle_points():
-    for geom, N in [(ki.sphere(), 32), (ki.star(), 32),
-                    (ki.ellipsoid((0.6, 0.45, 0.35), ki.seeded_rotation(3)), 32)]:
-        s = Solver(geom, ki.grid(N), device=False)
-        o = okfbim.Setup(geom, ki.grid(N))
+    for geom, grid in [(ki.sphere(), ki.grid(32)), (ki.star(), ki.grid(32)),
+                       (ki.ellipsoid((0.6, 0.45, 0.35), ki.seeded_rotation(3)), ki.grid(32)),
+                       (ki.example53_geometry(), ki.grid(64, -1.2, 1.2))]:
+        s = Solver(geom, grid, device=False)
+        o = okfbim.Setup(geom, grid)
         xyz, comp, axis, prim = s.points()
         assert s.n_points == o.cp.n and s.n_primary == o.n
         assert np.array_equal(comp, o.cp.comp) and np.array_equal(axis, o.cp.axis)

@@ -16,7 +16,7 @@ def _points(rng, n=40):
     return x[s > 0.05]
 
 
-@pytest.mark.parametrize("geom", GEOMS, ids=lambda g: g["kind"])
+@pytest.mark.parametrize("geom", GEOMS + [ki.torus()], ids=lambda g: g["kind"])
 def test_gradient_hessian_finite_differences(geom):
     rng = np.random.default_rng(11)
     X = _points(rng)
@@ -114,3 +114,21 @@ def test_normal_derivative_along_surface(geom):
             pts.append(geometry.frames(geom, p[None])[0][0])
         dn = (pts[0] - pts[1]) / (2 * eps)
         assert np.allclose(dn, K[a] @ T, atol=1e-5)
+
+
+def test_torus_curvature_closed_form():
+    """Principal curvatures of the torus (c - s)^2 + z^2 = a^2 at tube angle t:
+    1/a around the tube and cos t / (c + a cos t) around the axis (negative on
+    the inner side, where the surface is saddle-shaped)."""
+    g = ki.torus(0.35, 0.7)
+    t, f = np.meshgrid(np.linspace(0, 2 * np.pi, 9)[:-1], np.linspace(0, 2 * np.pi, 7)[:-1])
+    t, f = t.ravel(), f.ravel()
+    r = 0.7 + 0.35 * np.cos(t)
+    X = np.stack([r * np.cos(f), r * np.sin(f), 0.35 * np.sin(t)], -1)
+    assert np.abs(geometry.level_value(g, X)).max() < 1e-14
+    n, _, K = geometry.frames(g, X)
+    want_n = np.stack([np.cos(t) * np.cos(f), np.cos(t) * np.sin(f), np.sin(t)], -1)
+    assert np.abs(n - want_n).max() < 1e-14
+    got = np.sort(np.linalg.eigvalsh(K), axis=-1)
+    want = np.sort(np.stack([np.full_like(t, 1 / 0.35), np.cos(t) / r], -1), axis=-1)
+    assert np.abs(got - want).max() < 1e-12

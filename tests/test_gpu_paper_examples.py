@@ -1,0 +1,92 @@
+"""The paper's Stokes Examples 5.1 (sphere r = 1), 5.2 (ellipsoid
+x^2 + y^2/0.64 + z^2/0.36 = 1) and 5.3 (torus a = 0.35, c = 0.7) on
+[-1.2,1.2]^3 with GMRES tolerance 1e-9, MIXED precision, at N = 64 and 128:
+normalised maximum and l2 errors of u^(1..3) at the Omega face nodes and of p
+(up to a constant) at the Omega cells, against the paper's N = 128 rows
+(tests/golden/paper_examples_n128.json, cited there) within a factor 3 for the
+velocity, and second-order convergence from 64 to 128.  The paper's
+control-point fit is not specified, so only the size of the errors is
+compared."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import kfbim_inputs as ki
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2303_04992_gb300 import MIXED, Solver, build  # noqa: E402
+
+build()
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_examples_n128.json")))
+EXAMPLES = {
+    "5.1": (ki.sphere(1.0), ki.example51_velocity, ki.example51_pressure, ki.example51_forcing),
+    "5.2": (ki.example52_geometry(), ki.example52_velocity, ki.example52_pressure, ki.example52_forcing),
+    "5.3": (ki.example53_geometry(), ki.example53_velocity, ki.example53_pressure, ki.example53_forcing),
+}
+
+
+def node_xyz(s, c):
+    """Node coordinates (N, N, N, 3) of grid c (0 cells, 1..3 faces of u^(c)), [k, j, i]."""
+    N, lo, h = s.N, s.lo, s.h
+    idx = np.arange(N)
+    off = [0.5, 0.5, 0.5]
+    if c > 0:
+        off[c - 1] = 0.0
+    Z, Y, X = np.meshgrid(lo + (idx + off[2]) * h, lo + (idx + off[1]) * h, lo + (idx + off[0]) * h,
+                          indexing="ij")
+    return np.stack([X, Y, Z], -1)
+
+
+def errors(key, N):
+    geom, vel, pres, frc = EXAMPLES[key]
+    s = Solver(geom, ki.grid(N, *GOLD["box"]), precision=MIXED, gmres_tol=GOLD["gmres_tol"])
+    xyz, comp, _, prim = s.points()
+    rows = np.arange(len(comp))
+    g = torch.from_numpy(vel(xyz)[rows, comp - 1][prim]).cuda()
+    fp = torch.from_numpy(frc(xyz).T.copy()).cuda()
+    fg = torch.from_numpy(np.concatenate([frc(node_xyz(s, c))[..., c - 1].ravel() for c in (1, 2, 3)])).cuda()
+    phi = torch.zeros(s.n_primary, dtype=torch.float64, device="cuda")
+    u = torch.zeros(3 * N ** 3, dtype=torch.float64, device="cuda")
+    p = torch.zeros(N ** 3, dtype=torch.float64, device="cuda")
+    s.solve(g, phi, fp, fg, u, p)
+    iters = s.last_stats["gmres_iters"]
+    u = u.cpu().numpy().reshape(3, N, N, N)
+    out = {"max": {}, "l2": {}}
+    for c in (1, 2, 3):
+        m = s.sides(c).copy()
+        nrm = [slice(None)] * 3
+        nrm[2 - (c - 1)] = 0
+        m[tuple(nrm)] = False                       # wall faces are not unknowns
+        ue = vel(node_xyz(s, c))[..., c - 1][m]
+        d = u[c - 1][m] - ue
+        out["max"]["u%d" % c] = np.abs(d).max() / np.abs(ue).max()
+        out["l2"]["u%d" % c] = np.linalg.norm(d) / np.linalg.norm(ue)
+    m = s.sides(0)
+    pe = pres(node_xyz(s, 0))[m]
+    d = p.cpu().numpy().reshape(N, N, N)[m] - pe
+    d -= d.mean()
+    pe0 = pe - pe.mean()
+    out["max"]["p"] = np.abs(d).max() / np.abs(pe0).max()
+    out["l2"]["p"] = np.linalg.norm(d) / np.linalg.norm(pe0)
+    s.close()
+    return out, iters
+
+
+@pytest.mark.parametrize("key", sorted(EXAMPLES))
+def test_example_against_paper_table(key):
+    gold = GOLD[key]
+    e128, it128 = errors(key, 128)
+    e64, _ = errors(key, 64)
+    print("\nExample", key, "N=128 GMRES", it128, {k: {c: "%.2e" % v for c, v in d.items()} for k, d in e128.items()},
+          "N=64 max", {c: "%.2e" % v for c, v in e64["max"].items()})
+    assert 0.5 * gold["gmres_iterations"] <= it128 <= 2.5 * gold["gmres_iterations"], it128
+    for norm, table in (("max", gold["max_error"]), ("l2", gold["l2_error"])):
+        for c in ("u1", "u2", "u3"):
+            assert e128[norm][c] < 3.0 * table[c], (norm, c, e128[norm][c], table[c])
+        assert e128[norm]["p"] < 10.0 * table["p"], (norm, "p", e128[norm]["p"], table["p"])
+    for c in ("u1", "u2", "u3"):
+        assert e64["l2"][c] / e128["l2"][c] > 2.5, (c, e64["l2"][c], e128["l2"][c])

@@ -34,7 +34,7 @@ def oracle_setup(key, geom, N):
     return _ORACLE[key]
 
 
-CASES = [("sphere32", ki.sphere(), 32), ("star64", ki.star(), 64)]
+CASES = [("sphere32", ki.sphere(), 32), ("star64", ki.star(), 64), ("torus64", ki.torus(0.2, 0.5), 64)]
 
 
 @pytest.fixture(scope="module", params=CASES, ids=[c[0] for c in CASES])

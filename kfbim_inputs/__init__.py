@@ -261,6 +261,98 @@ def example53_forcing(x, mu=1.0):
     return -mu * lap + gp
 
 
+# ------------------------- paper Examples 5.4-5.6 (Navier, Lame data E, nu)
+class _Jet:
+    """Value, gradient (..., 3) and Hessian (..., 3, 3) of a scalar field, with
+    the sum, product and chain rules: enough to differentiate the examples'
+    fields exactly."""
+
+    def __init__(self, v, g, H):
+        self.v, self.g, self.H = v, g, H
+
+    @staticmethod
+    def coord(X, k):
+        g = np.zeros(X.shape)
+        g[..., k] = 1.0
+        return _Jet(X[..., k].copy(), g, np.zeros(X.shape + (3,)))
+
+    @staticmethod
+    def const(X, c):
+        return _Jet(np.full(X.shape[:-1], float(c)), np.zeros(X.shape), np.zeros(X.shape + (3,)))
+
+    def __add__(self, o):
+        return _Jet(self.v + o.v, self.g + o.g, self.H + o.H)
+
+    def __mul__(self, o):
+        if not isinstance(o, _Jet):
+            return _Jet(self.v * o, self.g * o, self.H * o)
+        outer = self.g[..., :, None] * o.g[..., None, :]
+        return _Jet(self.v * o.v, self.g * o.v[..., None] + o.g * self.v[..., None],
+                    self.H * o.v[..., None, None] + o.H * self.v[..., None, None] + outer
+                    + np.swapaxes(outer, -1, -2))
+
+    def apply(self, f, f1, f2):
+        """Chain rule for t -> f(t) with derivatives f1, f2."""
+        a, b = f1(self.v), f2(self.v)
+        return _Jet(f(self.v), self.g * a[..., None],
+                    self.H * a[..., None, None] + b[..., None, None] * self.g[..., :, None] * self.g[..., None, :])
+
+
+def _sin(j):
+    return j.apply(np.sin, np.cos, lambda t: -np.sin(t))
+
+
+def _cos(j):
+    return j.apply(np.cos, lambda t: -np.sin(t), lambda t: -np.cos(t))
+
+
+def _exp(j):
+    return j.apply(np.exp, np.exp, np.exp)
+
+
+def lame_from_young(E, nu):
+    """(mu, lambda) from Young's modulus and Poisson's ratio."""
+    return E / (2.0 * (1.0 + nu)), E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
+
+
+def _navier_jets(key, X):
+    X = np.asarray(X, dtype=np.float64)
+    x, y, z = (_Jet.coord(X, k) for k in range(3))
+    r2 = x * x + y * y + z * z
+    if key == "5.4":
+        S = _sin(r2 * (2.0 * np.pi))
+        return [S * _cos(y * 2.0) * _cos(z), S * _cos(x) * _cos(x + z), S * _cos(x * np.pi) * _cos(y)]
+    if key == "5.5":
+        base = r2 + _Jet.const(X, -4.0) + _cos(x) * _cos(y) * _cos(z)
+        return [base, base + x * y, base + y * z]
+    # 5.6
+    one = _Jet.const(X, 1.0)
+    return [_exp(one + y * y * -1.0 + z * z * -1.0) * _sin(x * x * 3.0 + _Jet.const(X, 2.0)),
+            _sin(one + r2 * -1.0), x * x * 3.0 + y * y * 2.0 + z * z]
+
+
+NAVIER_EXAMPLES = {
+    # key: (geometry, E, nu)
+    "5.4": (lambda: sphere(1.0), 1000.0, 0.1),
+    "5.5": (lambda: ellipsoid(axes=(1.0, 0.8, 0.6)), 4000.0, 0.05),
+    "5.6": (lambda: torus(0.35, 0.7), 2000.0, 0.4),
+}
+
+
+def navier_example_displacement(key, X):
+    return np.stack([j.v for j in _navier_jets(key, X)], axis=-1)
+
+
+def navier_example_forcing(key, X):
+    """f = -mu Lap u - (lambda + mu) grad(div u) with (mu, lambda) of the example."""
+    _, E, nu = NAVIER_EXAMPLES[key]
+    mu, lam = lame_from_young(E, nu)
+    J = _navier_jets(key, X)
+    lap = np.stack([np.trace(j.H, axis1=-2, axis2=-1) for j in J], axis=-1)
+    graddiv = sum(J[i].H[..., :, i] for i in range(3))
+    return -mu * lap - (lam + mu) * graddiv
+
+
 # ------------------------------------ manufactured Lame displacement (Navier)
 LAME_MU, LAME_LAMBDA = 1.0, 2.0
 

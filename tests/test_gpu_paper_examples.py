@@ -1,5 +1,6 @@
 """The paper's Stokes Examples 5.1 (sphere r = 1), 5.2 (ellipsoid
-x^2 + y^2/0.64 + z^2/0.36 = 1) and 5.3 (torus a = 0.35, c = 0.7) on
+x^2 + y^2/0.64 + z^2/0.36 = 1) and 5.3 (torus a = 0.35, c = 0.7), and its
+Navier Examples 5.4-5.6 on the same three domains (Lame data from E, nu), on
 [-1.2,1.2]^3 with GMRES tolerance 1e-9, MIXED precision, at N = 64 and 128:
 normalised maximum and l2 errors of u^(1..3) at the Omega face nodes and of p
 (up to a constant) at the Omega cells, against the paper's N = 128 rows
@@ -42,8 +43,18 @@ def node_xyz(s, c):
 
 
 def errors(key, N):
-    geom, vel, pres, frc = EXAMPLES[key]
-    s = Solver(geom, ki.grid(N, *GOLD["box"]), precision=MIXED, gmres_tol=GOLD["gmres_tol"])
+    if key in ki.NAVIER_EXAMPLES:
+        mk, E, nu = ki.NAVIER_EXAMPLES[key]
+        mu, lam = ki.lame_from_young(E, nu)
+        geom = mk()
+        vel = lambda X: ki.navier_example_displacement(key, X)  # noqa: E731
+        frc = lambda X: ki.navier_example_forcing(key, X)  # noqa: E731
+        pres = None
+        s = Solver(geom, ki.grid(N, *GOLD["box"]), precision=MIXED, gmres_tol=GOLD["gmres_tol"],
+                   mu=mu, lam=lam)
+    else:
+        geom, vel, pres, frc = EXAMPLES[key]
+        s = Solver(geom, ki.grid(N, *GOLD["box"]), precision=MIXED, gmres_tol=GOLD["gmres_tol"])
     xyz, comp, _, prim = s.points()
     rows = np.arange(len(comp))
     g = torch.from_numpy(vel(xyz)[rows, comp - 1][prim]).cuda()
@@ -65,6 +76,9 @@ def errors(key, N):
         d = u[c - 1][m] - ue
         out["max"]["u%d" % c] = np.abs(d).max() / np.abs(ue).max()
         out["l2"]["u%d" % c] = np.linalg.norm(d) / np.linalg.norm(ue)
+    if pres is None:
+        s.close()
+        return out, iters
     m = s.sides(0)
     pe = pres(node_xyz(s, 0))[m]
     d = p.cpu().numpy().reshape(N, N, N)[m] - pe
@@ -88,5 +102,20 @@ def test_example_against_paper_table(key):
         for c in ("u1", "u2", "u3"):
             assert e128[norm][c] < 3.0 * table[c], (norm, c, e128[norm][c], table[c])
         assert e128[norm]["p"] < 10.0 * table["p"], (norm, "p", e128[norm]["p"], table["p"])
+    for c in ("u1", "u2", "u3"):
+        assert e64["l2"][c] / e128["l2"][c] > 2.5, (c, e64["l2"][c], e128["l2"][c])
+
+
+@pytest.mark.parametrize("key", sorted(ki.NAVIER_EXAMPLES))
+def test_navier_example_against_paper_table(key):
+    gold = GOLD[key]
+    e128, it128 = errors(key, 128)
+    e64, _ = errors(key, 64)
+    print("\nExample", key, "N=128 GMRES", it128, {k: {c: "%.2e" % v for c, v in d.items()} for k, d in e128.items()},
+          "N=64 max", {c: "%.2e" % v for c, v in e64["max"].items()})
+    assert 0.5 * gold["gmres_iterations"] <= it128 <= 2.5 * gold["gmres_iterations"], it128
+    for norm, table in (("max", gold["max_error"]), ("l2", gold["l2_error"])):
+        for c in ("u1", "u2", "u3"):
+            assert e128[norm][c] < 3.0 * table[c], (norm, c, e128[norm][c], table[c])
     for c in ("u1", "u2", "u3"):
         assert e64["l2"][c] / e128["l2"][c] > 2.5, (c, e64["l2"][c], e128["l2"][c])

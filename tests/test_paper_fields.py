@@ -35,3 +35,31 @@ def test_fields_against_symbolic_derivatives(key):
     assert np.abs(fu(P) - u).max() <= 1e-13 * np.abs(u).max()
     assert np.abs(fp(P) - sp.lambdify((x, y, z), p)(*args)).max() <= 1e-13 * np.abs(fp(P)).max()
     assert np.abs(ff(P) - f).max() <= 1e-13 * np.abs(f).max()
+
+
+NAVIER = {
+    "5.4": [sp.sin(2 * sp.pi * (x**2 + y**2 + z**2)) * sp.cos(2 * y) * sp.cos(z),
+            sp.sin(2 * sp.pi * (x**2 + y**2 + z**2)) * sp.cos(x) * sp.cos(x + z),
+            sp.sin(2 * sp.pi * (x**2 + y**2 + z**2)) * sp.cos(sp.pi * x) * sp.cos(y)],
+    "5.5": [x**2 + y**2 + z**2 - 4 + sp.cos(x) * sp.cos(y) * sp.cos(z),
+            x**2 + y**2 + z**2 - 4 + x * y + sp.cos(x) * sp.cos(y) * sp.cos(z),
+            x**2 + y**2 + z**2 - 4 + y * z + sp.cos(x) * sp.cos(y) * sp.cos(z)],
+    "5.6": [sp.exp(1 - y**2 - z**2) * sp.sin(3 * x**2 + 2), sp.sin(1 - x**2 - y**2 - z**2),
+            3 * x**2 + 2 * y**2 + z**2],
+}
+
+
+@pytest.mark.parametrize("key", sorted(NAVIER))
+def test_navier_fields_against_symbolic_derivatives(key):
+    U = NAVIER[key]
+    _, E, nu = ki.NAVIER_EXAMPLES[key]
+    mu = E / (2 * (1 + nu))
+    lam = E * nu / ((1 + nu) * (1 - 2 * nu))
+    div = sum(sp.diff(U[i], v) for i, v in enumerate((x, y, z)))
+    P = np.random.default_rng(2).uniform(-1.1, 1.1, (40, 3))
+    args = (P[:, 0], P[:, 1], P[:, 2])
+    u = np.stack([sp.lambdify((x, y, z), U[i])(*args) for i in range(3)], -1)
+    f = np.stack([sp.lambdify((x, y, z), -mu * sum(sp.diff(U[i], v, 2) for v in (x, y, z))
+                              - (lam + mu) * sp.diff(div, (x, y, z)[i]))(*args) for i in range(3)], -1)
+    assert np.abs(ki.navier_example_displacement(key, P) - u).max() <= 1e-13 * np.abs(u).max()
+    assert np.abs(ki.navier_example_forcing(key, P) - f).max() <= 1e-12 * np.abs(f).max()

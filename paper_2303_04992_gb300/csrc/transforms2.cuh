@@ -10,6 +10,8 @@
 // (128 B coalesced rows for FP32 on the y and z axes).
 #pragma once
 
+#include <type_traits>
+
 #include "transforms.cuh"
 
 namespace kfbim {
@@ -78,7 +80,7 @@ struct Fft2Shape {
   static constexpr int M = L / 16;                                   // threads per pair
   static constexpr int PPR = (PASS2_THREADS / M < LPC2 / 2) ? PASS2_THREADS / M : LPC2 / 2;
   static constexpr int X = PPR * 16 * (M + 1);                       // exchange entries
-  static constexpr int Z = PPR * L;                                  // output entries
+  static constexpr int Z = PPR * (L + 1);                            // output entries (padded rows)
 };
 
 template <typename T, int N>
@@ -97,15 +99,71 @@ struct Pass2Smem {
   static constexpr size_t bytes = stage_al + xbuf + tables;
 };
 
-// One real transform of the LPC2 staged lines, in place in Rb.
+// Where the lines of a transform come from and go to.  Lines are taken in
+// pairs (2p, 2p + 1): the two real lines of one complex FFT.
+// The staged lines of a CTA in shared memory (row stride N + 1).
+template <typename T>
+struct SmemLines {
+  T* Rb;
+  int RS;
+  __device__ __forceinline__ T a(int p, int i) const { return Rb[(2 * p) * RS + i]; }
+  __device__ __forceinline__ T b(int p, int i) const { return Rb[(2 * p + 1) * RS + i]; }
+  __device__ __forceinline__ void put(int p, int o, T va, T vb) const {
+    Rb[(2 * p) * RS + o] = va;
+    Rb[(2 * p + 1) * RS + o] = vb;
+  }
+};
+// The CTA's lines straight from global memory: element i of line l at
+// base[l * ls + i * es].
+template <typename T, typename Tin>
+struct GlobalLines {
+  const Tin* base;
+  int64_t ls, es;
+  __device__ __forceinline__ T a(int p, int i) const { return T(base[(int64_t)(2 * p) * ls + (int64_t)i * es]); }
+  __device__ __forceinline__ T b(int p, int i) const { return T(base[(int64_t)(2 * p + 1) * ls + (int64_t)i * es]); }
+};
+// Results straight to global memory (out = scale * v, or out += scale * v).
+// Adjacent lines (ls == 1, the y and z passes) are written as one 2-vector.
+template <typename T, typename Tout>
+struct GlobalOut {
+  Tout* base;
+  int64_t ls, es;
+  T sc;
+  int acc;
+  __device__ __forceinline__ void put(int p, int o, T va, T vb) const {
+    Tout* q = base + (int64_t)(2 * p) * ls + (int64_t)o * es;
+    if (acc) {
+      va = T(q[0]) + sc * va;
+      vb = T(q[ls]) + sc * vb;
+    } else {
+      va = sc * va;
+      vb = sc * vb;
+    }
+    if constexpr (sizeof(Tout) == 4 || sizeof(Tout) == 8) {
+      if (ls == 1) {
+        using V2 = typename std::conditional<sizeof(Tout) == 4, float2, double2>::type;
+        *reinterpret_cast<V2*>(q) = V2{Tout(va), Tout(vb)};
+        return;
+      }
+    }
+    q[0] = Tout(va);
+    q[ls] = Tout(vb);
+  }
+};
+
+// One real transform of the CTA's LPC2 lines, read through `src` and written
+// through `dst` (which may be the same staged lines).
 // KIND: 0 DCT-II family, 1 DST-II family, 2 DST-I.  INV: inverse.
-template <typename T, int N, int KIND, bool INV>
-__device__ void xform2(T* Rb, C2<T>* Xb, C2<T>* Zb, const C2<T>* tw, const C2<T>* qN) {
-  constexpr int RS = N + 1;
+// lines_fast: the output loop runs along the lines (coalesced for the y and z
+// passes, whose lines are adjacent in memory) instead of along the index.
+template <typename T, int N, int KIND, bool INV, class Src, class Dst>
+__device__ void xform2(const Src& src, const Dst& dst, bool lines_fast, C2<T>* Xb, C2<T>* Zb, const C2<T>* tw,
+                       const C2<T>* qN) {
   constexpr int L = (KIND == 2) ? 2 * N : N;
   constexpr int R = 16;
   constexpr int M = L / R;
   constexpr int XS = M + 1;                       // padded exchange row
+  constexpr int ZS = L + 1;                       // padded output row
   constexpr int PAIRS = LPC2 / 2;
   constexpr int PPR = (PASS2_THREADS / M < PAIRS) ? PASS2_THREADS / M : PAIRS;  // pairs per round
   constexpr int ROUNDS = PAIRS / PPR;
@@ -118,10 +176,8 @@ __device__ void xform2(T* Rb, C2<T>* Xb, C2<T>* Zb, const C2<T>* tw, const C2<T>
     const int p = round * PPR + pl;
     const bool active = pl < PPR;
     C2<T>* Xp = Xb + pl * (R * XS);
-    C2<T>* Zp = Zb + pl * L;              // Zb aliases Xb
+    C2<T>* Zp = Zb + pl * ZS;             // Zb aliases Xb
     if (active) {
-      const T* RA = Rb + (2 * p) * RS;
-      const T* RB = RA + RS;
       C2<T> v[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) {
@@ -129,23 +185,23 @@ __device__ void xform2(T* Rb, C2<T>* Xb, C2<T>* Zb, const C2<T>* tw, const C2<T>
         C2<T> z;
         if constexpr (KIND == 2) {
           T a = 0, b = 0;
-          if (n > 0 && n < N) { a = RA[n]; b = RB[n]; }
-          else if (n > N) { a = -RA[L - n]; b = -RB[L - n]; }
+          if (n > 0 && n < N) { a = src.a(p, n); b = src.b(p, n); }
+          else if (n > N) { a = -src.a(p, L - n); b = -src.b(p, L - n); }
           z = {a, b};
         } else if constexpr (!INV) {
-          const int src = (n < N / 2) ? 2 * n : 2 * (N - 1 - n) + 1;
-          T a = RA[src], b = RB[src];
+          const int i = (n < N / 2) ? 2 * n : 2 * (N - 1 - n) + 1;
+          T a = src.a(p, i), b = src.b(p, i);
           if (KIND == 1 && n >= N / 2) { a = -a; b = -b; }
           z = {a, b};
         } else {
           const int k = n;
           T xa, xna, xb, xnb;
           if constexpr (KIND == 1) {
-            xa = RA[N - 1 - k]; xb = RB[N - 1 - k];
-            xna = k > 0 ? RA[k - 1] : T(0); xnb = k > 0 ? RB[k - 1] : T(0);
+            xa = src.a(p, N - 1 - k); xb = src.b(p, N - 1 - k);
+            xna = k > 0 ? src.a(p, k - 1) : T(0); xnb = k > 0 ? src.b(p, k - 1) : T(0);
           } else {
-            xa = RA[k]; xb = RB[k];
-            xna = k > 0 ? RA[N - k] : T(0); xnb = k > 0 ? RB[N - k] : T(0);
+            xa = src.a(p, k); xb = src.b(p, k);
+            xna = k > 0 ? src.a(p, N - k) : T(0); xnb = k > 0 ? src.b(p, N - k) : T(0);
           }
           const C2<T> q = qN[k];                  // V = conj(q) (x_k - i x_{N-k})
           const C2<T> VA = {q.x * xa - q.y * xna, -q.x * xna - q.y * xa};
@@ -187,48 +243,51 @@ __device__ void xform2(T* Rb, C2<T>* Xb, C2<T>* Zb, const C2<T>* tw, const C2<T>
       }
     }
     __syncthreads();
-    // post-processing: the PPR pairs of this round -> staged real lines; one
-    // pass over (pair, index) yields the outputs of both lines of the pair
-    for (int e = tid; e < PPR * N; e += PASS2_THREADS) {
-      const int pr = e / N, o = e - pr * N;       // pair within round, output index
-      const C2<T>* Z = Zb + pr * L;
-      T* RA = Rb + (round * 2 * PPR + 2 * pr) * RS;
-      T* RB = RA + RS;
+    // post-processing: output o of both lines of pair pr from the FFT row
+    auto post = [&](int pr, int o) {
+      const C2<T>* Z = Zb + pr * ZS;
+      T va, vb;
       if constexpr (KIND == 2) {
         const T sc = INV ? T(1) / T(N) : T(0.5);
         const C2<T> z = Z[o];
-        RA[o] = (o == 0) ? T(0) : -z.y * sc;
-        RB[o] = (o == 0) ? T(0) : z.x * sc;
+        va = (o == 0) ? T(0) : -z.y * sc;
+        vb = (o == 0) ? T(0) : z.x * sc;
       } else if constexpr (!INV) {
         const int k = (KIND == 1) ? (N - 1 - o) : o;
         const C2<T> zk = Z[k], zc = Z[(N - k) & (N - 1)];
         const C2<T> VA = {T(0.5) * (zk.x + zc.x), T(0.5) * (zk.y - zc.y)};
         const C2<T> VB = {T(0.5) * (zk.y + zc.y), T(-0.5) * (zk.x - zc.x)};
         const C2<T> q = qN[k];
-        RA[o] = q.x * VA.x - q.y * VA.y;
-        RB[o] = q.x * VB.x - q.y * VB.y;
+        va = q.x * VA.x - q.y * VA.y;
+        vb = q.x * VB.x - q.y * VB.y;
       } else {
         const int n = (o & 1) ? (N - 1 - (o >> 1)) : (o >> 1);
         const C2<T> z = Z[n];
         const T sc = (KIND == 1 && (o & 1)) ? -T(1) / T(N) : T(1) / T(N);
-        RA[o] = z.x * sc;
-        RB[o] = z.y * sc;
+        va = z.x * sc;
+        vb = z.y * sc;
       }
+      dst.put(round * PPR + pr, o, va, vb);
+    };
+    if (lines_fast) {
+      for (int e = tid; e < PPR * N; e += PASS2_THREADS) post(e % PPR, e / PPR);
+    } else {
+      for (int e = tid; e < PPR * N; e += PASS2_THREADS) post(e / N, e % N);
     }
     __syncthreads();
   }
 }
 
-template <typename T, int N>
-__device__ __forceinline__ void xform2_dispatch(int type, T* Rb, C2<T>* Xb, C2<T>* Zb,
-                                                const C2<T>* tw, const C2<T>* qN) {
+template <typename T, int N, class Src, class Dst>
+__device__ __forceinline__ void xform2_dispatch(int type, const Src& src, const Dst& dst, bool lines_fast, C2<T>* Xb,
+                                                C2<T>* Zb, const C2<T>* tw, const C2<T>* qN) {
   switch (type) {
-    case X_DCT2F: xform2<T, N, 0, false>(Rb, Xb, Zb, tw, qN); break;
-    case X_DCT2I: xform2<T, N, 0, true>(Rb, Xb, Zb, tw, qN); break;
-    case X_DST2F: xform2<T, N, 1, false>(Rb, Xb, Zb, tw, qN); break;
-    case X_DST2I: xform2<T, N, 1, true>(Rb, Xb, Zb, tw, qN); break;
-    case X_DST1F: xform2<T, N, 2, false>(Rb, Xb, Zb, tw, qN); break;
-    case X_DST1I: xform2<T, N, 2, true>(Rb, Xb, Zb, tw, qN); break;
+    case X_DCT2F: xform2<T, N, 0, false>(src, dst, lines_fast, Xb, Zb, tw, qN); break;
+    case X_DCT2I: xform2<T, N, 0, true>(src, dst, lines_fast, Xb, Zb, tw, qN); break;
+    case X_DST2F: xform2<T, N, 1, false>(src, dst, lines_fast, Xb, Zb, tw, qN); break;
+    case X_DST2I: xform2<T, N, 1, true>(src, dst, lines_fast, Xb, Zb, tw, qN); break;
+    case X_DST1F: xform2<T, N, 2, false>(src, dst, lines_fast, Xb, Zb, tw, qN); break;
+    case X_DST1I: xform2<T, N, 2, true>(src, dst, lines_fast, Xb, Zb, tw, qN); break;
     default: break;
   }
 }
@@ -282,6 +341,7 @@ k_axis_pass2(const __grid_constant__ PassJobs<Tin, Tout, MAXJ> jobs, const C2<T>
     if (e < 2 * N) tws[e] = tw[e];
     else qs[e - 2 * N] = qN[e - 2 * N];
   }
+  __syncthreads();   // the tables are read from the first gather on
   constexpr int RS = S::RS;
   const int line0 = blockIdx.x * LPC2;
   const int axis = a.axis;
@@ -290,30 +350,20 @@ k_axis_pass2(const __grid_constant__ PassJobs<Tin, Tout, MAXJ> jobs, const C2<T>
   const int64_t stride = axis == 0 ? 1 : (axis == 1 ? N : NN);
   const int64_t base0 = axis == 0 ? (int64_t)line0 * N
                                   : (axis == 1 ? (int64_t)(line0 / N) * NN + (line0 % N) : (int64_t)line0);
-  // for y and z the LPC2 lines of a CTA are consecutive in x (LPC2 divides N);
-  // all loads of a thread are issued before any is used
-  constexpr int PER = LPC2 * N / PASS2_THREADS;
-  {
-    Tin vals[PER];
-#pragma unroll
-    for (int q = 0; q < PER; ++q) {
-      const int e = threadIdx.x + q * PASS2_THREADS;
-      int64_t g;
-      if (axis == 0) g = base0 + e;
-      else { const int n = e / LPC2, l = e - n * LPC2; g = base0 + l + n * stride; }
-      vals[q] = in[g];
-    }
-#pragma unroll
-    for (int q = 0; q < PER; ++q) {
-      const int e = threadIdx.x + q * PASS2_THREADS;
-      int l, n;
-      if (axis == 0) { l = e / N; n = e - l * N; }
-      else { n = e / LPC2; l = e - n * LPC2; }
-      Rb[l * RS + n] = T(vals[q]);
-    }
+  // for y and z the LPC2 lines of a CTA are consecutive in x (LPC2 divides N)
+  const int64_t ls = axis == 0 ? (int64_t)N : 1;          // line stride
+  const int64_t es = stride;                               // element stride
+  const GlobalLines<T, Tin> gin{in + base0, ls, es};
+  const bool lines_fast = axis != 0;
+  if (a.wmode == W_NONE && a.type1 == X_NONE) {
+    // plain pass: lines gathered from global memory into the FFT registers,
+    // results written from the post-processing straight to global memory
+    const GlobalOut<T, Tout> gout{out + base0, ls, es, T(a.scale), a.accumulate};
+    xform2_dispatch<T, N>(a.type0, gin, gout, lines_fast, Xb, Zb, tws, qs);
+    return;
   }
-  __syncthreads();
-  xform2_dispatch<T, N>(a.type0, Rb, Xb, Zb, tws, qs);
+  const SmemLines<T> st{Rb, RS};
+  xform2_dispatch<T, N>(a.type0, gin, st, false, Xb, Zb, tws, qs);
   if (a.wmode != W_NONE) {
     const T inv_mu = T(1.0 / a.mu);
     for (int e = threadIdx.x; e < LPC2 * N; e += PASS2_THREADS) {
@@ -327,37 +377,22 @@ k_axis_pass2(const __grid_constant__ PassJobs<Tin, Tout, MAXJ> jobs, const C2<T>
     }
     __syncthreads();
   }
-  xform2_dispatch<T, N>(a.type1, Rb, Xb, Zb, tws, qs);
+  if (a.type1 != X_NONE) {
+    const GlobalOut<T, Tout> gout{out + base0, ls, es, T(a.scale), a.accumulate};
+    xform2_dispatch<T, N>(a.type1, st, gout, lines_fast, Xb, Zb, tws, qs);
+    return;
+  }
+  // weighted single transform: staged lines -> global
   const T sc = T(a.scale);
-  if (a.accumulate) {
-    Tout prev[PER];
+  constexpr int PER = LPC2 * N / PASS2_THREADS;
 #pragma unroll
-    for (int q = 0; q < PER; ++q) {
-      const int e = threadIdx.x + q * PASS2_THREADS;
-      int64_t g;
-      if (axis == 0) g = base0 + e;
-      else { const int n = e / LPC2, l = e - n * LPC2; g = base0 + l + n * stride; }
-      prev[q] = out[g];
-    }
-#pragma unroll
-    for (int q = 0; q < PER; ++q) {
-      const int e = threadIdx.x + q * PASS2_THREADS;
-      int l, n;
-      int64_t g;
-      if (axis == 0) { l = e / N; n = e - l * N; g = base0 + e; }
-      else { n = e / LPC2; l = e - n * LPC2; g = base0 + l + n * stride; }
-      out[g] = Tout(T(prev[q]) + sc * Rb[l * RS + n]);
-    }
-  } else {
-#pragma unroll
-    for (int q = 0; q < PER; ++q) {
-      const int e = threadIdx.x + q * PASS2_THREADS;
-      int l, n;
-      int64_t g;
-      if (axis == 0) { l = e / N; n = e - l * N; g = base0 + e; }
-      else { n = e / LPC2; l = e - n * LPC2; g = base0 + l + n * stride; }
-      out[g] = Tout(sc * Rb[l * RS + n]);
-    }
+  for (int q = 0; q < PER; ++q) {
+    const int e = threadIdx.x + q * PASS2_THREADS;
+    int l, n;
+    int64_t g;
+    if (axis == 0) { l = e / N; n = e - l * N; g = base0 + e; }
+    else { n = e / LPC2; l = e - n * LPC2; g = base0 + l + n * stride; }
+    out[g] = a.accumulate ? Tout(T(out[g]) + sc * Rb[l * RS + n]) : Tout(sc * Rb[l * RS + n]);
   }
 }
 

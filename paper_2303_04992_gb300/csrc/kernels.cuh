@@ -305,14 +305,14 @@ __global__ void k_cg_alpha(const T* __restrict__ d, T* __restrict__ q, const T* 
   __shared__ double total;
   if (s->done) return;
   const T cd = T(s->cdiag);
-  double acc = 0.0;
+  T acc = T(0);   // a thread's few terms in T; FP64 from the block sum on
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x) {
     const T qs = q[e] + q2[e] + q3[e] + cd * d[e];
     q[e] = qs;
-    acc += double(d[e] * qs);
+    acc += d[e] * qs;
   }
-  if (last_block_sum(acc, partial, &s->ticket[0], sh, &total) && threadIdx.x == 0) {
+  if (last_block_sum(double(acc), partial, &s->ticket[0], sh, &total) && threadIdx.x == 0) {
     const double den = total + s->sumd * s->sumd * s->rank1;
     s->dq = den;
     s->alpha = (den != 0.0) ? s->rr / den : 0.0;
@@ -327,18 +327,20 @@ __global__ void k_cg_update(T* __restrict__ x, T* __restrict__ r, const T* __res
   __shared__ double sh[32];
   __shared__ double total;
   if (s->done) return;
-  // element arithmetic in T (FP32 in MIXED), squared norm accumulated in FP64
+  // element arithmetic in T (FP32 in MIXED); a thread's few squares summed in
+  // T, the block and grid sums in FP64 (FP64 per element would make this
+  // kernel FP64-ALU-bound on a GPU whose FP64 rate is a small fraction of FP32)
   const T a = T(s->alpha);
   const T c1 = T(s->sumd * s->rank1);
-  double acc = 0.0;
+  T acc = T(0);
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x) {
     const T rv = r[e] - a * (q[e] + c1);
     x[e] = x[e] + a * d[e];
     r[e] = rv;
-    acc += double(rv * rv);
+    acc += rv * rv;
   }
-  if (last_block_sum(acc, partial, &s->ticket[1], sh, &total) && threadIdx.x == 0) {
+  if (last_block_sum(double(acc), partial, &s->ticket[1], sh, &total) && threadIdx.x == 0) {
     s->beta = (s->rr != 0.0) ? total / s->rr : 0.0;
     s->rr = total;
     s->iters += 1;
@@ -353,14 +355,14 @@ __global__ void k_cg_direction(T* __restrict__ d, const T* __restrict__ r, int64
   __shared__ double total;
   if (s->done) return;
   const T b = T(s->beta);
-  double acc = 0.0;
+  T acc = T(0);
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x) {
     const T v = r[e] + b * d[e];
     d[e] = v;
-    acc += double(v);
+    acc += v;
   }
-  if (last_block_sum(acc, partial, &s->ticket[2], sh, &total) && threadIdx.x == 0) {
+  if (last_block_sum(double(acc), partial, &s->ticket[2], sh, &total) && threadIdx.x == 0) {
     s->sumd = total;
     if (!(s->rr > s->stop)) s->done = 1;
   }

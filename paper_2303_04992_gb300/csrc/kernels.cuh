@@ -21,66 +21,63 @@ __device__ __forceinline__ void unflat(int64_t x, int lg, int& i, int& j, int& k
 }
 
 // ------------------------------------------------------------------ jumps
-// One warp per control point: fitted value and five surface derivatives of
-// each density component (weighted sums over primary neighbours), then the
-// per-point 11 x 18 jump map.  J is slot-major: J[s * n + y].
-__global__ void k_jumps(const double* __restrict__ phi, const double* __restrict__ fpts,
-                        int64_t n, const int32_t* __restrict__ comp, const int32_t* __restrict__ pid,
-                        const int64_t* __restrict__ fit_ptr, const int32_t* __restrict__ fit_col,
-                        const double* __restrict__ fit_w, int64_t fit_nnz,
-                        const double* __restrict__ jmap, double* __restrict__ J) {
-  const int lane = threadIdx.x & 31;
-  const int64_t y = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (y >= n) return;
-  const int c = comp[y] - 1;
-  double acc[3][6];
+// Jump values at every control point (Sec. 4.3).  One thread per fit row
+// (point y, component c'): the fitted value and surface derivatives
+// (d_1, d_2, d_11, d_12, d_22) of phi^(c') as a sequential sum over the row's
+// neighbours (weight-major weights, so consecutive entries of a row are
+// consecutive in memory); then, per block of JB points, the 11 x 18 jump map
+// from shared memory (one output slot per task, input-major map rows).  All
+// arithmetic is FP64.  J is slot-major: J[s * n + y].
+constexpr int JB = 32;                 // points per block (3 JB threads)
+__global__ void __launch_bounds__(3 * JB)
+k_jumps(const double* __restrict__ phi, const double* __restrict__ fpts, int64_t n,
+        const int32_t* __restrict__ comp, const int32_t* __restrict__ pid,
+        const int64_t* __restrict__ fit_ptr, const int32_t* __restrict__ fit_col,
+        const double* __restrict__ fit_w, int64_t fit_nnz, const double* __restrict__ jmap,
+        double* __restrict__ J) {
+  __shared__ double D[JB * 3][6];
+  const int64_t y0 = (int64_t)blockIdx.x * JB;
+  {
+    const int t = threadIdx.x;                  // row 3 * (y - y0) + c'
+    const int64_t y = y0 + t / 3;
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    if (y < n) {
+      const int64_t rr = 3 * y0 + t;
+      const int64_t b = fit_ptr[rr], e = fit_ptr[rr + 1];
+      for (int64_t q = b; q < e; ++q) {
+        const double v = phi[fit_col[q]];
 #pragma unroll
-  for (int cc = 0; cc < 3; ++cc)
+        for (int k = 0; k < 6; ++k) acc[k] += fit_w[k * fit_nnz + q] * v;
+      }
+    }
 #pragma unroll
-    for (int s = 0; s < 6; ++s) acc[cc][s] = 0.0;
-  // fit weights are stored weight-major (fit_w[s * nnz + entry]): lanes read
-  // consecutive entries
-#pragma unroll
-  for (int cc = 0; cc < 3; ++cc) {
-    const int64_t b = fit_ptr[3 * y + cc], e = fit_ptr[3 * y + cc + 1];
-    for (int64_t q = b + lane; q < e; q += 32) {
-      const double v = phi[fit_col[q]];
-#pragma unroll
-      for (int s = 0; s < 6; ++s) acc[cc][s] += fit_w[s * fit_nnz + q] * v;
+    for (int k = 0; k < 6; ++k) D[t][k] = acc[k];
+  }
+  __syncthreads();
+  // slot 0: the density itself at a primary point, its fitted value at a secondary one
+  if (threadIdx.x < JB) {
+    const int64_t y = y0 + threadIdx.x;
+    if (y < n) {
+      const int64_t p = pid[y];
+      J[y] = (p >= 0) ? phi[p] : D[3 * threadIdx.x + comp[y] - 1][0];
     }
   }
-#pragma unroll
-  for (int cc = 0; cc < 3; ++cc)
-#pragma unroll
-    for (int s = 0; s < 6; ++s)
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc[cc][s] += __shfl_xor_sync(0xffffffffu, acc[cc][s], o);
-  double in[18];
-#pragma unroll
-  for (int cc = 0; cc < 3; ++cc)
-#pragma unroll
-    for (int s = 0; s < 5; ++s) in[5 * cc + s] = acc[cc][s + 1];
-#pragma unroll
-  for (int cc = 0; cc < 3; ++cc) in[15 + cc] = fpts ? fpts[cc * n + y] : 0.0;
-  if (lane == 0) {
-    const int64_t p = pid[y];
-    double v0 = (p >= 0) ? phi[p] : 0.0;
-    if (p < 0) {
-      // secondary point: fitted value of its own component
-#pragma unroll
-      for (int cc = 0; cc < 3; ++cc)
-        if (cc == c) v0 = acc[cc][0];
-    }
-    J[y] = v0;
-  }
-  // jump map stored input-major per point (jmap[(y * 18 + q) * 11 + row]): the
-  // 11 lanes read 11 consecutive values per input
-  if (lane < 11) {
-    const double* M = jmap + (size_t)y * 18 * 11 + lane;
+  // slots 1..11: the jump map (input-major jmap[(y * 18 + q) * 11 + r])
+  for (int task = threadIdx.x; task < JB * 11; task += 3 * JB) {
+    const int yl = task / 11, r = task - yl * 11;
+    const int64_t y = y0 + yl;
+    if (y >= n) continue;
+    const double* M = jmap + (size_t)y * 18 * 11 + r;
     double s = 0.0;
 #pragma unroll
-    for (int q = 0; q < 18; ++q) s += M[q * 11] * in[q];
-    J[(int64_t)(lane + 1) * n + y] = s;
+    for (int cc = 0; cc < 3; ++cc)
+#pragma unroll
+      for (int k = 0; k < 5; ++k) s += M[(5 * cc + k) * 11] * D[3 * yl + cc][k + 1];
+    if (fpts) {
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) s += M[(15 + cc) * 11] * fpts[cc * n + y];
+    }
+    J[(int64_t)(r + 1) * n + y] = s;
   }
 }
 

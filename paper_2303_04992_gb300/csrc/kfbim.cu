@@ -646,8 +646,7 @@ int grid_solve_mixed(kfbim_ctx* c, cudaStream_t s) {
 int interface_solve(kfbim_ctx* c, const double* phi, const double* fpts, const double* fgrid,
                     cudaStream_t s) {
   const int64_t n = c->n_all;
-  const int wpb = 8;
-  k_jumps<<<(unsigned)((n + wpb - 1) / wpb), 32 * wpb, 0, s>>>(
+  k_jumps<<<(unsigned)((n + JB - 1) / JB), 3 * JB, 0, s>>>(
       phi, fpts, n, c->d_comp, c->d_pid, c->d_fit_ptr, c->d_fit_col, c->d_fit_w, c->fit_nnz, c->d_jmap,
       c->J); ++g_launches;
   check_launch();
@@ -1494,10 +1493,9 @@ void interface_batch(kfbim_ctx* c, const std::vector<int>& act, const std::vecto
                      const std::vector<const double*>& fpts, const std::vector<const double*>& fgrid,
                      cudaStream_t s) {
   const int64_t n = c->n_all;
-  const int wpb = 8;
   for (size_t q = 0; q < act.size(); ++q) {
     const kfbim_ctx::Slot& w = c->bs[act[q]];
-    k_jumps<<<(unsigned)((n + wpb - 1) / wpb), 32 * wpb, 0, s>>>(
+    k_jumps<<<(unsigned)((n + JB - 1) / JB), 3 * JB, 0, s>>>(
         phi[q], fpts[q], n, c->d_comp, c->d_pid, c->d_fit_ptr, c->d_fit_col, c->d_fit_w, c->fit_nnz,
         c->d_jmap, w.J);
     k_rhs_fill<<<grid_for(4 * c->N3), 256, 0, s>>>(fgrid[q], c->d_side[1], c->d_side[2], c->d_side[3],
@@ -1807,8 +1805,7 @@ int kfbim_jumps(kfbim_ctx* c, const double* phi, const double* fpts, double* Jou
     if (!phi || !Jout) return fail(c, KFBIM_E_INVALID, "kfbim_jumps: bad pointers");
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = c->n_all;
-    const int wpb = 8;
-    k_jumps<<<(unsigned)((n + wpb - 1) / wpb), 32 * wpb, 0, s>>>(
+    k_jumps<<<(unsigned)((n + JB - 1) / JB), 3 * JB, 0, s>>>(
         phi, fpts, n, c->d_comp, c->d_pid, c->d_fit_ptr, c->d_fit_col, c->d_fit_w, c->fit_nnz, c->d_jmap,
         Jout); ++g_launches;
     check_launch();

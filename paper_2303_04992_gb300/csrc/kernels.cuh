@@ -168,8 +168,10 @@ __global__ void k_mac_residual(const double* __restrict__ f, const double* __res
                                double* __restrict__ rf, double* __restrict__ rg) {
   const int N = 1 << lg;
   const int64_t N3 = (int64_t)1 << (3 * lg);
-  const double ih2 = 1.0 / (h * h), ih = 1.0 / h;
+  const double ih = 1.0 / h, c_lap = -mu / (h * h);
   const double gm = gmean[0];
+  // FP64 throughput is the bound here: the six neighbours are summed first and
+  // scaled once, rf = f - (c_lap (sum - 6 u0) + (p1 - p0) / h)
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < 4 * N3;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int c = (int)(e >> (3 * lg));
@@ -181,7 +183,7 @@ __global__ void k_mac_residual(const double* __restrict__ f, const double* __res
       if (nrm == 0) { rf[e] = 0.0; continue; }
       const double* uc = u + ((int64_t)c << (3 * lg));
       const double u0 = uc[x];
-      double lap = 0.0;
+      double sum = 0.0;
 #pragma unroll
       for (int b = 0; b < 3; ++b) {
         const int64_t st = (int64_t)1 << (b * lg);
@@ -194,10 +196,10 @@ __global__ void k_mac_residual(const double* __restrict__ f, const double* __res
           um = (ib > 0) ? uc[x - st] : -u0;
           up = (ib < N - 1) ? uc[x + st] : -u0;
         }
-        lap += (up - 2.0 * u0 + um) * ih2;
+        sum += up + um;
       }
-      const double gp = (p[x] - p[x - ((int64_t)1 << (c * lg))]) * ih;
-      rf[e] = f[e] - (-mu * lap + gp);
+      const double dp = p[x] - p[x - ((int64_t)1 << (c * lg))];
+      rf[e] = f[e] - fma(c_lap, fma(-6.0, u0, sum), dp * ih);
     } else {
       double d = 0.0;
 #pragma unroll
@@ -207,9 +209,9 @@ __global__ void k_mac_residual(const double* __restrict__ f, const double* __res
         const double* ub = u + ((int64_t)b << (3 * lg));
         const double lo = (ib >= 1) ? ub[x] : 0.0;
         const double hi = (ib + 1 <= N - 1) ? ub[x + st] : 0.0;
-        d += (hi - lo) * ih;
+        d += hi - lo;
       }
-      rg[x] = g[x] - gm - d - cpen * p[x];
+      rg[x] = fma(-cpen, p[x], g[x] - gm) - d * ih;
     }
   }
 }

@@ -297,13 +297,40 @@ __device__ __forceinline__ T spectral_weight2(const PassArgs& a, const T* __rest
                                               int i, int j, int k) {
   const T sum = s2[a.kind[0] * N + i] + s2[a.kind[1] * N + j] + s2[a.kind[2] * N + k];
   const int ac = a.wc == 0 ? i : (a.wc == 1 ? j : k);
-  const T isum = T(1) / sum;
+  // correctly rounded reciprocal: the same value as T(1) / sum
+  T isum;
+  if constexpr (sizeof(T) == 4) isum = __frcp_rn(sum);
+  else isum = __drcp_rn(sum);
   if (a.wmode == W_SCHUR) return s2[ac] * isum * inv_mu;
   if (ac == 0) return T(0);
   const T h = T(a.h);
   if (a.wmode == W_POISSON) return h * h * isum * inv_mu;
   return T(-2) * h * sqrt(T(0.25) * s2[ac]) * isum * inv_mu;   // W_RHS
 }
+
+// The staged lines of a CTA, written with the spectral weight applied (the
+// fused middle pass: first transform, weight, second transform).
+template <typename T, int N>
+struct WeightedSmemLines {
+  T* Rb;
+  int RS;
+  const PassArgs* a;
+  const T* s2;
+  T inv_mu;
+  int line0, axis;
+  __device__ __forceinline__ T w(int l, int n) const {
+    const int line = line0 + l;
+    int i, j, k;
+    if (axis == 0) { i = n; j = line % N; k = line / N; }
+    else if (axis == 1) { i = line % N; j = n; k = line / N; }
+    else { i = line % N; j = line / N; k = n; }
+    return spectral_weight2<T, N>(*a, s2, inv_mu, i, j, k);
+  }
+  __device__ __forceinline__ void put(int p, int o, T va, T vb) const {
+    Rb[(2 * p) * RS + o] = va * w(2 * p, o);
+    Rb[(2 * p + 1) * RS + o] = vb * w(2 * p + 1, o);
+  }
+};
 
 // Up to three independent passes in one launch (blockIdx.y selects the job):
 // the three components' transforms of one stage of the Schur apply, the
@@ -363,19 +390,11 @@ k_axis_pass2(const __grid_constant__ PassJobs<Tin, Tout, MAXJ> jobs, const C2<T>
     return;
   }
   const SmemLines<T> st{Rb, RS};
-  xform2_dispatch<T, N>(a.type0, gin, st, false, Xb, Zb, tws, qs);
   if (a.wmode != W_NONE) {
-    const T inv_mu = T(1.0 / a.mu);
-    for (int e = threadIdx.x; e < LPC2 * N; e += PASS2_THREADS) {
-      const int l = e / N, n = e - l * N;
-      const int line = line0 + l;
-      int i, j, k;
-      if (axis == 0) { i = n; j = line % N; k = line / N; }
-      else if (axis == 1) { i = line % N; j = n; k = line / N; }
-      else { i = line % N; j = line / N; k = n; }
-      Rb[l * RS + n] *= spectral_weight2<T, N>(a, s2, inv_mu, i, j, k);
-    }
-    __syncthreads();
+    const WeightedSmemLines<T, N> wst{Rb, RS, &a, s2, T(1.0 / a.mu), line0, axis};
+    xform2_dispatch<T, N>(a.type0, gin, wst, false, Xb, Zb, tws, qs);
+  } else {
+    xform2_dispatch<T, N>(a.type0, gin, st, false, Xb, Zb, tws, qs);
   }
   if (a.type1 != X_NONE) {
     const GlobalOut<T, Tout> gout{out + base0, ls, es, T(a.scale), a.accumulate};

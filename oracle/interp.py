@@ -73,3 +73,26 @@ def trace(grid, cp, S, fields, J):
     rhs = vals + np.where(outside, Ji, 0.0)
     a = np.linalg.solve(V, rhs[..., None])[..., 0]
     return a[:, 0]
+
+
+def pressure_trace(grid, cp, S, p, J):
+    """p^+ at every control point by linear interpolation (Sec. 4.4, last
+    paragraph: the stress needs no derivative of p, so a linear rule
+    suffices).  Reading: trilinear interpolation over the eight cell centres
+    around x; a cell in Omega^c contributes p + [p](x) (the jump [p] =
+    p^+ - p^- at the point itself, slot 10 of J), its Omega-side extension to
+    zeroth order.  p: cell field (N, N, N) in [k, j, i]; returns (n,)."""
+    N, h, lo = grid.N, grid.h, grid.lo
+    s = (cp.xyz - lo) / h - 0.5                       # cell-centre coordinates
+    i0 = np.clip(np.floor(s).astype(np.int64), 0, N - 2)
+    t = s - i0
+    out = np.zeros(cp.n)
+    for dk in (0, 1):
+        for dj in (0, 1):
+            for di in (0, 1):
+                ii, jj, kk = i0[:, 0] + di, i0[:, 1] + dj, i0[:, 2] + dk
+                w = ((t[:, 0] if di else 1 - t[:, 0]) * (t[:, 1] if dj else 1 - t[:, 1])
+                     * (t[:, 2] if dk else 1 - t[:, 2]))
+                v = p[kk, jj, ii] + np.where(S[0][kk, jj, ii], 0.0, J[:, 10])
+                out += w * v
+    return out

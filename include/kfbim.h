@@ -268,6 +268,18 @@ int kfbim_interface(kfbim_ctx* ctx, const double* phi_dev, const double* fpts_de
 int kfbim_trace(kfbim_ctx* ctx, const double* u_dev, const double* J_dev,
                 double* out_dev, void* stream);
 
+/* Boundary pressure p^+ at every control point (Sec. 4.4, last paragraph:
+ * the stress needs no derivative of p, so a linear rule suffices), e.g. for
+ * the traction -p n + mu (grad u + grad u^T) n on Gamma.  Trilinear
+ * interpolation over the eight cell centres around the point; cells in
+ * Omega^c contribute p + [p], the jump of slot 10 of J at the point.
+ *   p_dev [N^3] cell pressure (u_dev/p_dev of kfbim_solve or kfbim_interface);
+ *   J_dev [12*n_points] the jumps of the same density (kfbim_jumps);
+ *   out_dev [n_points], canonical point order.  First-order accurate next to
+ *   the interface (zeroth-order jump correction). */
+int kfbim_pressure_trace(kfbim_ctx* ctx, const double* p_dev, const double* J_dev,
+                         double* out_dev, void* stream);
+
 /* One FP32 axis pass (test entry point of the transform kernels): out = W . T in
  * along axis (0 x, 1 y, 2 z) of an N^3 field, T = transform `type` (1 DCT-II,
  * 2 its inverse, 3 DST-II, 4 its inverse, 5 DST-I, 6 its inverse; conventions

@@ -67,6 +67,7 @@ SYMBOLS = {
     "kfbim_transforms_info": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "kfbim_apply_adjoint": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "kfbim_solve_adjoint": (c_int, [c_void_p, c_void_p, c_void_p, ctypes.POINTER(Stats), c_void_p]),
+    "kfbim_pressure_trace": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "kfbim_jumps": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "kfbim_interface": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "kfbim_trace": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
@@ -269,6 +270,10 @@ class Solver:
         self._check(self._lib.kfbim_interface(self._ctx, _ptr(phi), _ptr(fpts), _ptr(fgrid), _ptr(u),
                                               _ptr(p), self._stream()))
         return u, p
+
+    def pressure_trace(self, p, J, out):
+        self._check(self._lib.kfbim_pressure_trace(self._ctx, _ptr(p), _ptr(J), _ptr(out), self._stream()))
+        return out
 
     def trace(self, u, J, out):
         self._check(self._lib.kfbim_trace(self._ctx, _ptr(u), _ptr(J), _ptr(out), self._stream()))

@@ -135,6 +135,38 @@ __global__ void k_trace(const double* __restrict__ u, const double* __restrict__
   }
 }
 
+// p^+ at every control point (Sec. 4.4, last paragraph: a linear rule is
+// enough for the pressure): trilinear interpolation over the eight cell
+// centres around the point; a cell in Omega^c contributes p + [p] (slot 10 of
+// J at the point), its Omega-side value to zeroth order.
+__global__ void k_pressure_trace(const double* __restrict__ p, const double* __restrict__ J,
+                                 const double* __restrict__ xyz, int64_t n, int N, double lo, double h,
+                                 const uint8_t* __restrict__ side0, double* __restrict__ out) {
+  for (int64_t y = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; y < n;
+       y += (int64_t)gridDim.x * blockDim.x) {
+    int i0[3];
+    double t[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double sc = (xyz[3 * y + a] - lo) / h - 0.5;
+      int f = (int)floor(sc);
+      f = f < 0 ? 0 : (f > N - 2 ? N - 2 : f);
+      i0[a] = f;
+      t[a] = sc - f;
+    }
+    const double jp = J[10 * n + y];
+    double acc = 0.0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int di = c & 1, dj = (c >> 1) & 1, dk = c >> 2;
+      const int64_t idx = ((int64_t)(i0[2] + dk) * N + (i0[1] + dj)) * N + (i0[0] + di);
+      const double w = (di ? t[0] : 1.0 - t[0]) * (dj ? t[1] : 1.0 - t[1]) * (dk ? t[2] : 1.0 - t[2]);
+      acc += w * (p[idx] + (side0[idx] ? 0.0 : jp));
+    }
+    out[y] = acc;
+  }
+}
+
 // --------------------------------------------------------- MAC stencils
 
 // r^(c) = f^(c) - G_c p   (face grid c; wall faces 0)

@@ -57,6 +57,7 @@ struct kfbim_ctx {
   C2<double>* d_twc64 = nullptr;  // full-circle twiddles exp(-2 pi i t / 2N), t < 2N
   C2<float>* d_twc32 = nullptr;
   float* d_s2f = nullptr;         // FP32 copy of the eigenvalue table
+  double* d_xyz = nullptr;        // control point coordinates (3 per point)
   // tensor-core passes (N = 128, MIXED): transform matrices [type 1..6][hi|lo][n][m],
   // the kernels' timeout flag, and the kernel chosen per stage kind (0 FFT, 1 GEMM)
   float* d_tc_mats = nullptr;
@@ -1028,6 +1029,7 @@ void fill_tables(kfbim_ctx* c) {
   for (int64_t y = 0; y < t.n_all; ++y)
     if (t.primary[y]) prim_of.push_back(y);
   c->d_prim_of = upload(c, prim_of);
+  c->d_xyz = upload(c, t.xyz);
   for (int g = 0; g < 4; ++g) c->d_side[g] = upload(c, t.side[g]);
   // twiddles exp(-2 pi i t / 2N), t < N; post twiddles exp(-i pi k / 2N), k < N
   std::vector<C2<double>> tw(N), q(N);
@@ -1831,6 +1833,17 @@ int kfbim_trace(kfbim_ctx* c, const double* u, const double* J, double* out, voi
   return guarded(c, [&]() -> int {
     if (!u || !J || !out) return fail(c, KFBIM_E_INVALID, "kfbim_trace: bad pointers");
     trace(c, u, J, out, (cudaStream_t)stream);
+    return KFBIM_OK;
+  });
+}
+
+int kfbim_pressure_trace(kfbim_ctx* c, const double* p, const double* J, double* out, void* stream) {
+  return guarded(c, [&]() -> int {
+    if (!p || !J || !out) return fail(c, KFBIM_E_INVALID, "kfbim_pressure_trace: bad pointers");
+    cudaStream_t s = (cudaStream_t)stream;
+    k_pressure_trace<<<grid_for(c->n_all), 256, 0, s>>>(p, J, c->d_xyz, c->n_all, c->N, c->host.lo, c->h,
+                                                         c->d_side[0], out); ++g_launches;
+    check_launch();
     return KFBIM_OK;
   });
 }

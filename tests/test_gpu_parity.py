@@ -115,6 +115,18 @@ def test_interface_solve(pair):
     assert rel(p.cpu().numpy().reshape(N, N, N), p_w) < 1e-10
 
 
+def test_pressure_trace(pair):
+    o, s = pair
+    N = s.N
+    rng = np.random.default_rng(21)
+    p = rng.standard_normal((N, N, N))
+    J = rng.standard_normal((o.cp.n, 12))
+    want = interp.pressure_trace(o.grid, o.cp, o.S, p, J)
+    out = torch.zeros(o.cp.n, dtype=torch.float64, device="cuda")
+    s.pressure_trace(cuda(p.ravel()), cuda(J.T.copy()), out)
+    assert rel(out.cpu().numpy(), want) < 1e-13
+
+
 def test_apply(pair):
     o, s = pair
     phi = np.random.default_rng(6).standard_normal(s.n_primary)

@@ -399,6 +399,92 @@ __global__ void k_cg_direction(T* __restrict__ d, const T* __restrict__ r, int64
   }
 }
 
+// The three CG kernels for a batch of independent CG runs in one launch each:
+// blockIdx.y selects the run (its vectors, scalars and partial buffer), the
+// blocks of one run reduce exactly as in the single-run kernels.
+constexpr int kCgBatchMax = 64;
+template <typename T>
+struct CgBatchArgs {
+  T *x[kCgBatchMax], *r[kCgBatchMax], *d[kCgBatchMax], *q[kCgBatchMax];
+  const T *q2[kCgBatchMax], *q3[kCgBatchMax];
+  CGScalars* s[kCgBatchMax];
+  double* partial[kCgBatchMax];
+};
+
+template <typename T>
+__global__ void k_cg_alpha_b(const __grid_constant__ CgBatchArgs<T> A, int64_t n) {
+  const int b = blockIdx.y;
+  CGScalars* s = A.s[b];
+  __shared__ double sh[32];
+  __shared__ double total;
+  if (s->done) return;
+  const T* d = A.d[b];
+  T* q = A.q[b];
+  const T *q2 = A.q2[b], *q3 = A.q3[b];
+  const T cd = T(s->cdiag);
+  T acc = T(0);
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const T qs = q[e] + q2[e] + q3[e] + cd * d[e];
+    q[e] = qs;
+    acc += d[e] * qs;
+  }
+  if (last_block_sum(double(acc), A.partial[b], &s->ticket[0], sh, &total) && threadIdx.x == 0) {
+    const double den = total + s->sumd * s->sumd * s->rank1;
+    s->dq = den;
+    s->alpha = (den != 0.0) ? s->rr / den : 0.0;
+  }
+}
+
+template <typename T>
+__global__ void k_cg_update_b(const __grid_constant__ CgBatchArgs<T> A, int64_t n) {
+  const int b = blockIdx.y;
+  CGScalars* s = A.s[b];
+  __shared__ double sh[32];
+  __shared__ double total;
+  if (s->done) return;
+  T *x = A.x[b], *r = A.r[b];
+  const T *d = A.d[b], *q = A.q[b];
+  const T a = T(s->alpha);
+  const T c1 = T(s->sumd * s->rank1);
+  T acc = T(0);
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const T rv = r[e] - a * (q[e] + c1);
+    x[e] = x[e] + a * d[e];
+    r[e] = rv;
+    acc += rv * rv;
+  }
+  if (last_block_sum(double(acc), A.partial[b], &s->ticket[1], sh, &total) && threadIdx.x == 0) {
+    s->beta = (s->rr != 0.0) ? total / s->rr : 0.0;
+    s->rr = total;
+    s->iters += 1;
+  }
+}
+
+template <typename T>
+__global__ void k_cg_direction_b(const __grid_constant__ CgBatchArgs<T> A, int64_t n) {
+  const int b = blockIdx.y;
+  CGScalars* s = A.s[b];
+  __shared__ double sh[32];
+  __shared__ double total;
+  if (s->done) return;
+  T* d = A.d[b];
+  const T* r = A.r[b];
+  const T be = T(s->beta);
+  T acc = T(0);
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const T v = r[e] + be * d[e];
+    d[e] = v;
+    acc += v;
+  }
+  if (last_block_sum(double(acc), A.partial[b], &s->ticket[2], sh, &total) && threadIdx.x == 0) {
+    s->sumd = total;
+    if (!(s->rr > s->stop)) s->done = 1;
+  }
+}
+
 // initial scalars: rr = bb = b.b, sumd = sum b, stop = tol^2 bb
 template <typename T>
 __global__ void k_cg_init(const T* __restrict__ b, int64_t n, CGScalars* s, double tol2, double rank1,

@@ -107,6 +107,7 @@ struct kfbim_ctx {
   CGScalars* bcgs = nullptr;   // one per slot, contiguous
   double* bscal = nullptr;     // 8 per slot, contiguous
   double* bgh = nullptr;       // (bm + 1) per slot, contiguous (slot.gh points into it)
+  double* bpartial = nullptr;  // RED_BLOCKS reduction partials per slot (batched CG kernels)
   void* bpinned = nullptr;     // host staging of bcgs / bscal / bgh
   int bcap = 0, bm = 0;
   std::vector<int> b_cg, b_sweeps, b_isolves;   // per-slot counters of the current call
@@ -1270,6 +1271,7 @@ void batch_alloc(kfbim_ctx* c, int B) {
   }
   c->bcgs = dalloc<CGScalars>(c, B);
   c->bscal = dalloc<double>(c, 8 * (size_t)B);
+  c->bpartial = dalloc<double>(c, (size_t)RED_BLOCKS * B);
   if (c->bpinned) CK(cudaFreeHost(c->bpinned));
   c->bpinned = nullptr;
   const size_t pin = std::max({sizeof(CGScalars) * B, sizeof(double) * 8 * B,
@@ -1367,15 +1369,27 @@ void cg_batch(kfbim_ctx* c, const std::vector<int>& act, double tol, cudaStream_
       if (!h[b].done) run.push_back(b);
     }
     if (run.empty() || launched >= c->opt.cg_max) break;
+    // the CG vector updates of every running instance in one launch per step,
+    // RED_BLOCKS blocks per instance (the single-run reduction order)
+    CgBatchArgs<float> A{};
+    for (size_t k = 0; k < run.size(); ++k) {
+      const kfbim_ctx::Slot& w = c->bs[run[k]];
+      A.x[k] = w.x;
+      A.r[k] = w.r;
+      A.d[k] = w.d;
+      A.q[k] = w.q;
+      A.q2[k] = w.q2;
+      A.q3[k] = w.q3;
+      A.s[k] = &c->bcgs[run[k]];
+      A.partial[k] = c->bpartial + (size_t)RED_BLOCKS * run[k];
+    }
+    const dim3 grid(RED_BLOCKS, (unsigned)run.size());
     for (int it = 0; it < kCgGraphIters; ++it) {
       schur_apply_batch(c, run, s);
-      for (int b : run) {
-        const kfbim_ctx::Slot& w = c->bs[b];
-        k_cg_alpha<float><<<RED_BLOCKS, RED_THREADS, 0, s>>>(w.d, w.q, w.q2, w.q3, n, &c->bcgs[b], c->partial);
-        k_cg_update<float><<<RED_BLOCKS, RED_THREADS, 0, s>>>(w.x, w.r, w.d, w.q, n, &c->bcgs[b], c->partial);
-        k_cg_direction<float><<<RED_BLOCKS, RED_THREADS, 0, s>>>(w.d, w.r, n, &c->bcgs[b], c->partial);
-        g_launches += 3;
-      }
+      k_cg_alpha_b<float><<<grid, RED_THREADS, 0, s>>>(A, n);
+      k_cg_update_b<float><<<grid, RED_THREADS, 0, s>>>(A, n);
+      k_cg_direction_b<float><<<grid, RED_THREADS, 0, s>>>(A, n);
+      g_launches += 3;
       check_launch();
     }
     launched += kCgGraphIters;

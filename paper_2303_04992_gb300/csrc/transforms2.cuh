@@ -95,7 +95,7 @@ struct Pass2Smem {
   // the exchange buffer also receives the FFT output (after a barrier)
   static constexpr size_t xbuf = sizeof(C2<T>) * (XA > XB ? XA : XB);
   // twiddle tables staged per CTA: full-circle tw (2N) and post-twiddles qN (N)
-  static constexpr size_t tables = sizeof(C2<T>) * 3 * N;
+  static constexpr size_t tables = sizeof(C2<T>) * 3 * N + sizeof(T) * 2 * N;   // + eigenvalue table
   static constexpr size_t bytes = stage_al + xbuf + tables;
 };
 
@@ -364,10 +364,13 @@ k_axis_pass2(const __grid_constant__ PassJobs<Tin, Tout, MAXJ> jobs, const C2<T>
   C2<T>* Zb = Xb;
   C2<T>* tws = reinterpret_cast<C2<T>*>(smem2 + S::stage_al + S::xbuf);
   C2<T>* qs = tws + 2 * N;
+  T* s2s = reinterpret_cast<T*>(qs + N);   // the eigenvalue table, read by the weight
   for (int e = threadIdx.x; e < 3 * N; e += PASS2_THREADS) {
     if (e < 2 * N) tws[e] = tw[e];
     else qs[e - 2 * N] = qN[e - 2 * N];
   }
+  if (a.wmode != W_NONE)
+    for (int e = threadIdx.x; e < 2 * N; e += PASS2_THREADS) s2s[e] = s2[e];
   __syncthreads();   // the tables are read from the first gather on
   constexpr int RS = S::RS;
   const int line0 = blockIdx.x * LPC2;
@@ -391,7 +394,7 @@ k_axis_pass2(const __grid_constant__ PassJobs<Tin, Tout, MAXJ> jobs, const C2<T>
   }
   const SmemLines<T> st{Rb, RS};
   if (a.wmode != W_NONE) {
-    const WeightedSmemLines<T, N> wst{Rb, RS, &a, s2, T(1.0 / a.mu), line0, axis};
+    const WeightedSmemLines<T, N> wst{Rb, RS, &a, s2s, T(1.0 / a.mu), line0, axis};
     xform2_dispatch<T, N>(a.type0, gin, wst, false, Xb, Zb, tws, qs);
   } else {
     xform2_dispatch<T, N>(a.type0, gin, st, false, Xb, Zb, tws, qs);

@@ -30,6 +30,11 @@
  *    The "primary" points (line most normal to Gamma) carry the density
  *    unknowns and the BIE equations; density vectors are ordered like the
  *    primary points.
+ *  - Threads: calls on different contexts may run at the same time from
+ *    different host threads, on one device or several (each context owns its
+ *    workspace; the kernel shared-memory limits the library raises are kept
+ *    per device under a lock).  Calls on one context must not overlap.  The
+ *    kernel_launches statistic counts the launches of the call's own thread.
  *  - Return value: KFBIM_OK or a negative kfbim_status; kfbim_last_error()
  *    returns the message of the last failure on that context.  Invalid inputs
  *    are reported, never aborted on.  On KFBIM_E_NOCONV the outputs still hold

@@ -158,27 +158,40 @@ inline int grid_for(int64_t n, int threads = 256) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 16));
 }
 
-int64_t g_launches = 0;   // kernel launches issued through this library
+// Kernel launches issued through this library by the calling host thread: an
+// entry point reports the difference across its own call, so calls running on
+// other threads (other contexts) do not enter its count.
+thread_local int64_t g_launches = 0;
 
 inline void check_launch() {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) throw CudaError{std::string("kernel launch: ") + cudaGetErrorString(e)};
 }
 
-// Raise, never lower, the dynamic shared-memory limit of a kernel that is
-// launched with several sizes (the runtime-N pass): setting the attribute to a
-// small size would also lower it below the 48 KiB default for every later
-// launch of that kernel, from any path of this library.
+// Raise, never lower, the dynamic shared-memory limit of a kernel on the
+// current device.  The attribute belongs to the device, so the limit already
+// set is tracked per (kernel, device); a kernel launched with several sizes
+// (the runtime-N pass) keeps the largest, since setting a small size would
+// also lower it below the 48 KiB default for every later launch of that
+// kernel, from any path of this library.  Safe to call from several threads.
 cudaError_t raise_dynamic_smem(const void* kern, size_t bytes) {
+  struct Limit {
+    const void* kern;
+    int dev;
+    size_t bytes;
+  };
   static std::mutex m;
-  static std::vector<std::pair<const void*, size_t>> limit;
+  static std::vector<Limit> limit;
+  int dev = 0;
+  const cudaError_t ge = cudaGetDevice(&dev);
+  if (ge != cudaSuccess) return ge;
   std::lock_guard<std::mutex> lock(m);
   size_t* cur = nullptr;
   for (auto& e : limit)
-    if (e.first == kern) cur = &e.second;
+    if (e.kern == kern && e.dev == dev) cur = &e.bytes;
   if (!cur) {
-    limit.push_back({kern, (size_t)48 * 1024});
-    cur = &limit.back().second;
+    limit.push_back({kern, dev, (size_t)48 * 1024});
+    cur = &limit.back().bytes;
   }
   if (bytes <= *cur) return cudaSuccess;
   const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -210,11 +223,7 @@ template <typename Tin, typename T, typename Tout, int N, int MAXJ>
 void launch_pass2(kfbim_ctx* c, const PassJobs<Tin, Tout, MAXJ>& jobs, int njobs, cudaStream_t s) {
   const size_t smem = Pass2Smem<T, N>::bytes;
   auto kern = k_axis_pass2<Tin, T, Tout, N, MAXJ>;
-  static size_t configured = 0;
-  if (smem > configured) {
-    CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    configured = smem;
-  }
+  CK(raise_dynamic_smem(reinterpret_cast<const void*>(kern), smem));
   kern<<<dim3((unsigned)(N * N / LPC2), (unsigned)njobs), PASS2_THREADS, smem, s>>>(
       jobs, Tw<T>::twc(c), Tw<T>::q(c), Tw<T>::s2(c));
 }
@@ -277,11 +286,7 @@ int tc_passes(kfbim_ctx* c, const std::vector<Job>& list, cudaStream_t s, const 
       *bytes += (double)c->N3 * sizeof(float) * (j.acc ? 3 : 2);
     }
     const int grid = std::min(c->num_sms, n * TC_TILES_PER_JOB);
-    static bool configured = false;
-    if (!configured) {
-      CK(cudaFuncSetAttribute(k_tc_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
-      configured = true;
-    }
+    CK(raise_dynamic_smem(reinterpret_cast<const void*>(k_tc_pass), TC_SMEM));
     k_tc_pass<<<grid, TC_THREADS, TC_SMEM, s>>>(jobs, n, c->d_tc_mats + (size_t)(type - 1) * 2 * TC_N * TC_N,
                                                 c->d_s2f, c->d_tc_err);
     ++g_launches;

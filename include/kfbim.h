@@ -30,6 +30,10 @@
  *    The "primary" points (line most normal to Gamma) carry the density
  *    unknowns and the BIE equations; density vectors are ordered like the
  *    primary points.
+ *  - Devices: a context belongs to the CUDA device that was current at
+ *    kfbim_setup.  Every call runs there, whichever device the calling thread
+ *    has current, and gives the thread its device back; `stream` must belong
+ *    to the context's device.
  *  - Threads: calls on different contexts may run at the same time from
  *    different host threads, on one device or several (each context owns its
  *    workspace; the kernel shared-memory limits the library raises are kept

@@ -84,6 +84,7 @@ struct kfbim_ctx {
   double *hs_g = nullptr, *hs_phi = nullptr, *hs_fp = nullptr, *hs_fg = nullptr, *hs_u = nullptr,
          *hs_p = nullptr;
   bool device = false;        // false for kfbim_setup_host contexts
+  int dev_id = -1;            // CUDA device holding the context's memory, streams and graphs (-1: none)
   // CUDA graphs of kCgGraphIters CG iterations (index 0: FP64, 1: FP32)
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t cg_exec[2] = {nullptr, nullptr};
@@ -1132,16 +1133,50 @@ int fail(kfbim_ctx* c, int code, const std::string& msg) {
   return code;
 }
 
+// Makes a context's device current for the duration of a call and gives the
+// calling thread its own current device back afterwards: the context's
+// memory, streams and graphs belong to the device it was set up on.  A
+// negative device (host-only context) makes no CUDA call.
+class DeviceScope {
+ public:
+  explicit DeviceScope(int dev) {
+    if (dev < 0) return;
+    st_ = cudaGetDevice(&prev_);
+    if (st_ == cudaSuccess && prev_ != dev) {
+      st_ = cudaSetDevice(dev);
+      switched_ = st_ == cudaSuccess;
+    }
+  }
+  ~DeviceScope() {
+    if (switched_) cudaSetDevice(prev_);
+  }
+  DeviceScope(const DeviceScope&) = delete;
+  DeviceScope& operator=(const DeviceScope&) = delete;
+  cudaError_t status() const { return st_; }
+
+ private:
+  int prev_ = 0;
+  bool switched_ = false;
+  cudaError_t st_ = cudaSuccess;
+};
+
+// Runs one entry point on a device context: on its device, with every C++
+// exception turned into a status (none crosses the C ABI).
 template <typename F>
 int guarded(kfbim_ctx* c, F&& f) {
   if (!c) return KFBIM_E_INVALID;
   if (!c->device) return fail(c, KFBIM_E_INVALID, "host-only context");
+  const DeviceScope scope(c->dev_id);
+  if (scope.status() != cudaSuccess)
+    return fail(c, KFBIM_E_CUDA, std::string("selecting the context's device: ") + cudaGetErrorString(scope.status()));
   try {
     return f();
   } catch (const CudaError& e) {
     return fail(c, e.code, e.msg);
   } catch (const std::bad_alloc&) {
     return fail(c, KFBIM_E_OOM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return fail(c, KFBIM_E_INVALID, std::string("internal error: ") + e.what());
   }
 }
 
@@ -1726,13 +1761,18 @@ static int setup_common(const kfbim_geometry* geom, const kfbim_grid* grid, cons
   c->corr_nnz = (int64_t)c->host.corr_src.size();
   c->n_corr_rows = (int64_t)c->host.corr_row.size();
   if (device) {
+    const cudaError_t ge = cudaGetDevice(&c->dev_id);
+    if (ge != cudaSuccess) {
+      std::fprintf(stderr, "kfbim_setup: cudaGetDevice: %s\n", cudaGetErrorString(ge));
+      return KFBIM_E_CUDA;
+    }
     try {
       fill_tables(c.get());
       adjoint_tables(c.get());   // before the host fit and correction tables are released
     } catch (const CudaError& e) {
       std::fprintf(stderr, "kfbim_setup: %s\n", e.msg.c_str());
-      for (void* p : c->allocs) cudaFree(p);
-      if (c->pinned) cudaFreeHost(c->pinned);
+      // releases whatever was created so far (memory, pinned buffers, stream, graphs)
+      kfbim_destroy(c.release());
       return e.msg.find("out of memory") != std::string::npos ? KFBIM_E_OOM : KFBIM_E_CUDA;
     }
     c->device = true;
@@ -1771,6 +1811,9 @@ int kfbim_table_sizes(const kfbim_ctx* c, int64_t* fit_nnz, int64_t* corr_rows, 
 
 int kfbim_destroy(kfbim_ctx* c) {
   if (!c) return KFBIM_E_INVALID;
+  // a context whose setup failed part-way has device resources (dev_id >= 0)
+  // but device == false; a host-only context has dev_id < 0 and no CUDA state
+  const DeviceScope scope(c->dev_id);
   if (c->device) cudaDeviceSynchronize();
   for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
   for (auto& e : c->cg_exec)

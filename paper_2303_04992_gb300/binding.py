@@ -107,7 +107,8 @@ def poisson_noalloc(c, N, lo, hi, r, u):
     caller-owned float64 CUDA tensors of N^3 values; torch's current stream."""
     import torch
     lib = load_library()
-    st = lib.kfbim_poisson_noalloc(c, N, lo, hi, _ptr(r), _ptr(u),
+    n = max(int(N), 0) ** 3
+    st = lib.kfbim_poisson_noalloc(c, N, lo, hi, _ptr(r, n, "r"), _ptr(u, n, "u"),
                                    c_void_p(torch.cuda.current_stream().cuda_stream))
     if st != 0:
         raise KfbimError(st, "kfbim_poisson_noalloc failed (see stderr)")
@@ -135,21 +136,61 @@ def _geometry(desc):
     return g
 
 
-def _ptr(t):
-    return None if t is None else c_void_p(t.data_ptr())
+E_INVALID = -1
 
 
-def _np_ptr(a):
-    return None if a is None else a.ctypes.data_as(c_void_p)
+def _ptr(t, n=0, name="tensor", dtype="float64", device=None):
+    """Device pointer of torch tensor t, after checking that the library may
+    access n values of it: dtype, C-contiguous, at least n elements, a CUDA
+    tensor (on CUDA device `device` when given).  None stays None (nullable
+    arguments).  A bad argument raises KfbimError(E_INVALID) before any call."""
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise KfbimError(E_INVALID, "%s: expected a torch tensor, got %s" % (name, type(t).__name__))
+    if t.dtype != getattr(torch, dtype):
+        raise KfbimError(E_INVALID, "%s: dtype %s, expected torch.%s" % (name, t.dtype, dtype))
+    if not t.is_contiguous():
+        raise KfbimError(E_INVALID, "%s: not contiguous" % name)
+    if t.numel() < n:
+        raise KfbimError(E_INVALID, "%s: %d values, at least %d needed" % (name, t.numel(), n))
+    if not t.is_cuda:
+        raise KfbimError(E_INVALID, "%s: not a CUDA tensor" % name)
+    if device is not None and t.device.index != device:
+        raise KfbimError(E_INVALID, "%s: on cuda:%s, the solver is on cuda:%d" % (name, t.device.index, device))
+    return c_void_p(t.data_ptr())
+
+
+def _np_ptr(a, n=0, name="array", dtype=np.float64):
+    """Host pointer of numpy array a after the same checks (dtype,
+    C-contiguous, at least n elements); None stays None."""
+    if a is None:
+        return None
+    if not isinstance(a, np.ndarray):
+        raise KfbimError(E_INVALID, "%s: expected a numpy array, got %s" % (name, type(a).__name__))
+    if a.dtype != dtype:
+        raise KfbimError(E_INVALID, "%s: dtype %s, expected %s" % (name, a.dtype, np.dtype(dtype)))
+    if not a.flags.c_contiguous:
+        raise KfbimError(E_INVALID, "%s: not C-contiguous" % name)
+    if a.size < n:
+        raise KfbimError(E_INVALID, "%s: %d values, at least %d needed" % (name, a.size, n))
+    return a.ctypes.data_as(c_void_p)
 
 
 class Solver:
-    """One geometry + grid.  Device arguments are torch float64 CUDA tensors
-    (contiguous); work goes on torch's current CUDA stream."""
+    """One geometry + grid on the CUDA device current at construction.  Device
+    arguments are contiguous torch float64 CUDA tensors on that device with at
+    least as many values as include/kfbim.h gives for the call (checked before
+    the call); work goes on torch's current CUDA stream of that device."""
 
     def __init__(self, geom, grid, mu=1.0, precision=0, device=True, lam=None, **opts):
         """lam = None: Stokes; lam = Lame lambda: Navier (Lame) problem."""
         lib = load_library()
+        self._device = None
+        if device:
+            import torch
+            self._device = torch.cuda.current_device()
         o = Options()
         lib.kfbim_default_options(ctypes.byref(o))
         o.mu = mu
@@ -191,10 +232,12 @@ class Solver:
         if st != 0:
             raise KfbimError(st, self._lib.kfbim_last_error(self._ctx).decode())
 
-    @staticmethod
-    def _stream():
+    def _stream(self):
         import torch
-        return c_void_p(torch.cuda.current_stream().cuda_stream)
+        return c_void_p(torch.cuda.current_stream(self._device).cuda_stream)
+
+    def _d(self, t, n, name, dtype="float64"):
+        return _ptr(t, n, name, dtype, self._device)
 
     # ------------------------------------------------------------ host data
     def points(self):
@@ -203,13 +246,13 @@ class Solver:
         comp = np.zeros(n, np.int32)
         axis = np.zeros(n, np.int32)
         prim = np.zeros(n, np.int32)
-        self._check(self._lib.kfbim_points(self._ctx, _np_ptr(xyz), _np_ptr(comp), _np_ptr(axis),
-                                           _np_ptr(prim)))
+        self._check(self._lib.kfbim_points(self._ctx, _np_ptr(xyz, 3 * n, "xyz"), _np_ptr(comp, n, "comp", np.int32),
+                                           _np_ptr(axis, n, "axis", np.int32), _np_ptr(prim, n, "prim", np.int32)))
         return xyz, comp, axis, prim.astype(bool)
 
     def sides(self, c):
         s = np.zeros(self.N ** 3, np.uint8)
-        self._check(self._lib.kfbim_sides(self._ctx, c, _np_ptr(s)))
+        self._check(self._lib.kfbim_sides(self._ctx, c, _np_ptr(s, self.N ** 3, "side", np.uint8)))
         return s.reshape(self.N, self.N, self.N).astype(bool)
 
     def table_sizes(self):
@@ -220,22 +263,27 @@ class Solver:
 
     # ----------------------------------------------------------- device ops
     def apply(self, phi, out):
-        self._check(self._lib.kfbim_apply(self._ctx, _ptr(phi), _ptr(out), self._stream()))
+        n = self.n_primary
+        self._check(self._lib.kfbim_apply(self._ctx, self._d(phi, n, "phi"), self._d(out, n, "out"),
+                                          self._stream()))
         return out
 
     def solve(self, g, phi, fpts=None, fgrid=None, u=None, p=None):
+        n, npt, N3 = self.n_primary, self.n_points, self.N ** 3
+        args = (self._d(g, n, "g"), self._d(fpts, 3 * npt, "fpts"), self._d(fgrid, 3 * N3, "fgrid"),
+                self._d(phi, n, "phi"), self._d(u, 3 * N3, "u"), self._d(p, N3, "p"))
         st = Stats()
-        self._check(self._lib.kfbim_solve(self._ctx, _ptr(g), _ptr(fpts), _ptr(fgrid), _ptr(phi),
-                                          _ptr(u), _ptr(p), ctypes.byref(st), self._stream()))
+        self._check(self._lib.kfbim_solve(self._ctx, *args, ctypes.byref(st), self._stream()))
         self.last_stats = {k: getattr(st, k) for k, _ in Stats._fields_}
         return phi
 
     def solve_host(self, g, phi, fpts=None, fgrid=None, u=None, p=None):
         """Host (numpy float64) buffers; copies happen inside the library call."""
+        n, npt, N3 = self.n_primary, self.n_points, self.N ** 3
+        args = (_np_ptr(g, n, "g"), _np_ptr(fpts, 3 * npt, "fpts"), _np_ptr(fgrid, 3 * N3, "fgrid"),
+                _np_ptr(phi, n, "phi"), _np_ptr(u, 3 * N3, "u"), _np_ptr(p, N3, "p"))
         st = Stats()
-        self._check(self._lib.kfbim_solve_host(self._ctx, _np_ptr(g), _np_ptr(fpts), _np_ptr(fgrid),
-                                               _np_ptr(phi), _np_ptr(u), _np_ptr(p), ctypes.byref(st),
-                                               self._stream()))
+        self._check(self._lib.kfbim_solve_host(self._ctx, *args, ctypes.byref(st), self._stream()))
         self.last_stats = {k: getattr(st, k) for k, _ in Stats._fields_}
         return phi
 
@@ -243,45 +291,64 @@ class Solver:
         """B solves in one call: g, phi are (B, n_primary) device tensors, fpts
         (B, 3 n_points), fgrid (B, 3 N^3), u (B, 3 N^3), p (B, N^3); each
         contiguous.  last_stats becomes a list of B dicts."""
+        if getattr(g, "dim", lambda: 0)() < 1:
+            raise KfbimError(E_INVALID, "g: expected a (B, n_primary) tensor")
         B = int(g.shape[0])
-        st = (Stats * B)()
-        self._check(self._lib.kfbim_solve_batch(self._ctx, B, _ptr(g), _ptr(fpts), _ptr(fgrid), _ptr(phi),
-                                                _ptr(u), _ptr(p), st, self._stream()))
+        n, npt, N3 = B * self.n_primary, B * self.n_points, B * self.N ** 3
+        args = (self._d(g, n, "g"), self._d(fpts, 3 * npt, "fpts"), self._d(fgrid, 3 * N3, "fgrid"),
+                self._d(phi, n, "phi"), self._d(u, 3 * N3, "u"), self._d(p, N3, "p"))
+        st = (Stats * max(B, 1))()
+        self._check(self._lib.kfbim_solve_batch(self._ctx, B, *args, st, self._stream()))
         self.last_stats = [{k: getattr(st[b], k) for k, _ in Stats._fields_} for b in range(B)]
         return phi
 
     def apply_adjoint(self, lam, out):
-        self._check(self._lib.kfbim_apply_adjoint(self._ctx, _ptr(lam), _ptr(out), self._stream()))
+        n = self.n_primary
+        self._check(self._lib.kfbim_apply_adjoint(self._ctx, self._d(lam, n, "lam"), self._d(out, n, "out"),
+                                                  self._stream()))
         return out
 
     def solve_adjoint(self, ubar, gbar):
         """gbar = dL/dg for ubar = dL/du (3 N^3 face-grid values)."""
         st = Stats()
-        self._check(self._lib.kfbim_solve_adjoint(self._ctx, _ptr(ubar), _ptr(gbar), ctypes.byref(st),
+        self._check(self._lib.kfbim_solve_adjoint(self._ctx, self._d(ubar, 3 * self.N ** 3, "ubar"),
+                                                  self._d(gbar, self.n_primary, "gbar"), ctypes.byref(st),
                                                   self._stream()))
         self.last_stats = {k: getattr(st, k) for k, _ in Stats._fields_}
         return gbar
 
     def jumps(self, phi, J, fpts=None):
-        self._check(self._lib.kfbim_jumps(self._ctx, _ptr(phi), _ptr(fpts), _ptr(J), self._stream()))
+        npt = self.n_points
+        self._check(self._lib.kfbim_jumps(self._ctx, self._d(phi, self.n_primary, "phi"),
+                                          self._d(fpts, 3 * npt, "fpts"), self._d(J, 12 * npt, "J"),
+                                          self._stream()))
         return J
 
     def interface(self, phi, u, p, fpts=None, fgrid=None):
-        self._check(self._lib.kfbim_interface(self._ctx, _ptr(phi), _ptr(fpts), _ptr(fgrid), _ptr(u),
-                                              _ptr(p), self._stream()))
+        N3 = self.N ** 3
+        self._check(self._lib.kfbim_interface(self._ctx, self._d(phi, self.n_primary, "phi"),
+                                              self._d(fpts, 3 * self.n_points, "fpts"),
+                                              self._d(fgrid, 3 * N3, "fgrid"), self._d(u, 3 * N3, "u"),
+                                              self._d(p, N3, "p"), self._stream()))
         return u, p
 
     def pressure_trace(self, p, J, out):
-        self._check(self._lib.kfbim_pressure_trace(self._ctx, _ptr(p), _ptr(J), _ptr(out), self._stream()))
+        npt = self.n_points
+        self._check(self._lib.kfbim_pressure_trace(self._ctx, self._d(p, self.N ** 3, "p"), self._d(J, 12 * npt, "J"),
+                                                   self._d(out, npt, "out"), self._stream()))
         return out
 
     def trace(self, u, J, out):
-        self._check(self._lib.kfbim_trace(self._ctx, _ptr(u), _ptr(J), _ptr(out), self._stream()))
+        self._check(self._lib.kfbim_trace(self._ctx, self._d(u, 3 * self.N ** 3, "u"),
+                                          self._d(J, 12 * self.n_points, "J"),
+                                          self._d(out, self.n_primary, "out"), self._stream()))
         return out
 
     def transform_f32(self, xform, axis, inp, out, backend, wmode=0, wc=0):
-        self._check(self._lib.kfbim_transform_f32(self._ctx, xform, axis, wmode, wc, _ptr(inp), _ptr(out),
-                                                  backend, self._stream()))
+        N3 = self.N ** 3
+        self._check(self._lib.kfbim_transform_f32(self._ctx, xform, axis, wmode, wc,
+                                                  self._d(inp, N3, "inp", "float32"),
+                                                  self._d(out, N3, "out", "float32"), backend, self._stream()))
         return out
 
     def transforms_info(self):
@@ -292,7 +359,8 @@ class Solver:
         return {"plain": pl.value, "fused": fu.value, "tune_ms": [round(float(x), 4) for x in ms]}
 
     def poisson(self, c, r, u):
-        self._check(self._lib.kfbim_poisson(self._ctx, c, _ptr(r), _ptr(u), self._stream()))
+        N3 = self.N ** 3
+        self._check(self._lib.kfbim_poisson(self._ctx, c, self._d(r, N3, "r"), self._d(u, N3, "u"), self._stream()))
         return u
 
     def profile(self, enable):
@@ -307,5 +375,7 @@ class Solver:
                 "fp32": (v[3].value, v[4].value, v[5].value)}
 
     def schur_apply(self, d, q):
-        self._check(self._lib.kfbim_schur_apply(self._ctx, _ptr(d), _ptr(q), self._stream()))
+        N3 = self.N ** 3
+        self._check(self._lib.kfbim_schur_apply(self._ctx, self._d(d, N3, "d"), self._d(q, N3, "q"),
+                                                self._stream()))
         return q

@@ -65,8 +65,17 @@ def parse():
     ap.add_argument("--batch", type=int, default=16,
                     help="instances of the batched leg (kfbim_solve_batch); 0 skips it")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
-    ap.add_argument("--interface-solves", type=int, default=18, help=argparse.SUPPRESS)
+    ap.add_argument("--interface-solves", type=int, default=None,
+                    help="interface solves per solve for the reference arm's scaling "
+                         "(default: the workload's count in INTERFACE_SOLVES)")
     return ap.parse_args()
+
+
+# Interface solves of one solve of each workload (GMRES iterations plus the
+# right-hand-side and final-field solves), as the GPU solves report them in
+# their stats (FP64 and MIXED alike): the reference arm times one oracle matvec
+# and scales it by this count.
+INTERFACE_SOLVES = {"sphere32": 18, "star128": 61}
 
 
 # ------------------------------------------------------------ oracle sample
@@ -198,6 +207,27 @@ def inputs(solver, geom, grid, navier=False):
                               lo + (idx + off[0]) * h, indexing="ij")      # [k, j, i]
         fg.append(frc(np.stack([X, Y, Z], -1))[..., c - 1].ravel())
     return g, fpts, np.concatenate(fg)
+
+
+def host_cpu():
+    """The host the oracle baseline runs on: architecture, logical CPUs and,
+    where /proc/cpuinfo names it, the CPU model (x86 "model name", Arm
+    implementer/part codes)."""
+    import platform
+    info = {"machine": platform.machine(), "logical_cpus": os.cpu_count()}
+    try:
+        with open("/proc/cpuinfo") as f:
+            fields = {}
+            for line in f:
+                k, _, v = line.partition(":")
+                fields.setdefault(k.strip(), v.strip())
+        if fields.get("model name"):
+            info["model"] = fields["model name"]
+        elif fields.get("CPU part"):
+            info["model"] = "implementer %s part %s" % (fields.get("CPU implementer", "?"), fields["CPU part"])
+    except OSError:
+        pass
+    return info
 
 
 def job_throughput(total_ms, steps, dist=None, device="cpu"):
@@ -453,7 +483,8 @@ def main_kfbim(args):
         cpu = {"value": round(o["value"], 6), "unit": "solves/s", "cores": 1, "kind": "oracle",
                "sample": "one oracle matvec (interface solve + trace) on %s, single thread, "
                          "%.1f s, scaled by the %d interface solves of one GPU solve"
-                         % (args.workload, o["matvec_s"], per_solve)}
+                         % (args.workload, o["matvec_s"], per_solve),
+               "host": host_cpu()}
 
     if rank == 0:
         st = stats[-1]
@@ -489,7 +520,11 @@ def main_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    per_solve = args.interface_solves
+    per_solve = args.interface_solves or INTERFACE_SOLVES.get(args.workload)
+    if per_solve is None:
+        print(json.dumps({"impl": "reference", "unavailable": "no interface-solve count for workload %s; "
+                          "pass --interface-solves" % args.workload}), flush=True)
+        return
     o = run_oracle_subprocess(args.workload, args.warmup + args.steps, per_solve)
     times = o["times"][args.warmup:]
     t_mv = sum(times) / len(times)
@@ -501,7 +536,8 @@ def main_reference(args):
             "config": {"workload": args.workload, "description": WORKLOAD_DESC},
             "cpu_baseline": {"kind": "oracle", "cores": 1, "value": round(value, 6),
                              "sample": "each step: one oracle matvec on %s (single thread), scaled "
-                                       "by %d interface solves per solve" % (args.workload, per_solve)},
+                                       "by %d interface solves per solve" % (args.workload, per_solve),
+                             "host": host_cpu()},
             "e2e": {"value": round(value, 6), "unit": "solves/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -510,7 +546,8 @@ def main_reference(args):
 if __name__ == "__main__":
     a = parse()
     if a.oracle_sample:
-        print(json.dumps(oracle_sample(a.workload, a.steps, a.interface_solves)))
+        per = a.interface_solves or INTERFACE_SOLVES.get(a.workload, 1)
+        print(json.dumps(oracle_sample(a.workload, a.steps, per)))
     elif a.impl == "reference":
         main_reference(a)
     else:

@@ -68,3 +68,35 @@ def test_reference_arm_non_zero_rank_does_no_work(monkeypatch):
     with redirect_stdout(buf):
         bench.main_reference(ns)
     assert buf.getvalue() == ""
+
+
+def test_host_cpu_description_is_json():
+    sys.path.insert(0, ROOT)
+    import bench
+    h = bench.host_cpu()
+    assert h["logical_cpus"] == os.cpu_count() and h["machine"]
+    json.dumps(h)
+
+
+def test_reference_arm_scales_by_the_workload_interface_solves(monkeypatch):
+    """Without --interface-solves the reference arm scales one oracle matvec by
+    the workload's own count (star128: 59 GMRES iterations + 2 solves)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setattr(bench, "run_oracle_subprocess",
+                        lambda workload, reps, per_solve: {"times": [2.0] * reps})
+    ns = type("A", (), {"interface_solves": None, "workload": "star128", "warmup": 1, "steps": 2,
+                        "gpus": 1})()
+    buf = io.StringIO()
+    with redirect_stdout(buf):
+        bench.main_reference(ns)
+    line = json.loads(buf.getvalue())
+    assert bench.INTERFACE_SOLVES["star128"] == 61
+    assert line["value"] == pytest.approx(1.0 / (2.0 * 61), rel=1e-4)
+    assert "61 interface solves" in line["cpu_baseline"]["sample"]
+    ns.workload = "star64"
+    buf = io.StringIO()
+    with redirect_stdout(buf):
+        bench.main_reference(ns)
+    assert "unavailable" in json.loads(buf.getvalue())

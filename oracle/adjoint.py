@@ -13,6 +13,7 @@ Small grids only (one interface solve per density unknown).
 import numpy as np
 
 
+# No passage: the paper solves forward problems only; A and U of the solve of Alg. 1, column by column.
 def dense_maps(setup):
     """(A, U): A (n, n) with columns A e_j; U (3 N^3, n) with columns the
     interface-solve velocity of e_j, component-blocked in C order [k, j, i]."""
@@ -30,6 +31,7 @@ def dense_maps(setup):
     return A, U
 
 
+# No passage: the gradient of a loss through the solve of Alg. 1 by its definition.
 def gradient_g(A, U, ubar):
     """dL/dg = A^-T U^T ubar for ubar = dL/du (3 N^3)."""
     return np.linalg.solve(A.T, U.T @ ubar)

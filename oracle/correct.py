@@ -18,10 +18,12 @@ corrections) and rows of g at cells (continuity corrections).
 import numpy as np
 
 
+# Sec. 4.3 items 1-4: the side sign chi_Q of a correction.
 def _chi(side):
     return np.where(side, 1.0, -1.0)
 
 
+# Sec. 4.3 items 1-4: the corrected right-hand sides of Eq. MAC.
 def corrections(grid, cp, S, J, mu):
     """Return (Cf (3 face fields), Cg (cell field)) from jump values J (n, 12)."""
     N, h = grid.N, grid.h

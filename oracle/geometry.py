@@ -9,6 +9,7 @@ the graph y + s tau_1 + t tau_2 - 1/2 (s,t) K (s,t)^T n + O(3).
 import numpy as np
 
 
+# Sphere |x - c| = R, the domain of Examples 5.1 and 5.4; Omega = {F < 0} (Sec. 2).
 def _sphere(geom, X):
     c = np.asarray(geom["center"])
     d = X - c
@@ -20,6 +21,7 @@ def _sphere(geom, X):
     return F, G, H
 
 
+# Ellipsoid in a rotated body frame, the domain of Examples 5.2 and 5.5 (Sec. 2 for F).
 def _ellipsoid(geom, X):
     c = np.asarray(geom["center"])
     Q = np.asarray(geom["rotation"]).reshape(3, 3)
@@ -33,6 +35,7 @@ def _ellipsoid(geom, X):
     return F, G, H
 
 
+# Star-shaped surface of the benchmark configuration (not one of the paper's examples); F as in Sec. 2.
 def _star(geom, X):
     """F = rho - R(theta, phi), theta = polar angle from +z, phi = azimuth.
 
@@ -103,16 +106,20 @@ def _torus(geom, X):
 _KINDS = {"sphere": _sphere, "ellipsoid": _ellipsoid, "star": _star, "torus": _torus}
 
 
+# Sec. 2: Gamma is the zero set of F and Omega = {F < 0}; Alg. 1 step 1.
 def level_set(geom, X):
     """Return (F, grad F, Hess F) at points X of shape (..., 3)."""
     X = np.asarray(X, dtype=np.float64)
     return _KINDS[geom["kind"]](geom, X)
 
 
+# Sec. 2: the value of F alone.
 def level_value(geom, X):
     return level_set(geom, X)[0]
 
 
+# Alg. 1 step 1 (tangential and normal unit directions); the curvature
+# enters the second-order jumps of Sec. 4.3.
 def frames(geom, X):
     """Outward normal n, tangents tau_1, tau_2 and curvature tensor K (2x2)
     at surface points X (..., 3).

@@ -25,6 +25,7 @@ import numpy as np
 from . import geometry
 
 
+# Sec. 4.2: the cell grid T_h^0 and the staggered face grids T_h^1..T_h^3 of the box B.
 class Grid:
     def __init__(self, N, lo, hi):
         self.N = int(N)
@@ -32,6 +33,7 @@ class Grid:
         self.hi = float(hi)
         self.h = (self.hi - self.lo) / self.N
 
+    # Sec. 4.2: node offsets of the grid sets.
     def offsets(self, c):
         """Per-axis offset (in units of h) of grid c's nodes from lo."""
         off = np.array([0.5, 0.5, 0.5])
@@ -39,16 +41,19 @@ class Grid:
             off[c - 1] = 0.0
         return off
 
+    # Sec. 4.2: node coordinates of the grid sets.
     def node_xyz(self, c, idx):
         """Coordinates of grid-c nodes; idx (..., 3) integer (i, j, k)."""
         return self.lo + (np.asarray(idx, dtype=np.float64) + self.offsets(c)) * self.h
 
+    # Sec. 4.2: the index set of a grid.
     def all_idx(self):
         """(N, N, N, 3) array of (i, j, k) in [k, j, i] layout."""
         N = self.N
         k, j, i = np.meshgrid(np.arange(N), np.arange(N), np.arange(N), indexing="ij")
         return np.stack([i, j, k], axis=-1)
 
+    # Sec. 4.2: the unknowns of u^(c) (wall faces excluded, IUS-5).
     def unknown_mask(self, c):
         """True where grid c carries an unknown ([k, j, i] layout)."""
         m = np.ones((self.N,) * 3, dtype=bool)
@@ -59,12 +64,14 @@ class Grid:
         return m
 
 
+# Alg. 1 step 1: the side of Gamma of every node of a grid.
 def sides(grid, geom, c):
     """Boolean [k, j, i] array: True where the grid-c node is in Omega."""
     X = grid.node_xyz(c, grid.all_idx())
     return geometry.level_value(geom, X) <= 0.0
 
 
+# Sec. 3: control points are the intersections of Gamma with the grid lines.
 class ControlPoints:
     """Intersections of Gamma with the grid lines of u^(1), u^(2), u^(3)."""
 
@@ -76,11 +83,13 @@ class ControlPoints:
         self.xyz = xyz        # (n, 3)
         self.n = len(comp)
 
+    # Sec. 3: numbering of the control-point sets X_1, X_2, X_3.
     def offsets(self):
         """Start offsets of X_1, X_2, X_3 in the concatenated numbering."""
         return np.array([np.sum(self.comp < c) for c in (1, 2, 3, 4)])
 
 
+# Alg. 1 step 1: intersection of Gamma with one grid-line segment.
 def _bisect(geom, x0, dirv, h, side0):
     """Root of F on the segment x0 + t h dirv, t in [0, 1], by 64 bisection
     steps; side0 is the side (F <= 0) of the t = 0 end."""
@@ -95,6 +104,7 @@ def _bisect(geom, x0, dirv, h, side0):
     return lo
 
 
+# Sec. 3 and Alg. 1 step 1: all control points, in canonical order.
 def control_points(grid, geom):
     """All control points in canonical order, plus per-grid side arrays."""
     N, h = grid.N, grid.h
@@ -136,6 +146,7 @@ def control_points(grid, geom):
     return ControlPoints(comp, axis, idx, theta, xyz), S
 
 
+# Ordering helper for the control points of Sec. 3 (no arithmetic of the method).
 def fine_keys(cp):
     """Integer position of each point's segment midpoint in units of h/2."""
     key = 2 * cp.idx + 1
@@ -144,6 +155,8 @@ def fine_keys(cp):
     return key
 
 
+# Reading of the resolution the method assumes (Sec. 4.3 needs single
+# crossings per segment and the fit neighbourhood inside the box).
 def check_geometry(grid, geom, cp, S):
     """Reject geometries the discretisation does not resolve (KFBIM_E_GEOMETRY):
     Gamma within 3h of the box wall, or a combined u^(a)/cell line whose

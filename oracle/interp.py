@@ -18,6 +18,7 @@ For nodes z_i in Omega^c the jump Taylor polynomial J_i is added (Sec. 4.4):
 import numpy as np
 
 
+# Sec. 4.4: the ten interpolation nodes of a control point.
 def stencil(cp):
     """Node indices (n, 10, 3) of each point's stencil on its own grid."""
     n = cp.n
@@ -37,6 +38,7 @@ def stencil(cp):
     return base[:, None, :] + np.stack(offs, axis=1)
 
 
+# Sec. 4.4: the quadratic Taylor basis of Eqs. Interpolation+/-.
 def _taylor_rows(d):
     """Rows (1, x, y, z, x^2/2, y^2/2, z^2/2, yz, xz, xy) of offsets d (..., 3)."""
     x, y, z = d[..., 0], d[..., 1], d[..., 2]
@@ -44,6 +46,7 @@ def _taylor_rows(d):
                      y * z, x * z, x * y], axis=-1)
 
 
+# Sec. 4.4, Eqs. Interpolation+/-: the jump-corrected quadratic interpolation of u^+.
 def trace(grid, cp, S, fields, J):
     """u^+ at every control point: solve the 10x10 Taylor system per point.
     fields: the three face fields; J (n, 12) jump values (jumps.py layout)."""

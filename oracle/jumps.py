@@ -47,6 +47,7 @@ FIT_SIGMA2 = 1.0     # Gaussian weight exp(-|z - y|^2 / (FIT_SIGMA2 h^2))
 MIN_NEIGHBOURS = 12
 
 
+# Sec. 4.3: the density's surface derivatives need neighbouring control points (our fit, parity unpinned).
 def neighbour_lists(cp, primary):
     """For each point y and component c' the indices of the primary points of
     X_c' within the fit radius (exact integer test on fine keys)."""
@@ -66,6 +67,7 @@ def neighbour_lists(cp, primary):
     return out
 
 
+# Sec. 4.3: surface derivatives of the density by a least-squares fit (our reading, parity unpinned).
 def surface_derivatives(cp, frames, nbrs, phi, h):
     """Fitted (value, d_1, d_2, d_11, d_12, d_22) of each phi^(c') at every
     point: array (n, 3, 6).  phi holds values at all points; only the
@@ -103,10 +105,12 @@ def surface_derivatives(cp, frames, nbrs, phi, h):
 SYM = [(0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1)]   # H entry order 11,22,33,23,13,12
 
 
+# Index helper for the Hessian unknowns of Sec. 4.3.
 def _hidx(k, l):
     return SYM.index((min(k, l), max(k, l)))
 
 
+# Sec. 4.1 remark, IUS-2..IUS-4: the first-order jumps.
 def first_order(n, T, dphi, mu, lam=None):
     """A (n,3,3) and q (n,) from the tangential derivatives dphi (n,3,2).
     lam = None: Stokes; else the Navier (Lame) relations."""
@@ -120,6 +124,7 @@ def first_order(n, T, dphi, mu, lam=None):
     return A, q
 
 
+# Sec. 4.3: second-order jumps from IUS-1..IUS-4 and their surface derivatives.
 def second_order_system(n, T, K, mu, lam=None):
     """Matrix L (n, 21, 21) of equations (i)-(iv) acting on
     x = (H^(1) (6), H^(2) (6), H^(3) (6), s (3)); lam = None for Stokes."""
@@ -155,6 +160,7 @@ def second_order_system(n, T, K, mu, lam=None):
     return L
 
 
+# Sec. 4.3: right-hand side of the second-order jump system.
 def second_order_rhs(n, T, K, A, q, d2phi, fy, mu, lam=None):
     """Right-hand side (n, 21) of (i)-(iv); d2phi (n, 3, 3) = (d_11, d_12, d_22)
     per component, fy (n, 3) = [f~] at the point; lam = None for Stokes."""
@@ -193,6 +199,7 @@ def primary_points(cp, frames):
     return na >= np.max(np.abs(n), axis=1) - 1e-12
 
 
+# Sec. 4.3: per-point data of the jump evaluation.
 class JumpData:
     """Per-point geometry and neighbour lists used by the jump evaluation."""
 

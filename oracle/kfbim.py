@@ -28,11 +28,13 @@ class Setup:
         self.jd = jumpmod.JumpData(self.grid, geom, self.cp)
         self.cg_iters = []
 
+    # Sec. 3: one density unknown per primary control point.
     @property
     def n(self):
         """Number of density unknowns (primary control points)."""
         return int(np.sum(self.jd.primary))
 
+    # Sec. 3: the primary control points.
     @property
     def primary(self):
         return self.jd.primary
@@ -55,15 +57,18 @@ class Setup:
         self.cg_iters.append(it)
         return u, p, J
 
+    # Sec. 4.4: u^+ at the primary control points.
     def trace(self, u, J):
         """u^+ at the primary control points from face fields u and jumps J."""
         return interp.trace(self.grid, self.cp, self.S, u, J)[self.primary]
 
+    # Prop. DBI and Eq. BIE-S: the GMRES matvec.
     def apply(self, phi):
         """(1/2 I - M_v) phi at the primary control points."""
         u, _, J = self.interface(phi, np.zeros((self.cp.n, 3)), None)
         return self.trace(u, J)
 
+    # Prop. FBI: the volume integral on Gamma.
     def volume_trace(self, fy, f_faces):
         """(G_v f) on Gamma at the primary control points."""
         u, _, J = self.interface(np.zeros(self.n), fy, f_faces)

@@ -21,10 +21,12 @@ import numpy as np
 import scipy.fft as sfft
 
 
+# Array axis of a grid axis (layout helper for Sec. 4.2).
 def _ax(a):
     return 2 - a
 
 
+# Sec. 4.2 and IUS-5: u = 0 on the wall faces.
 def zero_walls(u, c):
     sl = [slice(None)] * 3
     sl[_ax(c - 1)] = 0
@@ -33,6 +35,7 @@ def zero_walls(u, c):
     return u
 
 
+# Sec. 4.2, Eq. MAC: the difference operator delta^- on p (G).
 def grad(p, h):
     """G p: three face fields; face 0 (wall) left at 0."""
     out = []
@@ -50,6 +53,7 @@ def grad(p, h):
     return out
 
 
+# Sec. 4.2, Eq. MAC: the difference operator delta^+ on u (D = -G^T).
 def div(u, h):
     """D u at cells: sum_c (u^(c)_{m+1} - u^(c)_m) / h with wall faces 0."""
     N = u[0].shape[0]
@@ -68,6 +72,7 @@ def div(u, h):
     return out
 
 
+# Sec. 4.2, Eq. MAC: Delta_h with the ghost layers of T_h^1..T_h^3.
 def lap(uc, c, h):
     """Delta_h u^(c) on the unknown nodes (wall face entries returned as 0)."""
     u = zero_walls(uc, c)
@@ -89,6 +94,7 @@ def lap(uc, c, h):
     return zero_walls(out, c)
 
 
+# Sec. 4.2 item iii: the eigenvalues of the FFT (DST) solver.
 def _eig1(n_modes, N, first):
     m = np.arange(first, first + n_modes)
     return 4.0 * np.sin(np.pi * m / (2.0 * N)) ** 2
@@ -144,6 +150,7 @@ def schur_rhs(f, g, mu, h):
     return g - div(w, h) / mu
 
 
+# Sec. 4.2 items i-iii: CG on the Schur complement.
 def cg(apply, b, tol=1e-14, maxit=2000):
     """Unpreconditioned conjugate gradients from x = 0 (the paper uses no
     preconditioner).  Stops at ||r|| <= tol ||b||."""
@@ -168,6 +175,7 @@ def cg(apply, b, tol=1e-14, maxit=2000):
     return x, it
 
 
+# Sec. 4.2, Eqs. linearS and linearS1: the MAC system through its Schur complement.
 def interface_solve(f, g, mu, h, tol=1e-14, cpen=None):
     """Solve the (corrected) MAC system [-mu Lap, G; D, 0][u; p] = [f; g]
     through the augmented system with lambda_h (gamma = 1, alpha = mu N^3):

@@ -82,7 +82,8 @@ k_jumps(const double* __restrict__ phi, const double* __restrict__ fpts, int64_t
 }
 
 // ------------------------------------------------------------ RHS assembly
-// f~ on the face grids (f in Omega, 0 outside and on wall faces) and g = 0.
+// f~ on the face grids (f in Omega, 0 outside and on wall faces) and g = 0:
+// the extended source of the volume integral (Prop. FBI, Alg. 1 step 2).
 __global__ void k_rhs_fill(const double* __restrict__ fgrid, const uint8_t* __restrict__ side1,
                            const uint8_t* __restrict__ side2, const uint8_t* __restrict__ side3,
                            int lg, double* __restrict__ rhs) {
@@ -103,7 +104,8 @@ __global__ void k_rhs_fill(const double* __restrict__ fgrid, const uint8_t* __re
   }
 }
 
-// Correction rows: rhs[row] += sum coef * J[src] (CSR keyed by target, no atomics).
+// Correction rows (Sec. 4.3 items 1-4): rhs[row] += sum coef * J[src] (CSR
+// keyed by target, no atomics).
 __global__ void k_corrections(const int64_t* __restrict__ row, const int64_t* __restrict__ ptr,
                               const int64_t* __restrict__ src, const double* __restrict__ coef,
                               int64_t nrows, const double* __restrict__ J, double* __restrict__ rhs) {
@@ -116,6 +118,8 @@ __global__ void k_corrections(const int64_t* __restrict__ row, const int64_t* __
 }
 
 // ------------------------------------------------------------------ trace
+// u^+ at the primary points (Sec. 4.4, Eqs. Interpolation+/-): ten-node
+// quadratic interpolation with the jump Taylor terms of the Omega^c nodes.
 __global__ void k_trace(const double* __restrict__ u, const double* __restrict__ J, int64_t n_all,
                         int64_t n_prim, const int64_t* __restrict__ prim_of, int N,
                         const int32_t* __restrict__ tcomp, const int32_t* __restrict__ tnode,
@@ -249,6 +253,7 @@ __global__ void k_mac_residual(const double* __restrict__ f, const double* __res
 }
 
 // ------------------------------------------------------------ reductions
+// Dot products of the Schur CG (Sec. 4.2) and of GMRES (Alg. 1 step 3).
 template <typename Ta>
 __device__ __forceinline__ double block_sum(double v, double* sh) {
 #pragma unroll
@@ -289,6 +294,7 @@ __global__ void k_sum_partials(const double* __restrict__ partial, int nb, doubl
 }
 
 // ----------------------------------------------------------------- CG
+// Unpreconditioned CG on the Schur complement (Sec. 4.2, Eq. linearS1).
 // Device scalars of one CG run on (S + 1 1^T rank1) x = b.  Every reduction
 // is finished by the last block to arrive (fixed-order sum of the block
 // partials), which also updates the scalars, so one CG iteration is the
@@ -530,6 +536,8 @@ __global__ void k_cg_init(const T* __restrict__ b, int64_t n, CGScalars* s, doub
 }
 
 // --------------------------------------------------------- vector helpers
+// Streaming steps of the Schur solve (Sec. 4.2 items i-iii: right-hand side,
+// velocity recovery, pressure gauge) and of the FP64 refinement.
 // y += a x
 __global__ void k_axpy(const double* __restrict__ x, double a, double* __restrict__ y, int64_t n) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
@@ -577,6 +585,7 @@ __global__ void k_shift(double* __restrict__ b, const double* __restrict__ shift
 }
 
 // -------------------------------------------------------------- GMRES
+// Classical Gram-Schmidt twice for the Arnoldi step of GMRES (Alg. 1 step 3).
 // partial[j * nb + b] = sum_e V[j][e] w[e]
 __global__ void k_multidot_partial(const double* __restrict__ V, int64_t ld, const double* __restrict__ w,
                                    int64_t n, double* __restrict__ partial) {
@@ -615,6 +624,8 @@ __global__ void k_scale_copy(const double* __restrict__ a, double sc_host, const
 namespace kfbim {
 
 // ------------------------------------------------------------- adjoint
+// Not in the paper (it solves forward problems only): the transpose of the
+// matvec of Prop. DBI, for gradients with respect to the boundary data.
 // Transposes of the linear maps phi -> J (jumps), J -> rhs (corrections) and
 // (u, J) -> trace, each a gather over a transposed CSR built once on the
 // host (fixed summation order, no atomics).

@@ -65,7 +65,18 @@ typedef enum {
   KFBIM_E_OOM = -6        /* device or host allocation failed */
 } kfbim_status;
 
-typedef enum { KFBIM_SPHERE = 0, KFBIM_ELLIPSOID = 1, KFBIM_STAR = 2, KFBIM_TORUS = 3 } kfbim_geometry_kind;
+typedef enum {
+  KFBIM_SPHERE = 0,
+  KFBIM_ELLIPSOID = 1,
+  KFBIM_STAR = 2,
+  KFBIM_TORUS = 3,
+  KFBIM_CALLBACK = 4
+} kfbim_geometry_kind;
+
+/* CALLBACK level set: F(x, user) returns F at x; derivs(x, g, H, user) writes
+ * the gradient g[3] and the Hessian H[9] (row-major) at x. */
+typedef double (*kfbim_level_fn)(const double x[3], void* user);
+typedef void (*kfbim_level_derivs_fn)(const double x[3], double g[3], double H[9], void* user);
 
 /* Analytic interface, Omega = {F <= 0}.
  *   SPHERE:    params[0] = radius.
@@ -75,12 +86,22 @@ typedef enum { KFBIM_SPHERE = 0, KFBIM_ELLIPSOID = 1, KFBIM_STAR = 2, KFBIM_TORU
  *              cos(params[3] phi), theta polar angle from +z, phi azimuth.
  *   TORUS:     (params[1] - sqrt(x^2 + y^2))^2 + z^2 = params[0]^2 about the
  *              z axis through center: tube radius params[0] < axis distance
- *              params[1] (Example 5.3). */
+ *              params[1] (Example 5.3).
+ *   CALLBACK:  any level set supplied by the caller through F and derivs (both
+ *              non-null; center, rot and params are ignored).  They are called
+ *              only from the thread running kfbim_setup / kfbim_setup_host,
+ *              during that call, and must return finite values; the gradient
+ *              must not vanish on Gamma (a control point where it does, or
+ *              where it is not finite, gives E_GEOMETRY).  The tables are built
+ *              once, so the device path never calls them. */
 typedef struct {
   int kind;
   double center[3];
   double rot[9];
   double params[8];
+  kfbim_level_fn F;              /* CALLBACK only, else ignored */
+  kfbim_level_derivs_fn derivs;  /* CALLBACK only, else ignored */
+  void* user;                    /* CALLBACK only: passed to F and derivs */
 } kfbim_geometry;
 
 typedef struct {

@@ -14,6 +14,8 @@ Workloads (all in the bounding box [-1, 1]^3, viscosity 1):
 Boundary data come from the divergence-free manufactured field
 u = (sin x cos y cos z, -cos x sin y cos z, 0), p = sin(x + y + z).
 """
+import math
+
 import numpy as np
 
 BOX = (-1.0, 1.0)
@@ -27,6 +29,56 @@ def star(r0=0.5, eps=0.1, m=3, n=4, center=(0.0, 0.0, 0.0)):
     """Star surface r(theta, phi) = r0 + eps sin(m theta) cos(n phi)."""
     return {"kind": "star", "center": [float(c) for c in center], "r0": float(r0),
             "eps": float(eps), "m": int(m), "n": int(n)}
+
+
+def callback_sphere(radius=0.5, center=(0.0, 0.0, 0.0)):
+    """The sphere as a caller-supplied level set (CALLBACK geometry):
+    F = |x - c| - R with the arithmetic, in the same order, of the built-in
+    sphere, so that both give identical setups."""
+    cx, cy, cz = (float(v) for v in center)
+    R = float(radius)
+
+    def F(x):
+        d0, d1, d2 = x[0] - cx, x[1] - cy, x[2] - cz
+        return math.sqrt(d0 * d0 + d1 * d1 + d2 * d2) - R
+
+    def derivs(x):
+        d = (x[0] - cx, x[1] - cy, x[2] - cz)
+        r = math.sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2])
+        e = [di / r for di in d]
+        return e, [[((i == j) - e[i] * e[j]) / r for j in range(3)] for i in range(3)]
+
+    return {"kind": "callback", "F": F, "derivs": derivs}
+
+
+def peanut(a=0.3, b=0.38, center=(0.03, -0.02, 0.05)):
+    """A non-convex CALLBACK geometry: the Cassini surface of revolution about
+    the x axis, F = P Q - b^4 with P = |x - c - a e_x|^2 and
+    Q = |x - c + a e_x|^2 (one component with a waist for a < b < a sqrt 2).
+    grad F = Q grad P + P grad Q, Hess F = grad P grad Q^T + grad Q grad P^T
+    + 2 (P + Q) I."""
+    cx, cy, cz = (float(v) for v in center)
+    a, b4 = float(a), float(b) ** 4
+
+    def parts(x):
+        X, Y, Z = x[0] - cx, x[1] - cy, x[2] - cz
+        rho2 = Y * Y + Z * Z
+        P = (X - a) ** 2 + rho2
+        Q = (X + a) ** 2 + rho2
+        return P, Q, (2 * (X - a), 2 * Y, 2 * Z), (2 * (X + a), 2 * Y, 2 * Z)
+
+    def F(x):
+        P, Q, _, _ = parts(x)
+        return P * Q - b4
+
+    def derivs(x):
+        P, Q, gP, gQ = parts(x)
+        g = [Q * gP[i] + P * gQ[i] for i in range(3)]
+        H = [[gP[i] * gQ[j] + gQ[i] * gP[j] + (2 * (P + Q) if i == j else 0.0) for j in range(3)]
+             for i in range(3)]
+        return g, H
+
+    return {"kind": "callback", "F": F, "derivs": derivs}
 
 
 def torus(a=0.35, c=0.7, center=(0.0, 0.0, 0.0)):

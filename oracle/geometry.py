@@ -1,4 +1,6 @@
-"""Analytic level sets F (Omega = {F <= 0}), gradients and Hessians, and the
+"""Analytic level sets F (Omega = {F <= 0}), or a caller-supplied one (kind
+"callback": F and its derivatives as Python functions of a point), gradients
+and Hessians, and the
 local frame at surface points (Alg. 1 step 1: "compute tangential and normal
 unit directions").  The outward normal is n = grad F / |grad F| (Sec. 2).
 
@@ -103,7 +105,24 @@ def _torus(geom, X):
     return F, G, H
 
 
-_KINDS = {"sphere": _sphere, "ellipsoid": _ellipsoid, "star": _star, "torus": _torus}
+# Sec. 2 with a caller-supplied level set: F, gradient and Hessian point by point.
+def _callback(geom, X):
+    """Evaluate geom["F"](x) and geom["derivs"](x) -> (gradient, Hessian) at
+    every point of X (..., 3), one point at a time."""
+    pts = X.reshape(-1, 3)
+    F = np.empty(len(pts))
+    G = np.empty((len(pts), 3))
+    H = np.empty((len(pts), 3, 3))
+    for k, x in enumerate(pts):
+        F[k] = geom["F"](tuple(x))
+        g, h = geom["derivs"](tuple(x))
+        G[k] = g
+        H[k] = np.asarray(h).reshape(3, 3)
+    return F.reshape(X.shape[:-1]), G.reshape(X.shape), H.reshape(X.shape + (3,))
+
+
+_KINDS = {"sphere": _sphere, "ellipsoid": _ellipsoid, "star": _star, "torus": _torus,
+          "callback": _callback}
 
 
 # Sec. 2: Gamma is the zero set of F and Omega = {F < 0}; Alg. 1 step 1.
@@ -115,6 +134,9 @@ def level_set(geom, X):
 
 # Sec. 2: the value of F alone.
 def level_value(geom, X):
+    if geom["kind"] == "callback":
+        X = np.asarray(X, dtype=np.float64)
+        return np.array([geom["F"](tuple(x)) for x in X.reshape(-1, 3)]).reshape(X.shape[:-1])
     return level_set(geom, X)[0]
 
 

@@ -10,7 +10,7 @@ c_int, c_double, c_int64, c_void_p = ctypes.c_int, ctypes.c_double, ctypes.c_int
 
 STATUS = {0: "OK", -1: "E_INVALID", -2: "E_GEOMETRY", -3: "E_NOCONV", -4: "E_NONFINITE",
           -5: "E_CUDA", -6: "E_OOM"}
-KINDS = {"sphere": 0, "ellipsoid": 1, "star": 2, "torus": 3}
+KINDS = {"sphere": 0, "ellipsoid": 1, "star": 2, "torus": 3, "callback": 4}
 
 
 class KfbimError(RuntimeError):
@@ -19,9 +19,15 @@ class KfbimError(RuntimeError):
         self.code = code
 
 
+LEVEL_FN = ctypes.CFUNCTYPE(c_double, ctypes.POINTER(c_double), c_void_p)
+LEVEL_DERIVS_FN = ctypes.CFUNCTYPE(None, ctypes.POINTER(c_double), ctypes.POINTER(c_double),
+                                   ctypes.POINTER(c_double), c_void_p)
+
+
 class Geometry(ctypes.Structure):
     _fields_ = [("kind", c_int), ("center", c_double * 3), ("rot", c_double * 9),
-                ("params", c_double * 8)]
+                ("params", c_double * 8), ("F", LEVEL_FN), ("derivs", LEVEL_DERIVS_FN),
+                ("user", c_void_p)]
 
 
 class Grid(ctypes.Structure):
@@ -115,9 +121,33 @@ def poisson_noalloc(c, N, lo, hi, r, u):
     return u
 
 
+def _level_callbacks(desc):
+    """C callbacks for a "callback" geometry: desc["F"](x) -> float and
+    desc["derivs"](x) -> (gradient (3,), Hessian (3, 3)) at a point x (3
+    floats).  The returned objects must stay referenced while setup runs."""
+    F, derivs = desc["F"], desc["derivs"]
+
+    def f_c(x, user):
+        return float(F((x[0], x[1], x[2])))
+
+    def d_c(x, g, H, user):
+        gv, Hv = derivs((x[0], x[1], x[2]))
+        gv = np.asarray(gv, dtype=np.float64).reshape(3)
+        Hv = np.asarray(Hv, dtype=np.float64).reshape(9)
+        for i in range(3):
+            g[i] = gv[i]
+        for i in range(9):
+            H[i] = Hv[i]
+
+    return LEVEL_FN(f_c), LEVEL_DERIVS_FN(d_c)
+
+
 def _geometry(desc):
     g = Geometry()
     g.kind = KINDS[desc["kind"]]
+    if desc["kind"] == "callback":
+        g.F, g.derivs = _level_callbacks(desc)
+        return g
     for i, v in enumerate(desc.get("center", (0.0, 0.0, 0.0))):
         g.center[i] = v
     rot = desc.get("rotation", np.eye(3).reshape(-1).tolist())
@@ -204,7 +234,8 @@ class Solver:
         gr = Grid(int(grid["N"]), float(grid["lo"]), float(grid["hi"]))
         ctx = c_void_p()
         fn = lib.kfbim_setup if device else lib.kfbim_setup_host
-        st = fn(ctypes.byref(_geometry(geom)), ctypes.byref(gr), ctypes.byref(o), ctypes.byref(ctx))
+        gm = _geometry(geom)      # holds the ctypes callbacks of a "callback" geometry during setup
+        st = fn(ctypes.byref(gm), ctypes.byref(gr), ctypes.byref(o), ctypes.byref(ctx))
         if st != 0:
             raise KfbimError(st, "setup failed (see stderr)")
         self._lib, self._ctx = lib, ctx

@@ -1727,7 +1727,8 @@ static int setup_common(const kfbim_geometry* geom, const kfbim_grid* grid, cons
   if (!(opt->mu > 0) || opt->gmres_max < 1 || opt->gmres_max > 200 || opt->cg_max < 1 ||
       (opt->precision != KFBIM_FP64 && opt->precision != KFBIM_MIXED))
     return KFBIM_E_INVALID;
-  if (geom->kind < KFBIM_SPHERE || geom->kind > KFBIM_TORUS) return KFBIM_E_INVALID;
+  if (geom->kind < KFBIM_SPHERE || geom->kind > KFBIM_CALLBACK) return KFBIM_E_INVALID;
+  if (geom->kind == KFBIM_CALLBACK && (!geom->F || !geom->derivs)) return KFBIM_E_INVALID;
   if (geom->kind == KFBIM_TORUS && !(geom->params[0] > 0.0 && geom->params[1] > geom->params[0]))
     return KFBIM_E_INVALID;
   if (opt->pde != KFBIM_STOKES && opt->pde != KFBIM_NAVIER) return KFBIM_E_INVALID;

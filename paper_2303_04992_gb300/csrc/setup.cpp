@@ -35,6 +35,16 @@ struct Level {
   const kfbim_geometry& g;
   // F, gradient (3), Hessian (9, row-major); G and H nullable.
   void eval(const double* x, double* F, double* G, double* H) const {
+    if (g.kind == KFBIM_CALLBACK) {
+      *F = g.F(x, g.user);
+      if (G || H) {
+        double gg[3], hh[9];
+        g.derivs(x, gg, hh, g.user);
+        if (G) std::memcpy(G, gg, sizeof(gg));
+        if (H) std::memcpy(H, hh, sizeof(hh));
+      }
+      return;
+    }
     const double d0 = x[0] - g.center[0], d1 = x[1] - g.center[1], d2 = x[2] - g.center[2];
     if (g.kind == KFBIM_SPHERE) {
       const double r = std::sqrt(d0 * d0 + d1 * d1 + d2 * d2);
@@ -412,6 +422,14 @@ int build_tables(const kfbim_geometry& geom, const kfbim_grid& grid, double mu, 
   t.pid.assign(n, -1);
   for (int64_t y = 0; y < n; ++y) {
     fr[y] = make_frame(lev, &t.xyz[3 * y]);
+    bool finite = true;
+    for (int i = 0; i < 3; ++i) finite = finite && std::isfinite(fr[y].n[i]);
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) finite = finite && std::isfinite(fr[y].K[a][b]);
+    if (!finite) {
+      err = "level-set gradient vanishes or is not finite at a control point";
+      return KFBIM_E_GEOMETRY;
+    }
     const double* nn = fr[y].n;
     const double mx = std::max(std::fabs(nn[0]), std::max(std::fabs(nn[1]), std::fabs(nn[2])));
     if (std::fabs(nn[t.axis[y]]) >= mx - 1e-12) {

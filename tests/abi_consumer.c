@@ -13,6 +13,21 @@
 
 #include "kfbim.h"
 
+/* The sphere of radius *(double*)user about the origin as a CALLBACK level
+ * set, with the built-in sphere's arithmetic. */
+static double sphere_F(const double x[3], void* user) {
+  return sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]) - *(const double*)user;
+}
+
+static void sphere_derivs(const double x[3], double g[3], double H[9], void* user) {
+  const double r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+  int i, j;
+  (void)user;
+  for (i = 0; i < 3; ++i) g[i] = x[i] / r;
+  for (i = 0; i < 3; ++i)
+    for (j = 0; j < 3; ++j) H[3 * i + j] = ((i == j) - g[i] * g[j]) / r;
+}
+
 static int fail(const char* what, int st) {
   fprintf(stderr, "%s: status %d\n", what, st);
   return 1;
@@ -71,6 +86,32 @@ int main(void) {
   if (!kfbim_last_error(ctx) || !kfbim_last_error(ctx)[0]) return fail("kfbim_last_error", st_apply);
   st = kfbim_destroy(ctx);
   if (st != KFBIM_OK) return fail("kfbim_destroy", st);
+
+  /* the same sphere through the CALLBACK kind: identical sizes and points */
+  {
+    kfbim_geometry cb;
+    kfbim_ctx* cctx = NULL;
+    double radius = 0.5;
+    int64_t cn = 0, cprim = 0;
+    double* cxyz;
+    memset(&cb, 0, sizeof cb);
+    cb.kind = KFBIM_CALLBACK;
+    cb.F = sphere_F;
+    cb.derivs = sphere_derivs;
+    cb.user = &radius;
+    st = kfbim_setup_host(&cb, &grid, &opt, &cctx);
+    if (st != KFBIM_OK || !cctx) return fail("kfbim_setup_host (callback)", st);
+    st = kfbim_sizes(cctx, &cn, &cprim, NULL);
+    if (st != KFBIM_OK) return fail("kfbim_sizes (callback)", st);
+    cxyz = (double*)malloc(sizeof(double) * 3 * (size_t)cn);
+    if (!cxyz) return fail("malloc", -6);
+    st = kfbim_points(cctx, cxyz, NULL, NULL, NULL);
+    if (st != KFBIM_OK) return fail("kfbim_points (callback)", st);
+    printf("callback_equal %d\n",
+           cn == n_points && cprim == n_primary && memcmp(cxyz, xyz, sizeof(double) * 3 * (size_t)cn) == 0);
+    free(cxyz);
+    kfbim_destroy(cctx);
+  }
 
   /* N = 24 is not a power of two: refused, *ctx set to NULL */
   grid.N = 24;

@@ -72,3 +72,52 @@ def test_host_only_context_refuses_device_calls():
     with pytest.raises(KfbimError) as e:
         s._check(s._lib.kfbim_apply(s._ctx, None, None, None))
     assert e.value.code == -1
+
+
+def test_callback_sphere_reproduces_the_builtin_setup():
+    """A caller-supplied level set with the built-in sphere's arithmetic gives
+    the same control points, sides and tables, bit for bit."""
+    a = Solver(ki.sphere(), ki.grid(32), device=False)
+    b = Solver(ki.callback_sphere(), ki.grid(32), device=False)
+    assert (a.n_points, a.n_primary) == (b.n_points, b.n_primary)
+    assert a.table_sizes() == b.table_sizes()
+    for x, y in zip(a.points(), b.points()):
+        assert np.array_equal(x, y)
+    for c in range(4):
+        assert np.array_equal(a.sides(c), b.sides(c))
+
+
+def test_callback_peanut_matches_oracle_points():
+    """A non-convex shape that no built-in kind covers (a Cassini surface of
+    revolution with a waist), through the CALLBACK kind, against the oracle
+    evaluating the same level set."""
+    geom = ki.peanut()
+    s = Solver(geom, ki.grid(32), device=False)
+    o = okfbim.Setup(geom, ki.grid(32))
+    xyz, comp, axis, prim = s.points()
+    assert s.n_points == o.cp.n and s.n_primary == o.n
+    assert np.array_equal(comp, o.cp.comp) and np.array_equal(axis, o.cp.axis)
+    assert np.array_equal(prim, o.primary)
+    assert np.abs(xyz - o.cp.xyz).max() < 1e-14
+    for c in range(4):
+        assert np.array_equal(s.sides(c), o.S[c])
+
+
+def test_callback_geometry_errors():
+    import ctypes
+    import pytest
+    from paper_2303_04992_gb300.binding import Geometry, Grid, Options
+    lib = load_library()
+    o = Options()
+    lib.kfbim_default_options(ctypes.byref(o))
+    g = Geometry()
+    g.kind = 4                                          # CALLBACK without functions
+    ctx = ctypes.c_void_p()
+    assert lib.kfbim_setup_host(ctypes.byref(g), ctypes.byref(Grid(32, -1.0, 1.0)), ctypes.byref(o),
+                                ctypes.byref(ctx)) == -1
+    assert not ctx.value
+    flat = dict(ki.peanut())
+    flat["derivs"] = lambda x: ([0.0, 0.0, 0.0], [[0.0] * 3] * 3)   # vanishing gradient
+    with pytest.raises(KfbimError) as e:
+        Solver(flat, ki.grid(32), device=False)
+    assert e.value.code == -2

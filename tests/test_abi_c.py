@@ -2,7 +2,8 @@
 as strict C99 and as C++17 with warnings as errors, links against the built
 library and runs its host-only entry points (no GPU).  Its output must match
 the Python binding's view of the same context and the geometry: every control
-point on the sphere, one primary flag per density unknown."""
+point on the sphere, one primary flag per density unknown, and the same sphere
+given as C callbacks (CALLBACK kind) reproduces the built-in setup."""
 import os
 import shutil
 import subprocess
@@ -46,3 +47,4 @@ def test_c_consumer_matches_binding(tmp_path, compiler, std):
     assert got["max_distance"] < 1e-12
     assert got["omega_cells"] == int(np.count_nonzero(s.sides(0)))
     assert got["status_apply"] == -1 and got["status_bad_grid"] == -1
+    assert got["callback_equal"] == 1

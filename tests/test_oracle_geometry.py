@@ -16,7 +16,8 @@ def _points(rng, n=40):
     return x[s > 0.05]
 
 
-@pytest.mark.parametrize("geom", GEOMS + [ki.torus()], ids=lambda g: g["kind"])
+@pytest.mark.parametrize("geom", GEOMS + [ki.torus(), ki.peanut(), ki.callback_sphere(0.4, (0.1, 0, 0))],
+                         ids=lambda g: g["kind"])
 def test_gradient_hessian_finite_differences(geom):
     rng = np.random.default_rng(11)
     X = _points(rng)

@@ -198,6 +198,10 @@ int kfbim_table_sizes(const kfbim_ctx* ctx, int64_t* fit_nnz, int64_t* corr_rows
 int kfbim_points(const kfbim_ctx* ctx, double* xyz_host, int32_t* comp_host,
                  int32_t* axis_host, int32_t* primary_host);
 
+/* Outward unit normal grad F / |grad F| at every control point (Sec. 2),
+ * normal_host [n_points*3] in the order of kfbim_points; host memory. */
+int kfbim_normals(const kfbim_ctx* ctx, double* normal_host);
+
 /* Side of every node of grid c (0 = cells, 1..3 = faces of u^(c)), 1 = Omega;
  * N^3 bytes in field layout. */
 int kfbim_sides(const kfbim_ctx* ctx, int c, uint8_t* side_host);

@@ -61,6 +61,7 @@ SYMBOLS = {
                                   ctypes.POINTER(c_int64)]),
     "kfbim_points": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "kfbim_sides": (c_int, [c_void_p, c_int, c_void_p]),
+    "kfbim_normals": (c_int, [c_void_p, c_void_p]),
     "kfbim_apply": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "kfbim_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                             ctypes.POINTER(Stats), c_void_p]),
@@ -280,6 +281,12 @@ class Solver:
         self._check(self._lib.kfbim_points(self._ctx, _np_ptr(xyz, 3 * n, "xyz"), _np_ptr(comp, n, "comp", np.int32),
                                            _np_ptr(axis, n, "axis", np.int32), _np_ptr(prim, n, "prim", np.int32)))
         return xyz, comp, axis, prim.astype(bool)
+
+    def normals(self):
+        """Outward unit normals (n_points, 3) at the control points."""
+        nrm = np.zeros((self.n_points, 3))
+        self._check(self._lib.kfbim_normals(self._ctx, _np_ptr(nrm, 3 * self.n_points, "normal")))
+        return nrm
 
     def sides(self, c):
         s = np.zeros(self.N ** 3, np.uint8)

@@ -30,6 +30,7 @@ struct HostTables {
   std::vector<int32_t> comp, axis, primary, pid;   // pid: primary index or -1
   std::vector<int32_t> idx;                        // 3 per point: lower node (i,j,k)
   std::vector<double> theta, xyz;                  // xyz: 3 per point
+  std::vector<double> normal;                      // 3 per point: outward unit normal
   std::vector<uint8_t> side[4];                    // N^3 per grid (0 cells, 1..3 faces)
   // surface fits: CSR over rows y*3 + c'; columns are primary indices
   std::vector<int64_t> fit_ptr;

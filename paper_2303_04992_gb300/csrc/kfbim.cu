@@ -1847,6 +1847,12 @@ int kfbim_points(const kfbim_ctx* c, double* xyz, int32_t* comp, int32_t* axis, 
   return KFBIM_OK;
 }
 
+int kfbim_normals(const kfbim_ctx* c, double* normal) {
+  if (!c || !normal) return KFBIM_E_INVALID;
+  std::memcpy(normal, c->host.normal.data(), sizeof(double) * 3 * c->host.n_all);
+  return KFBIM_OK;
+}
+
 int kfbim_sides(const kfbim_ctx* c, int g, uint8_t* side) {
   if (!c || g < 0 || g > 3 || !side) return KFBIM_E_INVALID;
   std::memcpy(side, c->host.side[g].data(), c->N3);

@@ -418,6 +418,7 @@ int build_tables(const kfbim_geometry& geom, const kfbim_grid& grid, double mu, 
     return KFBIM_E_GEOMETRY;
   }
   std::vector<Frame> fr(n);
+  t.normal.assign(3 * n, 0.0);
   t.primary.assign(n, 0);
   t.pid.assign(n, -1);
   for (int64_t y = 0; y < n; ++y) {
@@ -431,6 +432,7 @@ int build_tables(const kfbim_geometry& geom, const kfbim_grid& grid, double mu, 
       return KFBIM_E_GEOMETRY;
     }
     const double* nn = fr[y].n;
+    for (int i = 0; i < 3; ++i) t.normal[3 * y + i] = nn[i];
     const double mx = std::max(std::fabs(nn[0]), std::max(std::fabs(nn[1]), std::fabs(nn[2])));
     if (std::fabs(nn[t.axis[y]]) >= mx - 1e-12) {
       t.primary[y] = 1;

@@ -121,3 +121,17 @@ def test_callback_geometry_errors():
     with pytest.raises(KfbimError) as e:
         Solver(flat, ki.grid(32), device=False)
     assert e.value.code == -2
+
+
+def test_normals_match_the_oracle_frames():
+    from oracle import geometry
+    for geom in (ki.star(), ki.peanut(), ki.sphere(0.45, (0.01, -0.02, 0.0))):
+        s = Solver(geom, ki.grid(32), device=False)
+        xyz = s.points()[0]
+        got = s.normals()
+        want = geometry.frames(geom, xyz)[0]
+        assert np.abs(got - want).max() < 1e-13
+        assert np.abs(np.linalg.norm(got, axis=1) - 1.0).max() < 1e-14
+        if geom["kind"] == "sphere":
+            d = xyz - np.array(geom["center"])
+            assert np.abs(got - d / np.linalg.norm(d, axis=1)[:, None]).max() < 1e-13

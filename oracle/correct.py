@@ -55,11 +55,12 @@ def corrections(grid, cp, S, J, mu):
 
     s0 = side(c, P0)
     s1 = side(c, P1)
-    # item 1-3: Laplacian, coefficient -mu/h^2 on each across-neighbour
+    # item 1-3: Laplacian, coefficient -mu/h^2 on each across-neighbour; the
+    # faces of a grazing segment are on one side (no Laplacian correction)
     lap_a = -mu / (h * h)
     v0 = lap_a * _chi(s1) * Ju((1.0 - th) * h)      # row P0, neighbour P1
     v1 = lap_a * _chi(s0) * Ju(-th * h)             # row P1, neighbour P0
-    for m in range(cp.n):
+    for m in np.nonzero(cp.graze == 0)[0]:
         cf = Cf[c[m] - 1]
         i, j, k = P0[m]
         cf[k, j, i] += v0[m]
@@ -72,7 +73,10 @@ def corrections(grid, cp, S, J, mu):
     for m in np.nonzero(c == a + 1)[0]:
         i, j, k = P0[m]
         sC = bool(S[0][k, j, i])                     # cell C between P0 and P1
-        if sC == bool(s1[m]):                        # crossing between P0 and C
+        # crossing between P0 and C, or between C and P1 (a grazing segment
+        # has one of each: its two roots)
+        below = cp.graze[m] == 1 if cp.graze[m] else sC == bool(s1[m])
+        if below:                                    # crossing between P0 and C
             Cg[k, j, i] += (-1.0 / h) * _chi(s0[m]) * u_left[m]
             Cf[c[m] - 1][k, j, i] += (1.0 / h) * _chi(sC) * p_mid[m]
         else:                                        # crossing between C and P1

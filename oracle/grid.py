@@ -75,13 +75,17 @@ def sides(grid, geom, c):
 class ControlPoints:
     """Intersections of Gamma with the grid lines of u^(1), u^(2), u^(3)."""
 
-    def __init__(self, comp, axis, idx, theta, xyz):
+    def __init__(self, comp, axis, idx, theta, xyz, graze=None):
         self.comp = comp      # (n,) component c in 1..3
         self.axis = axis      # (n,) line axis a in 0..2
         self.idx = idx        # (n, 3) lower node (i, j, k) of the segment, grid c
         self.theta = theta    # (n,) fraction in [0, 1) from the lower node
         self.xyz = xyz        # (n, 3)
         self.n = len(comp)
+        # (n,) 0, or 1 / 2 for the root below / above the cell centre of a
+        # grazing face segment (both face nodes on one side, the cell centre
+        # between them on the other)
+        self.graze = np.zeros(self.n, dtype=np.int8) if graze is None else graze
 
     # Sec. 3: numbering of the control-point sets X_1, X_2, X_3.
     def offsets(self):
@@ -90,11 +94,11 @@ class ControlPoints:
 
 
 # Alg. 1 step 1: intersection of Gamma with one grid-line segment.
-def _bisect(geom, x0, dirv, h, side0):
-    """Root of F on the segment x0 + t h dirv, t in [0, 1], by 64 bisection
-    steps; side0 is the side (F <= 0) of the t = 0 end."""
-    lo = np.zeros(len(x0))
-    hi = np.ones(len(x0))
+def _bisect(geom, x0, dirv, h, side0, t0=0.0, t1=1.0):
+    """Root of F on the segment x0 + t h dirv, t in [t0, t1] (default the whole
+    segment), by 64 bisection steps; side0 is the side (F <= 0) of the t0 end."""
+    lo = np.full(len(x0), float(t0))
+    hi = np.full(len(x0), float(t1))
     for _ in range(64):
         mid = 0.5 * (lo + hi)
         s = geometry.level_value(geom, x0 + (mid * h)[:, None] * dirv) <= 0.0
@@ -109,7 +113,7 @@ def control_points(grid, geom):
     """All control points in canonical order, plus per-grid side arrays."""
     N, h = grid.N, grid.h
     S = {c: sides(grid, geom, c) for c in range(4)}
-    comps, axes, idxs, thetas = [], [], [], []
+    comps, axes, idxs, thetas, grazes = [], [], [], [], []
     for c in (1, 2, 3):
         Sc = S[c]
         unk = grid.unknown_mask(c)
@@ -119,31 +123,49 @@ def control_points(grid, geom):
             sl1 = [slice(None)] * 3
             sl0[ax] = slice(0, N - 1)
             sl1[ax] = slice(1, N)
-            cross = (Sc[tuple(sl0)] != Sc[tuple(sl1)]) & unk[tuple(sl0)] & unk[tuple(sl1)]
+            both = unk[tuple(sl0)] & unk[tuple(sl1)]
+            cross = (Sc[tuple(sl0)] != Sc[tuple(sl1)]) & both
             kk, jj, ii = np.nonzero(cross)
             idx = np.stack([ii, jj, kk], axis=-1)
-            other = [b for b in range(3) if b != a]      # increasing axis order
-            # canonical order: outer = higher other axis, inner = lower, then along a
-            order = np.lexsort((idx[:, a], idx[:, other[0]], idx[:, other[1]]))
-            idx = idx[order]
-            x0 = grid.node_xyz(c, idx)
             dirv = np.zeros(3)
             dirv[a] = 1.0
             side0 = Sc[idx[:, 2], idx[:, 1], idx[:, 0]]
-            t = _bisect(geom, x0, dirv, h, side0)
+            t = _bisect(geom, grid.node_xyz(c, idx), dirv, h, side0)
+            g = np.zeros(len(idx), dtype=np.int8)
+            if c == a + 1:
+                # grazing face segments of the combined u^(c)/cell line: the
+                # cell centre between two same-side faces lies on the other
+                # side, so Gamma crosses once below and once above it
+                Cs = S[0][tuple(sl0)]
+                graze = (Sc[tuple(sl0)] == Sc[tuple(sl1)]) & (Cs != Sc[tuple(sl0)]) & both
+                kk, jj, ii = np.nonzero(graze)
+                gidx = np.stack([ii, jj, kk], axis=-1)
+                gs0 = Sc[gidx[:, 2], gidx[:, 1], gidx[:, 0]]
+                gx0 = grid.node_xyz(c, gidx)
+                tl = _bisect(geom, gx0, dirv, h, gs0, 0.0, 0.5)
+                tr = _bisect(geom, gx0, dirv, h, ~gs0, 0.5, 1.0)
+                idx = np.concatenate([idx, gidx, gidx])
+                t = np.concatenate([t, tl, tr])
+                g = np.concatenate([g, np.full(len(gidx), 1, np.int8), np.full(len(gidx), 2, np.int8)])
+            other = [b for b in range(3) if b != a]      # increasing axis order
+            # canonical order: outer = higher other axis, inner = lower, then
+            # along a (the two roots of a grazing segment in increasing t)
+            order = np.lexsort((t, idx[:, a], idx[:, other[0]], idx[:, other[1]]))
             comps.append(np.full(len(idx), c))
             axes.append(np.full(len(idx), a))
-            idxs.append(idx)
-            thetas.append(t)
+            idxs.append(idx[order])
+            thetas.append(t[order])
+            grazes.append(g[order])
     comp = np.concatenate(comps)
     axis = np.concatenate(axes)
     idx = np.concatenate(idxs).astype(np.int64)
     theta = np.concatenate(thetas)
+    graze = np.concatenate(grazes)
     off = np.full((len(comp), 3), 0.5)
     off[np.arange(len(comp)), comp - 1] = 0.0
     xyz = grid.lo + (idx + off) * h
     xyz[np.arange(len(comp)), axis] += theta * h
-    return ControlPoints(comp, axis, idx, theta, xyz), S
+    return ControlPoints(comp, axis, idx, theta, xyz, graze), S
 
 
 # Ordering helper for the control points of Sec. 3 (no arithmetic of the method).
@@ -155,13 +177,13 @@ def fine_keys(cp):
     return key
 
 
-# Reading of the resolution the method assumes (Sec. 4.3 needs single
-# crossings per segment and the fit neighbourhood inside the box).
+# Reading of the resolution the method assumes: the fit neighbourhood of
+# Sec. 4.3 inside the box.
 def check_geometry(grid, geom, cp, S):
     """Reject geometries the discretisation does not resolve (KFBIM_E_GEOMETRY):
-    Gamma within 3h of the box wall, or a combined u^(a)/cell line whose
-    half-spacing lattice changes side more often than its face lattice."""
-    N = grid.N
+    Gamma within 3h of the box wall.  A combined u^(a)/cell line that changes
+    side twice within one face segment (a grazing segment) is resolved by its
+    two roots (control_points), so it is no longer an error."""
     for c in range(4):
         Sc = S[c]
         band = np.zeros_like(Sc)
@@ -170,16 +192,4 @@ def check_geometry(grid, geom, cp, S):
         band[:, :, :3], band[:, :, -3:] = True, True
         if np.any(Sc & band):
             raise ValueError("interface closer than 3h to the box wall")
-    for a in range(3):
-        c = a + 1
-        ax = 2 - a
-        F = np.moveaxis(S[c], ax, -1)[..., 1:]            # faces 1..N-1
-        P = np.moveaxis(S[0], ax, -1)                     # cells 0..N-1
-        fine = np.empty(F.shape[:-1] + (2 * N - 1,), dtype=bool)
-        fine[..., 0::2] = P
-        fine[..., 1::2] = F
-        n_fine = np.sum(fine[..., 1:] != fine[..., :-1])
-        n_face = np.sum(F[..., 1:] != F[..., :-1])
-        if n_face != n_fine:
-            raise ValueError("interface crosses a grid segment twice")
     return True

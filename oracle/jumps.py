@@ -196,7 +196,9 @@ def primary_points(cp, frames):
     secondary point is the fitted value from nearby primary points."""
     n = frames[0]
     na = np.abs(n[np.arange(cp.n), cp.axis])
-    return na >= np.max(np.abs(n), axis=1) - 1e-12
+    # the two roots of a grazing segment lie where their line is nearly tangent
+    # to Gamma: always secondary
+    return (na >= np.max(np.abs(n), axis=1) - 1e-12) & (cp.graze == 0)
 
 
 # Sec. 4.3: per-point data of the jump evaluation.

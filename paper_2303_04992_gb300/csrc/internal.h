@@ -31,6 +31,10 @@ struct HostTables {
   std::vector<int32_t> idx;                        // 3 per point: lower node (i,j,k)
   std::vector<double> theta, xyz;                  // xyz: 3 per point
   std::vector<double> normal;                      // 3 per point: outward unit normal
+  // 0, or 1 / 2 for the root below / above the cell centre of a grazing face
+  // segment (both face nodes on one side, the cell centre between them on the
+  // other; combined u^(c)/cell lines only)
+  std::vector<int8_t> graze;
   std::vector<uint8_t> side[4];                    // N^3 per grid (0 cells, 1..3 faces)
   // surface fits: CSR over rows y*3 + c'; columns are primary indices
   std::vector<int64_t> fit_ptr;

@@ -342,36 +342,9 @@ int build_tables(const kfbim_geometry& geom, const kfbim_grid& grid, double mu, 
             return KFBIM_E_GEOMETRY;
           }
         }
-  // combined u^(a)/cell lines: one side change per face segment at most
-  for (int a = 0; a < 3; ++a) {
-    const int c = a + 1;
-    for (int q = 0; q < N; ++q)
-      for (int p = 0; p < N; ++p) {
-        int nf = 0, nc = 0;
-        int prev_f = -1, prev_fine = -1;
-        for (int s = 0; s < N; ++s) {
-          int id[3];
-          const int o1 = (a + 1) % 3, o2 = (a + 2) % 3;
-          id[a] = s;
-          id[std::min(o1, o2)] = p;
-          id[std::max(o1, o2)] = q;
-          const int cell = t.side[0][flat(N, id[0], id[1], id[2])];
-          if (s >= 1) {
-            const int face = t.side[c][flat(N, id[0], id[1], id[2])];
-            if (prev_f >= 0 && face != prev_f) ++nf;
-            prev_f = face;
-            if (face != prev_fine) ++nc;
-            prev_fine = face;
-          }
-          if (prev_fine >= 0 && cell != prev_fine) ++nc;
-          prev_fine = cell;
-        }
-        if (nf != nc) {
-          err = "interface crosses a grid segment twice";
-          return KFBIM_E_GEOMETRY;
-        }
-      }
-  }
+  // A combined u^(a)/cell line may change side twice within one face segment
+  // (a grazing segment: both faces on one side, the cell centre between them
+  // on the other); its two roots become control points below.
 
   // ---- control points: component c, line axis a, outer/inner line index, position
   for (int c = 1; c <= 3; ++c) {
@@ -390,24 +363,34 @@ int build_tables(const kfbim_geometry& geom, const kfbim_grid& grid, double mu, 
             id1[a] = s + 1;
             const int s0 = t.side[c][flat(N, id0[0], id0[1], id0[2])];
             const int s1 = t.side[c][flat(N, id1[0], id1[1], id1[2])];
-            if (s0 == s1) continue;
+            const bool graze = s0 == s1 && c == a + 1 && t.side[0][flat(N, id0[0], id0[1], id0[2])] != s0;
+            if (s0 == s1 && !graze) continue;
             double x0[3];
             node_x(c, id0[0], id0[1], id0[2], x0);
-            double lo_t = 0.0, hi_t = 1.0;
-            for (int it = 0; it < 64; ++it) {
-              const double mid = 0.5 * (lo_t + hi_t);
+            // root of F on [t0, t1] of the segment by 64 bisection steps; side0 at t0
+            auto add_root = [&](double lo_t, double hi_t, int side0, int8_t gflag) {
+              for (int it = 0; it < 64; ++it) {
+                const double mid = 0.5 * (lo_t + hi_t);
+                double x[3] = {x0[0], x0[1], x0[2]};
+                x[a] = x0[a] + mid * h;
+                const int sm = lev.value(x) <= 0.0 ? 1 : 0;
+                if (sm == side0) lo_t = mid; else hi_t = mid;
+              }
+              t.comp.push_back(c);
+              t.axis.push_back(a);
+              for (int b = 0; b < 3; ++b) t.idx.push_back(id0[b]);
+              t.theta.push_back(lo_t);
+              t.graze.push_back(gflag);
               double x[3] = {x0[0], x0[1], x0[2]};
-              x[a] = x0[a] + mid * h;
-              const int sm = lev.value(x) <= 0.0 ? 1 : 0;
-              if (sm == s0) lo_t = mid; else hi_t = mid;
+              x[a] += lo_t * h;
+              for (int b = 0; b < 3; ++b) t.xyz.push_back(x[b]);
+            };
+            if (!graze) {
+              add_root(0.0, 1.0, s0, 0);
+            } else {  // once below and once above the cell centre
+              add_root(0.0, 0.5, s0, 1);
+              add_root(0.5, 1.0, 1 - s0, 2);
             }
-            t.comp.push_back(c);
-            t.axis.push_back(a);
-            for (int b = 0; b < 3; ++b) t.idx.push_back(id0[b]);
-            t.theta.push_back(lo_t);
-            double x[3] = {x0[0], x0[1], x0[2]};
-            x[a] += lo_t * h;
-            for (int b = 0; b < 3; ++b) t.xyz.push_back(x[b]);
           }
     }
   }
@@ -434,7 +417,8 @@ int build_tables(const kfbim_geometry& geom, const kfbim_grid& grid, double mu, 
     const double* nn = fr[y].n;
     for (int i = 0; i < 3; ++i) t.normal[3 * y + i] = nn[i];
     const double mx = std::max(std::fabs(nn[0]), std::max(std::fabs(nn[1]), std::fabs(nn[2])));
-    if (std::fabs(nn[t.axis[y]]) >= mx - 1e-12) {
+    // the roots of a grazing segment (line nearly tangent to Gamma) are secondary
+    if (t.graze[y] == 0 && std::fabs(nn[t.axis[y]]) >= mx - 1e-12) {
       t.primary[y] = 1;
       t.pid[y] = (int32_t)t.n_prim++;
     }
@@ -574,13 +558,17 @@ int build_tables(const kfbim_geometry& geom, const kfbim_grid& grid, double mu, 
       ent.emplace_back(target, (int64_t)11 * n + y, coef * xi);
     };
     const double lap = -mu / (h * h);
-    add_u(tP0, lap * chi(s1), (1.0 - th) * h);  // row P0, neighbour P1 across
-    add_u(tP1, lap * chi(s0), -th * h);         // row P1, neighbour P0 across
+    if (t.graze[y] == 0) {  // the faces of a grazing segment are on one side
+      add_u(tP0, lap * chi(s1), (1.0 - th) * h);  // row P0, neighbour P1 across
+      add_u(tP1, lap * chi(s0), -th * h);         // row P1, neighbour P0 across
+    }
     if (c == a + 1) {
       const int sC = t.side[0][flat(N, P0[0], P0[1], P0[2])];
       const int64_t tC = 3 * N3 + flat(N, P0[0], P0[1], P0[2]);
       const double xiC = 0.5 * h - th * h;
-      if (sC == s1) {  // crossing between P0 and the cell centre C
+      // a grazing segment has one root below and one above C
+      const bool below = t.graze[y] ? t.graze[y] == 1 : sC == s1;
+      if (below) {  // crossing between P0 and the cell centre C
         add_u(tC, (-1.0 / h) * chi(s0), -th * h);
         add_p(tP0, (1.0 / h) * chi(sC), xiC);
       } else {         // crossing between C and P1

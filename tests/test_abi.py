@@ -135,3 +135,21 @@ def test_normals_match_the_oracle_frames():
         if geom["kind"] == "sphere":
             d = xyz - np.array(geom["center"])
             assert np.abs(got - d / np.linalg.norm(d, axis=1)[:, None]).max() < 1e-13
+
+
+def test_grazing_sphere_matches_oracle_points():
+    """A sphere whose surface grazes grid lines (a chord shorter than h between
+    two same-side faces, the cell centre between them on the other side): the
+    two roots of each such segment are secondary control points, in the
+    library's host setup exactly as in the oracle."""
+    geom, grid = ki.sphere(0.5, (0.01, -0.02, 0.0)), ki.grid(32)
+    s = Solver(geom, grid, device=False)
+    o = okfbim.Setup(geom, grid)
+    assert int(np.sum(o.cp.graze > 0)) == 4 and not np.any(o.primary[o.cp.graze > 0])
+    xyz, comp, axis, prim = s.points()
+    assert s.n_points == o.cp.n and s.n_primary == o.n
+    assert np.array_equal(comp, o.cp.comp) and np.array_equal(axis, o.cp.axis)
+    assert np.array_equal(prim, o.primary)
+    assert np.abs(xyz - o.cp.xyz).max() < 1e-14
+    for c in range(4):
+        assert np.array_equal(s.sides(c), o.S[c])

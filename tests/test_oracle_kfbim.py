@@ -110,3 +110,43 @@ def test_navier_constant_density_and_convergence():
         its.append(r["iters"])
     assert errs[0] / errs[1] > 3.5
     assert max(its) <= 25
+
+
+def _stokes_velocity_error(geom, N):
+    """Max velocity error of the manufactured Stokes pair over the Omega face
+    nodes, relative to the largest exact value there."""
+    s = kfbim.Setup(geom, ki.grid(N))
+    x = s.cp.xyz
+    g = ki.stokes_velocity(x)[np.arange(s.cp.n), s.cp.comp - 1][s.primary]
+    ff = [ki.stokes_forcing(s.grid.node_xyz(c, s.grid.all_idx()))[..., c - 1] for c in (1, 2, 3)]
+    r = s.solve(g, ki.stokes_forcing(x), ff)
+    err = scale = 0.0
+    for c in (1, 2, 3):
+        m = s.S[c]
+        ue = ki.stokes_velocity(s.grid.node_xyz(c, s.grid.all_idx()))[..., c - 1]
+        err = max(err, np.abs((r["u"][c - 1] - ue)[m]).max())
+        scale = max(scale, np.abs(ue[m]).max())
+    return s, err / scale
+
+
+def test_grazing_segments_are_resolved(monkeypatch):
+    """R = 0.5 about (0.01, -0.02, 0) at N = 32 grazes two combined face/cell
+    segments (both faces outside, the cell centre inside).  Their two roots
+    each, with the divergence and gradient corrections of their half-segment,
+    make it as accurate as R = 0.45 about the same centre (no grazing); with
+    the corrections of those roots dropped (a mistake planted in the oracle)
+    the error grows several times, so the pin sees them."""
+    s, e_graze = _stokes_velocity_error(ki.sphere(0.5, (0.01, -0.02, 0.0)), 32)
+    assert int(np.sum(s.cp.graze > 0)) == 4
+    _, e_plain = _stokes_velocity_error(ki.sphere(0.45, (0.01, -0.02, 0.0)), 32)
+    assert e_graze < 1.5 * e_plain
+    orig = kfbim.correct.corrections
+
+    def dropped(grid, cp, S, J, mu):
+        J = J.copy()
+        J[cp.graze > 0] = 0.0
+        return orig(grid, cp, S, J, mu)
+
+    monkeypatch.setattr(kfbim.correct, "corrections", dropped)
+    _, e_dropped = _stokes_velocity_error(ki.sphere(0.5, (0.01, -0.02, 0.0)), 32)
+    assert e_dropped > 4 * e_graze

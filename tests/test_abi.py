@@ -153,3 +153,17 @@ def test_grazing_sphere_matches_oracle_points():
     assert np.abs(xyz - o.cp.xyz).max() < 1e-14
     for c in range(4):
         assert np.array_equal(s.sides(c), o.S[c])
+
+
+def test_correction_rows_match_the_oracle():
+    """The library's correction table touches exactly the right-hand-side
+    rows the oracle's corrections touch (random jumps), for built-in, CALLBACK
+    and grazing geometries."""
+    from oracle import correct as ocorrect
+    for geom in (ki.sphere(), ki.star(), ki.peanut(), ki.sphere(0.5, (0.01, -0.02, 0.0))):
+        o = okfbim.Setup(geom, ki.grid(32))
+        J = np.random.default_rng(1).standard_normal((o.cp.n, 12))
+        Cf, Cg = ocorrect.corrections(o.grid, o.cp, o.S, J, 1.0)
+        rows = sum(int(np.count_nonzero(f)) for f in Cf) + int(np.count_nonzero(Cg))
+        s = Solver(geom, ki.grid(32), device=False)
+        assert s.table_sizes()[1] == rows

@@ -167,3 +167,22 @@ def test_correction_rows_match_the_oracle():
         rows = sum(int(np.count_nonzero(f)) for f in Cf) + int(np.count_nonzero(Cg))
         s = Solver(geom, ki.grid(32), device=False)
         assert s.table_sizes()[1] == rows
+
+
+def test_random_sphere_placements_set_up_like_the_oracle():
+    """Generic placements (radius and centre drawn at random) all set up; many
+    graze grid lines, which were rejected before grazing segments got their two
+    roots.  Points, flags and sides agree with the oracle."""
+    rng = np.random.default_rng(2024)
+    grazing = 0
+    for _ in range(8):
+        geom = ki.sphere(rng.uniform(0.35, 0.55), tuple(rng.uniform(-0.05, 0.05, 3)))
+        s = Solver(geom, ki.grid(32), device=False)
+        o = okfbim.Setup(geom, ki.grid(32))
+        grazing += int(np.any(o.cp.graze > 0))
+        xyz, comp, axis, prim = s.points()
+        assert s.n_points == o.cp.n and np.array_equal(prim, o.primary)
+        assert np.array_equal(comp, o.cp.comp) and np.array_equal(axis, o.cp.axis)
+        assert np.abs(xyz - o.cp.xyz).max() < 1e-14
+        assert np.array_equal(s.sides(0), o.S[0])
+    assert grazing >= 2

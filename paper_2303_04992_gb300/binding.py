@@ -122,19 +122,29 @@ def poisson_noalloc(c, N, lo, hi, r, u):
     return u
 
 
-def _level_callbacks(desc):
+def _level_callbacks(desc, errors):
     """C callbacks for a "callback" geometry: desc["F"](x) -> float and
     desc["derivs"](x) -> (gradient (3,), Hessian (3, 3)) at a point x (3
-    floats).  The returned objects must stay referenced while setup runs."""
+    floats).  An exception cannot cross the C call: the first one is kept in
+    `errors` and the callback returns NaN values.  The returned objects must
+    stay referenced while setup runs."""
     F, derivs = desc["F"], desc["derivs"]
 
     def f_c(x, user):
-        return float(F((x[0], x[1], x[2])))
+        try:
+            return float(F((x[0], x[1], x[2])))
+        except Exception as e:  # re-raised by the caller after setup
+            errors.append(e)
+            return float("nan")
 
     def d_c(x, g, H, user):
-        gv, Hv = derivs((x[0], x[1], x[2]))
-        gv = np.asarray(gv, dtype=np.float64).reshape(3)
-        Hv = np.asarray(Hv, dtype=np.float64).reshape(9)
+        try:
+            gv, Hv = derivs((x[0], x[1], x[2]))
+            gv = np.asarray(gv, dtype=np.float64).reshape(3)
+            Hv = np.asarray(Hv, dtype=np.float64).reshape(9)
+        except Exception as e:  # re-raised by the caller after setup
+            errors.append(e)
+            gv, Hv = np.full(3, np.nan), np.full(9, np.nan)
         for i in range(3):
             g[i] = gv[i]
         for i in range(9):
@@ -143,11 +153,11 @@ def _level_callbacks(desc):
     return LEVEL_FN(f_c), LEVEL_DERIVS_FN(d_c)
 
 
-def _geometry(desc):
+def _geometry(desc, errors=None):
     g = Geometry()
     g.kind = KINDS[desc["kind"]]
     if desc["kind"] == "callback":
-        g.F, g.derivs = _level_callbacks(desc)
+        g.F, g.derivs = _level_callbacks(desc, [] if errors is None else errors)
         return g
     for i, v in enumerate(desc.get("center", (0.0, 0.0, 0.0))):
         g.center[i] = v
@@ -235,8 +245,13 @@ class Solver:
         gr = Grid(int(grid["N"]), float(grid["lo"]), float(grid["hi"]))
         ctx = c_void_p()
         fn = lib.kfbim_setup if device else lib.kfbim_setup_host
-        gm = _geometry(geom)      # holds the ctypes callbacks of a "callback" geometry during setup
+        errors = []
+        gm = _geometry(geom, errors)   # holds the ctypes callbacks of a "callback" geometry during setup
         st = fn(ctypes.byref(gm), ctypes.byref(gr), ctypes.byref(o), ctypes.byref(ctx))
+        if errors:
+            if st == 0:
+                lib.kfbim_destroy(ctx)
+            raise errors[0]
         if st != 0:
             raise KfbimError(st, "setup failed (see stderr)")
         self._lib, self._ctx = lib, ctx

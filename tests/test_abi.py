@@ -186,3 +186,15 @@ def test_random_sphere_placements_set_up_like_the_oracle():
         assert np.abs(xyz - o.cp.xyz).max() < 1e-14
         assert np.array_equal(s.sides(0), o.S[0])
     assert grazing >= 2
+
+
+def test_callback_exception_is_raised_after_setup():
+    import pytest
+    geom = dict(ki.peanut())
+
+    def bad(x):
+        raise ZeroDivisionError("level set failed")
+
+    geom["F"] = bad
+    with pytest.raises(ZeroDivisionError):
+        Solver(geom, ki.grid(16), device=False)

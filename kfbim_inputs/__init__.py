@@ -1,16 +1,18 @@
 """Seeded synthetic inputs shared by the CUDA path's tests/bench and by the oracle.
 
 This module holds no arithmetic of the method itself: only geometry
-descriptors (plain parameters of analytic surfaces), closed-form manufactured
-Stokes fields used as boundary data and forcing, and seeded random densities.
-Each consumer evaluates level sets, control points and everything else with
-its own code.
+descriptors (plain parameters of analytic surfaces, or, for the CALLBACK kind,
+a level set and its derivatives as functions of a point), closed-form
+manufactured Stokes and Lame fields used as boundary data and forcing, the
+paper's example fields, seeded divergence-free harmonic fields and seeded
+random densities.  Each consumer evaluates control points, jumps and
+everything else with its own code.
 
 Workloads (all in the bounding box [-1, 1]^3, viscosity 1):
   * sphere: radius 0.5 centred at the origin, N = 32 (plain FP64 case);
   * star:   r(theta, phi) = 0.5 + 0.1 sin(3 theta) cos(4 phi) (theta = polar
             angle, phi = azimuth), N = 64 and N = 128 (headline case);
-  * ellipsoid: semi-axes (0.6, 0.45, 0.35) under a seeded rotation.
+  * ellipsoid: semi-axes (0.6, 0.45, 0.35) under a seeded rotation (Navier).
 Boundary data come from the divergence-free manufactured field
 u = (sin x cos y cos z, -cos x sin y cos z, 0), p = sin(x + y + z).
 """

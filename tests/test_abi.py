@@ -4,6 +4,7 @@ import os
 import re
 
 import numpy as np
+import pytest
 
 import kfbim_inputs as ki
 from oracle import kfbim as okfbim
@@ -198,3 +199,32 @@ def test_callback_exception_is_raised_after_setup():
     geom["F"] = bad
     with pytest.raises(ZeroDivisionError):
         Solver(geom, ki.grid(16), device=False)
+
+
+def _bad_setup_cases():
+    good_geom, good_grid = ki.sphere(), ki.grid(32)
+    return [
+        ("N not a power of two", good_geom, ki.grid(48), {}),
+        ("N below 16", good_geom, ki.grid(8), {}),
+        ("N above 256", good_geom, ki.grid(512), {}),
+        ("empty box", good_geom, {"N": 32, "lo": 1.0, "hi": 1.0}, {}),
+        ("mu <= 0", good_geom, good_grid, {"mu": 0.0}),
+        ("gmres_max 0", good_geom, good_grid, {"gmres_max": 0}),
+        ("gmres_max 201", good_geom, good_grid, {"gmres_max": 201}),
+        ("cg_max 0", good_geom, good_grid, {"cg_max": 0}),
+        ("precision 7", good_geom, good_grid, {"precision": 7}),
+        ("pde 5", good_geom, good_grid, {"pde": 5}),
+        ("transforms 9", good_geom, good_grid, {"transforms": 9}),
+        ("lambda + mu <= 0", good_geom, good_grid, {"lam": -2.0}),
+        ("torus a >= c", ki.torus(0.5, 0.4), good_grid, {}),
+    ]
+
+
+@pytest.mark.parametrize("case", _bad_setup_cases(), ids=lambda c: c[0])
+def test_setup_rejects_invalid_arguments(case):
+    _, geom, grid, opts = case
+    with pytest.raises(KfbimError) as e:
+        Solver(geom, grid, device=False, **opts)
+    assert e.value.code == -1
+    # the library stays usable
+    Solver(ki.sphere(), ki.grid(16), device=False).close()

@@ -110,10 +110,19 @@ typedef struct {
 } kfbim_grid;
 
 typedef enum {
-  KFBIM_FP64 = 0,  /* every step in FP64 */
-  KFBIM_MIXED = 1  /* FP32 transforms and Schur CG inside FP64 iterative
-                      refinement of the corrected MAC system; jumps,
-                      corrections, traces, residuals and GMRES stay FP64 */
+  KFBIM_FP64 = 0,       /* every step in FP64 */
+  KFBIM_MIXED = 1,      /* FP32 transforms and Schur CG inside FP64 iterative
+                           refinement of the corrected MAC system; jumps,
+                           corrections, traces, residuals and GMRES stay FP64 */
+  KFBIM_FP32 = 2,       /* the grid solve in FP32 only: one FP32 Schur CG (to
+                           inner_tol) and FP32 transforms, no FP64 refinement;
+                           jumps, corrections, traces and GMRES stay FP64.  The
+                           matvec is accurate to about 1e-6 relative, so
+                           gmres_tol should not be below about 1e-6.  A forward
+                           mode for large grids (the benchmark spec C5's 256^3 run) */
+  KFBIM_MIXED_TF32 = 3  /* MIXED with every FP32 transform on the tensor cores
+                           (3xTF32 transform-matrix GEMMs, transforms = TENSOR);
+                           N = 128 only, else E_INVALID */
 } kfbim_precision;
 
 typedef enum {
@@ -142,13 +151,23 @@ typedef struct {
   int transforms;     /* kfbim_transforms: kernels of the FP32 (MIXED) axis passes */
 } kfbim_options;
 
-/* Kernels of the FP32 axis passes of MIXED contexts.  The tensor-core form
- * (a dense 3xTF32 transform-matrix GEMM on tcgen05) exists for N = 128 only;
- * elsewhere, and for every FP64 pass, the FFT pass runs. */
+/* Kernels of the FP32 transforms of MIXED contexts.
+ * The Schur CG (Sec. 4.2, the dominant cost) runs, for N = 32, 64 and 128, as
+ * four kernels per iteration: the transforms along z of the CG direction, one
+ * CTA per (x, y) plane for the rest of the three spectral terms in shared
+ * memory, the inverse transforms along z with the first dot product, and the
+ * vector update (the "slab" iteration).  The other FP32 transforms (Schur
+ * right-hand side, velocity recovery) run as one-axis passes: four-step FFT
+ * passes on the CUDA cores, or, for N = 128, a dense 3xTF32
+ * transform-matrix GEMM on the tensor cores (tcgen05).  FP64 passes are
+ * always FFT passes. */
 typedef enum {
-  KFBIM_XF_AUTO = 0,    /* timed at setup: the faster of the two per stage kind */
-  KFBIM_XF_FFT = 1,     /* four-step FFT passes (CUDA cores) */
-  KFBIM_XF_TENSOR = 2   /* tensor-core GEMM passes where N = 128 */
+  KFBIM_XF_AUTO = 0,    /* slab CG; one-axis passes timed at setup, the faster of the
+                           FFT and tensor-core forms per stage kind */
+  KFBIM_XF_FFT = 1,     /* slab CG; FFT one-axis passes */
+  KFBIM_XF_TENSOR = 2,  /* tensor-core passes where N = 128, CG included (one-axis stages) */
+  KFBIM_XF_STAGED = 3   /* FFT one-axis passes everywhere, CG included (five staged
+                           launches per Schur apply, three CG vector kernels) */
 } kfbim_transforms;
 
 typedef struct {
@@ -171,6 +190,14 @@ void kfbim_default_options(kfbim_options* opt);
  * neighbours), E_OOM, E_CUDA.  On error *ctx is NULL. */
 int kfbim_setup(const kfbim_geometry* geom, const kfbim_grid* grid,
                 const kfbim_options* opt, kfbim_ctx** ctx);
+
+/* kfbim_setup with its device work (table uploads, workspace clears) ordered
+ * on `stream` (a cudaStream_t of the current device) instead of the legacy
+ * default stream, so that it does not serialise with other streams of the
+ * caller; the call synchronises `stream` before returning (the host tables
+ * are released afterwards).  Same arguments and errors as kfbim_setup. */
+int kfbim_setup_async(const kfbim_geometry* geom, const kfbim_grid* grid,
+                      const kfbim_options* opt, void* stream, kfbim_ctx** ctx);
 
 /* Host-only variant of kfbim_setup: builds the control points and every table
  * on the host and touches no GPU (for inspection and host-side tests).  The
@@ -197,6 +224,23 @@ int kfbim_table_sizes(const kfbim_ctx* ctx, int64_t* fit_nnz, int64_t* corr_rows
  * axis (0..2), primary flag (0/1). */
 int kfbim_points(const kfbim_ctx* ctx, double* xyz_host, int32_t* comp_host,
                  int32_t* axis_host, int32_t* primary_host);
+
+/* The control points of component comp (1..3) that carry density unknowns
+ * (Sec. 3: the intersections of Gamma with the grid lines of u^(comp)'s own
+ * grid, the primary ones, Alg. 1 step 1), in the order of the comp-th block of
+ * every density and boundary-data vector: g_dev of kfbim_solve is
+ * [g^(1) at control_points(1) | g^(2) at control_points(2) | g^(3) at
+ * control_points(3)].  *n receives the count; xyz_host [n*3] and normal_host
+ * [n*3] (outward unit normals, Sec. 2) are filled when non-null (query the
+ * count first with both null).  Host memory; works on host-only contexts. */
+int kfbim_control_points(const kfbim_ctx* ctx, int comp, int64_t* n, double* xyz_host,
+                         double* normal_host);
+
+/* The points where the forcing f^+ is needed for the jump conditions (Sec. 4.3:
+ * [[f]] enters the second-order jumps at every control point, primary or not):
+ * all n_points control points in the canonical order of fpts_dev.  *n receives
+ * n_points; xyz_host [n*3] is filled when non-null.  Host memory. */
+int kfbim_jump_points(const kfbim_ctx* ctx, int64_t* n, double* xyz_host);
 
 /* Outward unit normal grad F / |grad F| at every control point (Sec. 2),
  * normal_host [n_points*3] in the order of kfbim_points; host memory. */
@@ -291,6 +335,29 @@ int kfbim_solve_batch(kfbim_ctx* ctx, int B, const double* g_dev, const double* 
 int kfbim_profile(kfbim_ctx* ctx, int enable, double* ms64, int64_t* launches64,
                   double* bytes64, double* ms32, int64_t* launches32, double* bytes32);
 
+/* Kernel classes of kfbim_profile_kernels. */
+typedef enum {
+  KFBIM_KCLASS_TRANSFORM_FP64 = 0,  /* one-axis transform passes, FP64 */
+  KFBIM_KCLASS_TRANSFORM_FP32 = 1,  /* one-axis transform passes, FP32 (FFT or tensor core) */
+  KFBIM_KCLASS_CG_ZFWD = 2,         /* slab CG: d = r + beta d, z transforms (5 N^3 floats) */
+  KFBIM_KCLASS_CG_XY = 3,           /* slab CG: xy planes of the three terms (4 N^3 floats) */
+  KFBIM_KCLASS_CG_ZINV = 4,         /* slab CG: inverse z transforms, d.q (4 N^3 floats) */
+  KFBIM_KCLASS_CG_UPDATE = 5,       /* slab CG: x, r update, r.r (6 N^3 floats) */
+  KFBIM_KCLASS_CG_VECTOR = 6,       /* staged CG: the three vector kernels (14 N^3 values) */
+  KFBIM_KCLASS_MAC_RESIDUAL = 7,    /* MIXED refinement: FP64 MAC residual (12 N^3 doubles) */
+  KFBIM_KCLASS_JUMPS = 8,           /* jump evaluation (fit rows, jump maps, jumps) */
+  KFBIM_KCLASS_COUNT = 9
+} kfbim_kernel_class;
+
+/* Per-class totals of the timing started by kfbim_profile(ctx, 1, ...):
+ * for k < n, ms[k] device milliseconds between CUDA events recorded on the
+ * call's stream around each launch group of class k, launches[k] kernels and
+ * bytes[k] algorithmic bytes (the values the class's kernels must read and
+ * write, counted once).  Classes >= KFBIM_KCLASS_COUNT read 0.  Output arrays
+ * are host memory, nullable.  While timing is on, the Schur CG runs without
+ * CUDA graphs.  Synchronises the device. */
+int kfbim_profile_kernels(kfbim_ctx* ctx, int n, double* ms, int64_t* launches, double* bytes);
+
 /* Stage entry points (same kernels as the solve path, exposed for parity tests).
  * kfbim_jumps: jump values at every control point (Sec. 4.3), layout
  *   J_dev[12 * n_points] slot-major: slot s of point y at s*n_points + y with
@@ -344,13 +411,19 @@ int kfbim_poisson(kfbim_ctx* ctx, int c, const double* r_dev, double* u_dev, voi
  * alpha = mu N^3 (Stokes), or + c d (Navier); d_dev, q_dev N^3 doubles (cells). */
 int kfbim_schur_apply(kfbim_ctx* ctx, const double* d_dev, double* q_dev, void* stream);
 
+/* The FP32 Schur operator of the slab CG iteration (test entry point of its
+ * kernels; MIXED contexts with N = 32, 64 or 128 and transforms AUTO or FFT,
+ * else E_INVALID): q = (1/mu) sum_c G_c^T (-Delta_c)^{-1} G_c d (+ c d for
+ * Navier), without the rank-one term of kfbim_schur_apply; d_dev, q_dev N^3
+ * floats (cells, must not alias).  Synchronises the stream. */
+int kfbim_schur_apply_f32(kfbim_ctx* ctx, const float* d_dev, float* q_dev, void* stream);
+
 /* Allocation-free variant of kfbim_poisson, for callers that may not allocate
  * device memory: code that runs under a memory manager owning the whole device
  * heap (a caching allocator that reserved HBM up front, or a host application
  * that hands its plug-ins only buffers it allocated itself), and loops where
  * cudaMalloc's implicit device synchronisation is not acceptable.  The paper has
- * no counterpart: this is a deployment convenience around the FFT Poisson solve
- * of Sec. 4.2 item ii.
+ * no counterpart: it is a deployment convenience around the FFT Poisson solve.
  *
  * Solves -Delta_h u = r on face grid c (1..3) of an N^3 grid on [lo, hi]^3,
  * N a power of two with 16 <= N <= 64; r_dev and u_dev are caller-owned N^3
@@ -358,16 +431,20 @@ int kfbim_schur_apply(kfbim_ctx* ctx, const double* d_dev, double* q_dev, void* 
  * cudaMalloc/cudaFree and no allocating library routine: the scratch (two N^3
  * fields) and the transform tables live in file-scope static device arrays of
  * 4 MiB + 2 KiB, which every GPU that loads the library holds until exit.
- * The first call on a device resolves the arrays' device addresses
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Outside a stream capture every call looks up the arrays' device addresses
+ * (cudaGetSymbolAddress, no allocation); under capture the addresses of the
+ * last call on that device are used, so make a first call on each device
+ * before any stream capture (a first call under capture returns
+ * KFBIM_E_INVALID).
  * All calls share the arrays: calls that overlap on the GPU (different
  * streams, or several host threads on one device) race and corrupt each
  * other's results; calls on one stream are ordered and each call rewrites the
  * whole scratch and tables before reading them, so nothing from a previous
  * call leaks into the next.
  * Errors: KFBIM_E_INVALID for a bad argument or N > 64 (a message names the
- * limit on stderr), KFBIM_E_CUDA if the symbols cannot be resolved or a launch
- * fails. */
+ * limit on stderr), KFBIM_E_CUDA if the symbols cannot be resolved or one of
+ * this call's launches fails (an error left pending by earlier, unrelated work
+ * is neither reported nor cleared). */
 int kfbim_poisson_noalloc(int c, int N, double lo, double hi, const double* r_dev,
                           double* u_dev, void* stream);
 

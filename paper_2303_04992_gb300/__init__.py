@@ -13,6 +13,9 @@ from .autograd import solve_velocity  # noqa: F401
 
 FP64 = 0
 MIXED = 1
-XF_AUTO = 0      # FP32 axis passes: timed choice per stage kind
-XF_FFT = 1       # four-step FFT passes
-XF_TENSOR = 2    # tcgen05 transform-matrix GEMM passes (N = 128)
+FP32 = 2         # FP32 grid solve without FP64 refinement (matvec ~1e-6)
+MIXED_TF32 = 3   # MIXED on tensor-core (3xTF32) transform passes, N = 128
+XF_AUTO = 0      # slab CG; one-axis passes: timed choice per stage kind
+XF_FFT = 1       # slab CG; four-step FFT one-axis passes
+XF_TENSOR = 2    # tcgen05 transform-matrix GEMM passes (N = 128), CG included
+XF_STAGED = 3    # one-axis FFT passes everywhere, CG included

@@ -53,6 +53,10 @@ SYMBOLS = {
                             ctypes.POINTER(c_void_p)]),
     "kfbim_setup_host": (c_int, [ctypes.POINTER(Geometry), ctypes.POINTER(Grid),
                                  ctypes.POINTER(Options), ctypes.POINTER(c_void_p)]),
+    "kfbim_setup_async": (c_int, [ctypes.POINTER(Geometry), ctypes.POINTER(Grid), ctypes.POINTER(Options),
+                                  c_void_p, ctypes.POINTER(c_void_p)]),
+    "kfbim_control_points": (c_int, [c_void_p, c_int, ctypes.POINTER(c_int64), c_void_p, c_void_p]),
+    "kfbim_jump_points": (c_int, [c_void_p, ctypes.POINTER(c_int64), c_void_p]),
     "kfbim_destroy": (c_int, [c_void_p]),
     "kfbim_last_error": (ctypes.c_char_p, [c_void_p]),
     "kfbim_sizes": (c_int, [c_void_p, ctypes.POINTER(c_int64), ctypes.POINTER(c_int64),
@@ -80,10 +84,12 @@ SYMBOLS = {
     "kfbim_trace": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "kfbim_poisson": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     "kfbim_schur_apply": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "kfbim_schur_apply_f32": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "kfbim_poisson_noalloc": (c_int, [c_int, c_int, c_double, c_double, c_void_p, c_void_p,
                                       c_void_p]),
     "kfbim_profile": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                               c_void_p]),
+    "kfbim_profile_kernels": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
 }
 
 _lib = None
@@ -244,10 +250,16 @@ class Solver:
         self.options = o
         gr = Grid(int(grid["N"]), float(grid["lo"]), float(grid["hi"]))
         ctx = c_void_p()
-        fn = lib.kfbim_setup if device else lib.kfbim_setup_host
         errors = []
         gm = _geometry(geom, errors)   # holds the ctypes callbacks of a "callback" geometry during setup
-        st = fn(ctypes.byref(gm), ctypes.byref(gr), ctypes.byref(o), ctypes.byref(ctx))
+        if device:
+            # device work of the setup on torch's current stream
+            import torch
+            stream = c_void_p(torch.cuda.current_stream(self._device).cuda_stream)
+            st = lib.kfbim_setup_async(ctypes.byref(gm), ctypes.byref(gr), ctypes.byref(o), stream,
+                                       ctypes.byref(ctx))
+        else:
+            st = lib.kfbim_setup_host(ctypes.byref(gm), ctypes.byref(gr), ctypes.byref(o), ctypes.byref(ctx))
         if errors:
             if st == 0:
                 lib.kfbim_destroy(ctx)
@@ -296,6 +308,26 @@ class Solver:
         self._check(self._lib.kfbim_points(self._ctx, _np_ptr(xyz, 3 * n, "xyz"), _np_ptr(comp, n, "comp", np.int32),
                                            _np_ptr(axis, n, "axis", np.int32), _np_ptr(prim, n, "prim", np.int32)))
         return xyz, comp, axis, prim.astype(bool)
+
+    def control_points(self, comp):
+        """(xyz (n, 3), outward normals (n, 3)) of component comp's density
+        unknowns, in the order of that component's block of g and phi."""
+        n = c_int64()
+        self._check(self._lib.kfbim_control_points(self._ctx, comp, ctypes.byref(n), None, None))
+        xyz = np.zeros((n.value, 3))
+        nrm = np.zeros((n.value, 3))
+        self._check(self._lib.kfbim_control_points(self._ctx, comp, ctypes.byref(n),
+                                                   _np_ptr(xyz, 3 * n.value, "xyz"),
+                                                   _np_ptr(nrm, 3 * n.value, "normal")))
+        return xyz, nrm
+
+    def jump_points(self):
+        """(n_points, 3) coordinates where f is needed (fpts of solve)."""
+        n = c_int64()
+        self._check(self._lib.kfbim_jump_points(self._ctx, ctypes.byref(n), None))
+        xyz = np.zeros((n.value, 3))
+        self._check(self._lib.kfbim_jump_points(self._ctx, ctypes.byref(n), _np_ptr(xyz, 3 * n.value, "xyz")))
+        return xyz
 
     def normals(self):
         """Outward unit normals (n_points, 3) at the control points."""
@@ -427,8 +459,26 @@ class Solver:
         return {"fp64": (v[0].value, v[1].value, v[2].value),
                 "fp32": (v[3].value, v[4].value, v[5].value)}
 
+    KERNEL_CLASSES = ("transform_fp64", "transform_fp32", "cg_zfwd", "cg_xy", "cg_zinv", "cg_update",
+                      "cg_vector", "mac_residual", "jumps")
+
+    def profile_kernels(self):
+        """{class: (ms, launches, algorithmic bytes)} since profile(True)."""
+        n = len(self.KERNEL_CLASSES)
+        ms, bytes_ = (c_double * n)(), (c_double * n)()
+        launches = (c_int64 * n)()
+        self._check(self._lib.kfbim_profile_kernels(self._ctx, n, ms, launches, bytes_))
+        return {k: (ms[i], launches[i], bytes_[i]) for i, k in enumerate(self.KERNEL_CLASSES)}
+
     def schur_apply(self, d, q):
         N3 = self.N ** 3
         self._check(self._lib.kfbim_schur_apply(self._ctx, self._d(d, N3, "d"), self._d(q, N3, "q"),
                                                 self._stream()))
+        return q
+
+    def schur_apply_f32(self, d, q):
+        """FP32 Schur operator of the slab CG (no rank-one term): d, q float32."""
+        N3 = self.N ** 3
+        self._check(self._lib.kfbim_schur_apply_f32(self._ctx, self._d(d, N3, "d", "float32"),
+                                                    self._d(q, N3, "q", "float32"), self._stream()))
         return q

@@ -1,9 +1,10 @@
 """In-tree build of the KFBI CUDA library (libkfbim.so) for sm_103a.
 
-Two translation units compiled in parallel: the host setup (g++, FP
-contraction off so that every discrete choice of the setup is reproducible
-across x86 and Arm hosts) and the CUDA solver (nvcc), linked by nvcc.
+Translation units compiled in parallel: the host setup (g++, FP contraction
+off so that every discrete choice of the setup is reproducible across x86 and
+Arm hosts), the CUDA solver and the slab CG kernels (nvcc), linked by nvcc.
 """
+import hashlib
 import os
 import shutil
 import subprocess
@@ -35,28 +36,46 @@ def sources():
     return sorted(os.path.join(SRC, f) for f in os.listdir(SRC))
 
 
+def source_digest():
+    """SHA-256 over the sources and the header (names and contents)."""
+    h = hashlib.sha256()
+    for path in sources() + [os.path.join(os.path.dirname(HERE), "include", "kfbim.h")]:
+        h.update(os.path.basename(path).encode())
+        with open(path, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
 def build(force=False, verbose=False):
-    """Compile libkfbim.so if any source is newer than it; return its path."""
+    """Compile libkfbim.so unless it was built from the current sources (a
+    digest of them, taken before compiling, is kept beside the library);
+    return its path."""
     os.makedirs(OUT, exist_ok=True)
-    if not force and os.path.exists(LIB):
-        t = os.path.getmtime(LIB)
-        inc = os.path.join(os.path.dirname(HERE), "include", "kfbim.h")
-        if all(os.path.getmtime(s) <= t for s in sources() + [inc]):
-            return LIB
+    stamp = os.path.join(OUT, "sources.sha256")
+    digest = source_digest()
+    if not force and os.path.exists(LIB) and os.path.exists(stamp):
+        with open(stamp) as f:
+            if f.read().strip() == digest:
+                return LIB
     nvcc = _nvcc()
     inc = "-I" + os.path.join(os.path.dirname(HERE), "include")
     o_setup = os.path.join(OUT, "setup.o")
-    o_cu = os.path.join(OUT, "kfbim.o")
+    cu_units = ["kfbim", "slab"]
+    objs = [os.path.join(OUT, u + ".o") for u in cu_units]
     cmds = [
         ["g++", "-std=c++17", "-O2", "-fPIC", "-ffp-contract=off", inc, "-c",
          os.path.join(SRC, "setup.cpp"), "-o", o_setup],
+    ] + [
         [nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", inc,
-         "-Xptxas", "-v" if verbose else "-O3", "-c", os.path.join(SRC, "kfbim.cu"), "-o", o_cu],
+         "-Xptxas", "-v" if verbose else "-O3", "-c", os.path.join(SRC, u + ".cu"), "-o", o]
+        for u, o in zip(cu_units, objs)
     ]
-    with ThreadPoolExecutor(2) as ex:
+    with ThreadPoolExecutor(len(cmds)) as ex:
         logs = list(ex.map(_run, cmds))
-    logs.append(_run([nvcc, ARCH, "-shared", o_setup, o_cu, "-o", LIB + ".tmp", "-lcudart"]))
+    logs.append(_run([nvcc, ARCH, "-shared", o_setup] + objs + ["-o", LIB + ".tmp", "-lcudart"]))
     os.replace(LIB + ".tmp", LIB)
+    with open(stamp, "w") as f:
+        f.write(digest + "\n")
     if verbose:
         sys.stdout.write("".join(logs))
     return LIB

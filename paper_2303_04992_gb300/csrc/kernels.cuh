@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "cg_common.cuh"
+
 namespace kfbim {
 
 constexpr int RED_THREADS = 256;
@@ -253,23 +255,6 @@ __global__ void k_mac_residual(const double* __restrict__ f, const double* __res
 }
 
 // ------------------------------------------------------------ reductions
-// Dot products of the Schur CG (Sec. 4.2) and of GMRES (Alg. 1 step 3).
-template <typename Ta>
-__device__ __forceinline__ double block_sum(double v, double* sh) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) sh[w] = v;
-  __syncthreads();
-  v = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
-  if (w == 0) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  }
-  __syncthreads();
-  return v;
-}
-
 // partial[blockIdx.x] = sum x*y (y == nullptr: sum x; x == y allowed)
 template <typename Ta, typename Tb>
 __global__ void k_dot_partial(const Ta* __restrict__ x, const Tb* __restrict__ y, int64_t n,
@@ -294,43 +279,6 @@ __global__ void k_sum_partials(const double* __restrict__ partial, int nb, doubl
 }
 
 // ----------------------------------------------------------------- CG
-// Unpreconditioned CG on the Schur complement (Sec. 4.2, Eq. linearS1).
-// Device scalars of one CG run on (S + 1 1^T rank1) x = b.  Every reduction
-// is finished by the last block to arrive (fixed-order sum of the block
-// partials), which also updates the scalars, so one CG iteration is the
-// Schur apply plus three kernels and needs no host round trip.  Once
-// rr <= stop the iteration is a no-op (done = 1): alpha = beta = 0 and the
-// transform passes of S d return immediately.
-struct CGScalars {
-  double rr, bb, stop, dq, alpha, beta, sumd, rank1, cdiag;
-  int done, iters;
-  unsigned int ticket[3];
-};
-
-// Sum of the gridDim.x partials by the last block; returns true in that block.
-__device__ __forceinline__ bool last_block_sum(double v, double* __restrict__ partial,
-                                               unsigned int* ticket, double* sh, double* out) {
-  __shared__ bool is_last;
-  v = block_sum<double>(v, sh);
-  if (threadIdx.x == 0) {
-    partial[blockIdx.x] = v;
-    __threadfence();
-    const unsigned int t = atomicAdd(ticket, 1u);
-    is_last = (t == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!is_last) return false;
-  __threadfence();
-  double s = 0.0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s += ((volatile double*)partial)[b];
-  s = block_sum<double>(s, sh);
-  if (threadIdx.x == 0) {
-    *out = s;
-    *ticket = 0u;
-  }
-  return true;
-}
-
 // q_S = q + q2 + q3 + cdiag d (the three component terms and, for the
 // Navier system, the c p block; summed in place into q);
 // dq = d . q_S; alpha = rr / (dq + sumd^2 rank1)
@@ -342,14 +290,14 @@ __global__ void k_cg_alpha(const T* __restrict__ d, T* __restrict__ q, const T* 
   __shared__ double total;
   if (s->done) return;
   const T cd = T(s->cdiag);
-  T acc = T(0);   // a thread's few terms in T; FP64 from the block sum on
+  CgAcc<T> acc;   // a thread's few terms, compensated in FP32 (MIXED); FP64 from the block sum on
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x) {
     const T qs = q[e] + q2[e] + q3[e] + cd * d[e];
     q[e] = qs;
-    acc += d[e] * qs;
+    acc.add_prod(d[e], qs);
   }
-  if (last_block_sum(double(acc), partial, &s->ticket[0], sh, &total) && threadIdx.x == 0) {
+  if (last_block_sum(acc.value(), partial, &s->ticket[0], sh, &total) && threadIdx.x == 0) {
     const double den = total + s->sumd * s->sumd * s->rank1;
     s->dq = den;
     s->alpha = (den != 0.0) ? s->rr / den : 0.0;
@@ -364,20 +312,19 @@ __global__ void k_cg_update(T* __restrict__ x, T* __restrict__ r, const T* __res
   __shared__ double sh[32];
   __shared__ double total;
   if (s->done) return;
-  // element arithmetic in T (FP32 in MIXED); a thread's few squares summed in
-  // T, the block and grid sums in FP64 (FP64 per element would make this
-  // kernel FP64-ALU-bound on a GPU whose FP64 rate is a small fraction of FP32)
+  // element arithmetic in T (FP32 in MIXED); a thread's few squares summed
+  // with compensation (CgAcc), the block and grid sums in FP64
   const T a = T(s->alpha);
   const T c1 = T(s->sumd * s->rank1);
-  T acc = T(0);
+  CgAcc<T> acc;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x) {
     const T rv = r[e] - a * (q[e] + c1);
     x[e] = x[e] + a * d[e];
     r[e] = rv;
-    acc += rv * rv;
+    acc.add_prod(rv, rv);
   }
-  if (last_block_sum(double(acc), partial, &s->ticket[1], sh, &total) && threadIdx.x == 0) {
+  if (last_block_sum(acc.value(), partial, &s->ticket[1], sh, &total) && threadIdx.x == 0) {
     s->beta = (s->rr != 0.0) ? total / s->rr : 0.0;
     s->rr = total;
     s->iters += 1;
@@ -392,14 +339,14 @@ __global__ void k_cg_direction(T* __restrict__ d, const T* __restrict__ r, int64
   __shared__ double total;
   if (s->done) return;
   const T b = T(s->beta);
-  T acc = T(0);
+  CgAcc<T> acc;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x) {
     const T v = r[e] + b * d[e];
     d[e] = v;
-    acc += v;
+    acc.add(v);
   }
-  if (last_block_sum(double(acc), partial, &s->ticket[2], sh, &total) && threadIdx.x == 0) {
+  if (last_block_sum(acc.value(), partial, &s->ticket[2], sh, &total) && threadIdx.x == 0) {
     s->sumd = total;
     if (!(s->rr > s->stop)) s->done = 1;
   }
@@ -428,14 +375,14 @@ __global__ void k_cg_alpha_b(const __grid_constant__ CgBatchArgs<T> A, int64_t n
   T* q = A.q[b];
   const T *q2 = A.q2[b], *q3 = A.q3[b];
   const T cd = T(s->cdiag);
-  T acc = T(0);
+  CgAcc<T> acc;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x) {
     const T qs = q[e] + q2[e] + q3[e] + cd * d[e];
     q[e] = qs;
-    acc += d[e] * qs;
+    acc.add_prod(d[e], qs);
   }
-  if (last_block_sum(double(acc), A.partial[b], &s->ticket[0], sh, &total) && threadIdx.x == 0) {
+  if (last_block_sum(acc.value(), A.partial[b], &s->ticket[0], sh, &total) && threadIdx.x == 0) {
     const double den = total + s->sumd * s->sumd * s->rank1;
     s->dq = den;
     s->alpha = (den != 0.0) ? s->rr / den : 0.0;
@@ -453,15 +400,15 @@ __global__ void k_cg_update_b(const __grid_constant__ CgBatchArgs<T> A, int64_t 
   const T *d = A.d[b], *q = A.q[b];
   const T a = T(s->alpha);
   const T c1 = T(s->sumd * s->rank1);
-  T acc = T(0);
+  CgAcc<T> acc;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x) {
     const T rv = r[e] - a * (q[e] + c1);
     x[e] = x[e] + a * d[e];
     r[e] = rv;
-    acc += rv * rv;
+    acc.add_prod(rv, rv);
   }
-  if (last_block_sum(double(acc), A.partial[b], &s->ticket[1], sh, &total) && threadIdx.x == 0) {
+  if (last_block_sum(acc.value(), A.partial[b], &s->ticket[1], sh, &total) && threadIdx.x == 0) {
     s->beta = (s->rr != 0.0) ? total / s->rr : 0.0;
     s->rr = total;
     s->iters += 1;
@@ -478,14 +425,14 @@ __global__ void k_cg_direction_b(const __grid_constant__ CgBatchArgs<T> A, int64
   T* d = A.d[b];
   const T* r = A.r[b];
   const T be = T(s->beta);
-  T acc = T(0);
+  CgAcc<T> acc;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x) {
     const T v = r[e] + be * d[e];
     d[e] = v;
-    acc += v;
+    acc.add(v);
   }
-  if (last_block_sum(double(acc), A.partial[b], &s->ticket[2], sh, &total) && threadIdx.x == 0) {
+  if (last_block_sum(acc.value(), A.partial[b], &s->ticket[2], sh, &total) && threadIdx.x == 0) {
     s->sumd = total;
     if (!(s->rr > s->stop)) s->done = 1;
   }

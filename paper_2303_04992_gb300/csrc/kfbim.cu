@@ -29,6 +29,7 @@
 #include "transforms.cuh"
 #include "transforms2.cuh"
 #include "tc_pass.cuh"
+#include "slab.h"
 
 using namespace kfbim;
 
@@ -63,6 +64,14 @@ struct kfbim_ctx {
   float* d_tc_mats = nullptr;
   int* d_tc_err = nullptr;
   int xf_plain = 0, xf_fused = 0;
+  // MIXED Schur CG as the four-kernel z-pencil / xy-slab iteration (slab.cuh)
+  bool slab = false;
+  // precision requested at setup (FP32 and MIXED_TF32 run as MIXED internally:
+  // FP32 without the FP64 refinement sweeps, MIXED_TF32 on tensor-core passes)
+  int precision_requested = KFBIM_FP64;
+  bool fp32_only = false;
+  // stream of the setup's device work (kfbim_setup_async; null: legacy stream)
+  cudaStream_t setup_stream = nullptr;
   int num_sms = 152;
   float tune_ms[4] = {0, 0, 0, 0};   // plain FFT, plain GEMM, fused FFT, fused GEMM (ms per stage)
   // FP64 workspace
@@ -90,14 +99,15 @@ struct kfbim_ctx {
   cudaGraphExec_t cg_exec[2] = {nullptr, nullptr};
   int64_t cg_graph_kernels[2] = {0, 0};
   bool use_graphs = true;
-  // optional per-kernel timing of the transform passes (kfbim_profile)
+  // optional per-kernel timing (kfbim_profile, kfbim_profile_kernels): CUDA
+  // events around launches, totals per kernel class (kfbim_kernel_class)
   bool prof = false;
   std::vector<cudaEvent_t> prof_ev;    // pairs (start, stop)
   int prof_used = 0;
-  double prof_ms[2] = {0, 0};          // total ms: FP64 passes, FP32 passes
-  int64_t prof_count[2] = {0, 0};
-  std::vector<int> prof_tag;           // precision slot of each event pair
-  double prof_bytes[2] = {0, 0};       // algorithmic bytes moved by those launches
+  double prof_ms[KFBIM_KCLASS_COUNT] = {};
+  int64_t prof_count[KFBIM_KCLASS_COUNT] = {};
+  std::vector<int> prof_tag;           // kernel class of each event pair
+  double prof_bytes[KFBIM_KCLASS_COUNT] = {};   // algorithmic bytes moved by those launches
   int64_t fit_nnz = 0, corr_nnz = 0;
   // batch of instances on this geometry (kfbim_solve_batch), allocated on demand
   struct Slot {
@@ -147,10 +157,14 @@ T* dalloc(kfbim_ctx* c, size_t count) {
   return static_cast<T*>(p);
 }
 
+// Copies a host table to new device memory, ordered on the setup stream
+// (the caller's stream for kfbim_setup_async); setup synchronises that stream
+// before the host tables are released.
 template <typename T>
 T* upload(kfbim_ctx* c, const std::vector<T>& v) {
   T* d = dalloc<T>(c, v.size());
-  if (!v.empty()) CK(cudaMemcpy(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  if (!v.empty())
+    CK(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, c->setup_stream));
   return d;
 }
 
@@ -359,7 +373,7 @@ void stage_list(kfbim_ctx* c, const std::vector<Job>& list, cudaStream_t s, cons
   check_launch();
   if (prof) {
     CK(cudaEventRecord(c->prof_ev[c->prof_used + 1], s));
-    const int slot = sizeof(T) == 8 ? 0 : 1;
+    const int slot = sizeof(T) == 8 ? KFBIM_KCLASS_TRANSFORM_FP64 : KFBIM_KCLASS_TRANSFORM_FP32;
     c->prof_tag[c->prof_used / 2] = slot;
     c->prof_used += 2;
     c->prof_count[slot] += launches;
@@ -370,6 +384,24 @@ void stage_list(kfbim_ctx* c, const std::vector<Job>& list, cudaStream_t s, cons
 template <typename Tin, typename T, typename Tout>
 void stage(kfbim_ctx* c, std::initializer_list<Job> list, cudaStream_t s, const int* skip = nullptr) {
   stage_list<Tin, T, Tout>(c, std::vector<Job>(list), s, skip);
+}
+
+// Timing of one launch group of a kernel class: prof_begin records the start
+// event (returns -1 when profiling is off or the event pool is full),
+// prof_end the stop event and the group's launches and algorithmic bytes.
+int prof_begin(kfbim_ctx* c, cudaStream_t s) {
+  if (!c->prof || c->prof_used + 2 > (int)c->prof_ev.size()) return -1;
+  CK(cudaEventRecord(c->prof_ev[c->prof_used], s));
+  return c->prof_used;
+}
+
+void prof_end(kfbim_ctx* c, cudaStream_t s, int at, int cls, int launches, double bytes) {
+  if (at < 0) return;
+  CK(cudaEventRecord(c->prof_ev[at + 1], s));
+  c->prof_tag[at / 2] = cls;
+  c->prof_used = at + 2;
+  c->prof_count[cls] += launches;
+  c->prof_bytes[cls] += bytes;
 }
 
 // Fold recorded event pairs into the totals (the stream must be idle).
@@ -492,10 +524,32 @@ CgWs<float> ws32(kfbim_ctx* c) { return {c->fx, c->fr, c->fd, c->fq, c->fq2, c->
 template <typename T>
 void cg_iteration(kfbim_ctx* c, const CgWs<T>& w, cudaStream_t s) {
   const int64_t n = c->N3;
+  if constexpr (std::is_same<T, float>::value) {
+    if (c->slab) {
+      // d = r + beta d and the z transforms; the xy planes; the inverse z
+      // transforms with d.q; the vector update with r.r (slab.cuh)
+      SlabCg a{c->N, w.x, w.r, w.d, w.q, w.T6, w.T6 + n, c->d_twc32, c->d_q32, c->d_s2f,
+               (float)(1.0 / c->mu), c->cgs, c->partial};
+      if (c->prof) {
+        for (int k = 0; k < 4; ++k) {
+          const int at = prof_begin(c, s);
+          g_launches += slab_launch(k, a, s);
+          prof_end(c, s, at, KFBIM_KCLASS_CG_ZFWD + k, 1, (double)kSlabValues[k] * n * sizeof(float));
+        }
+      } else {
+        g_launches += slab_cg_iteration(a, s);
+      }
+      check_launch();
+      return;
+    }
+  }
   schur_apply3<T>(c, w.d, w.q, w.q2, w.q3, w.T6, s, &c->cgs->done);
+  const int at = prof_begin(c, s);
   k_cg_alpha<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(w.d, w.q, w.q2, w.q3, n, c->cgs, c->partial); ++g_launches;
   k_cg_update<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(w.x, w.r, w.d, w.q, n, c->cgs, c->partial); ++g_launches;
   k_cg_direction<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(w.d, w.r, n, c->cgs, c->partial); ++g_launches;
+  // values moved: alpha 5 N^3 (d, q, q2, q3 read, q written), update 6, direction 3
+  prof_end(c, s, at, KFBIM_KCLASS_CG_VECTOR, 3, 14.0 * n * sizeof(T));
   check_launch();
 }
 
@@ -614,7 +668,11 @@ int grid_solve_mixed(kfbim_ctx* c, cudaStream_t s) {
   int status = KFBIM_OK;
   for (int sweep = 0;; ++sweep) {
     if (sweep > 0) {
+      if (c->fp32_only) break;   // FP32: one correction solve, no FP64 residual
+      const int at = prof_begin(c, s);
       k_mac_residual<<<grid_for(4 * N3), 256, 0, s>>>(f, g, gmean, c->u, c->p, c->lg, c->h, c->mu, c->cpen, resf, resg); ++g_launches;
+      // reads f, g, u, p (8 N^3 doubles), writes rf, rg (4 N^3)
+      prof_end(c, s, at, KFBIM_KCLASS_MAC_RESIDUAL, 1, 12.0 * N3 * sizeof(double));
       check_launch();
       dot(c, resf, resf, 4 * N3, sc, 1.0, s);
       const double r2 = read_scalar(c, sc, s);
@@ -654,9 +712,14 @@ int grid_solve_mixed(kfbim_ctx* c, cudaStream_t s) {
 int interface_solve(kfbim_ctx* c, const double* phi, const double* fpts, const double* fgrid,
                     cudaStream_t s) {
   const int64_t n = c->n_all;
+  const int at = prof_begin(c, s);
   k_jumps<<<(unsigned)((n + JB - 1) / JB), 3 * JB, 0, s>>>(
       phi, fpts, n, c->d_comp, c->d_pid, c->d_fit_ptr, c->d_fit_col, c->d_fit_w, c->fit_nnz, c->d_jmap,
       c->J); ++g_launches;
+  // fit rows (column index, six weights, the density value), the 11 x 18 jump
+  // map, the forcing and the twelve jump slots per point
+  prof_end(c, s, at, KFBIM_KCLASS_JUMPS, 1,
+           (double)c->fit_nnz * (4 + 6 * 8 + 8) + (double)n * 8 * (11 * 18 + 3 * (fpts ? 1 : 0) + 12));
   check_launch();
   k_rhs_fill<<<grid_for(4 * c->N3), 256, 0, s>>>(fgrid, c->d_side[1], c->d_side[2], c->d_side[3],
                                                   c->lg, c->rhs); ++g_launches;
@@ -1084,7 +1147,7 @@ void fill_tables(kfbim_ctx* c) {
   c->cq = dalloc<double>(c, N3);
   c->rres = dalloc<double>(c, N3);
   c->zero_phi = dalloc<double>(c, std::max<int64_t>(1, t.n_prim));
-  CK(cudaMemset(c->zero_phi, 0, std::max<int64_t>(1, t.n_prim) * sizeof(double)));
+  CK(cudaMemsetAsync(c->zero_phi, 0, std::max<int64_t>(1, t.n_prim) * sizeof(double), c->setup_stream));
   c->partial = dalloc<double>(c, (size_t)RED_BLOCKS * 256);
   c->scal = dalloc<double>(c, 64);
   c->cgs = dalloc<CGScalars>(c, 1);
@@ -1113,13 +1176,21 @@ void fill_tables(kfbim_ctx* c) {
   void* ph = nullptr;
   CK(cudaMallocHost(&ph, sizeof(double) * 256));
   c->pinned = static_cast<double*>(ph);
-  if (c->opt.precision == KFBIM_MIXED && N == TC_N && c->opt.transforms != KFBIM_XF_FFT) {
+  if (c->opt.precision == KFBIM_MIXED && slab_supported(N) && c->opt.transforms != KFBIM_XF_TENSOR &&
+      c->opt.transforms != KFBIM_XF_STAGED) {
+    CK(slab_prepare(N));
+    c->slab = true;
+  }
+  // the autotuner below runs on the capture stream: the uploads come first
+  CK(cudaStreamSynchronize(c->setup_stream));
+  if (c->opt.precision == KFBIM_MIXED && N == TC_N &&
+      (c->opt.transforms == KFBIM_XF_AUTO || c->opt.transforms == KFBIM_XF_TENSOR)) {
     int dev = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev));
     c->d_tc_mats = upload(c, tc_matrices(N));
     c->d_tc_err = dalloc<int>(c, 1);
-    CK(cudaMemset(c->d_tc_err, 0, sizeof(int)));
+    CK(cudaMemsetAsync(c->d_tc_err, 0, sizeof(int), c->setup_stream));
     if (c->opt.transforms == KFBIM_XF_TENSOR) {
       c->xf_plain = c->xf_fused = 1;
     } else {
@@ -1228,29 +1299,49 @@ __global__ void k_na_tables(int N, C2<double>* tw, C2<double>* q, double* s2) {
   }
 }
 
-int noalloc_symbols(NoAllocSymbols** out) {
+// The device addresses of the static arrays on the current device.  Outside
+// a stream capture they are looked up on every call (a lookup, no
+// allocation), so a context torn down by cudaDeviceReset never leaves stale
+// addresses behind; inside a capture, where the lookup may have to load the
+// module and is not allowed, the addresses of the last call on this device
+// are used, and a first call under capture is rejected.
+int noalloc_symbols(cudaStream_t s, NoAllocSymbols** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return KFBIM_E_CUDA;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return KFBIM_E_CUDA;
   std::lock_guard<std::mutex> lock(g_na_mutex);
   NoAllocSymbols& d = g_na_dev[dev];
-  if (!d.ready) {
-    cudaError_t e = cudaGetSymbolAddress((void**)&d.scratch, g_na_scratch);
-    if (e == cudaSuccess) e = cudaGetSymbolAddress((void**)&d.tw, g_na_tw);
-    if (e == cudaSuccess) e = cudaGetSymbolAddress((void**)&d.q, g_na_q);
-    if (e == cudaSuccess) e = cudaGetSymbolAddress((void**)&d.s2, g_na_s2);
-    if (e != cudaSuccess) {
-      std::fprintf(stderr, "kfbim_poisson_noalloc: resolving the static scratch failed: %s\n",
-                   cudaGetErrorString(e));
-      return KFBIM_E_CUDA;
+  if (cap != cudaStreamCaptureStatusNone) {
+    if (!d.ready) {
+      std::fprintf(stderr, "kfbim_poisson_noalloc: the first call on a device must come before any "
+                           "stream capture\n");
+      return KFBIM_E_INVALID;
     }
-    d.ready = true;
+    *out = &d;
+    return KFBIM_OK;
   }
+  NoAllocSymbols f;
+  cudaError_t e = cudaGetSymbolAddress((void**)&f.scratch, g_na_scratch);
+  if (e == cudaSuccess) e = cudaGetSymbolAddress((void**)&f.tw, g_na_tw);
+  if (e == cudaSuccess) e = cudaGetSymbolAddress((void**)&f.q, g_na_q);
+  if (e == cudaSuccess) e = cudaGetSymbolAddress((void**)&f.s2, g_na_s2);
+  if (e != cudaSuccess) {
+    std::fprintf(stderr, "kfbim_poisson_noalloc: resolving the static scratch failed: %s\n",
+                 cudaGetErrorString(e));
+    return KFBIM_E_CUDA;
+  }
+  f.ready = true;
+  d = f;
   *out = &d;
   return KFBIM_OK;
 }
 
-void noalloc_pass(const NoAllocSymbols& d, int N, double h, const double* in, double* out, int axis,
-                  int t0, int t1, int wmode, int wc, cudaStream_t s) {
+// One pass of the allocation-free Poisson solve; returns the launch's own
+// status (cudaLaunchKernel reports it directly, so an error left behind by
+// unrelated earlier work is neither reported as this call's nor cleared).
+cudaError_t noalloc_pass(const NoAllocSymbols& d, int N, double h, const double* in, double* out, int axis,
+                         int t0, int t1, int wmode, int wc, cudaStream_t s) {
   PassArgs a{};  // value-initialised: every field, skip included, starts at zero
   a.N = N;
   a.axis = axis;
@@ -1268,8 +1359,12 @@ void noalloc_pass(const NoAllocSymbols& d, int N, double h, const double* in, do
   // 48 KiB default; the kernel's limit may only have been raised by other
   // paths of this library (raise_dynamic_smem never lowers it)
   const size_t smem = pass_smem_bytes(N, sizeof(double));
-  k_axis_pass<double, double, double><<<(unsigned)(N * N / LPC), PASS_THREADS, smem, s>>>(
-      in, out, a, d.tw, d.q, d.s2);
+  const C2<double>* tw = d.tw;
+  const C2<double>* q = d.q;
+  const double* s2 = d.s2;
+  void* args[] = {(void*)&in, (void*)&out, (void*)&a, (void*)&tw, (void*)&q, (void*)&s2};
+  return cudaLaunchKernel((const void*)k_axis_pass<double, double, double>, dim3((unsigned)(N * N / LPC)),
+                          dim3(PASS_THREADS), args, smem, s);
 }
 }  // namespace
 
@@ -1475,6 +1570,7 @@ void grid_solve_batch(kfbim_ctx* c, const std::vector<int>& act, cudaStream_t s)
     if (ref2[q] > 0.0) live.push_back(act[q]);
   for (int sweep = 0; !live.empty(); ++sweep) {
     if (sweep > 0) {
+      if (c->fp32_only) break;   // FP32: one correction solve, no FP64 residual
       for (int b : live) {
         const kfbim_ctx::Slot& w = c->bs[b];
         k_mac_residual<<<grid_for(4 * N3), 256, 0, s>>>(w.rhs, w.rhs + 3 * N3, c->bscal + 8 * b, w.u, w.p,
@@ -1718,26 +1814,36 @@ void kfbim_default_options(kfbim_options* o) {
 }
 
 static int setup_common(const kfbim_geometry* geom, const kfbim_grid* grid, const kfbim_options* opt,
-                        kfbim_ctx** out, bool device) {
+                        kfbim_ctx** out, bool device, cudaStream_t stream = nullptr) {
   if (!out) return KFBIM_E_INVALID;
   *out = nullptr;
   if (!geom || !grid || !opt) return KFBIM_E_INVALID;
   const int N = grid->N;
   if (N < 16 || N > 256 || (N & (N - 1)) != 0 || !(grid->hi > grid->lo)) return KFBIM_E_INVALID;
   if (!(opt->mu > 0) || opt->gmres_max < 1 || opt->gmres_max > 200 || opt->cg_max < 1 ||
-      (opt->precision != KFBIM_FP64 && opt->precision != KFBIM_MIXED))
+      opt->precision < KFBIM_FP64 || opt->precision > KFBIM_MIXED_TF32)
     return KFBIM_E_INVALID;
+  if (opt->precision == KFBIM_MIXED_TF32 && N != TC_N) return KFBIM_E_INVALID;
   if (geom->kind < KFBIM_SPHERE || geom->kind > KFBIM_CALLBACK) return KFBIM_E_INVALID;
   if (geom->kind == KFBIM_CALLBACK && (!geom->F || !geom->derivs)) return KFBIM_E_INVALID;
   if (geom->kind == KFBIM_TORUS && !(geom->params[0] > 0.0 && geom->params[1] > geom->params[0]))
     return KFBIM_E_INVALID;
   if (opt->pde != KFBIM_STOKES && opt->pde != KFBIM_NAVIER) return KFBIM_E_INVALID;
-  if (opt->transforms < KFBIM_XF_AUTO || opt->transforms > KFBIM_XF_TENSOR) return KFBIM_E_INVALID;
+  if (opt->transforms < KFBIM_XF_AUTO || opt->transforms > KFBIM_XF_STAGED) return KFBIM_E_INVALID;
   if (opt->pde == KFBIM_NAVIER && !(opt->lambda >= 0.0 && opt->lambda + opt->mu > 0.0))
     return KFBIM_E_INVALID;
   std::unique_ptr<kfbim_ctx> c(new (std::nothrow) kfbim_ctx());
   if (!c) return KFBIM_E_OOM;
   c->opt = *opt;
+  c->precision_requested = opt->precision;
+  if (opt->precision == KFBIM_FP32) {
+    c->opt.precision = KFBIM_MIXED;
+    c->fp32_only = true;
+  } else if (opt->precision == KFBIM_MIXED_TF32) {
+    c->opt.precision = KFBIM_MIXED;
+    c->opt.transforms = KFBIM_XF_TENSOR;
+  }
+  c->setup_stream = stream;
   c->N = N;
   while ((1 << c->lg) < N) ++c->lg;
   c->N3 = (int64_t)N * N * N;
@@ -1770,6 +1876,7 @@ static int setup_common(const kfbim_geometry* geom, const kfbim_grid* grid, cons
     try {
       fill_tables(c.get());
       adjoint_tables(c.get());   // before the host fit and correction tables are released
+      CK(cudaStreamSynchronize(stream));   // every upload has left the host tables
     } catch (const CudaError& e) {
       std::fprintf(stderr, "kfbim_setup: %s\n", e.msg.c_str());
       // releases whatever was created so far (memory, pinned buffers, stream, graphs)
@@ -1800,6 +1907,35 @@ int kfbim_setup(const kfbim_geometry* geom, const kfbim_grid* grid, const kfbim_
 int kfbim_setup_host(const kfbim_geometry* geom, const kfbim_grid* grid, const kfbim_options* opt,
                      kfbim_ctx** out) {
   return setup_common(geom, grid, opt, out, false);
+}
+
+int kfbim_setup_async(const kfbim_geometry* geom, const kfbim_grid* grid, const kfbim_options* opt,
+                      void* stream, kfbim_ctx** out) {
+  return setup_common(geom, grid, opt, out, true, (cudaStream_t)stream);
+}
+
+int kfbim_control_points(const kfbim_ctx* c, int comp, int64_t* n, double* xyz, double* normal) {
+  if (!c || !n || comp < 1 || comp > 3) return KFBIM_E_INVALID;
+  const HostTables& t = c->host;
+  int64_t k = 0;
+  for (int64_t y = 0; y < t.n_all; ++y) {
+    if (!t.primary[y] || t.comp[y] != comp) continue;
+    for (int a = 0; a < 3; ++a) {
+      if (xyz) xyz[3 * k + a] = t.xyz[3 * y + a];
+      if (normal) normal[3 * k + a] = t.normal[3 * y + a];
+    }
+    ++k;
+  }
+  *n = k;
+  return KFBIM_OK;
+}
+
+int kfbim_jump_points(const kfbim_ctx* c, int64_t* n, double* xyz) {
+  if (!c || !n) return KFBIM_E_INVALID;
+  const HostTables& t = c->host;
+  *n = t.n_all;
+  if (xyz) std::memcpy(xyz, t.xyz.data(), (size_t)t.n_all * 3 * sizeof(double));
+  return KFBIM_OK;
 }
 
 int kfbim_table_sizes(const kfbim_ctx* c, int64_t* fit_nnz, int64_t* corr_rows, int64_t* corr_nnz) {
@@ -1958,6 +2094,29 @@ int kfbim_poisson(kfbim_ctx* c, int comp, const double* r, double* u, void* stre
     face_poisson<double, double, double>(c, comp - 1, r, c->cr, c->t1, c->t2, s);
     k_scale_copy<<<grid_for(c->N3), 256, 0, s>>>(c->cr, c->mu, nullptr, u, c->N3); ++g_launches;
     check_launch();
+    return KFBIM_OK;
+  });
+}
+
+int kfbim_schur_apply_f32(kfbim_ctx* c, const float* d, float* q, void* stream) {
+  return guarded(c, [&]() -> int {
+    if (!d || !q || d == q) return fail(c, KFBIM_E_INVALID, "kfbim_schur_apply_f32: bad pointers");
+    if (!c->slab) return fail(c, KFBIM_E_INVALID, "kfbim_schur_apply_f32: no slab CG on this context");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = c->N3;
+    const CgWs<float> w = ws32(c);
+    // scalars of a fresh run: beta = 0 (so d = r), not done, the Navier c p block
+    CGScalars h{};
+    h.cdiag = c->cpen;
+    std::memcpy(c->pinned, &h, sizeof(CGScalars));
+    CK(cudaMemcpyAsync(c->cgs, c->pinned, sizeof(CGScalars), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(w.r, d, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemsetAsync(w.d, 0, n * sizeof(float), s));
+    SlabCg a{c->N, w.x, w.r, w.d, q, w.T6, w.T6 + n, c->d_twc32, c->d_q32, c->d_s2f, (float)(1.0 / c->mu),
+             c->cgs, c->partial};
+    g_launches += slab_schur_apply(a, s);
+    check_launch();
+    CK(cudaStreamSynchronize(s));   // the pinned scalars are reused by the next call
     return KFBIM_OK;
   });
 }
@@ -2156,9 +2315,10 @@ int kfbim_profile(kfbim_ctx* c, int enable, double* ms64, int64_t* launches64, d
       }
       c->prof = enable != 0;
       c->prof_used = 0;
-      c->prof_ms[0] = c->prof_ms[1] = 0;
-      c->prof_count[0] = c->prof_count[1] = 0;
-      c->prof_bytes[0] = c->prof_bytes[1] = 0;
+      for (int k = 0; k < KFBIM_KCLASS_COUNT; ++k) {
+        c->prof_ms[k] = c->prof_bytes[k] = 0;
+        c->prof_count[k] = 0;
+      }
       return KFBIM_OK;
     }
     CK(cudaDeviceSynchronize());
@@ -2173,6 +2333,21 @@ int kfbim_profile(kfbim_ctx* c, int enable, double* ms64, int64_t* launches64, d
   });
 }
 
+int kfbim_profile_kernels(kfbim_ctx* c, int n, double* ms, int64_t* launches, double* bytes) {
+  return guarded(c, [&]() -> int {
+    if (n < 0) return fail(c, KFBIM_E_INVALID, "kfbim_profile_kernels: negative count");
+    CK(cudaDeviceSynchronize());
+    if (c->prof_used) prof_collect(c);
+    for (int k = 0; k < n; ++k) {
+      const bool in = k < KFBIM_KCLASS_COUNT;
+      if (ms) ms[k] = in ? c->prof_ms[k] : 0.0;
+      if (launches) launches[k] = in ? c->prof_count[k] : 0;
+      if (bytes) bytes[k] = in ? c->prof_bytes[k] : 0.0;
+    }
+    return KFBIM_OK;
+  });
+}
+
 int kfbim_poisson_noalloc(int c, int N, double lo, double hi, const double* r, double* u,
                           void* stream) {
   if (c < 1 || c > 3 || !r || !u || r == u || !(hi > lo) || N < 16 || (N & (N - 1)) != 0)
@@ -2182,10 +2357,10 @@ int kfbim_poisson_noalloc(int c, int N, double lo, double hi, const double* r, d
                  N, kNoAllocMaxN);
     return KFBIM_E_INVALID;
   }
-  NoAllocSymbols* d = nullptr;
-  int st = noalloc_symbols(&d);
-  if (st != KFBIM_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
+  NoAllocSymbols* d = nullptr;
+  int st = noalloc_symbols(s, &d);
+  if (st != KFBIM_OK) return st;
   const double h = (hi - lo) / N;
   const int64_t N3 = (int64_t)N * N * N;
   double* t1 = d->scratch;
@@ -2193,14 +2368,22 @@ int kfbim_poisson_noalloc(int c, int N, double lo, double hi, const double* r, d
   const int cax = c - 1;
   int o1, o2;
   others(cax, o1, o2);
-  k_na_tables<<<1, 64, 0, s>>>(N, d->tw, d->q, d->s2);
-  noalloc_pass(*d, N, h, r, t1, o2, X_DST2F, X_NONE, W_NONE, cax, s);
-  noalloc_pass(*d, N, h, t1, t2, o1, X_DST2F, X_NONE, W_NONE, cax, s);
-  noalloc_pass(*d, N, h, t2, t1, cax, X_DST1F, X_DST1I, W_POISSON, cax, s);
-  noalloc_pass(*d, N, h, t1, t2, o1, X_DST2I, X_NONE, W_NONE, cax, s);
-  noalloc_pass(*d, N, h, t2, u, o2, X_DST2I, X_NONE, W_NONE, cax, s);
-  const cudaError_t e = cudaGetLastError();
+  const cudaError_t pending = cudaPeekAtLastError();
+  int Nv = N;
+  C2<double>* tw = d->tw;
+  C2<double>* q = d->q;
+  double* s2 = d->s2;
+  void* targs[] = {(void*)&Nv, (void*)&tw, (void*)&q, (void*)&s2};
+  cudaError_t e = cudaLaunchKernel((const void*)k_na_tables, dim3(1), dim3(64), targs, 0, s);
+  if (e == cudaSuccess) e = noalloc_pass(*d, N, h, r, t1, o2, X_DST2F, X_NONE, W_NONE, cax, s);
+  if (e == cudaSuccess) e = noalloc_pass(*d, N, h, t1, t2, o1, X_DST2F, X_NONE, W_NONE, cax, s);
+  if (e == cudaSuccess) e = noalloc_pass(*d, N, h, t2, t1, cax, X_DST1F, X_DST1I, W_POISSON, cax, s);
+  if (e == cudaSuccess) e = noalloc_pass(*d, N, h, t1, t2, o1, X_DST2I, X_NONE, W_NONE, cax, s);
+  if (e == cudaSuccess) e = noalloc_pass(*d, N, h, t2, u, o2, X_DST2I, X_NONE, W_NONE, cax, s);
   if (e != cudaSuccess) {
+    // clear this call's own launch error from the thread's last-error state,
+    // unless an earlier, unrelated error was already pending there
+    if (pending == cudaSuccess) (void)cudaGetLastError();
     std::fprintf(stderr, "kfbim_poisson_noalloc: launch failed: %s\n", cudaGetErrorString(e));
     return KFBIM_E_CUDA;
   }

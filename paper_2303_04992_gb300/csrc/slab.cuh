@@ -1,0 +1,602 @@
+// FP32 Schur-complement CG iteration in four kernels (Sec. 4.2, Eq. linearS1
+// and items i-iii), for N = 32, 64, 128.
+//
+// The Schur operator is applied in spectral form,
+//   S d = (1/mu) sum_c B_c^-1 Lambda_c B_c d (+ rank-one / c d terms),
+// B_c = DCT-II along axis c and DST-II along the other two axes, Lambda_c =
+// sin^2(a_c) / sum_b sin^2(a_b).  The transforms along z come first: terms 1
+// and 2 share DST-II along z, term 3 takes DCT-II along z.  After that every
+// (x, y) plane of the two z-transformed fields is independent, so one CTA per
+// plane does the rest of the three terms in shared memory:
+//   W12 = T1 + T2 with T1 = (C_x S_y)^-1 L1 (C_x S_y) Z1, T2 = (S_x C_y)^-1 L2 (S_x C_y) Z1,
+//   W3  = (S_x S_y)^-1 L3 (S_x S_y) Z3,
+// the weights taking the plane's z mode.  The inverse z transforms of W12
+// (DST-III) and W3 (DCT-III) are summed into q.  One CG iteration:
+//   k_cg_zfwd  d = r + beta d, Z1 = S_z d, Z3 = C_z d, sum(d)       (1 read r, d; 3 writes)
+//   k_cg_xy    W12, W3 in place of Z1, Z3                          (2 reads, 2 writes)
+//   k_cg_zinv  q = S_z^-1 W12 + C_z^-1 W3 + cdiag d, d.q, alpha     (3 reads, 1 write)
+//   k_cg_upd   x += alpha d, r -= alpha (q + rank-one), r.r, beta  (4 reads, 2 writes)
+// i.e. 17 N^3 values moved per iteration, against 28 for the transform
+// passes of Schur apply run one axis at a time plus 14 for the CG vectors.
+//
+// Transforms: the real DCT-II/DST-II (and inverses) of transforms.cuh via
+// Makhoul's reordering, two real lines per complex FFT of length N (or the
+// DCT-II and DST-II of one line together, since the DST-II input is the
+// DCT-II input with its second half negated).  A team of M = N/16 threads
+// computes one complex FFT: a radix-16 DFT in registers, a twiddle, an
+// exchange through the team's own shared-memory buffer and radix-M DFTs in
+// registers.  Within a warp the teams only synchronise with __syncwarp.
+//
+// Shared-memory layouts avoid bank conflicts for the access patterns of the
+// team FFT (stride 2 and runs of 8 along a line, 4 teams per warp):
+//   plane: element x of row y at y N + (x ^ plane_sw(y)),
+//   z tile: element z of line l (32 lines) at 32 z + (l ^ tile_sw(z)),
+//   exchange: separate real and imaginary arrays, rows of M + 1 floats,
+//   team buffers 8 banks apart.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "cg_common.cuh"
+#include "transforms.cuh"
+#include "transforms2.cuh"
+
+namespace kfbim {
+namespace slab {
+
+template <int N>
+struct Cfg {
+  static constexpr int M = N / 16;                        // threads per complex FFT
+  static constexpr int NS = 16 / M;                       // radix-M DFTs per thread
+  static constexpr int XS = M + 1;                        // exchange row (floats)
+  static constexpr int XN = (16 * XS > N) ? 16 * XS : N;  // exchange floats per team (Re or Im)
+  static constexpr int TS = (XN + 31) / 32 * 32 + 8;      // team stride, 8 banks apart
+  static constexpr int PLANE_TEAMS = N / 2;               // xy kernel: one pair of lines per team
+  static constexpr int PLANE_THREADS = PLANE_TEAMS * M;
+  static constexpr int TILE = 32;                         // z kernels: lines per CTA
+  static constexpr int TILE_THREADS = TILE * M;           // one line per team
+};
+
+template <int N>
+struct XySmem {
+  using C = Cfg<N>;
+  static constexpr size_t plane = sizeof(float) * N * N;
+  static constexpr size_t xch = sizeof(float) * C::PLANE_TEAMS * C::TS;
+  static constexpr size_t bytes = 2 * plane + 2 * xch + sizeof(C2<float>) * 3 * N + sizeof(float) * 2 * N;
+};
+
+template <int N>
+struct ZSmem {
+  using C = Cfg<N>;
+  static constexpr size_t tile = sizeof(float) * N * C::TILE;
+  static constexpr size_t xch = sizeof(float) * C::TILE * C::TS;
+  static constexpr size_t bytes = 2 * tile + 2 * xch + sizeof(C2<float>) * 3 * N;
+};
+
+// Row swizzle of a plane: bits 0, 3 and 4 of the column index, from the row
+// index mod 16, chosen so that (a) the rows 8w + 2t (t = 0..3; likewise the
+// odd rows) of the four teams of a warp map a stride-2 run and an aligned
+// run of 8 columns to disjoint banks, and (b) down a column, any 8 rows with
+// distinct (y mod 16) >> 1, any 8 even or odd rows of 16, and any aligned 8
+// rows fall on distinct banks.
+__device__ __forceinline__ int plane_sw(int y) {
+  const int y0 = y & 1, y1 = (y >> 1) & 1, y2 = (y >> 2) & 1, y3 = (y >> 3) & 1;
+  return (y0 ^ y1 ^ y3) | (y1 << 3) | (y2 << 4);
+}
+
+// Line swizzle of a z tile (32 lines): bits 2..4 of the line index, from
+// z mod 16, bijective on even z, odd z, z < 8 and z >= 8 of each 16; the four
+// teams of a warp take lines 4w + t (bits 0, 1).  Multiples of 4 keep
+// 16-byte groups of lines together for vector copies.
+__device__ __forceinline__ int tile_sw(int z) { return (((z >> 1) ^ ((z & 1) << 2)) & 7) << 2; }
+
+template <int N>
+struct PlaneRow {
+  float* p;
+  int sw;
+  __device__ __forceinline__ float& operator[](int x) const { return p[x ^ sw]; }
+};
+template <int N>
+__device__ __forceinline__ PlaneRow<N> plane_row(float* plane, int y) {
+  return {plane + y * N, plane_sw(y)};
+}
+template <int N>
+struct PlaneCol {
+  float* p;
+  int x;
+  __device__ __forceinline__ float& operator[](int y) const { return p[y * N + (x ^ plane_sw(y))]; }
+};
+struct TileCol {
+  float* p;
+  int l;
+  __device__ __forceinline__ float& operator[](int z) const { return p[z * 32 + (l ^ tile_sw(z))]; }
+};
+
+// One complex FFT of length N by a team of M threads (lane m).  On entry
+// v[r] = z[m + M r], r = 0..15; on return the team's exchange buffer (xr, xi)
+// holds Z[k] at index k, INV: exp(+2 pi i n k / N).  Four steps:
+// Y[m][s] = DFT16_r z[m + M r], times w_N^{m s}, exchanged, then
+// Z[s + 16 k] = DFT_M over m of the twiddled Y[m][s].
+template <int N, bool INV>
+__device__ __forceinline__ void team_fft(C2<float> (&v)[16], float* xr, float* xi, const C2<float>* tw, int m) {
+  using C = Cfg<N>;
+  constexpr int M = C::M, NS = C::NS, XS = C::XS;
+  dft_reg<16, INV, float>(v);
+  __syncwarp();   // the team's previous reads of the exchange buffer are done
+#pragma unroll
+  for (int s = 0; s < 16; ++s) {
+    C2<float> y = v[s];
+    if (s != 0) {
+      C2<float> w = tw[2 * m * s];   // exp(-2 pi i m s / N) from the table over 2N
+      if (INV) w.y = -w.y;
+      y = cmul(y, w);
+    }
+    xr[s * XS + m] = y.x;
+    xi[s * XS + m] = y.y;
+  }
+  __syncwarp();
+  C2<float> w2[NS][M];
+#pragma unroll
+  for (int q = 0; q < NS; ++q)
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+      const int s = q * M + m;
+      w2[q][k] = {xr[s * XS + k], xi[s * XS + k]};
+    }
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < NS; ++q) {
+    dft_reg<M, INV, float>(w2[q]);
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+      const int idx = q * M + m + 16 * k;
+      xr[idx] = w2[q][k].x;
+      xi[idx] = w2[q][k].y;
+    }
+  }
+  __syncwarp();
+}
+
+// Forward input of a pair of lines (DCT-II or DST-II each; DST-II negates the
+// second half of Makhoul's reordering v_n = x_{2n}, v_{N-1-n} = x_{2n+1}).
+template <int N, class LA, class LB>
+__device__ __forceinline__ void pre_fwd_pair(C2<float> (&v)[16], const LA& A, const LB& B, bool dsta, bool dstb,
+                                             int m) {
+  constexpr int M = Cfg<N>::M;
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const int n = m + M * r;
+    const bool hi = r >= 8;   // n >= N / 2
+    const int i = hi ? 2 * (N - 1 - n) + 1 : 2 * n;
+    float a = A[i], b = B[i];
+    if (hi && dsta) a = -a;
+    if (hi && dstb) b = -b;
+    v[r] = {a, b};
+  }
+}
+
+// Forward input of one line whose DCT-II (real part) and DST-II (imaginary
+// part) are wanted together.
+template <int N, class L>
+__device__ __forceinline__ void pre_fwd_cs(C2<float> (&v)[16], const L& A, int m) {
+  constexpr int M = Cfg<N>::M;
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const int n = m + M * r;
+    const bool hi = r >= 8;
+    const float a = A[hi ? 2 * (N - 1 - n) + 1 : 2 * n];
+    v[r] = {a, hi ? -a : a};
+  }
+}
+
+// Forward output: for k = m + M r the transforms of both packed lines at
+// mode k, X_k = Re(exp(-i pi k / 2N) V_k) (DCT-II at position k; DST-II at
+// position N - 1 - k), handed to put(k, xa, xb).
+template <int N, class F>
+__device__ __forceinline__ void post_fwd(const float* xr, const float* xi, const C2<float>* qN, int m, F&& put) {
+  constexpr int M = Cfg<N>::M;
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const int k = m + M * r;
+    const int kc = (N - k) & (N - 1);
+    const float zkx = xr[k], zky = xi[k], zcx = xr[kc], zcy = xi[kc];
+    const float vax = 0.5f * (zkx + zcx), vay = 0.5f * (zky - zcy);
+    const float vbx = 0.5f * (zky + zcy), vby = -0.5f * (zkx - zcx);
+    const C2<float> q = qN[k];
+    put(k, q.x * vax - q.y * vay, q.x * vbx - q.y * vby);
+  }
+}
+
+// Inverse input of a pair of lines (DCT-III when dst = false, DST-III when
+// true): V_k = conj(q_k) (x_k - i x_{N-k}) with the DST-III line read backwards.
+template <int N, class LA, class LB>
+__device__ __forceinline__ void pre_inv_pair(C2<float> (&v)[16], const LA& A, const LB& B, bool dsta, bool dstb,
+                                             const C2<float>* qN, int m) {
+  constexpr int M = Cfg<N>::M;
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const int k = m + M * r;
+    const bool k0 = (k == 0);
+    const float xa = dsta ? A[N - 1 - k] : A[k];
+    const float xna = k0 ? 0.f : (dsta ? A[k - 1] : A[N - k]);
+    const float xb = dstb ? B[N - 1 - k] : B[k];
+    const float xnb = k0 ? 0.f : (dstb ? B[k - 1] : B[N - k]);
+    const C2<float> q = qN[k];
+    const float vax = q.x * xa - q.y * xna, vay = -q.x * xna - q.y * xa;
+    const float vbx = q.x * xb - q.y * xnb, vby = -q.x * xnb - q.y * xb;
+    v[r] = {vax - vby, vay + vbx};
+  }
+}
+
+// Inverse output: x_{2n} = v_n, x_{2n+1} = v_{N-1-n} (1/N; DST-III negates the
+// odd outputs); for o = m + M r, put(o, xa, xb).
+template <int N, class F>
+__device__ __forceinline__ void post_inv(const float* xr, const float* xi, bool dsta, bool dstb, int m, F&& put) {
+  constexpr int M = Cfg<N>::M;
+  constexpr float invN = 1.0f / N;
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const int o = m + M * r;
+    const bool odd = (o & 1) != 0;
+    const int n = odd ? N - 1 - (o >> 1) : (o >> 1);
+    const float sa = (dsta && odd) ? -invN : invN;
+    const float sb = (dstb && odd) ? -invN : invN;
+    put(o, xr[n] * sa, xi[n] * sb);
+  }
+}
+
+// sin^2 weights (Lambda_c / mu) of the Schur terms at modes (ax, ay, az):
+// s2[a] = 4 sin^2(pi a / 2N) for the DCT modes, s2[N + a] = 4 sin^2(pi (a+1) / 2N)
+// for the DST modes; the numerator is the DCT axis's.
+__device__ __forceinline__ float schur_w(float num, float sum, float inv_mu) {
+  return num * __frcp_rn(sum) * inv_mu;
+}
+
+template <int N>
+__device__ __forceinline__ void load_tables(C2<float>* tw, C2<float>* qN, float* s2, const C2<float>* __restrict__ twg,
+                                            const C2<float>* __restrict__ qg, const float* __restrict__ s2g,
+                                            int threads) {
+  for (int e = threadIdx.x; e < 3 * N; e += threads) {
+    if (e < 2 * N) tw[e] = twg[e];
+    else qN[e - 2 * N] = qg[e - 2 * N];
+  }
+  if (s2)
+    for (int e = threadIdx.x; e < 2 * N; e += threads) s2[e] = s2g[e];
+}
+
+// Plane y-major, N^2 floats from global memory into the swizzled layout.
+template <int N, int THREADS>
+__device__ __forceinline__ void load_plane(float* P, const float* __restrict__ g) {
+  constexpr int PER = N * N / THREADS;
+  float t[PER];
+#pragma unroll
+  for (int j = 0; j < PER; ++j) t[j] = g[threadIdx.x + j * THREADS];
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    const int e = threadIdx.x + j * THREADS;
+    const int y = e / N, x = e % N;
+    P[y * N + (x ^ plane_sw(y))] = t[j];
+  }
+}
+
+// ------------------------------------------------------------ the kernels
+
+// d = r + beta d; Z1 = DST-II_z d, Z3 = DCT-II_z d; sumd = sum d.  CTA: 32
+// lines along z at x = x0 .. x0 + 31, y fixed (1D grid, N/32 x N blocks).
+template <int N>
+__global__ void __launch_bounds__(Cfg<N>::TILE_THREADS)
+k_cg_zfwd(const float* __restrict__ r, float* __restrict__ d, float* __restrict__ z1, float* __restrict__ z3,
+          const C2<float>* __restrict__ twg, const C2<float>* __restrict__ qg, CGScalars* s,
+          double* __restrict__ partial) {
+  using C = Cfg<N>;
+  constexpr int T = C::TILE_THREADS, M = C::M;
+  __shared__ double sh[32];
+  __shared__ double total;
+  if (s->done) return;
+  extern __shared__ __align__(16) unsigned char smz[];
+  float* D = reinterpret_cast<float*>(smz);
+  float* E = D + N * C::TILE;
+  float* Xr = E + N * C::TILE;
+  float* Xi = Xr + C::TILE * C::TS;
+  C2<float>* tw = reinterpret_cast<C2<float>*>(Xi + C::TILE * C::TS);
+  C2<float>* qN = tw + 2 * N;
+  load_tables<N>(tw, qN, nullptr, twg, qg, nullptr, T);
+  const int xb = blockIdx.x % (N / C::TILE), y = blockIdx.x / (N / C::TILE);
+  const int x0 = xb * C::TILE;
+  const float beta = float(s->beta);
+  CgAcc<float> acc;
+  for (int e4 = threadIdx.x; e4 < N * 8; e4 += T) {
+    const int z = e4 >> 3, c4 = (e4 & 7) * 4;
+    const int64_t g = ((int64_t)z * N + y) * N + x0 + c4;
+    const float4 rv = *reinterpret_cast<const float4*>(r + g);
+    const float4 dv = *reinterpret_cast<const float4*>(d + g);
+    float4 nv;
+    nv.x = rv.x + beta * dv.x;
+    nv.y = rv.y + beta * dv.y;
+    nv.z = rv.z + beta * dv.z;
+    nv.w = rv.w + beta * dv.w;
+    *reinterpret_cast<float4*>(d + g) = nv;
+    *reinterpret_cast<float4*>(D + z * 32 + (c4 ^ tile_sw(z))) = nv;
+    acc.add(nv.x);
+    acc.add(nv.y);
+    acc.add(nv.z);
+    acc.add(nv.w);
+  }
+  __syncthreads();
+  {
+    const int tm = threadIdx.x / M, m = threadIdx.x % M;
+    const TileCol src{D, tm}, ce{E, tm};
+    C2<float> v[16];
+    pre_fwd_cs<N>(v, src, m);
+    team_fft<N, false>(v, Xr + tm * C::TS, Xi + tm * C::TS, tw, m);
+    post_fwd<N>(Xr + tm * C::TS, Xi + tm * C::TS, qN, m, [&](int k, float c, float sn) {
+      ce[k] = c;             // DCT-II mode k -> Z3
+      src[N - 1 - k] = sn;   // DST-II mode N-1-k -> Z1
+    });
+  }
+  __syncthreads();
+  for (int e4 = threadIdx.x; e4 < N * 8; e4 += T) {
+    const int z = e4 >> 3, c4 = (e4 & 7) * 4;
+    const int64_t g = ((int64_t)z * N + y) * N + x0 + c4;
+    const int a = z * 32 + (c4 ^ tile_sw(z));
+    *reinterpret_cast<float4*>(z1 + g) = *reinterpret_cast<const float4*>(D + a);
+    *reinterpret_cast<float4*>(z3 + g) = *reinterpret_cast<const float4*>(E + a);
+  }
+  if (last_block_sum(acc.value(), partial, &s->ticket[2], sh, &total) && threadIdx.x == 0) s->sumd = total;
+}
+
+// The (x, y) part of the three Schur terms on plane kz = blockIdx.x of the
+// z-transformed fields, in place: Z1 -> W12 = T1 + T2, Z3 -> W3 = T3.
+template <int N>
+__global__ void __launch_bounds__(Cfg<N>::PLANE_THREADS, 1)
+k_cg_xy(float* __restrict__ z1, float* __restrict__ z3, const C2<float>* __restrict__ twg,
+        const C2<float>* __restrict__ qg, const float* __restrict__ s2g, float inv_mu,
+        const CGScalars* __restrict__ s) {
+  using C = Cfg<N>;
+  constexpr int T = C::PLANE_THREADS, M = C::M;
+  if (s->done) return;
+  extern __shared__ __align__(16) unsigned char smx[];
+  float* P = reinterpret_cast<float*>(smx);
+  float* Q = P + N * N;
+  float* Xr = Q + N * N;
+  float* Xi = Xr + C::PLANE_TEAMS * C::TS;
+  C2<float>* tw = reinterpret_cast<C2<float>*>(Xi + C::PLANE_TEAMS * C::TS);
+  C2<float>* qN = tw + 2 * N;
+  float* s2 = reinterpret_cast<float*>(qN + N);
+  load_tables<N>(tw, qN, s2, twg, qg, s2g, T);
+  const int kz = blockIdx.x;
+  const int64_t off = (int64_t)kz * N * N;
+  const int tm = threadIdx.x / M, m = threadIdx.x % M;
+  float* xr = Xr + tm * C::TS;
+  float* xi = Xi + tm * C::TS;
+  load_plane<N, T>(P, z1 + off);
+  __syncthreads();   // tables and plane
+  const float s2zs = s2[N + kz];   // z mode of terms 1, 2 (DST)
+  // terms 1 and 2 along x: DCT-II (term 1, into P) and DST-II (term 2, into Q) of each row
+#pragma unroll 1
+  for (int rho = 0; rho < 2; ++rho) {
+    const int y = 2 * tm + rho;
+    const PlaneRow<N> rp = plane_row<N>(P, y), rq = plane_row<N>(Q, y);
+    C2<float> v[16];
+    pre_fwd_cs<N>(v, rp, m);
+    team_fft<N, false>(v, xr, xi, tw, m);
+    post_fwd<N>(xr, xi, qN, m, [&](int k, float c, float sn) {
+      rp[k] = c;
+      rq[N - 1 - k] = sn;
+    });
+  }
+  __syncthreads();
+  const int xa = 2 * tm, xb = xa + 1;
+  {
+    // term 1 along y: DST-II, weight s2_x / (s2_x + s2_y + s2_z) (x DCT, y and z DST), DST-III
+    const PlaneCol<N> A{P, xa}, B{P, xb};
+    C2<float> v[16];
+    pre_fwd_pair<N>(v, A, B, true, true, m);
+    team_fft<N, false>(v, xr, xi, tw, m);
+    const float nxa = s2[xa], nxb = s2[xb];
+    post_fwd<N>(xr, xi, qN, m, [&](int k, float va, float vb) {
+      const int o = N - 1 - k;
+      const float sy = s2[N + o] + s2zs;
+      A[o] = va * schur_w(nxa, nxa + sy, inv_mu);
+      B[o] = vb * schur_w(nxb, nxb + sy, inv_mu);
+    });
+    __syncwarp();
+    pre_inv_pair<N>(v, A, B, true, true, qN, m);
+    team_fft<N, true>(v, xr, xi, tw, m);
+    post_inv<N>(xr, xi, true, true, m, [&](int o, float va, float vb) {
+      A[o] = va;
+      B[o] = vb;
+    });
+  }
+  {
+    // term 2 along y: DCT-II, weight s2_y / (s2_x + s2_y + s2_z) (y DCT, x and z DST), DCT-III
+    const PlaneCol<N> A{Q, xa}, B{Q, xb};
+    C2<float> v[16];
+    pre_fwd_pair<N>(v, A, B, false, false, m);
+    team_fft<N, false>(v, xr, xi, tw, m);
+    const float sxa = s2[N + xa] + s2zs, sxb = s2[N + xb] + s2zs;
+    post_fwd<N>(xr, xi, qN, m, [&](int k, float va, float vb) {
+      const float ny = s2[k];
+      A[k] = va * schur_w(ny, ny + sxa, inv_mu);
+      B[k] = vb * schur_w(ny, ny + sxb, inv_mu);
+    });
+    __syncwarp();
+    pre_inv_pair<N>(v, A, B, false, false, qN, m);
+    team_fft<N, true>(v, xr, xi, tw, m);
+    post_inv<N>(xr, xi, false, false, m, [&](int o, float va, float vb) {
+      A[o] = va;
+      B[o] = vb;
+    });
+  }
+  __syncthreads();
+  // back along x: DCT-III of term 1 plus DST-III of term 2 in one FFT per row -> W12
+#pragma unroll 1
+  for (int rho = 0; rho < 2; ++rho) {
+    const int y = 2 * tm + rho;
+    const PlaneRow<N> rp = plane_row<N>(P, y), rq = plane_row<N>(Q, y);
+    C2<float> v[16];
+    pre_inv_pair<N>(v, rp, rq, false, true, qN, m);
+    team_fft<N, true>(v, xr, xi, tw, m);
+    float* out = z1 + off + (int64_t)y * N;
+    post_inv<N>(xr, xi, false, true, m, [&](int o, float va, float vb) { out[o] = va + vb; });
+  }
+  __syncthreads();
+  // term 3: S_x S_y, weight s2_z / (s2_x + s2_y + s2_z) (z DCT), inverse
+  load_plane<N, T>(P, z3 + off);
+  __syncthreads();
+  const float s2zc = s2[kz];
+  const int ya = 2 * tm, yb = ya + 1;
+  {
+    const PlaneRow<N> A = plane_row<N>(P, ya), B = plane_row<N>(P, yb);
+    C2<float> v[16];
+    pre_fwd_pair<N>(v, A, B, true, true, m);
+    team_fft<N, false>(v, xr, xi, tw, m);
+    post_fwd<N>(xr, xi, qN, m, [&](int k, float va, float vb) {
+      A[N - 1 - k] = va;
+      B[N - 1 - k] = vb;
+    });
+  }
+  __syncthreads();
+  {
+    const PlaneCol<N> A{P, xa}, B{P, xb};
+    C2<float> v[16];
+    pre_fwd_pair<N>(v, A, B, true, true, m);
+    team_fft<N, false>(v, xr, xi, tw, m);
+    const float sxa = s2[N + xa] + s2zc, sxb = s2[N + xb] + s2zc;
+    post_fwd<N>(xr, xi, qN, m, [&](int k, float va, float vb) {
+      const int o = N - 1 - k;
+      const float sy = s2[N + o];
+      A[o] = va * schur_w(s2zc, sxa + sy, inv_mu);
+      B[o] = vb * schur_w(s2zc, sxb + sy, inv_mu);
+    });
+    __syncwarp();
+    pre_inv_pair<N>(v, A, B, true, true, qN, m);
+    team_fft<N, true>(v, xr, xi, tw, m);
+    post_inv<N>(xr, xi, true, true, m, [&](int o, float va, float vb) {
+      A[o] = va;
+      B[o] = vb;
+    });
+  }
+  __syncthreads();
+  {
+    const PlaneRow<N> A = plane_row<N>(P, ya), B = plane_row<N>(P, yb);
+    C2<float> v[16];
+    pre_inv_pair<N>(v, A, B, true, true, qN, m);
+    team_fft<N, true>(v, xr, xi, tw, m);
+    float* oa = z3 + off + (int64_t)ya * N;
+    float* ob = z3 + off + (int64_t)yb * N;
+    post_inv<N>(xr, xi, true, true, m, [&](int o, float va, float vb) {
+      oa[o] = va;
+      ob[o] = vb;
+    });
+  }
+}
+
+// q = DST-III_z W12 + DCT-III_z W3 + cdiag d; dq = d . q; alpha.  Tiles as
+// k_cg_zfwd.
+template <int N>
+__global__ void __launch_bounds__(Cfg<N>::TILE_THREADS)
+k_cg_zinv(const float* __restrict__ w12, const float* __restrict__ w3, const float* __restrict__ d,
+          float* __restrict__ q, const C2<float>* __restrict__ twg, const C2<float>* __restrict__ qg, CGScalars* s,
+          double* __restrict__ partial) {
+  using C = Cfg<N>;
+  constexpr int T = C::TILE_THREADS, M = C::M;
+  __shared__ double sh[32];
+  __shared__ double total;
+  if (s->done) return;
+  extern __shared__ __align__(16) unsigned char smi[];
+  float* D = reinterpret_cast<float*>(smi);
+  float* E = D + N * C::TILE;
+  float* Xr = E + N * C::TILE;
+  float* Xi = Xr + C::TILE * C::TS;
+  C2<float>* tw = reinterpret_cast<C2<float>*>(Xi + C::TILE * C::TS);
+  C2<float>* qN = tw + 2 * N;
+  load_tables<N>(tw, qN, nullptr, twg, qg, nullptr, T);
+  const int xb = blockIdx.x % (N / C::TILE), y = blockIdx.x / (N / C::TILE);
+  const int x0 = xb * C::TILE;
+  for (int e4 = threadIdx.x; e4 < N * 8; e4 += T) {
+    const int z = e4 >> 3, c4 = (e4 & 7) * 4;
+    const int64_t g = ((int64_t)z * N + y) * N + x0 + c4;
+    const int a = z * 32 + (c4 ^ tile_sw(z));
+    *reinterpret_cast<float4*>(D + a) = *reinterpret_cast<const float4*>(w12 + g);
+    *reinterpret_cast<float4*>(E + a) = *reinterpret_cast<const float4*>(w3 + g);
+  }
+  __syncthreads();
+  {
+    const int tm = threadIdx.x / M, m = threadIdx.x % M;
+    const TileCol A{D, tm}, B{E, tm};
+    C2<float> v[16];
+    pre_inv_pair<N>(v, A, B, true, false, qN, m);
+    team_fft<N, true>(v, Xr + tm * C::TS, Xi + tm * C::TS, tw, m);
+    post_inv<N>(Xr + tm * C::TS, Xi + tm * C::TS, true, false, m, [&](int o, float va, float vb) { A[o] = va + vb; });
+  }
+  __syncthreads();
+  const float cd = float(s->cdiag);
+  CgAcc<float> acc;
+  for (int e4 = threadIdx.x; e4 < N * 8; e4 += T) {
+    const int z = e4 >> 3, c4 = (e4 & 7) * 4;
+    const int64_t g = ((int64_t)z * N + y) * N + x0 + c4;
+    const float4 t = *reinterpret_cast<const float4*>(D + z * 32 + (c4 ^ tile_sw(z)));
+    const float4 dv = *reinterpret_cast<const float4*>(d + g);
+    float4 qv;
+    qv.x = t.x + cd * dv.x;
+    qv.y = t.y + cd * dv.y;
+    qv.z = t.z + cd * dv.z;
+    qv.w = t.w + cd * dv.w;
+    *reinterpret_cast<float4*>(q + g) = qv;
+    acc.add_prod(dv.x, qv.x);
+    acc.add_prod(dv.y, qv.y);
+    acc.add_prod(dv.z, qv.z);
+    acc.add_prod(dv.w, qv.w);
+  }
+  if (last_block_sum(acc.value(), partial, &s->ticket[0], sh, &total) && threadIdx.x == 0) {
+    const double den = total + s->sumd * s->sumd * s->rank1;
+    s->dq = den;
+    s->alpha = (den != 0.0) ? s->rr / den : 0.0;
+  }
+}
+
+// x += alpha d; r -= alpha (q + sumd rank1); rr = r . r; beta; done once
+// rr <= stop.  Float4 vectors (n4 = N^3 / 4).
+__global__ void __launch_bounds__(256)
+k_cg_upd(float* __restrict__ x, float* __restrict__ r, const float* __restrict__ d, const float* __restrict__ q,
+         int64_t n4, CGScalars* s, double* __restrict__ partial) {
+  __shared__ double sh[32];
+  __shared__ double total;
+  if (s->done) return;
+  const float a = float(s->alpha);
+  const float c1 = float(s->sumd * s->rank1);
+  CgAcc<float> acc;
+  float4* x4 = reinterpret_cast<float4*>(x);
+  float4* r4 = reinterpret_cast<float4*>(r);
+  const float4* d4 = reinterpret_cast<const float4*>(d);
+  const float4* q4 = reinterpret_cast<const float4*>(q);
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n4; e += (int64_t)gridDim.x * blockDim.x) {
+    const float4 dv = d4[e], qv = q4[e];
+    float4 rv = r4[e], xv = x4[e];
+    rv.x = rv.x - a * (qv.x + c1);
+    rv.y = rv.y - a * (qv.y + c1);
+    rv.z = rv.z - a * (qv.z + c1);
+    rv.w = rv.w - a * (qv.w + c1);
+    xv.x = xv.x + a * dv.x;
+    xv.y = xv.y + a * dv.y;
+    xv.z = xv.z + a * dv.z;
+    xv.w = xv.w + a * dv.w;
+    r4[e] = rv;
+    x4[e] = xv;
+    acc.add_prod(rv.x, rv.x);
+    acc.add_prod(rv.y, rv.y);
+    acc.add_prod(rv.z, rv.z);
+    acc.add_prod(rv.w, rv.w);
+  }
+  if (last_block_sum(acc.value(), partial, &s->ticket[1], sh, &total) && threadIdx.x == 0) {
+    s->beta = (s->rr != 0.0) ? total / s->rr : 0.0;
+    s->rr = total;
+    s->iters += 1;
+    if (!(s->rr > s->stop)) s->done = 1;
+  }
+}
+
+}  // namespace slab
+}  // namespace kfbim

@@ -3,9 +3,11 @@
  * for the sphere of radius 0.5 at N = 32 on [-1, 1]^3 and prints, one
  * "key value" pair per line: the sizes, the table sizes, the number of
  * primary flags, the largest distance of a control point from the sphere, the
- * number of Omega cells, the status of a solver call on the host-only context
- * and of a setup whose grid size is not a power of two.  Exits non-zero when a
- * call that must succeed fails. */
+ * number of Omega cells, the control points per component (kfbim_control_points)
+ * with the largest deviation of their normals from the sphere's, the number of
+ * jump points (kfbim_jump_points), the status of a solver call on the
+ * host-only context and of a setup whose grid size is not a power of two.
+ * Exits non-zero when a call that must succeed fails. */
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -80,6 +82,38 @@ int main(void) {
   st = kfbim_sides(ctx, 0, side);
   if (st != KFBIM_OK) return fail("kfbim_sides", st);
   for (i = 0; i < (int64_t)N * N * N; ++i) n_cells += side[i] != 0;
+
+  /* the density unknowns per component with their normals, and the jump points */
+  {
+    int64_t per[3] = {0, 0, 0}, total = 0, nj = 0;
+    double ndev = 0.0;
+    int c;
+    for (c = 1; c <= 3; ++c) {
+      double *cx, *cn;
+      st = kfbim_control_points(ctx, c, &per[c - 1], NULL, NULL);
+      if (st != KFBIM_OK) return fail("kfbim_control_points (count)", st);
+      cx = (double*)malloc(sizeof(double) * 3 * (size_t)(per[c - 1] + 1));
+      cn = (double*)malloc(sizeof(double) * 3 * (size_t)(per[c - 1] + 1));
+      if (!cx || !cn) return fail("malloc", -6);
+      st = kfbim_control_points(ctx, c, &per[c - 1], cx, cn);
+      if (st != KFBIM_OK) return fail("kfbim_control_points", st);
+      for (i = 0; i < per[c - 1]; ++i) {
+        int a;
+        for (a = 0; a < 3; ++a) {
+          const double dv = fabs(cn[3 * i + a] - cx[3 * i + a] / 0.5);
+          if (dv > ndev) ndev = dv;
+        }
+      }
+      total += per[c - 1];
+      free(cx);
+      free(cn);
+    }
+    st = kfbim_jump_points(ctx, &nj, NULL);
+    if (st != KFBIM_OK) return fail("kfbim_jump_points", st);
+    printf("control_points_total %lld\ncontrol_points_1 %lld\nnormal_deviation %.3e\njump_points %lld\n",
+           (long long)total, (long long)per[0], ndev, (long long)nj);
+    if (kfbim_control_points(ctx, 4, &nj, NULL, NULL) != KFBIM_E_INVALID) return fail("kfbim_control_points(4)", 0);
+  }
 
   /* a solver call on a host-only context is refused, with a message */
   st_apply = kfbim_apply(ctx, NULL, NULL, NULL);

@@ -46,6 +46,31 @@ def test_host_setup_matches_oracle_points():
         s.close()
 
 
+def test_control_points_are_the_density_blocks():
+    """kfbim_control_points(c) lists component c's density unknowns in the
+    order of its block of g and phi; kfbim_jump_points lists every control
+    point (where f is needed), in the order of fpts."""
+    geom, grid = ki.star(), ki.grid(32)
+    s = Solver(geom, grid, device=False)
+    o = okfbim.Setup(geom, grid)
+    xyz, comp, _, prim = s.points()
+    nrm = s.normals()
+    blocks = []
+    for c in (1, 2, 3):
+        cx, cn = s.control_points(c)
+        sel = prim & (comp == c)
+        assert np.array_equal(cx, xyz[sel]) and np.array_equal(cn, nrm[sel])
+        assert np.abs(cx - o.cp.xyz[o.primary & (o.cp.comp == c)]).max() < 1e-14
+        blocks.append(cx)
+    # the blocks concatenated are the primary points in density order
+    assert np.array_equal(np.concatenate(blocks), xyz[prim])
+    assert np.array_equal(s.jump_points(), xyz)
+    with pytest.raises(KfbimError) as e:
+        s.control_points(0)
+    assert e.value.code == -1
+    s.close()
+
+
 def test_host_setup_navier_matches_oracle_points():
     geom = ki.ellipsoid((0.6, 0.45, 0.35), ki.seeded_rotation(3))
     s = Solver(geom, ki.grid(32), device=False, lam=2.0)

@@ -48,3 +48,8 @@ def test_c_consumer_matches_binding(tmp_path, compiler, std):
     assert got["omega_cells"] == int(np.count_nonzero(s.sides(0)))
     assert got["status_apply"] == -1 and got["status_bad_grid"] == -1
     assert got["callback_equal"] == 1
+    _, comp, _, prim = s.points()
+    assert got["control_points_total"] == s.n_primary
+    assert got["control_points_1"] == int(np.count_nonzero(prim & (comp == 1)))
+    assert got["normal_deviation"] < 1e-12
+    assert got["jump_points"] == s.n_points

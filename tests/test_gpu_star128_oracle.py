@@ -1,0 +1,96 @@
+"""The full solve of the headline workload (star r = 0.5 + 0.1 sin 3theta
+cos 4phi, 128^3, manufactured forced Stokes pair, Alg. 1 step 3 plus the final
+interface solve) against the FP64 oracle's solve of the same inputs, stored by
+tests/golden/make_star128_solve.py (which calls only oracle/).
+
+* FP64 path: GMRES to a relative residual of 1e-13 like the stored oracle
+  solve, so that neither stopping point matters; density, velocity and
+  pressure within 1e-10 (relative max-norm; velocity and pressure at the
+  stored seeded sample of nodes, relative to the whole field's max-norm).
+* MIXED path in the benchmark's configuration (GMRES 1e-10, FP32 transforms
+  and CG inside FP64 refinement): density and velocity within 1e-8 and the
+  pressure within 1e-8 of the oracle.
+The oracle stops at 1e-13, so the MIXED figures also include the GMRES
+stopping error of the benchmark tolerance."""
+import os
+
+import numpy as np
+import pytest
+
+import kfbim_inputs as ki
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2303_04992_gb300 import FP64, MIXED, Solver, build  # noqa: E402
+
+build()
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "star128_solve.npz")
+GEOM, GRID = ki.WORKLOADS["star128"]
+
+
+def _inputs(s):
+    xyz, comp, _, prim = s.points()
+    rows = np.arange(len(comp))
+    g = ki.stokes_velocity(xyz)[rows, comp - 1][prim]
+    fpts = ki.stokes_forcing(xyz).T.copy()
+    N, h = s.N, s.h
+    idx = np.arange(N)
+    fg = []
+    for c in (1, 2, 3):
+        off = [0.5, 0.5, 0.5]
+        off[c - 1] = 0.0
+        Z, Y, X = np.meshgrid(s.lo + (idx + off[2]) * h, s.lo + (idx + off[1]) * h,
+                              s.lo + (idx + off[0]) * h, indexing="ij")
+        fg.append(ki.stokes_forcing(np.stack([X, Y, Z], -1))[..., c - 1].ravel())
+    return g, fpts, np.concatenate(fg)
+
+
+def errors_vs_oracle(s, want):
+    """Relative max-norm differences of phi (all points), u^(c) and p (at the
+    stored node sample, relative to the oracle field's max-norm)."""
+    g, fpts, fg = _inputs(s)
+    N3 = s.N ** 3
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    phi = torch.zeros(s.n_primary, dtype=torch.float64, device="cuda")
+    u = torch.zeros(3 * N3, dtype=torch.float64, device="cuda")
+    p = torch.zeros(N3, dtype=torch.float64, device="cuda")
+    s.solve(dev(g), phi, dev(fpts), dev(fg), u, p)
+    phi, u, p = phi.cpu().numpy(), u.cpu().numpy(), p.cpu().numpy()
+    out = {"phi": np.abs(phi - want["phi"]).max() / np.abs(want["phi"]).max()}
+    for c in (1, 2, 3):
+        uc = u[(c - 1) * N3:c * N3]
+        out["u%d" % c] = np.abs(uc[want["u%d_idx" % c]] - want["u%d_val" % c]).max() / float(want["u%d_max" % c])
+    out["p"] = np.abs(p[want["p_idx"]] - want["p_val"]).max() / float(want["p_max"])
+    out["gmres_iters"] = s.last_stats["gmres_iters"]
+    return out
+
+
+@pytest.fixture(scope="module")
+def want():
+    if not os.path.exists(GOLDEN):
+        pytest.fail("missing %s: run tests/golden/make_star128_solve.py" % GOLDEN)
+    return dict(np.load(GOLDEN))
+
+
+def test_golden_file_is_the_headline_workload(want):
+    assert int(want["N"]) == GRID["N"]
+    assert float(want["gmres_residual"]) < 1e-13
+
+
+def test_fp64_solve_matches_oracle_at_128(want):
+    s = Solver(GEOM, GRID, precision=FP64, gmres_tol=1e-13)
+    assert s.n_primary == len(want["phi"])
+    e = errors_vs_oracle(s, want)
+    s.close()
+    for k in ("phi", "u1", "u2", "u3", "p"):
+        assert e[k] < 1e-10, e
+    assert abs(e["gmres_iters"] - int(want["gmres_iters"])) <= 2, e
+
+
+def test_mixed_solve_matches_oracle_at_128(want):
+    s = Solver(GEOM, GRID, precision=MIXED)
+    e = errors_vs_oracle(s, want)
+    s.close()
+    for k in ("phi", "u1", "u2", "u3", "p"):
+        assert e[k] < 1e-8, e

@@ -4,10 +4,12 @@ CALLBACK level set (Python functions called by the host setup), and a sphere
 R = 0.5 about (0.01, -0.02, 0) at N = 32 whose surface grazes grid lines (two
 face segments whose cell centre lies on the other side, each resolved by two
 roots).  The matvec is compared as in the parity tests (FP64 <= 1e-10, MIXED
-<= 1e-8).  The solve is compared at 1e-8: each GMRES stops at a relative
-residual of 1e-10, so two solves with matvecs equal to rounding differ by up
-to kappa(A) * 2e-10, and the peanut's GMRES (53 iterations at N = 32, with a
-slow tail) shows a larger kappa than the sphere's (16 iterations)."""
+<= 1e-8).  The FP64 solve is compared at 1e-10 with both GMRES iterations
+(oracle and GPU) run to a relative residual of 1e-13: two solves whose matvecs
+agree to rounding but that stop at a residual of 1e-10 may differ by up to
+kappa(A) * 2e-10, and the peanut's GMRES (53 iterations at N = 32, with a
+slow tail) shows a larger kappa than the sphere's, so the stopping point,
+not the arithmetic, would decide a comparison at the workload tolerance."""
 import numpy as np
 import pytest
 
@@ -60,17 +62,17 @@ def test_solve_fp64_matches_oracle(case):
     g = ki.stokes_velocity(x)[np.arange(o.cp.n), o.cp.comp - 1][o.primary]
     fy = ki.stokes_forcing(x)
     ff = [ki.stokes_forcing(o.grid.node_xyz(c, o.grid.all_idx()))[..., c - 1] for c in (1, 2, 3)]
-    want = o.solve(g, fy, ff)
-    s = Solver(geom, ki.grid(N))
+    want = o.solve(g, fy, ff, tol=1e-13)
+    s = Solver(geom, ki.grid(N), gmres_tol=1e-13)
     phi = torch.zeros(s.n_primary, dtype=torch.float64, device="cuda")
     u = torch.zeros(3 * N ** 3, dtype=torch.float64, device="cuda")
     p = torch.zeros(N ** 3, dtype=torch.float64, device="cuda")
     s.solve(cuda(g), phi, cuda(fy.T.copy()), cuda(np.concatenate([f.ravel() for f in ff])), u, p)
-    assert s.last_stats["gmres_residual"] < 1e-10
-    assert rel(phi.cpu().numpy(), want["phi"]) < 1e-8
+    assert s.last_stats["gmres_residual"] < 1e-13
+    assert rel(phi.cpu().numpy(), want["phi"]) < 1e-10
     ug = u.cpu().numpy().reshape(3, N, N, N)
     for c in range(3):
-        assert rel(ug[c], want["u"][c]) < 1e-8
-    assert rel(p.cpu().numpy().reshape(N, N, N), want["p"]) < 1e-8
+        assert rel(ug[c], want["u"][c]) < 1e-10
+    assert rel(p.cpu().numpy().reshape(N, N, N), want["p"]) < 1e-10
     assert abs(s.last_stats["gmres_iters"] - want["iters"]) <= 2
     s.close()

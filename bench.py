@@ -59,12 +59,13 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--refine-tol", type=float, default=None, help="MIXED refinement tolerance")
     ap.add_argument("--inner-tol", type=float, default=None, help="MIXED inner FP32 CG tolerance")
-    ap.add_argument("--transforms", default="auto", choices=["auto", "fft", "tensor"],
+    ap.add_argument("--transforms", default="auto", choices=["auto", "fft", "tensor", "staged"],
                     help="kernels of the FP32 axis passes (auto: the setup-time autotuner's choice)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (gradient) leg")
     ap.add_argument("--batch", type=int, default=16,
                     help="instances of the batched leg (kfbim_solve_batch); 0 skips it")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-solve", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--interface-solves", type=int, default=None,
                     help="interface solves per solve for the reference arm's scaling "
                          "(default: the workload's count in INTERFACE_SOLVES)")
@@ -92,6 +93,53 @@ def oracle_sample(workload, reps, per_solve):
         times.append(time.perf_counter() - t)
     t_mv = statistics.median(times)
     return {"matvec_s": t_mv, "times": times, "value": 1.0 / (t_mv * per_solve)}
+
+
+def oracle_full_solve(workload):
+    """One complete oracle solve (Alg. 1: right-hand-side volume solve, GMRES
+    to 1e-10, final fields) of a workload's manufactured data, timed."""
+    from oracle import kfbim as okfbim
+    geom, grid = ki.WORKLOADS[workload]
+    t0 = time.perf_counter()
+    s = okfbim.Setup(geom, grid)
+    t_setup = time.perf_counter() - t0
+    x = s.cp.xyz
+    g = ki.stokes_velocity(x)[np.arange(s.cp.n), s.cp.comp - 1][s.primary]
+    fy = ki.stokes_forcing(x)
+    ff = [ki.stokes_forcing(s.grid.node_xyz(c, s.grid.all_idx()))[..., c - 1] for c in (1, 2, 3)]
+    t0 = time.perf_counter()
+    sol = s.solve(g, fy, ff)
+    t = time.perf_counter() - t0
+    return {"workload": workload, "solve_s": round(t, 3), "setup_s": round(t_setup, 3),
+            "solves_per_s": round(1.0 / t, 5), "gmres_iters": int(sol["iters"]),
+            "value_kind": "timed", "threads": 1}
+
+
+def run_oracle_solve_subprocess(workload):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-solve", "--workload", workload],
+                       capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError("oracle solve failed:\n" + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def run_oracle_parallel(workload, procs):
+    """`procs` single-threaded oracle processes, each one full solve of the
+    workload, started together on the host's cores: aggregate solves/s over
+    the wall time of the slowest."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-solve", "--workload", workload]
+    t0 = time.perf_counter()
+    ps = [subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env)
+          for _ in range(procs)]
+    outs = [p.communicate() for p in ps]
+    wall = time.perf_counter() - t0
+    if any(p.returncode != 0 for p in ps):
+        raise RuntimeError("parallel oracle solve failed:\n" + outs[0][1][-2000:])
+    return {"workload": workload, "processes": procs, "wall_s": round(wall, 3),
+            "solves_per_s": round(procs / wall, 4), "value_kind": "timed",
+            "sample": "%d concurrent single-threaded full oracle solves of %s" % (procs, workload)}
 
 
 def run_oracle_subprocess(workload, reps, per_solve):
@@ -185,6 +233,89 @@ def ncu_traffic(workload, kind="fft"):
     if not m or not t or m.group(1) != kernel_source_hash(kind):
         return None
     return float(t.group(1))
+
+
+# Algorithmic bytes of the hot path by the survey's model (FP32 values, b = 4):
+# one Schur apply S d moves 20 N^3 b (three passes over three fields, read and
+# written, plus d read and q written); the CG vector updates 7 N^3 b (x, r, d,
+# q read; x, r, d written); one CG iteration 27 N^3 b.  The middle pass of
+# the Schur apply (forward transform, spectral weight, inverse transform of
+# the three fields) is 6 N^3 b of the 20.
+MODEL_B = 4
+MODEL_SCHUR_VALUES = 20
+MODEL_CG_VECTOR_VALUES = 7
+MODEL_MIDDLE_PASS_VALUES = 6
+SLAB_CLASSES = ("cg_zfwd", "cg_xy", "cg_zinv", "cg_update")
+
+
+def ncu_traffic_slab(workload):
+    """DRAM bytes per launch of k_cg_xy from the committed ncu summary, if it
+    was taken on the current slab source (else None)."""
+    p = os.path.join(ROOT, "profiles", "cg_xy_%s.md" % workload)
+    if not os.path.exists(p):
+        return None
+    txt = open(p).read()
+    h = hashlib.sha256()
+    for f in ("slab.cuh", "cg_common.cuh", "transforms2.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2303_04992_gb300", "csrc", f), "rb").read())
+    m = re.search(r"kernel_source_sha256_12:\s*([0-9a-f]+)", txt)
+    t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not m or not t or m.group(1) != h.hexdigest()[:12]:
+        return None
+    return float(t.group(1))
+
+
+def roofline_line(kernels, kprof, N3, cg_iters, args, peak, peak_kind):
+    """The roofline object of the bench line.  Dominant kernel: the one with
+    the largest share of the step.  For the slab CG the algorithmic bytes per
+    launch are the survey model's figure for the work the kernel does: k_cg_xy
+    does the middle pass of the Schur apply on all three terms (6 N^3 b); the
+    whole CG iteration (four kernels) is reported beside it against 27 N^3 b."""
+    dom = max(kernels, key=lambda k: kernels[k]["share_of_step"])
+    kd = kernels[dom]
+    line = {"bound": "hbm", "peak": peak, "unit": "GB/s", "peak_source": peak_kind,
+            "kernel": dom, "avg_launch_us": kd["avg_launch_us"], "launches_per_step": kd["launches_per_step"],
+            "share_of_step": kd["share_of_step"], "build_bytes_per_launch": kd["build_bytes_per_launch"],
+            "achieved_build_bytes": kd["achieved_gbs_build_bytes"]}
+    if dom == "cg_xy":
+        model = MODEL_MIDDLE_PASS_VALUES * N3 * MODEL_B
+        line["model"] = "survey 8(d): middle pass of S d on three fields, 6 N^3 b, b = 4"
+        line["traffic"] = ncu_traffic_slab(args.workload)
+    elif dom in ("transform_fp32", "transform_fp64"):
+        # one one-axis pass of one field: 2 N^3 b per job, at the launch's jobs
+        model = kd["build_bytes_per_launch"]
+        line["model"] = "one-axis pass: N^3 values read and written per job"
+        line["traffic"] = ncu_traffic(args.workload, "fft")
+    else:
+        model = kd["build_bytes_per_launch"]
+        line["model"] = "values read and written once"
+        line["traffic"] = None
+    achieved = model / (kd["avg_launch_us"] * 1e-6) / 1e9
+    line["algorithmic_bytes_per_launch"] = model
+    line["achieved"] = round(achieved, 1)
+    line["frac"] = round(achieved / peak, 4)
+    if all(k in kprof and kprof[k][1] for k in SLAB_CLASSES) and cg_iters:
+        ms_cg = sum(kprof[k][0] for k in SLAB_CLASSES)
+        it_us = ms_cg / cg_iters * 1e3
+        bytes_it = (MODEL_SCHUR_VALUES + MODEL_CG_VECTOR_VALUES) * N3 * MODEL_B
+        line["cg_iteration"] = {"us": round(it_us, 3), "model_bytes": bytes_it,
+                                "achieved": round(bytes_it / (it_us * 1e-6) / 1e9, 1),
+                                "frac": round(bytes_it / (it_us * 1e-6) / 1e9 / peak, 4),
+                                "model": "survey 8(d): 27 N^3 b per CG iteration (S d 20, vectors 7)"}
+    return line
+
+
+def golden_error(workload, phi):
+    """Relative max-norm difference of a density from the FP64 oracle's
+    solve of the workload (tests/golden, written by a script that calls only
+    the oracle), or None when no stored solve exists."""
+    p = os.path.join(ROOT, "tests", "golden", "%s_solve.npz" % workload)
+    if not os.path.exists(p):
+        return None
+    want = np.load(p)["phi"]
+    if len(want) != len(phi):
+        return None
+    return float(np.abs(phi - want).max() / np.abs(want).max())
 
 
 def inputs(solver, geom, grid, navier=False):
@@ -362,7 +493,7 @@ def main_kfbim(args):
         mixed_opts["refine_tol"] = args.refine_tol
     if args.inner_tol is not None:
         mixed_opts["inner_tol"] = args.inner_tol
-    mixed_opts["transforms"] = {"auto": 0, "fft": 1, "tensor": 2}[args.transforms]
+    mixed_opts["transforms"] = {"auto": 0, "fft": 1, "tensor": 2, "staged": 3}[args.transforms]
     solver = Solver(geom, grid, precision=MIXED, **mixed_opts, **pde)
     g_h, fpts_h, fgrid_h = inputs(solver, geom, grid, navier)
     g = torch.from_numpy(g_h).to(dev)
@@ -408,23 +539,23 @@ def main_kfbim(args):
     launches = int(sum(s["kernel_launches"] for s in stats))
     phi_mixed = phi.cpu().numpy().copy()
 
-    # dominant kernel: FP32 transform passes, timed around each launch
-    _, _, prof = timed(args.steps, profile=True)
-    ms32, n32, bytes32 = prof["fp32"]
+    # every kernel class timed with CUDA events around its launches (a second
+    # run of the same steps, CG without graphs)
+    _, pstats, _ = timed(args.steps, profile=True)
+    kprof = solver.profile_kernels()
     peak, peak_kind = measured_peaks()
-    achieved = (bytes32 / n32) / (ms32 / n32 * 1e-3) / 1e9 if n32 else 0.0
     tinfo = solver.transforms_info()
-    kind = "tensor" if tinfo["plain"] else "fft"
-    traffic = ncu_traffic(args.workload, kind)
-    kname = ("k_tc_pass (tcgen05 3xTF32 transform-matrix GEMM pass)" if kind == "tensor"
-             else "k_axis_pass2<float> (four-step FFT transform pass)")
-    roofline = {"bound": "hbm", "kernel": kname,
-                "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "peak_source": peak_kind,
-                "traffic": traffic, "algorithmic_bytes_per_launch": bytes32 / max(n32, 1),
-                "avg_launch_us": round(ms32 / max(n32, 1) * 1e3, 3),
-                "launches_per_step": n32 // args.steps,
-                "share_of_step": round(ms32 / args.steps / ms_per_step, 3)}
+    N3 = solver.N ** 3
+    cg_iters_prof = sum(s["cg_iters"] for s in pstats)
+    kernels = {}
+    for k, (ms, n, b) in kprof.items():
+        if n == 0:
+            continue
+        kernels[k] = {"launches_per_step": n // args.steps, "avg_launch_us": round(ms / n * 1e3, 3),
+                      "ms_per_step": round(ms / args.steps, 3), "share_of_step": round(ms / args.steps / ms_per_step, 3),
+                      "build_bytes_per_launch": b / n,
+                      "achieved_gbs_build_bytes": round((b / n) / (ms / n * 1e-3) / 1e9, 1)}
+    roofline = roofline_line(kernels, kprof, N3, cg_iters_prof, args, peak, peak_kind)
 
     # e2e: host buffers through kfbim_solve_host (H2D of g, f; D2H of phi)
     g_pin = torch.from_numpy(g_h).pin_memory().numpy()
@@ -465,7 +596,8 @@ def main_kfbim(args):
         rel = float(np.abs(phi_mixed - p64).max() / np.abs(p64).max())
         fp64 = {"solves_per_s": round(1e3 / ms, 4), "ms_per_solve": round(ms, 2),
                 "gmres_iters": s64.last_stats["gmres_iters"], "cg_iters": s64.last_stats["cg_iters"],
-                "mixed_speedup": round((1e3 / ms_per_step) / (1e3 / ms), 2)}
+                "mixed_speedup": round((1e3 / ms_per_step) / (1e3 / ms), 2),
+                "rel_err_vs_oracle": golden_error(args.workload, p64)}
         s64.close()
 
     adjoint = None
@@ -480,11 +612,14 @@ def main_kfbim(args):
     if rank == 0 and not args.no_cpu:
         per_solve = stats[-1]["interface_solves"]
         o = run_oracle_subprocess(args.workload, 1, per_solve)
+        full = run_oracle_solve_subprocess("sphere32")
+        full["all_cores"] = run_oracle_parallel("sphere32", os.cpu_count() or 1)
         cpu = {"value": round(o["value"], 6), "unit": "solves/s", "cores": 1, "kind": "oracle",
-               "sample": "one oracle matvec (interface solve + trace) on %s, single thread, "
-                         "%.1f s, scaled by the %d interface solves of one GPU solve"
+               "value_kind": "projected",
+               "sample": "projected: one oracle matvec (interface solve + trace) on %s, single thread, "
+                         "%.1f s, times the %d interface solves of one GPU solve"
                          % (args.workload, o["matvec_s"], per_solve),
-               "host": host_cpu()}
+               "timed_solve": full, "host": host_cpu()}
 
     if rank == 0:
         st = stats[-1]
@@ -505,8 +640,11 @@ def main_kfbim(args):
                            "cg_iters": st["cg_iters"], "refine_sweeps": st["refine_sweeps"],
                            "parallelism": "replicas" if world > 1 else "single"},
                 "transforms": dict(tinfo, requested=args.transforms), "adjoint": adjoint,
-                "fp64": fp64, "rel_err_vs_fp64": rel, "batched": batched,
-                "roofline": roofline, "cpu_baseline": cpu,
+                "fp64": fp64, "rel_err_vs_fp64": rel,
+                "rel_err_vs_oracle": golden_error(args.workload, phi_mixed),
+                "oracle_reference": "FP64 oracle solve of the same inputs, GMRES to 1e-13 "
+                                    "(tests/golden/%s_solve.npz)" % args.workload,
+                "batched": batched, "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu,
                 "e2e": e2e, "gpu_launches": launches, "clocks": clk}
         print(json.dumps(line), flush=True)
     if dist:
@@ -534,9 +672,9 @@ def main_reference(args):
             "ms_per_step": round(t_mv * per_solve * 1e3, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "description": WORKLOAD_DESC},
-            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": round(value, 6),
-                             "sample": "each step: one oracle matvec on %s (single thread), scaled "
-                                       "by %d interface solves per solve" % (args.workload, per_solve),
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": round(value, 6), "value_kind": "projected",
+                             "sample": "projected: each step is one oracle matvec on %s (single thread), "
+                                       "times %d interface solves per solve" % (args.workload, per_solve),
                              "host": host_cpu()},
             "e2e": {"value": round(value, 6), "unit": "solves/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -548,6 +686,8 @@ if __name__ == "__main__":
     if a.oracle_sample:
         per = a.interface_solves or INTERFACE_SOLVES.get(a.workload, 1)
         print(json.dumps(oracle_sample(a.workload, a.steps, per)))
+    elif a.oracle_solve:
+        print(json.dumps(oracle_full_solve(a.workload)))
     elif a.impl == "reference":
         main_reference(a)
     else:

@@ -47,6 +47,7 @@
 #ifndef KFBIM_H
 #define KFBIM_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -198,6 +199,27 @@ int kfbim_setup(const kfbim_geometry* geom, const kfbim_grid* grid,
  * are released afterwards).  Same arguments and errors as kfbim_setup. */
 int kfbim_setup_async(const kfbim_geometry* geom, const kfbim_grid* grid,
                       const kfbim_options* opt, void* stream, kfbim_ctx** ctx);
+
+/* Device memory for a context from the caller instead of cudaMalloc, e.g.
+ * a framework's caching allocator that owns the device heap.  alloc returns
+ * `bytes` of device memory on the current device (the context's), at least
+ * 256-byte aligned (else setup fails with E_INVALID), or NULL when it cannot
+ * (E_OOM); free gets back every block, with its size, from kfbim_destroy,
+ * after the device has been synchronised.  Both are called on the thread of
+ * the library call: alloc during setup and, for workspace allocated on first
+ * use (kfbim_solve_batch, kfbim_solve_host), during that call.  Pinned host
+ * buffers and streams still come from the CUDA runtime. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* user);
+  void (*free)(void* ptr, size_t bytes, void* user);
+  void* user;
+} kfbim_allocator;
+
+/* kfbim_setup_async with an optional allocator (NULL: cudaMalloc).  The
+ * allocator struct is copied; its user pointer must stay valid until
+ * kfbim_destroy. */
+int kfbim_setup_ex(const kfbim_geometry* geom, const kfbim_grid* grid, const kfbim_options* opt,
+                   void* stream, const kfbim_allocator* alloc, kfbim_ctx** ctx);
 
 /* Host-only variant of kfbim_setup: builds the control points and every table
  * on the host and touches no GPU (for inspection and host-side tests).  The

@@ -30,6 +30,35 @@ class Geometry(ctypes.Structure):
                 ("user", c_void_p)]
 
 
+ALLOC_FN = ctypes.CFUNCTYPE(c_void_p, ctypes.c_size_t, c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, c_void_p, ctypes.c_size_t, c_void_p)
+
+
+class Allocator(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", c_void_p)]
+
+
+def torch_allocator(device):
+    """kfbim_allocator over torch's CUDA caching allocator on `device`: the
+    context's workspace is then part of torch's memory pool (and of
+    torch.cuda.memory_allocated).  Returns the ctypes struct; it holds the
+    callbacks, which must stay referenced while the context lives."""
+    import torch
+
+    def alloc(nbytes, user):
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes), device))
+        except Exception:   # the library reports E_OOM
+            return None
+
+    def free(ptr, nbytes, user):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    a = Allocator()
+    a.alloc, a.free = ALLOC_FN(alloc), FREE_FN(free)
+    return a
+
+
 class Grid(ctypes.Structure):
     _fields_ = [("N", c_int), ("lo", c_double), ("hi", c_double)]
 
@@ -55,6 +84,8 @@ SYMBOLS = {
                                  ctypes.POINTER(Options), ctypes.POINTER(c_void_p)]),
     "kfbim_setup_async": (c_int, [ctypes.POINTER(Geometry), ctypes.POINTER(Grid), ctypes.POINTER(Options),
                                   c_void_p, ctypes.POINTER(c_void_p)]),
+    "kfbim_setup_ex": (c_int, [ctypes.POINTER(Geometry), ctypes.POINTER(Grid), ctypes.POINTER(Options),
+                               c_void_p, ctypes.POINTER(Allocator), ctypes.POINTER(c_void_p)]),
     "kfbim_control_points": (c_int, [c_void_p, c_int, ctypes.POINTER(c_int64), c_void_p, c_void_p]),
     "kfbim_jump_points": (c_int, [c_void_p, ctypes.POINTER(c_int64), c_void_p]),
     "kfbim_destroy": (c_int, [c_void_p]),
@@ -231,8 +262,10 @@ class Solver:
     least as many values as include/kfbim.h gives for the call (checked before
     the call); work goes on torch's current CUDA stream of that device."""
 
-    def __init__(self, geom, grid, mu=1.0, precision=0, device=True, lam=None, **opts):
-        """lam = None: Stokes; lam = Lame lambda: Navier (Lame) problem."""
+    def __init__(self, geom, grid, mu=1.0, precision=0, device=True, lam=None, allocator=None, **opts):
+        """lam = None: Stokes; lam = Lame lambda: Navier (Lame) problem.
+        allocator = "torch": the context's device workspace comes from torch's
+        caching allocator (kfbim_setup_ex) instead of cudaMalloc."""
         lib = load_library()
         self._device = None
         if device:
@@ -252,12 +285,20 @@ class Solver:
         ctx = c_void_p()
         errors = []
         gm = _geometry(geom, errors)   # holds the ctypes callbacks of a "callback" geometry during setup
+        self._allocator = None
         if device:
             # device work of the setup on torch's current stream
             import torch
             stream = c_void_p(torch.cuda.current_stream(self._device).cuda_stream)
-            st = lib.kfbim_setup_async(ctypes.byref(gm), ctypes.byref(gr), ctypes.byref(o), stream,
-                                       ctypes.byref(ctx))
+            if allocator == "torch":
+                self._allocator = torch_allocator(self._device)
+                st = lib.kfbim_setup_ex(ctypes.byref(gm), ctypes.byref(gr), ctypes.byref(o), stream,
+                                        ctypes.byref(self._allocator), ctypes.byref(ctx))
+            elif allocator is None:
+                st = lib.kfbim_setup_async(ctypes.byref(gm), ctypes.byref(gr), ctypes.byref(o), stream,
+                                           ctypes.byref(ctx))
+            else:
+                raise KfbimError(E_INVALID, "allocator: None or 'torch'")
         else:
             st = lib.kfbim_setup_host(ctypes.byref(gm), ctypes.byref(gr), ctypes.byref(o), ctypes.byref(ctx))
         if errors:

@@ -36,6 +36,7 @@ struct CGScalars {
   double rr, bb, stop, dq, alpha, beta, sumd, rank1, cdiag;
   int done, iters;
   unsigned int ticket[3];
+  int trips;   // iterations run by the device-side loop of a conditional graph
 };
 
 // Sum of the gridDim.x partials by the last block; returns true in that block.

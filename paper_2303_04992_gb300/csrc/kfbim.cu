@@ -37,6 +37,10 @@ struct kfbim_ctx {
   kfbim_options opt{};
   std::string err;
   HostTables host;
+  // device memory through the caller's allocator (kfbim_setup_ex), if any
+  kfbim_allocator allocator{};
+  bool custom_alloc = false;
+  std::vector<size_t> alloc_bytes;   // sizes of `allocs`, for the caller's free
   int N = 0, lg = 0;   // lg = log2 N
   int64_t N3 = 0, n_all = 0, n_prim = 0, n_corr_rows = 0;
   double h = 0, mu = 1;
@@ -98,6 +102,9 @@ struct kfbim_ctx {
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t cg_exec[2] = {nullptr, nullptr};
   int64_t cg_graph_kernels[2] = {0, 0};
+  // whether cg_exec[slot] is the device-side while loop (conditional node)
+  // or kCgGraphIters iterations in a row
+  bool cg_loop[2] = {false, false};
   bool use_graphs = true;
   // optional per-kernel timing (kfbim_profile, kfbim_profile_kernels): CUDA
   // events around launches, totals per kernel class (kfbim_kernel_class)
@@ -147,13 +154,26 @@ struct CudaError {
     if (e_ != cudaSuccess) throw CudaError{std::string(#call) + ": " + cudaGetErrorString(e_)}; \
   } while (0)
 
+// Device memory of the context: from the caller's allocator when setup was
+// given one (kfbim_setup_ex; at least 256-byte aligned), else cudaMalloc.
 template <typename T>
 T* dalloc(kfbim_ctx* c, size_t count) {
   void* p = nullptr;
   if (count == 0) count = 1;
-  cudaError_t e = cudaMalloc(&p, count * sizeof(T));
-  if (e != cudaSuccess) throw CudaError{std::string("cudaMalloc: ") + cudaGetErrorString(e)};
+  const size_t bytes = count * sizeof(T);
+  if (c->custom_alloc) {
+    p = c->allocator.alloc(bytes, c->allocator.user);
+    if (!p) throw CudaError{"allocator callback: out of memory", KFBIM_E_OOM};
+    if (reinterpret_cast<uintptr_t>(p) % 256 != 0) {
+      c->allocator.free(p, bytes, c->allocator.user);
+      throw CudaError{"allocator callback: memory not 256-byte aligned", KFBIM_E_INVALID};
+    }
+  } else {
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) throw CudaError{std::string("cudaMalloc: ") + cudaGetErrorString(e)};
+  }
   c->allocs.push_back(p);
+  c->alloc_bytes.push_back(bytes);
   return static_cast<T*>(p);
 }
 
@@ -560,8 +580,19 @@ struct Slot<double> { static constexpr int v = 0; };
 template <>
 struct Slot<float> { static constexpr int v = 1; };
 
-// The graph of kCgGraphIters iterations for this precision (captured once per
-// context: every pointer it uses is a fixed workspace buffer).
+// Device side of the CG loop of a conditional graph: counts the trip and
+// keeps the loop going while the run is neither converged (done) nor at its
+// iteration cap, so the loop always ends after at most maxit trips.
+__global__ void k_cg_cond(cudaGraphConditionalHandle h, CGScalars* s, int maxit) {
+  const int t = ++s->trips;
+  cudaGraphSetConditional(h, (!s->done && t < maxit) ? 1u : 0u);
+}
+
+// The CG graph of this precision, captured once per context (every pointer
+// it uses is a fixed workspace buffer): a conditional while node whose body is
+// one CG iteration and k_cg_cond, so that a whole CG run is one graph launch
+// and one read of the scalars; where conditional nodes are not available,
+// kCgGraphIters iterations in a row, launched until the run is done.
 template <typename T>
 cudaGraphExec_t cg_graph(kfbim_ctx* c, const CgWs<T>& w) {
   const int slot = Slot<T>::v;
@@ -575,19 +606,45 @@ cudaGraphExec_t cg_graph(kfbim_ctx* c, const CgWs<T>& w) {
   CK(cudaStreamSynchronize(c->cap_stream));
   const int64_t per_iter = g_launches - before;
   g_launches = before;
-  cudaGraph_t graph;
-  CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-  for (int it = 0; it < kCgGraphIters; ++it) cg_iteration<T>(c, w, c->cap_stream);
-  CK(cudaStreamEndCapture(c->cap_stream, &graph));
+  cudaGraph_t graph = nullptr;
+  CK(cudaGraphCreate(&graph, 0));
+  cudaGraphConditionalHandle h{};
+  bool loop = cudaGraphConditionalHandleCreate(&h, graph, 1u, cudaGraphCondAssignDefault) == cudaSuccess;
+  if (loop) {
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    loop = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np) == cudaSuccess;
+    if (loop) {
+      cudaGraph_t body = np.conditional.phGraph_out[0];
+      CK(cudaStreamBeginCaptureToGraph(c->cap_stream, body, nullptr, nullptr, 0,
+                                       cudaStreamCaptureModeThreadLocal));
+      cg_iteration<T>(c, w, c->cap_stream);
+      k_cg_cond<<<1, 1, 0, c->cap_stream>>>(h, c->cgs, std::max(1, c->opt.cg_max));
+      CK(cudaStreamEndCapture(c->cap_stream, &body));
+    }
+  }
+  if (!loop) {
+    (void)cudaGetLastError();   // a refused conditional node is not an error of this call
+    CK(cudaGraphDestroy(graph));
+    CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    for (int it = 0; it < kCgGraphIters; ++it) cg_iteration<T>(c, w, c->cap_stream);
+    CK(cudaStreamEndCapture(c->cap_stream, &graph));
+  }
   g_launches = before;
   CK(cudaGraphInstantiate(&c->cg_exec[slot], graph, 0));
   CK(cudaGraphDestroy(graph));
-  c->cg_graph_kernels[slot] = per_iter * kCgGraphIters;
+  c->cg_loop[slot] = loop;
+  c->cg_graph_kernels[slot] = loop ? per_iter + 1 : per_iter * kCgGraphIters;
   return c->cg_exec[slot];
 }
 
 // CG on (S + 1 1^T / (mu N^3)) x = b from x = 0, vectors of type T, FP64
-// scalars.  The host reads the status once per kCgGraphIters iterations.
+// scalars.  With a loop graph the host reads the scalars once per run; else
+// once per kCgGraphIters iterations.
 template <typename T>
 int cg(kfbim_ctx* c, const T* b, const CgWs<T>& w, double tol, int maxit, cudaStream_t s, int* iters) {
   const int64_t n = c->N3;
@@ -602,6 +659,8 @@ int cg(kfbim_ctx* c, const T* b, const CgWs<T>& w, double tol, int maxit, cudaSt
                                                    c->partial);
   ++g_launches;
   check_launch();
+  const bool loop = graphs && c->cg_loop[Slot<T>::v];
+  if (loop) CK(cudaGraphLaunch(exec, s));
   int launched = 0;
   while (true) {
     CK(cudaMemcpyAsync(c->pinned, c->cgs, sizeof(CGScalars), cudaMemcpyDeviceToHost, s));
@@ -610,9 +669,10 @@ int cg(kfbim_ctx* c, const T* b, const CgWs<T>& w, double tol, int maxit, cudaSt
     CGScalars h;
     std::memcpy(&h, c->pinned, sizeof(CGScalars));
     *iters = h.iters;
+    if (loop) g_launches += (int64_t)h.trips * c->cg_graph_kernels[Slot<T>::v];
     if (!std::isfinite(h.rr)) return KFBIM_E_NONFINITE;
     if (h.done) return KFBIM_OK;
-    if (launched >= maxit) return KFBIM_E_NOCONV;
+    if (loop || launched >= maxit) return KFBIM_E_NOCONV;
     if (graphs) {
       CK(cudaGraphLaunch(exec, s));
       g_launches += c->cg_graph_kernels[Slot<T>::v];
@@ -1814,7 +1874,8 @@ void kfbim_default_options(kfbim_options* o) {
 }
 
 static int setup_common(const kfbim_geometry* geom, const kfbim_grid* grid, const kfbim_options* opt,
-                        kfbim_ctx** out, bool device, cudaStream_t stream = nullptr) {
+                        kfbim_ctx** out, bool device, cudaStream_t stream = nullptr,
+                        const kfbim_allocator* alloc = nullptr) {
   if (!out) return KFBIM_E_INVALID;
   *out = nullptr;
   if (!geom || !grid || !opt) return KFBIM_E_INVALID;
@@ -1824,6 +1885,7 @@ static int setup_common(const kfbim_geometry* geom, const kfbim_grid* grid, cons
       opt->precision < KFBIM_FP64 || opt->precision > KFBIM_MIXED_TF32)
     return KFBIM_E_INVALID;
   if (opt->precision == KFBIM_MIXED_TF32 && N != TC_N) return KFBIM_E_INVALID;
+  if (alloc && (!alloc->alloc || !alloc->free)) return KFBIM_E_INVALID;
   if (geom->kind < KFBIM_SPHERE || geom->kind > KFBIM_CALLBACK) return KFBIM_E_INVALID;
   if (geom->kind == KFBIM_CALLBACK && (!geom->F || !geom->derivs)) return KFBIM_E_INVALID;
   if (geom->kind == KFBIM_TORUS && !(geom->params[0] > 0.0 && geom->params[1] > geom->params[0]))
@@ -1844,6 +1906,10 @@ static int setup_common(const kfbim_geometry* geom, const kfbim_grid* grid, cons
     c->opt.transforms = KFBIM_XF_TENSOR;
   }
   c->setup_stream = stream;
+  if (alloc) {
+    c->allocator = *alloc;
+    c->custom_alloc = true;
+  }
   c->N = N;
   while ((1 << c->lg) < N) ++c->lg;
   c->N3 = (int64_t)N * N * N;
@@ -1881,6 +1947,7 @@ static int setup_common(const kfbim_geometry* geom, const kfbim_grid* grid, cons
       std::fprintf(stderr, "kfbim_setup: %s\n", e.msg.c_str());
       // releases whatever was created so far (memory, pinned buffers, stream, graphs)
       kfbim_destroy(c.release());
+      if (e.code != KFBIM_E_CUDA) return e.code;
       return e.msg.find("out of memory") != std::string::npos ? KFBIM_E_OOM : KFBIM_E_CUDA;
     }
     c->device = true;
@@ -1912,6 +1979,11 @@ int kfbim_setup_host(const kfbim_geometry* geom, const kfbim_grid* grid, const k
 int kfbim_setup_async(const kfbim_geometry* geom, const kfbim_grid* grid, const kfbim_options* opt,
                       void* stream, kfbim_ctx** out) {
   return setup_common(geom, grid, opt, out, true, (cudaStream_t)stream);
+}
+
+int kfbim_setup_ex(const kfbim_geometry* geom, const kfbim_grid* grid, const kfbim_options* opt, void* stream,
+                   const kfbim_allocator* alloc, kfbim_ctx** out) {
+  return setup_common(geom, grid, opt, out, true, (cudaStream_t)stream, alloc);
 }
 
 int kfbim_control_points(const kfbim_ctx* c, int comp, int64_t* n, double* xyz, double* normal) {
@@ -1956,7 +2028,10 @@ int kfbim_destroy(kfbim_ctx* c) {
   for (auto& e : c->cg_exec)
     if (e) cudaGraphExecDestroy(e);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
-  for (void* p : c->allocs) cudaFree(p);
+  for (size_t k = 0; k < c->allocs.size(); ++k) {
+    if (c->custom_alloc) c->allocator.free(c->allocs[k], c->alloc_bytes[k], c->allocator.user);
+    else cudaFree(c->allocs[k]);
+  }
   if (c->pinned) cudaFreeHost(c->pinned);
   if (c->bpinned) cudaFreeHost(c->bpinned);
   delete c;

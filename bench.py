@@ -522,7 +522,7 @@ def main_kfbim(args):
         torch.cuda.synchronize()
         prof = None
         if profile:
-            prof = solver.profile(None)
+            prof = solver.profile_kernels()
             solver.profile(False)
         return sum(s.elapsed_time(e) for s, e in zip(starts, ends)), stats, prof
 
@@ -541,8 +541,7 @@ def main_kfbim(args):
 
     # every kernel class timed with CUDA events around its launches (a second
     # run of the same steps, CG without graphs)
-    _, pstats, _ = timed(args.steps, profile=True)
-    kprof = solver.profile_kernels()
+    _, pstats, kprof = timed(args.steps, profile=True)
     peak, peak_kind = measured_peaks()
     tinfo = solver.transforms_info()
     N3 = solver.N ** 3

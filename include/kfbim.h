@@ -39,6 +39,11 @@
  *    workspace; the kernel shared-memory limits the library raises are kept
  *    per device under a lock).  Calls on one context must not overlap.  The
  *    kernel_launches statistic counts the launches of the call's own thread.
+ *  - CUDA graphs: iterative loops (the Schur CG) run as captured CUDA graphs,
+ *    the CG as one graph with a device-side loop (a conditional node).  With
+ *    the environment variable KFBIM_CUDA_GRAPHS=0 at kfbim_setup the kernels
+ *    are launched one by one instead (same results; kernel profilers cannot
+ *    profile kernels inside graphs with conditional nodes).
  *  - Return value: KFBIM_OK or a negative kfbim_status; kfbim_last_error()
  *    returns the message of the last failure on that context.  Invalid inputs
  *    are reported, never aborted on.  On KFBIM_E_NOCONV the outputs still hold

@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <mutex>
@@ -1579,13 +1580,28 @@ void cg_batch(kfbim_ctx* c, const std::vector<int>& act, double tol, cudaStream_
       A.partial[k] = c->bpartial + (size_t)RED_BLOCKS * run[k];
     }
     const dim3 grid(RED_BLOCKS, (unsigned)run.size());
-    for (int it = 0; it < kCgGraphIters; ++it) {
-      schur_apply_batch(c, run, s);
-      k_cg_alpha_b<float><<<grid, RED_THREADS, 0, s>>>(A, n);
-      k_cg_update_b<float><<<grid, RED_THREADS, 0, s>>>(A, n);
-      k_cg_direction_b<float><<<grid, RED_THREADS, 0, s>>>(A, n);
-      g_launches += 3;
-      check_launch();
+    if (c->slab) {
+      // the four slab kernels of all running instances, one launch each per
+      // iteration (blockIdx.y = instance; the single-run arithmetic)
+      std::vector<SlabCg> runs;
+      for (int b : run) {
+        const kfbim_ctx::Slot& w = c->bs[b];
+        runs.push_back({c->N, w.x, w.r, w.d, w.q, w.T6, w.T6 + n, c->d_twc32, c->d_q32, c->d_s2f,
+                        (float)(1.0 / c->mu), &c->bcgs[b], c->bpartial + (size_t)RED_BLOCKS * b});
+      }
+      for (int it = 0; it < kCgGraphIters; ++it) {
+        g_launches += slab_cg_iteration_batch(runs.data(), (int)runs.size(), s);
+        check_launch();
+      }
+    } else {
+      for (int it = 0; it < kCgGraphIters; ++it) {
+        schur_apply_batch(c, run, s);
+        k_cg_alpha_b<float><<<grid, RED_THREADS, 0, s>>>(A, n);
+        k_cg_update_b<float><<<grid, RED_THREADS, 0, s>>>(A, n);
+        k_cg_direction_b<float><<<grid, RED_THREADS, 0, s>>>(A, n);
+        g_launches += 3;
+        check_launch();
+      }
     }
     launched += kCgGraphIters;
   }
@@ -1906,6 +1922,9 @@ static int setup_common(const kfbim_geometry* geom, const kfbim_grid* grid, cons
     c->opt.transforms = KFBIM_XF_TENSOR;
   }
   c->setup_stream = stream;
+  // KFBIM_CUDA_GRAPHS=0 launches the CG kernels one by one (kernel profilers
+  // cannot look inside graphs with conditional nodes)
+  if (const char* g = std::getenv("KFBIM_CUDA_GRAPHS")) c->use_graphs = std::strcmp(g, "0") != 0;
   if (alloc) {
     c->allocator = *alloc;
     c->custom_alloc = true;

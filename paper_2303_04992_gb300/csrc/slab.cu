@@ -12,53 +12,88 @@ namespace {
 
 constexpr int kUpdBlocks = 1216;   // 8 x 152 SMs
 
-template <int N>
-cudaError_t prepare_n() {
-  cudaError_t e = cudaFuncSetAttribute(slab::k_cg_xy<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+template <int N, int MAXB>
+cudaError_t prepare_nb() {
+  cudaError_t e = cudaFuncSetAttribute(slab::k_cg_xy<N, MAXB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)slab::XySmem<N>::bytes);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(slab::k_cg_zfwd<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(slab::k_cg_zfwd<N, MAXB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)slab::ZSmem<N>::bytes);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(slab::k_cg_zinv<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(slab::k_cg_zinv<N, MAXB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)slab::ZSmem<N>::bytes);
   return e;
 }
 
-// Kernel `which` of the iteration: 0 k_cg_zfwd, 1 k_cg_xy, 2 k_cg_zinv, 3 k_cg_upd.
 template <int N>
-void launch_n(int which, const SlabCg& a, cudaStream_t st) {
+cudaError_t prepare_n() {
+  cudaError_t e = prepare_nb<N, 1>();
+  return e == cudaSuccess ? prepare_nb<N, kSlabBatchMax>() : e;
+}
+
+template <int MAXB>
+slab::SlabArgs<MAXB> make_args(const SlabCg* runs, int nrun) {
+  slab::SlabArgs<MAXB> a{};
+  for (int k = 0; k < nrun; ++k) {
+    a.x[k] = runs[k].x;
+    a.r[k] = runs[k].r;
+    a.d[k] = runs[k].d;
+    a.q[k] = runs[k].q;
+    a.z1[k] = runs[k].z1;
+    a.z3[k] = runs[k].z3;
+    a.s[k] = runs[k].s;
+    a.partial[k] = runs[k].partial;
+  }
+  return a;
+}
+
+// Kernel `which` of the iteration: 0 k_cg_zfwd, 1 k_cg_xy, 2 k_cg_zinv, 3 k_cg_upd.
+template <int N, int MAXB>
+void launch_nb(int which, const slab::SlabArgs<MAXB>& args, const SlabCg& t, int nrun, cudaStream_t st) {
   using C = slab::Cfg<N>;
-  const int zblocks = (N / C::TILE) * N;
+  const unsigned zblocks = (N / C::TILE) * N;
   switch (which) {
     case 0:
-      slab::k_cg_zfwd<N><<<zblocks, C::TILE_THREADS, slab::ZSmem<N>::bytes, st>>>(a.r, a.d, a.z1, a.z3, a.tw, a.qN,
-                                                                                  a.s, a.partial);
+      slab::k_cg_zfwd<N, MAXB><<<dim3(zblocks, nrun), C::TILE_THREADS, slab::ZSmem<N>::bytes, st>>>(args, t.tw,
+                                                                                                     t.qN);
       break;
     case 1:
-      slab::k_cg_xy<N><<<N, C::PLANE_THREADS, slab::XySmem<N>::bytes, st>>>(a.z1, a.z3, a.tw, a.qN, a.s2,
-                                                                            a.inv_mu, a.s);
+      slab::k_cg_xy<N, MAXB><<<dim3(N, nrun), C::PLANE_THREADS, slab::XySmem<N>::bytes, st>>>(args, t.tw, t.qN,
+                                                                                              t.s2, t.inv_mu);
       break;
     case 2:
-      slab::k_cg_zinv<N><<<zblocks, C::TILE_THREADS, slab::ZSmem<N>::bytes, st>>>(a.z1, a.z3, a.d, a.q, a.tw,
-                                                                                  a.qN, a.s, a.partial);
+      slab::k_cg_zinv<N, MAXB><<<dim3(zblocks, nrun), C::TILE_THREADS, slab::ZSmem<N>::bytes, st>>>(args, t.tw,
+                                                                                                     t.qN);
       break;
     default: {
       const int64_t n4 = (int64_t)N * N * N / 4;
-      const int blocks = (int)((n4 + 255) / 256 < kUpdBlocks ? (n4 + 255) / 256 : kUpdBlocks);
-      slab::k_cg_upd<<<blocks, 256, 0, st>>>(a.x, a.r, a.d, a.q, n4, a.s, a.partial);
+      const unsigned blocks = (unsigned)((n4 + 255) / 256 < kUpdBlocks ? (n4 + 255) / 256 : kUpdBlocks);
+      slab::k_cg_upd<MAXB><<<dim3(blocks, nrun), 256, 0, st>>>(args, n4);
     }
   }
 }
 
 template <int N>
+void launch_n(int which, const SlabCg& a, cudaStream_t st) {
+  launch_nb<N, 1>(which, make_args<1>(&a, 1), a, 1, st);
+}
+
+template <int N>
 void schur_n(const SlabCg& a, cudaStream_t st) {
-  for (int k = 0; k < 3; ++k) launch_n<N>(k, a, st);
+  const slab::SlabArgs<1> args = make_args<1>(&a, 1);
+  for (int k = 0; k < 3; ++k) launch_nb<N, 1>(k, args, a, 1, st);
 }
 
 template <int N>
 void iteration_n(const SlabCg& a, cudaStream_t st) {
-  for (int k = 0; k < 4; ++k) launch_n<N>(k, a, st);
+  const slab::SlabArgs<1> args = make_args<1>(&a, 1);
+  for (int k = 0; k < 4; ++k) launch_nb<N, 1>(k, args, a, 1, st);
+}
+
+template <int N>
+void iteration_batch_n(const SlabCg* runs, int nrun, cudaStream_t st) {
+  const slab::SlabArgs<kSlabBatchMax> args = make_args<kSlabBatchMax>(runs, nrun);
+  for (int k = 0; k < 4; ++k) launch_nb<N, kSlabBatchMax>(k, args, runs[0], nrun, st);
 }
 
 }  // namespace
@@ -77,6 +112,17 @@ int slab_cg_iteration(const SlabCg& a, cudaStream_t st) {
     case 128: iteration_n<128>(a, st); break;
     case 64: iteration_n<64>(a, st); break;
     case 32: iteration_n<32>(a, st); break;
+    default: return 0;
+  }
+  return 4;
+}
+
+int slab_cg_iteration_batch(const SlabCg* runs, int nrun, cudaStream_t st) {
+  if (nrun < 1 || nrun > kSlabBatchMax) return 0;
+  switch (runs[0].N) {
+    case 128: iteration_batch_n<128>(runs, nrun, st); break;
+    case 64: iteration_batch_n<64>(runs, nrun, st); break;
+    case 32: iteration_batch_n<32>(runs, nrun, st); break;
     default: return 0;
   }
   return 4;

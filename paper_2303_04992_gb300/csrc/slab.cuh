@@ -24,15 +24,18 @@
 // DCT-II and DST-II of one line together, since the DST-II input is the
 // DCT-II input with its second half negated).  A team of M = N/16 threads
 // computes one complex FFT: a radix-16 DFT in registers, a twiddle, an
-// exchange through the team's own shared-memory buffer and radix-M DFTs in
-// registers.  Within a warp the teams only synchronise with __syncwarp.
+// exchange through the shared memory of the team's own two lines and radix-M
+// DFTs in registers.  Within a warp the teams only synchronise with
+// __syncwarp.
 //
 // Shared-memory layouts avoid bank conflicts for the access patterns of the
 // team FFT (stride 2 and runs of 8 along a line, 4 teams per warp):
 //   plane: element x of row y at y N + (x ^ plane_sw(y)),
 //   z tile: element z of line l (32 lines) at 32 z + (l ^ tile_sw(z)),
-//   exchange: separate real and imaginary arrays, rows of M + 1 floats,
-//   team buffers 8 banks apart.
+//   exchange: in the z kernels the team's own two lines (real parts in one,
+//   imaginary parts in the other, index c at position xpi(c)); in the plane
+//   kernel a separate buffer per team (rows of M + 1, teams 8 banks apart),
+//   which keeps its register use within the 128 of 512 threads.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -49,9 +52,6 @@ template <int N>
 struct Cfg {
   static constexpr int M = N / 16;                        // threads per complex FFT
   static constexpr int NS = 16 / M;                       // radix-M DFTs per thread
-  static constexpr int XS = M + 1;                        // exchange row (floats)
-  static constexpr int XN = (16 * XS > N) ? 16 * XS : N;  // exchange floats per team (Re or Im)
-  static constexpr int TS = (XN + 31) / 32 * 32 + 8;      // team stride, 8 banks apart
   static constexpr int PLANE_TEAMS = N / 2;               // xy kernel: one pair of lines per team
   static constexpr int PLANE_THREADS = PLANE_TEAMS * M;
   static constexpr int TILE = 32;                         // z kernels: lines per CTA
@@ -60,18 +60,17 @@ struct Cfg {
 
 template <int N>
 struct XySmem {
-  using C = Cfg<N>;
   static constexpr size_t plane = sizeof(float) * N * N;
-  static constexpr size_t xch = sizeof(float) * C::PLANE_TEAMS * C::TS;
+  // two planes (Z1 -> P and Q; Z3 -> P after them), the teams' exchange
+  // buffers (real and imaginary arrays) and the tables
+  static constexpr size_t xch = sizeof(float) * Cfg<N>::PLANE_TEAMS * ((16 * (Cfg<N>::M + 1) + 31) / 32 * 32 + 8);
   static constexpr size_t bytes = 2 * plane + 2 * xch + sizeof(C2<float>) * 3 * N + sizeof(float) * 2 * N;
 };
 
 template <int N>
 struct ZSmem {
-  using C = Cfg<N>;
-  static constexpr size_t tile = sizeof(float) * N * C::TILE;
-  static constexpr size_t xch = sizeof(float) * C::TILE * C::TS;
-  static constexpr size_t bytes = 2 * tile + 2 * xch + sizeof(C2<float>) * 3 * N;
+  static constexpr size_t tile = sizeof(float) * N * Cfg<N>::TILE;
+  static constexpr size_t bytes = 2 * tile + sizeof(C2<float>) * 3 * N;
 };
 
 // Row swizzle of a plane: bits 0, 3 and 4 of the column index, from the row
@@ -81,7 +80,8 @@ struct ZSmem {
 // distinct (y mod 16) >> 1, any 8 even or odd rows of 16, and any aligned 8
 // rows fall on distinct banks.
 __device__ __forceinline__ int plane_sw(int y) {
-  const int y0 = y & 1, y1 = (y >> 1) & 1, y2 = (y >> 2) & 1, y3 = (y >> 3) & 1;
+  const int y16 = y & 15;
+  const int y0 = y16 & 1, y1 = (y16 >> 1) & 1, y2 = (y16 >> 2) & 1, y3 = y16 >> 3;
   return (y0 ^ y1 ^ y3) | (y1 << 3) | (y2 << 4);
 }
 
@@ -90,6 +90,14 @@ __device__ __forceinline__ int plane_sw(int y) {
 // teams of a warp take lines 4w + t (bits 0, 1).  Multiples of 4 keep
 // 16-byte groups of lines together for vector copies.
 __device__ __forceinline__ int tile_sw(int z) { return (((z >> 1) ^ ((z & 1) << 2)) & 7) << 2; }
+
+// Position along the team's two lines of logical exchange index c (the
+// team's lines double as its exchange buffer: real parts in line a,
+// imaginary parts in line b).  Flipping bits 0..2 by bits 4..6 makes the
+// exchange's three access patterns (8 consecutive indices; stride 16; the
+// natural index of the FFT output) fall on distinct banks with the swizzles
+// above.
+__device__ __forceinline__ int xpi(int c) { return c ^ ((c >> 4) & 7); }
 
 template <int N>
 struct PlaneRow {
@@ -113,17 +121,45 @@ struct TileCol {
   __device__ __forceinline__ float& operator[](int z) const { return p[z * 32 + (l ^ tile_sw(z))]; }
 };
 
-// One complex FFT of length N by a team of M threads (lane m).  On entry
-// v[r] = z[m + M r], r = 0..15; on return the team's exchange buffer (xr, xi)
-// holds Z[k] at index k, INV: exp(+2 pi i n k / N).  Four steps:
-// Y[m][s] = DFT16_r z[m + M r], times w_N^{m s}, exchanged, then
-// Z[s + 16 k] = DFT_M over m of the twiddled Y[m][s].
-template <int N, bool INV>
-__device__ __forceinline__ void team_fft(C2<float> (&v)[16], float* xr, float* xi, const C2<float>* tw, int m) {
+// The exchange buffer of a team's complex FFT, logical index c = s M + m in
+// the first step and the natural index k of the FFT output Z[k] after it.
+// XLines: the team's own two lines (in place; the post-processing reads all
+// of Z before it writes the lines).  XBuf: a separate buffer of the team
+// (separate real and imaginary arrays, rows of M + 1 floats).
+template <class LA, class LB>
+struct XLines {
+  LA A;
+  LB B;
+  static constexpr bool in_place = true;
+  __device__ __forceinline__ float& re(int c) const { return A[xpi(c)]; }
+  __device__ __forceinline__ float& im(int c) const { return B[xpi(c)]; }
+};
+template <class LA, class LB>
+__device__ __forceinline__ XLines<LA, LB> xlines(const LA& A, const LB& B) {
+  return {A, B};
+}
+template <int N>
+struct XBuf {
+  float* xr;
+  float* xi;
+  static constexpr bool in_place = false;
+  static constexpr int TS = (16 * (Cfg<N>::M + 1) + 31) / 32 * 32 + 8;   // team stride, 8 banks apart
+  __device__ __forceinline__ float& re(int c) const { return xr[c + c / Cfg<N>::M]; }
+  __device__ __forceinline__ float& im(int c) const { return xi[c + c / Cfg<N>::M]; }
+};
+
+// One complex FFT of length N by a team of M threads (lane m) through the
+// exchange X.  On entry v[r] = z[m + M r], r = 0..15, the inputs already read
+// from the lines; on return X holds Z[k] at logical index k, INV:
+// exp(+2 pi i n k / N).  Four steps: Y[m][s] = DFT16_r z[m + M r], times
+// w_N^{m s}, exchanged, then Z[s + 16 k] = DFT_M over m of the twiddled
+// Y[m][s], lane m taking s = NS m + q.
+template <int N, bool INV, class X>
+__device__ __forceinline__ void team_fft(C2<float> (&v)[16], const X& x, const C2<float>* tw, int m) {
   using C = Cfg<N>;
-  constexpr int M = C::M, NS = C::NS, XS = C::XS;
+  constexpr int M = C::M, NS = C::NS;
   dft_reg<16, INV, float>(v);
-  __syncwarp();   // the team's previous reads of the exchange buffer are done
+  __syncwarp();   // the team has read its inputs and the previous output
 #pragma unroll
   for (int s = 0; s < 16; ++s) {
     C2<float> y = v[s];
@@ -132,8 +168,8 @@ __device__ __forceinline__ void team_fft(C2<float> (&v)[16], float* xr, float* x
       if (INV) w.y = -w.y;
       y = cmul(y, w);
     }
-    xr[s * XS + m] = y.x;
-    xi[s * XS + m] = y.y;
+    x.re(s * M + m) = y.x;
+    x.im(s * M + m) = y.y;
   }
   __syncwarp();
   C2<float> w2[NS][M];
@@ -141,8 +177,8 @@ __device__ __forceinline__ void team_fft(C2<float> (&v)[16], float* xr, float* x
   for (int q = 0; q < NS; ++q)
 #pragma unroll
     for (int k = 0; k < M; ++k) {
-      const int s = q * M + m;
-      w2[q][k] = {xr[s * XS + k], xi[s * XS + k]};
+      const int c = (NS * m + q) * M + k;
+      w2[q][k] = {x.re(c), x.im(c)};
     }
   __syncwarp();
 #pragma unroll
@@ -150,9 +186,9 @@ __device__ __forceinline__ void team_fft(C2<float> (&v)[16], float* xr, float* x
     dft_reg<M, INV, float>(w2[q]);
 #pragma unroll
     for (int k = 0; k < M; ++k) {
-      const int idx = q * M + m + 16 * k;
-      xr[idx] = w2[q][k].x;
-      xi[idx] = w2[q][k].y;
+      const int c = NS * m + q + 16 * k;
+      x.re(c) = w2[q][k].x;
+      x.im(c) = w2[q][k].y;
     }
   }
   __syncwarp();
@@ -164,6 +200,7 @@ template <int N, class LA, class LB>
 __device__ __forceinline__ void pre_fwd_pair(C2<float> (&v)[16], const LA& A, const LB& B, bool dsta, bool dstb,
                                              int m) {
   constexpr int M = Cfg<N>::M;
+  __syncwarp();   // the team's earlier writes to the lines are visible
 #pragma unroll
   for (int r = 0; r < 16; ++r) {
     const int n = m + M * r;
@@ -181,6 +218,7 @@ __device__ __forceinline__ void pre_fwd_pair(C2<float> (&v)[16], const LA& A, co
 template <int N, class L>
 __device__ __forceinline__ void pre_fwd_cs(C2<float> (&v)[16], const L& A, int m) {
   constexpr int M = Cfg<N>::M;
+  __syncwarp();
 #pragma unroll
   for (int r = 0; r < 16; ++r) {
     const int n = m + M * r;
@@ -191,20 +229,35 @@ __device__ __forceinline__ void pre_fwd_cs(C2<float> (&v)[16], const L& A, int m
 }
 
 // Forward output: for k = m + M r the transforms of both packed lines at
-// mode k, X_k = Re(exp(-i pi k / 2N) V_k) (DCT-II at position k; DST-II at
-// position N - 1 - k), handed to put(k, xa, xb).
-template <int N, class F>
-__device__ __forceinline__ void post_fwd(const float* xr, const float* xi, const C2<float>* qN, int m, F&& put) {
+// mode k, X_k = Re(exp(-i pi k / 2N) V_k) (a DCT-II line puts it at position
+// k, a DST-II line at N - 1 - k), handed to put(k, xa, xb).  In place, every
+// value is computed before any put, once the whole team has read Z.
+template <int N, class X, class F>
+__device__ __forceinline__ void post_fwd(const X& x, const C2<float>* qN, int m, F&& put) {
   constexpr int M = Cfg<N>::M;
-#pragma unroll
-  for (int r = 0; r < 16; ++r) {
-    const int k = m + M * r;
+  auto value = [&](int k, float& va, float& vb) {
     const int kc = (N - k) & (N - 1);
-    const float zkx = xr[k], zky = xi[k], zcx = xr[kc], zcy = xi[kc];
+    const float zkx = x.re(k), zky = x.im(k), zcx = x.re(kc), zcy = x.im(kc);
     const float vax = 0.5f * (zkx + zcx), vay = 0.5f * (zky - zcy);
     const float vbx = 0.5f * (zky + zcy), vby = -0.5f * (zkx - zcx);
     const C2<float> q = qN[k];
-    put(k, q.x * vax - q.y * vay, q.x * vbx - q.y * vby);
+    va = q.x * vax - q.y * vay;
+    vb = q.x * vbx - q.y * vby;
+  };
+  if constexpr (X::in_place) {
+    float oa[16], ob[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) value(m + M * r, oa[r], ob[r]);
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < 16; ++r) put(m + M * r, oa[r], ob[r]);
+  } else {
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      float va, vb;
+      value(m + M * r, va, vb);
+      put(m + M * r, va, vb);
+    }
   }
 }
 
@@ -214,6 +267,7 @@ template <int N, class LA, class LB>
 __device__ __forceinline__ void pre_inv_pair(C2<float> (&v)[16], const LA& A, const LB& B, bool dsta, bool dstb,
                                              const C2<float>* qN, int m) {
   constexpr int M = Cfg<N>::M;
+  __syncwarp();
 #pragma unroll
   for (int r = 0; r < 16; ++r) {
     const int k = m + M * r;
@@ -230,19 +284,32 @@ __device__ __forceinline__ void pre_inv_pair(C2<float> (&v)[16], const LA& A, co
 }
 
 // Inverse output: x_{2n} = v_n, x_{2n+1} = v_{N-1-n} (1/N; DST-III negates the
-// odd outputs); for o = m + M r, put(o, xa, xb).
-template <int N, class F>
-__device__ __forceinline__ void post_inv(const float* xr, const float* xi, bool dsta, bool dstb, int m, F&& put) {
+// odd outputs); for o = m + M r, put(o, xa, xb), in place after the whole
+// team has read Z.
+template <int N, class X, class F>
+__device__ __forceinline__ void post_inv(const X& x, bool dsta, bool dstb, int m, F&& put) {
   constexpr int M = Cfg<N>::M;
   constexpr float invN = 1.0f / N;
-#pragma unroll
-  for (int r = 0; r < 16; ++r) {
-    const int o = m + M * r;
+  auto value = [&](int o, float& va, float& vb) {
     const bool odd = (o & 1) != 0;
-    const int n = odd ? N - 1 - (o >> 1) : (o >> 1);
-    const float sa = (dsta && odd) ? -invN : invN;
-    const float sb = (dstb && odd) ? -invN : invN;
-    put(o, xr[n] * sa, xi[n] * sb);
+    const int c = odd ? N - 1 - (o >> 1) : (o >> 1);
+    va = x.re(c) * ((dsta && odd) ? -invN : invN);
+    vb = x.im(c) * ((dstb && odd) ? -invN : invN);
+  };
+  if constexpr (X::in_place) {
+    float oa[16], ob[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) value(m + M * r, oa[r], ob[r]);
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < 16; ++r) put(m + M * r, oa[r], ob[r]);
+  } else {
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      float va, vb;
+      value(m + M * r, va, vb);
+      put(m + M * r, va, vb);
+    }
   }
 }
 
@@ -280,26 +347,45 @@ __device__ __forceinline__ void load_plane(float* P, const float* __restrict__ g
   }
 }
 
+
 // ------------------------------------------------------------ the kernels
+// The buffers of up to MAXB independent CG runs on one grid (blockIdx.y
+// selects the run): each run's blocks reduce exactly as a single run's, so a
+// run's arithmetic does not depend on the batch it is part of.
+template <int MAXB>
+struct SlabArgs {
+  float* x[MAXB];
+  float* r[MAXB];
+  float* d[MAXB];
+  float* q[MAXB];
+  float* z1[MAXB];
+  float* z3[MAXB];
+  CGScalars* s[MAXB];
+  double* partial[MAXB];
+};
 
 // d = r + beta d; Z1 = DST-II_z d, Z3 = DCT-II_z d; sumd = sum d.  CTA: 32
-// lines along z at x = x0 .. x0 + 31, y fixed (1D grid, N/32 x N blocks).
-template <int N>
+// lines along z at x = x0 .. x0 + 31, y fixed (grid N/32 x N blocks per run).
+template <int N, int MAXB>
 __global__ void __launch_bounds__(Cfg<N>::TILE_THREADS)
-k_cg_zfwd(const float* __restrict__ r, float* __restrict__ d, float* __restrict__ z1, float* __restrict__ z3,
-          const C2<float>* __restrict__ twg, const C2<float>* __restrict__ qg, CGScalars* s,
-          double* __restrict__ partial) {
+k_cg_zfwd(const __grid_constant__ SlabArgs<MAXB> args, const C2<float>* __restrict__ twg,
+          const C2<float>* __restrict__ qg) {
   using C = Cfg<N>;
   constexpr int T = C::TILE_THREADS, M = C::M;
   __shared__ double sh[32];
   __shared__ double total;
+  const int b = blockIdx.y;
+  CGScalars* s = args.s[b];
   if (s->done) return;
+  const float* __restrict__ r = args.r[b];
+  float* __restrict__ d = args.d[b];
+  float* __restrict__ z1 = args.z1[b];
+  float* __restrict__ z3 = args.z3[b];
+  double* __restrict__ partial = args.partial[b];
   extern __shared__ __align__(16) unsigned char smz[];
   float* D = reinterpret_cast<float*>(smz);
   float* E = D + N * C::TILE;
-  float* Xr = E + N * C::TILE;
-  float* Xi = Xr + C::TILE * C::TS;
-  C2<float>* tw = reinterpret_cast<C2<float>*>(Xi + C::TILE * C::TS);
+  C2<float>* tw = reinterpret_cast<C2<float>*>(E + N * C::TILE);
   C2<float>* qN = tw + 2 * N;
   load_tables<N>(tw, qN, nullptr, twg, qg, nullptr, T);
   const int xb = blockIdx.x % (N / C::TILE), y = blockIdx.x / (N / C::TILE);
@@ -326,13 +412,14 @@ k_cg_zfwd(const float* __restrict__ r, float* __restrict__ d, float* __restrict_
   __syncthreads();
   {
     const int tm = threadIdx.x / M, m = threadIdx.x % M;
-    const TileCol src{D, tm}, ce{E, tm};
+    const TileCol A{D, tm}, B{E, tm};
     C2<float> v[16];
-    pre_fwd_cs<N>(v, src, m);
-    team_fft<N, false>(v, Xr + tm * C::TS, Xi + tm * C::TS, tw, m);
-    post_fwd<N>(Xr + tm * C::TS, Xi + tm * C::TS, qN, m, [&](int k, float c, float sn) {
-      ce[k] = c;             // DCT-II mode k -> Z3
-      src[N - 1 - k] = sn;   // DST-II mode N-1-k -> Z1
+    pre_fwd_cs<N>(v, A, m);
+    const auto X = xlines(A, B);
+    team_fft<N, false>(v, X, tw, m);
+    post_fwd<N>(X, qN, m, [&](int k, float c, float sn) {
+      B[k] = c;             // DCT-II mode k -> Z3
+      A[N - 1 - k] = sn;    // DST-II mode N-1-k -> Z1
     });
   }
   __syncthreads();
@@ -346,33 +433,60 @@ k_cg_zfwd(const float* __restrict__ r, float* __restrict__ d, float* __restrict_
   if (last_block_sum(acc.value(), partial, &s->ticket[2], sh, &total) && threadIdx.x == 0) s->sumd = total;
 }
 
+// Forward transform, spectral weight and inverse transform along the columns
+// xa, xa + 1 of a plane (the y part of a Schur term), in place.  dst:
+// DST-II/III (else DCT-II/III) along y; w(o, l) the weight of output position
+// o of column xa + l.
+template <int N, class X, class W>
+__device__ __forceinline__ void y_fused(float* plane, int xa, bool dst, const X& x, const C2<float>* tw,
+                                        const C2<float>* qN, int m, W&& w) {
+  const PlaneCol<N> A{plane, xa}, B{plane, xa + 1};
+  C2<float> v[16];
+  pre_fwd_pair<N>(v, A, B, dst, dst, m);
+  team_fft<N, false>(v, x, tw, m);
+  post_fwd<N>(x, qN, m, [&](int k, float va, float vb) {
+    const int o = dst ? N - 1 - k : k;
+    A[o] = va * w(o, 0);
+    B[o] = vb * w(o, 1);
+  });
+  pre_inv_pair<N>(v, A, B, dst, dst, qN, m);
+  team_fft<N, true>(v, x, tw, m);
+  post_inv<N>(x, dst, dst, m, [&](int o, float va, float vb) {
+    A[o] = va;
+    B[o] = vb;
+  });
+}
+
 // The (x, y) part of the three Schur terms on plane kz = blockIdx.x of the
-// z-transformed fields, in place: Z1 -> W12 = T1 + T2, Z3 -> W3 = T3.
-template <int N>
+// z-transformed fields of run blockIdx.y, in place: Z1 -> W12 = T1 + T2,
+// Z3 -> W3 = T3.
+template <int N, int MAXB>
 __global__ void __launch_bounds__(Cfg<N>::PLANE_THREADS, 1)
-k_cg_xy(float* __restrict__ z1, float* __restrict__ z3, const C2<float>* __restrict__ twg,
-        const C2<float>* __restrict__ qg, const float* __restrict__ s2g, float inv_mu,
-        const CGScalars* __restrict__ s) {
+k_cg_xy(const __grid_constant__ SlabArgs<MAXB> args, const C2<float>* __restrict__ twg,
+        const C2<float>* __restrict__ qg, const float* __restrict__ s2g, float inv_mu) {
   using C = Cfg<N>;
-  constexpr int T = C::PLANE_THREADS, M = C::M;
-  if (s->done) return;
+  constexpr int T = C::PLANE_THREADS, M = C::M, TS = XBuf<N>::TS;
+  const int b = blockIdx.y;
+  if (args.s[b]->done) return;
+  float* __restrict__ z1 = args.z1[b];
+  float* __restrict__ z3 = args.z3[b];
   extern __shared__ __align__(16) unsigned char smx[];
   float* P = reinterpret_cast<float*>(smx);
   float* Q = P + N * N;
   float* Xr = Q + N * N;
-  float* Xi = Xr + C::PLANE_TEAMS * C::TS;
-  C2<float>* tw = reinterpret_cast<C2<float>*>(Xi + C::PLANE_TEAMS * C::TS);
+  float* Xi = Xr + C::PLANE_TEAMS * TS;
+  C2<float>* tw = reinterpret_cast<C2<float>*>(Xi + C::PLANE_TEAMS * TS);
   C2<float>* qN = tw + 2 * N;
   float* s2 = reinterpret_cast<float*>(qN + N);
-  load_tables<N>(tw, qN, s2, twg, qg, s2g, T);
   const int kz = blockIdx.x;
   const int64_t off = (int64_t)kz * N * N;
+  load_tables<N>(tw, qN, s2, twg, qg, s2g, T);
   const int tm = threadIdx.x / M, m = threadIdx.x % M;
-  float* xr = Xr + tm * C::TS;
-  float* xi = Xi + tm * C::TS;
+  const XBuf<N> X{Xr + tm * TS, Xi + tm * TS};
   load_plane<N, T>(P, z1 + off);
   __syncthreads();   // tables and plane
   const float s2zs = s2[N + kz];   // z mode of terms 1, 2 (DST)
+  const float s2zc = s2[kz];       // z mode of term 3 (DCT)
   // terms 1 and 2 along x: DCT-II (term 1, into P) and DST-II (term 2, into Q) of each row
 #pragma unroll 1
   for (int rho = 0; rho < 2; ++rho) {
@@ -380,53 +494,26 @@ k_cg_xy(float* __restrict__ z1, float* __restrict__ z3, const C2<float>* __restr
     const PlaneRow<N> rp = plane_row<N>(P, y), rq = plane_row<N>(Q, y);
     C2<float> v[16];
     pre_fwd_cs<N>(v, rp, m);
-    team_fft<N, false>(v, xr, xi, tw, m);
-    post_fwd<N>(xr, xi, qN, m, [&](int k, float c, float sn) {
+    team_fft<N, false>(v, X, tw, m);
+    post_fwd<N>(X, qN, m, [&](int k, float c, float sn) {
       rp[k] = c;
       rq[N - 1 - k] = sn;
     });
   }
   __syncthreads();
-  const int xa = 2 * tm, xb = xa + 1;
+  const int xa = 2 * tm;
   {
-    // term 1 along y: DST-II, weight s2_x / (s2_x + s2_y + s2_z) (x DCT, y and z DST), DST-III
-    const PlaneCol<N> A{P, xa}, B{P, xb};
-    C2<float> v[16];
-    pre_fwd_pair<N>(v, A, B, true, true, m);
-    team_fft<N, false>(v, xr, xi, tw, m);
-    const float nxa = s2[xa], nxb = s2[xb];
-    post_fwd<N>(xr, xi, qN, m, [&](int k, float va, float vb) {
-      const int o = N - 1 - k;
-      const float sy = s2[N + o] + s2zs;
-      A[o] = va * schur_w(nxa, nxa + sy, inv_mu);
-      B[o] = vb * schur_w(nxb, nxb + sy, inv_mu);
+    // term 1 along y: DST, weight s2_x / (s2_x + s2_y + s2_z) (x DCT; y, z DST)
+    const float nx0 = s2[xa], nx1 = s2[xa + 1];
+    y_fused<N>(P, xa, true, X, tw, qN, m, [&](int o, int l) {
+      const float nx = l ? nx1 : nx0;
+      return schur_w(nx, nx + s2[N + o] + s2zs, inv_mu);
     });
-    __syncwarp();
-    pre_inv_pair<N>(v, A, B, true, true, qN, m);
-    team_fft<N, true>(v, xr, xi, tw, m);
-    post_inv<N>(xr, xi, true, true, m, [&](int o, float va, float vb) {
-      A[o] = va;
-      B[o] = vb;
-    });
-  }
-  {
-    // term 2 along y: DCT-II, weight s2_y / (s2_x + s2_y + s2_z) (y DCT, x and z DST), DCT-III
-    const PlaneCol<N> A{Q, xa}, B{Q, xb};
-    C2<float> v[16];
-    pre_fwd_pair<N>(v, A, B, false, false, m);
-    team_fft<N, false>(v, xr, xi, tw, m);
-    const float sxa = s2[N + xa] + s2zs, sxb = s2[N + xb] + s2zs;
-    post_fwd<N>(xr, xi, qN, m, [&](int k, float va, float vb) {
-      const float ny = s2[k];
-      A[k] = va * schur_w(ny, ny + sxa, inv_mu);
-      B[k] = vb * schur_w(ny, ny + sxb, inv_mu);
-    });
-    __syncwarp();
-    pre_inv_pair<N>(v, A, B, false, false, qN, m);
-    team_fft<N, true>(v, xr, xi, tw, m);
-    post_inv<N>(xr, xi, false, false, m, [&](int o, float va, float vb) {
-      A[o] = va;
-      B[o] = vb;
+    // term 2 along y: DCT, weight s2_y / (s2_x + s2_y + s2_z) (y DCT; x, z DST)
+    const float sx0 = s2[N + xa] + s2zs, sx1 = s2[N + xa + 1] + s2zs;
+    y_fused<N>(Q, xa, false, X, tw, qN, m, [&](int o, int l) {
+      const float ny = s2[o];
+      return schur_w(ny, ny + (l ? sx1 : sx0), inv_mu);
     });
   }
   __syncthreads();
@@ -437,80 +524,69 @@ k_cg_xy(float* __restrict__ z1, float* __restrict__ z3, const C2<float>* __restr
     const PlaneRow<N> rp = plane_row<N>(P, y), rq = plane_row<N>(Q, y);
     C2<float> v[16];
     pre_inv_pair<N>(v, rp, rq, false, true, qN, m);
-    team_fft<N, true>(v, xr, xi, tw, m);
+    team_fft<N, true>(v, X, tw, m);
     float* out = z1 + off + (int64_t)y * N;
-    post_inv<N>(xr, xi, false, true, m, [&](int o, float va, float vb) { out[o] = va + vb; });
+    post_inv<N>(X, false, true, m, [&](int o, float va, float vb) { out[o] = va + vb; });
   }
   __syncthreads();
   // term 3: S_x S_y, weight s2_z / (s2_x + s2_y + s2_z) (z DCT), inverse
   load_plane<N, T>(P, z3 + off);
   __syncthreads();
-  const float s2zc = s2[kz];
-  const int ya = 2 * tm, yb = ya + 1;
+  const int ya = 2 * tm;
   {
-    const PlaneRow<N> A = plane_row<N>(P, ya), B = plane_row<N>(P, yb);
+    const PlaneRow<N> A = plane_row<N>(P, ya), B = plane_row<N>(P, ya + 1);
     C2<float> v[16];
     pre_fwd_pair<N>(v, A, B, true, true, m);
-    team_fft<N, false>(v, xr, xi, tw, m);
-    post_fwd<N>(xr, xi, qN, m, [&](int k, float va, float vb) {
+    team_fft<N, false>(v, X, tw, m);
+    post_fwd<N>(X, qN, m, [&](int k, float va, float vb) {
       A[N - 1 - k] = va;
       B[N - 1 - k] = vb;
     });
   }
   __syncthreads();
   {
-    const PlaneCol<N> A{P, xa}, B{P, xb};
-    C2<float> v[16];
-    pre_fwd_pair<N>(v, A, B, true, true, m);
-    team_fft<N, false>(v, xr, xi, tw, m);
-    const float sxa = s2[N + xa] + s2zc, sxb = s2[N + xb] + s2zc;
-    post_fwd<N>(xr, xi, qN, m, [&](int k, float va, float vb) {
-      const int o = N - 1 - k;
-      const float sy = s2[N + o];
-      A[o] = va * schur_w(s2zc, sxa + sy, inv_mu);
-      B[o] = vb * schur_w(s2zc, sxb + sy, inv_mu);
-    });
-    __syncwarp();
-    pre_inv_pair<N>(v, A, B, true, true, qN, m);
-    team_fft<N, true>(v, xr, xi, tw, m);
-    post_inv<N>(xr, xi, true, true, m, [&](int o, float va, float vb) {
-      A[o] = va;
-      B[o] = vb;
+    const float sx0 = s2[N + xa] + s2zc, sx1 = s2[N + xa + 1] + s2zc;
+    y_fused<N>(P, xa, true, X, tw, qN, m, [&](int o, int l) {
+      return schur_w(s2zc, (l ? sx1 : sx0) + s2[N + o], inv_mu);
     });
   }
   __syncthreads();
   {
-    const PlaneRow<N> A = plane_row<N>(P, ya), B = plane_row<N>(P, yb);
+    const PlaneRow<N> A = plane_row<N>(P, ya), B = plane_row<N>(P, ya + 1);
     C2<float> v[16];
     pre_inv_pair<N>(v, A, B, true, true, qN, m);
-    team_fft<N, true>(v, xr, xi, tw, m);
-    float* oa = z3 + off + (int64_t)ya * N;
-    float* ob = z3 + off + (int64_t)yb * N;
-    post_inv<N>(xr, xi, true, true, m, [&](int o, float va, float vb) {
-      oa[o] = va;
-      ob[o] = vb;
+    team_fft<N, true>(v, X, tw, m);
+    float* outa = z3 + off + (int64_t)ya * N;
+    float* outb = outa + N;
+    post_inv<N>(X, true, true, m, [&](int o, float va, float vb) {
+      outa[o] = va;
+      outb[o] = vb;
     });
   }
 }
 
 // q = DST-III_z W12 + DCT-III_z W3 + cdiag d; dq = d . q; alpha.  Tiles as
 // k_cg_zfwd.
-template <int N>
+template <int N, int MAXB>
 __global__ void __launch_bounds__(Cfg<N>::TILE_THREADS)
-k_cg_zinv(const float* __restrict__ w12, const float* __restrict__ w3, const float* __restrict__ d,
-          float* __restrict__ q, const C2<float>* __restrict__ twg, const C2<float>* __restrict__ qg, CGScalars* s,
-          double* __restrict__ partial) {
+k_cg_zinv(const __grid_constant__ SlabArgs<MAXB> args, const C2<float>* __restrict__ twg,
+          const C2<float>* __restrict__ qg) {
   using C = Cfg<N>;
   constexpr int T = C::TILE_THREADS, M = C::M;
   __shared__ double sh[32];
   __shared__ double total;
+  const int b = blockIdx.y;
+  CGScalars* s = args.s[b];
   if (s->done) return;
+  const float* __restrict__ w12 = args.z1[b];
+  const float* __restrict__ w3 = args.z3[b];
+  const float* __restrict__ d = args.d[b];
+  float* __restrict__ q = args.q[b];
+  double* __restrict__ partial = args.partial[b];
   extern __shared__ __align__(16) unsigned char smi[];
   float* D = reinterpret_cast<float*>(smi);
   float* E = D + N * C::TILE;
-  float* Xr = E + N * C::TILE;
-  float* Xi = Xr + C::TILE * C::TS;
-  C2<float>* tw = reinterpret_cast<C2<float>*>(Xi + C::TILE * C::TS);
+  C2<float>* tw = reinterpret_cast<C2<float>*>(E + N * C::TILE);
   C2<float>* qN = tw + 2 * N;
   load_tables<N>(tw, qN, nullptr, twg, qg, nullptr, T);
   const int xb = blockIdx.x % (N / C::TILE), y = blockIdx.x / (N / C::TILE);
@@ -528,8 +604,9 @@ k_cg_zinv(const float* __restrict__ w12, const float* __restrict__ w3, const flo
     const TileCol A{D, tm}, B{E, tm};
     C2<float> v[16];
     pre_inv_pair<N>(v, A, B, true, false, qN, m);
-    team_fft<N, true>(v, Xr + tm * C::TS, Xi + tm * C::TS, tw, m);
-    post_inv<N>(Xr + tm * C::TS, Xi + tm * C::TS, true, false, m, [&](int o, float va, float vb) { A[o] = va + vb; });
+    const auto X = xlines(A, B);
+    team_fft<N, true>(v, X, tw, m);
+    post_inv<N>(X, true, false, m, [&](int o, float va, float vb) { A[o] = va + vb; });
   }
   __syncthreads();
   const float cd = float(s->cdiag);
@@ -559,12 +636,19 @@ k_cg_zinv(const float* __restrict__ w12, const float* __restrict__ w3, const flo
 
 // x += alpha d; r -= alpha (q + sumd rank1); rr = r . r; beta; done once
 // rr <= stop.  Float4 vectors (n4 = N^3 / 4).
+template <int MAXB>
 __global__ void __launch_bounds__(256)
-k_cg_upd(float* __restrict__ x, float* __restrict__ r, const float* __restrict__ d, const float* __restrict__ q,
-         int64_t n4, CGScalars* s, double* __restrict__ partial) {
+k_cg_upd(const __grid_constant__ SlabArgs<MAXB> args, int64_t n4) {
   __shared__ double sh[32];
   __shared__ double total;
+  const int b = blockIdx.y;
+  CGScalars* s = args.s[b];
   if (s->done) return;
+  float* __restrict__ x = args.x[b];
+  float* __restrict__ r = args.r[b];
+  const float* __restrict__ d = args.d[b];
+  const float* __restrict__ q = args.q[b];
+  double* __restrict__ partial = args.partial[b];
   const float a = float(s->alpha);
   const float c1 = float(s->sumd * s->rank1);
   CgAcc<float> acc;

@@ -27,6 +27,15 @@ struct SlabCg {
   double* partial;
 };
 
+// Largest number of CG runs one launch of the iteration's kernels serves.
+constexpr int kSlabBatchMax = 64;
+
+// The iteration for `nrun` independent CG runs on one grid at once
+// (blockIdx.y = run; each run's arithmetic and reduction order are those of a
+// single run): run k uses the buffers and scalars of runs[k], which hold the
+// shared tables too (only runs[0]'s tables, N and inv_mu are read).
+int slab_cg_iteration_batch(const SlabCg* runs, int nrun, cudaStream_t st);
+
 // Grids the four-kernel iteration covers (N = 32, 64, 128: a whole plane of
 // floats and its team exchange buffers fit in one CTA's shared memory).
 bool slab_supported(int N);

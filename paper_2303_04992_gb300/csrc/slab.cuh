@@ -30,12 +30,13 @@
 //
 // Shared-memory layouts avoid bank conflicts for the access patterns of the
 // team FFT (stride 2 and runs of 8 along a line, 4 teams per warp):
-//   plane: element x of row y at y N + (x ^ plane_sw(y)),
+//   plane: rows of N + 1 floats (element x of row y at y (N + 1) + x),
 //   z tile: element z of line l (32 lines) at 32 z + (l ^ tile_sw(z)),
 //   exchange: in the z kernels the team's own two lines (real parts in one,
 //   imaginary parts in the other, index c at position xpi(c)); in the plane
 //   kernel a separate buffer per team (rows of M + 1, teams 8 banks apart),
-//   which keeps its register use within the 128 of 512 threads.
+//   which keeps its register use within the 128 of 512 threads.  The plane
+//   kernel runs its twelve line operations through one copy of the FFT.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -60,7 +61,8 @@ struct Cfg {
 
 template <int N>
 struct XySmem {
-  static constexpr size_t plane = sizeof(float) * N * N;
+  static constexpr int RS = N + 1;   // padded plane row
+  static constexpr size_t plane = sizeof(float) * N * RS;
   // two planes (Z1 -> P and Q; Z3 -> P after them), the teams' exchange
   // buffers (real and imaginary arrays) and the tables
   static constexpr size_t xch = sizeof(float) * Cfg<N>::PLANE_TEAMS * ((16 * (Cfg<N>::M + 1) + 31) / 32 * 32 + 8);
@@ -72,18 +74,6 @@ struct ZSmem {
   static constexpr size_t tile = sizeof(float) * N * Cfg<N>::TILE;
   static constexpr size_t bytes = 2 * tile + sizeof(C2<float>) * 3 * N;
 };
-
-// Row swizzle of a plane: bits 0, 3 and 4 of the column index, from the row
-// index mod 16, chosen so that (a) the rows 8w + 2t (t = 0..3; likewise the
-// odd rows) of the four teams of a warp map a stride-2 run and an aligned
-// run of 8 columns to disjoint banks, and (b) down a column, any 8 rows with
-// distinct (y mod 16) >> 1, any 8 even or odd rows of 16, and any aligned 8
-// rows fall on distinct banks.
-__device__ __forceinline__ int plane_sw(int y) {
-  const int y16 = y & 15;
-  const int y0 = y16 & 1, y1 = (y16 >> 1) & 1, y2 = (y16 >> 2) & 1, y3 = y16 >> 3;
-  return (y0 ^ y1 ^ y3) | (y1 << 3) | (y2 << 4);
-}
 
 // Line swizzle of a z tile (32 lines): bits 2..4 of the line index, from
 // z mod 16, bijective on even z, odd z, z < 8 and z >= 8 of each 16; the four
@@ -99,21 +89,12 @@ __device__ __forceinline__ int tile_sw(int z) { return (((z >> 1) ^ ((z & 1) << 
 // above.
 __device__ __forceinline__ int xpi(int c) { return c ^ ((c >> 4) & 7); }
 
-template <int N>
-struct PlaneRow {
-  float* p;
-  int sw;
-  __device__ __forceinline__ float& operator[](int x) const { return p[x ^ sw]; }
-};
-template <int N>
-__device__ __forceinline__ PlaneRow<N> plane_row(float* plane, int y) {
-  return {plane + y * N, plane_sw(y)};
-}
-template <int N>
-struct PlaneCol {
-  float* p;
-  int x;
-  __device__ __forceinline__ float& operator[](int y) const { return p[y * N + (x ^ plane_sw(y))]; }
+// Element p of a line of a padded plane (rows of N + 1 floats): a row has
+// stride 1, a column stride N + 1; one multiply-add per access either way.
+struct Line {
+  float* base;
+  int stride;
+  __device__ __forceinline__ float& operator[](int p) const { return base[p * stride]; }
 };
 struct TileCol {
   float* p;
@@ -313,6 +294,23 @@ __device__ __forceinline__ void post_inv(const X& x, bool dsta, bool dstb, int m
   }
 }
 
+// Inverse output with run-time kinds and scales: x_{2n} = v_n, x_{2n+1} =
+// v_{N-1-n} times sa (line a) and sb (line b), a DST-III line negating its
+// odd outputs; put(o, xa, xb) for o = m + M r.  The exchange X is a separate
+// buffer (written by the team's FFT only).
+template <int N, class X, class F>
+__device__ __forceinline__ void post_inv_rt(const X& x, int ka, int kb, float sa, float sb, int m, F&& put) {
+  constexpr int M = Cfg<N>::M;
+  static_assert(!X::in_place, "run-time kinds with a separate exchange only");
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const int o = m + M * r;
+    const bool odd = (o & 1) != 0;
+    const int c = odd ? N - 1 - (o >> 1) : (o >> 1);
+    put(o, x.re(c) * ((ka && odd) ? -sa : sa), x.im(c) * ((kb && odd) ? -sb : sb));
+  }
+}
+
 // sin^2 weights (Lambda_c / mu) of the Schur terms at modes (ax, ay, az):
 // s2[a] = 4 sin^2(pi a / 2N) for the DCT modes, s2[N + a] = 4 sin^2(pi (a+1) / 2N)
 // for the DST modes; the numerator is the DCT axis's.
@@ -332,7 +330,7 @@ __device__ __forceinline__ void load_tables(C2<float>* tw, C2<float>* qN, float*
     for (int e = threadIdx.x; e < 2 * N; e += threads) s2[e] = s2g[e];
 }
 
-// Plane y-major, N^2 floats from global memory into the swizzled layout.
+// Plane y-major, N^2 floats from global memory into rows of N + 1 floats.
 template <int N, int THREADS>
 __device__ __forceinline__ void load_plane(float* P, const float* __restrict__ g) {
   constexpr int PER = N * N / THREADS;
@@ -342,11 +340,9 @@ __device__ __forceinline__ void load_plane(float* P, const float* __restrict__ g
 #pragma unroll
   for (int j = 0; j < PER; ++j) {
     const int e = threadIdx.x + j * THREADS;
-    const int y = e / N, x = e % N;
-    P[y * N + (x ^ plane_sw(y))] = t[j];
+    P[(e / N) * (N + 1) + (e % N)] = t[j];
   }
 }
-
 
 // ------------------------------------------------------------ the kernels
 // The buffers of up to MAXB independent CG runs on one grid (blockIdx.y
@@ -433,47 +429,80 @@ k_cg_zfwd(const __grid_constant__ SlabArgs<MAXB> args, const C2<float>* __restri
   if (last_block_sum(acc.value(), partial, &s->ticket[2], sh, &total) && threadIdx.x == 0) s->sumd = total;
 }
 
-// Forward transform, spectral weight and inverse transform along the columns
-// xa, xa + 1 of a plane (the y part of a Schur term), in place.  dst:
-// DST-II/III (else DCT-II/III) along y; w(o, l) the weight of output position
-// o of column xa + l.
-template <int N, class X, class W>
-__device__ __forceinline__ void y_fused(float* plane, int xa, bool dst, const X& x, const C2<float>* tw,
-                                        const C2<float>* qN, int m, W&& w) {
-  const PlaneCol<N> A{plane, xa}, B{plane, xa + 1};
-  C2<float> v[16];
-  pre_fwd_pair<N>(v, A, B, dst, dst, m);
-  team_fft<N, false>(v, x, tw, m);
-  post_fwd<N>(x, qN, m, [&](int k, float va, float vb) {
-    const int o = dst ? N - 1 - k : k;
-    A[o] = va * w(o, 0);
-    B[o] = vb * w(o, 1);
-  });
-  pre_inv_pair<N>(v, A, B, dst, dst, qN, m);
-  team_fft<N, true>(v, x, tw, m);
-  post_inv<N>(x, dst, dst, m, [&](int o, float va, float vb) {
-    A[o] = va;
-    B[o] = vb;
-  });
+// Makhoul input of a forward line pair with the kinds known only at run
+// time (kind 1: DST-II, the second half negated; B may be A, for the DCT-II
+// and DST-II of one line).
+template <int N, class LA, class LB>
+__device__ __forceinline__ void pre_fwd_rt(C2<float> (&v)[16], const LA& A, const LB& B, int ka, int kb, int m) {
+  constexpr int M = Cfg<N>::M;
+  __syncwarp();
+  const float sa = ka ? -1.f : 1.f, sb = kb ? -1.f : 1.f;
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const int n = m + M * r;
+    const bool hi = r >= 8;
+    const int i = hi ? 2 * (N - 1 - n) + 1 : 2 * n;
+    const float a = A[i], b = B[i];
+    v[r] = {hi ? sa * a : a, hi ? sb * b : b};
+  }
 }
+
+// Makhoul input of an inverse line pair (kind 0: DCT-III, 1: DST-III) at run
+// time, conjugated: the forward FFT of conj(V) is the conjugate of the
+// inverse FFT of V, so one FFT code serves both directions.
+template <int N, class LA, class LB>
+__device__ __forceinline__ void pre_inv_rt(C2<float> (&v)[16], const LA& A, const LB& B, int ka, int kb,
+                                           const C2<float>* qN, int m) {
+  constexpr int M = Cfg<N>::M;
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const int k = m + M * r;
+    const bool k0 = (k == 0);
+    const float xa = A[ka ? N - 1 - k : k];
+    const float xna = k0 ? 0.f : A[ka ? k - 1 : N - k];
+    const float xb = B[kb ? N - 1 - k : k];
+    const float xnb = k0 ? 0.f : B[kb ? k - 1 : N - k];
+    const C2<float> q = qN[k];
+    const float vax = q.x * xa - q.y * xna, vay = -q.x * xna - q.y * xa;
+    const float vbx = q.x * xb - q.y * xnb, vby = -q.x * xnb - q.y * xb;
+    v[r] = {vax - vby, -(vay + vbx)};
+  }
+}
+
+// The twelve line operations of k_cg_xy, per team (two lines each):
+//   0, 1   x forward of Z1: DCT-II (term 1, into P) and DST-II (term 2, into Q)
+//          of rows 2t, 2t + 1
+//   2, 3   y of term 1 on P: DST-II with its weight, DST-III (columns 2t, 2t + 1)
+//   4, 5   y of term 2 on Q: DCT-II with its weight, DCT-III
+//   6, 7   x inverse: DCT-III of P plus DST-III of Q, rows 2t, 2t + 1 -> W12
+//   (Z3 into P)
+//   8      x forward of Z3: DST-II of rows 2t, 2t + 1
+//   9, 10  y of term 3: DST-II with its weight, DST-III
+//   11     x inverse: DST-III of rows 2t, 2t + 1 -> W3
+// One loop runs them all through one copy of the FFT code (a fully
+// unrolled kernel with a copy per operation does not fit the instruction
+// cache).  Barriers follow operations 1, 5, 7, 8 and 10.
+constexpr int kXyOps = 12;
 
 // The (x, y) part of the three Schur terms on plane kz = blockIdx.x of the
 // z-transformed fields of run blockIdx.y, in place: Z1 -> W12 = T1 + T2,
-// Z3 -> W3 = T3.
+// Z3 -> W3 = T3.  Plane rows of N + 1 floats.
 template <int N, int MAXB>
 __global__ void __launch_bounds__(Cfg<N>::PLANE_THREADS, 1)
 k_cg_xy(const __grid_constant__ SlabArgs<MAXB> args, const C2<float>* __restrict__ twg,
         const C2<float>* __restrict__ qg, const float* __restrict__ s2g, float inv_mu) {
   using C = Cfg<N>;
-  constexpr int T = C::PLANE_THREADS, M = C::M, TS = XBuf<N>::TS;
+  constexpr int T = C::PLANE_THREADS, M = C::M, TS = XBuf<N>::TS, S = N + 1;
+  constexpr float invN = 1.0f / N;
   const int b = blockIdx.y;
   if (args.s[b]->done) return;
   float* __restrict__ z1 = args.z1[b];
   float* __restrict__ z3 = args.z3[b];
   extern __shared__ __align__(16) unsigned char smx[];
   float* P = reinterpret_cast<float*>(smx);
-  float* Q = P + N * N;
-  float* Xr = Q + N * N;
+  float* Q = P + N * S;
+  float* Xr = Q + N * S;
   float* Xi = Xr + C::PLANE_TEAMS * TS;
   C2<float>* tw = reinterpret_cast<C2<float>*>(Xi + C::PLANE_TEAMS * TS);
   C2<float>* qN = tw + 2 * N;
@@ -485,83 +514,81 @@ k_cg_xy(const __grid_constant__ SlabArgs<MAXB> args, const C2<float>* __restrict
   const XBuf<N> X{Xr + tm * TS, Xi + tm * TS};
   load_plane<N, T>(P, z1 + off);
   __syncthreads();   // tables and plane
-  const float s2zs = s2[N + kz];   // z mode of terms 1, 2 (DST)
-  const float s2zc = s2[kz];       // z mode of term 3 (DCT)
-  // terms 1 and 2 along x: DCT-II (term 1, into P) and DST-II (term 2, into Q) of each row
+  const int l0 = 2 * tm;   // this team's pair of rows, or of columns
 #pragma unroll 1
-  for (int rho = 0; rho < 2; ++rho) {
-    const int y = 2 * tm + rho;
-    const PlaneRow<N> rp = plane_row<N>(P, y), rq = plane_row<N>(Q, y);
+  for (int op = 0; op < kXyOps; ++op) {
+    if (op == 8) {
+      load_plane<N, T>(P, z3 + off);
+      __syncthreads();
+    }
+    const bool inv = op == 3 || op == 5 || op == 6 || op == 7 || op == 10 || op == 11;
+    const bool col = (op >= 2 && op <= 5) || op == 9 || op == 10;
+    const int row = op == 0 || op == 6 ? l0 : (op == 1 || op == 7 ? l0 + 1 : l0);
+    int ka = 1, kb = 1, term = 0;
+    Line A, B, DA, DB;
+    if (col) {
+      float* pl = (op == 4 || op == 5) ? Q : P;
+      A = {pl + l0, S};
+      B = {pl + l0 + 1, S};
+      if (op == 4 || op == 5) ka = kb = 0;
+      term = op == 2 ? 1 : (op == 4 ? 2 : (op == 9 ? 3 : 0));
+    } else if (op <= 1) {
+      A = B = {P + row * S, 1};   // one row, DCT-II into P and DST-II into Q
+      ka = 0;
+      kb = 1;
+    } else if (op <= 7) {
+      A = {P + row * S, 1};       // DCT-III of term 1 and DST-III of term 2
+      B = {Q + row * S, 1};
+      ka = 0;
+      kb = 1;
+    } else {
+      A = {P + l0 * S, 1};
+      B = {P + (l0 + 1) * S, 1};
+    }
+    DA = A;
+    DB = (op <= 1) ? Line{Q + row * S, 1} : B;
     C2<float> v[16];
-    pre_fwd_cs<N>(v, rp, m);
+    if (inv) pre_inv_rt<N>(v, A, B, ka, kb, qN, m);
+    else pre_fwd_rt<N>(v, A, B, ka, kb, m);
     team_fft<N, false>(v, X, tw, m);
-    post_fwd<N>(X, qN, m, [&](int k, float c, float sn) {
-      rp[k] = c;
-      rq[N - 1 - k] = sn;
-    });
-  }
-  __syncthreads();
-  const int xa = 2 * tm;
-  {
-    // term 1 along y: DST, weight s2_x / (s2_x + s2_y + s2_z) (x DCT; y, z DST)
-    const float nx0 = s2[xa], nx1 = s2[xa + 1];
-    y_fused<N>(P, xa, true, X, tw, qN, m, [&](int o, int l) {
-      const float nx = l ? nx1 : nx0;
-      return schur_w(nx, nx + s2[N + o] + s2zs, inv_mu);
-    });
-    // term 2 along y: DCT, weight s2_y / (s2_x + s2_y + s2_z) (y DCT; x, z DST)
-    const float sx0 = s2[N + xa] + s2zs, sx1 = s2[N + xa + 1] + s2zs;
-    y_fused<N>(Q, xa, false, X, tw, qN, m, [&](int o, int l) {
-      const float ny = s2[o];
-      return schur_w(ny, ny + (l ? sx1 : sx0), inv_mu);
-    });
-  }
-  __syncthreads();
-  // back along x: DCT-III of term 1 plus DST-III of term 2 in one FFT per row -> W12
-#pragma unroll 1
-  for (int rho = 0; rho < 2; ++rho) {
-    const int y = 2 * tm + rho;
-    const PlaneRow<N> rp = plane_row<N>(P, y), rq = plane_row<N>(Q, y);
-    C2<float> v[16];
-    pre_inv_pair<N>(v, rp, rq, false, true, qN, m);
-    team_fft<N, true>(v, X, tw, m);
-    float* out = z1 + off + (int64_t)y * N;
-    post_inv<N>(X, false, true, m, [&](int o, float va, float vb) { out[o] = va + vb; });
-  }
-  __syncthreads();
-  // term 3: S_x S_y, weight s2_z / (s2_x + s2_y + s2_z) (z DCT), inverse
-  load_plane<N, T>(P, z3 + off);
-  __syncthreads();
-  const int ya = 2 * tm;
-  {
-    const PlaneRow<N> A = plane_row<N>(P, ya), B = plane_row<N>(P, ya + 1);
-    C2<float> v[16];
-    pre_fwd_pair<N>(v, A, B, true, true, m);
-    team_fft<N, false>(v, X, tw, m);
-    post_fwd<N>(X, qN, m, [&](int k, float va, float vb) {
-      A[N - 1 - k] = va;
-      B[N - 1 - k] = vb;
-    });
-  }
-  __syncthreads();
-  {
-    const float sx0 = s2[N + xa] + s2zc, sx1 = s2[N + xa + 1] + s2zc;
-    y_fused<N>(P, xa, true, X, tw, qN, m, [&](int o, int l) {
-      return schur_w(s2zc, (l ? sx1 : sx0) + s2[N + o], inv_mu);
-    });
-  }
-  __syncthreads();
-  {
-    const PlaneRow<N> A = plane_row<N>(P, ya), B = plane_row<N>(P, ya + 1);
-    C2<float> v[16];
-    pre_inv_pair<N>(v, A, B, true, true, qN, m);
-    team_fft<N, true>(v, X, tw, m);
-    float* outa = z3 + off + (int64_t)ya * N;
-    float* outb = outa + N;
-    post_inv<N>(X, true, true, m, [&](int o, float va, float vb) {
-      outa[o] = va;
-      outb[o] = vb;
-    });
+    if (!inv) {
+      // weights of the y passes: sin^2 of the DCT axis over the sum of the
+      // three axes' sin^2, over mu; the x and z modes are fixed per line
+      const float az = term == 3 ? s2[kz] : s2[N + kz];
+      const float ax0 = s2[(term == 1 ? 0 : N) + l0], ax1 = s2[(term == 1 ? 0 : N) + l0 + 1];
+      post_fwd<N>(X, qN, m, [&](int k, float va, float vb) {
+        const int oa = ka ? N - 1 - k : k, ob = kb ? N - 1 - k : k;
+        if (term) {
+          const float ay = s2[(term == 2 ? 0 : N) + oa];
+          const float n0 = term == 1 ? ax0 : (term == 2 ? ay : az);
+          const float n1 = term == 1 ? ax1 : (term == 2 ? ay : az);
+          va *= schur_w(n0, ax0 + ay + az, inv_mu);
+          vb *= schur_w(n1, ax1 + ay + az, inv_mu);
+        }
+        DA[oa] = va;
+        DB[ob] = vb;
+      });
+    } else {
+      const float sa = invN, sb = -invN;   // 1/N, and the conjugation of the imaginary part
+      float* outa = nullptr;
+      float* outb = nullptr;
+      if (op == 6 || op == 7) outa = z1 + off + (int64_t)row * N;
+      if (op == 11) {
+        outa = z3 + off + (int64_t)l0 * N;
+        outb = outa + N;
+      }
+      post_inv_rt<N>(X, ka, kb, sa, sb, m, [&](int o, float va, float vb) {
+        if (op == 6 || op == 7) outa[o] = va + vb;
+        else if (op == 11) {
+          outa[o] = va;
+          outb[o] = vb;
+        } else {
+          A[o] = va;
+          B[o] = vb;
+        }
+      });
+    }
+    if (op == 1 || op == 5 || op == 7 || op == 8 || op == 10) __syncthreads();
   }
 }
 

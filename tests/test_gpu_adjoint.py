@@ -1,8 +1,8 @@
 """Adjoint on the GPU: the transposed matvec against the forward matvec (inner
 product identity), the gradient of a velocity loss against the oracle's
 brute-force adjoint on 16^3, against central differences along 32 random
-directions on 32^3 (through the torch.autograd binding), and MIXED against
-FP64 at 128^3.  The loss is quadratic in g, so central differences carry no
+directions on the sphere at 32^3 and the star at 128^3 (through the
+torch.autograd binding), and MIXED against FP64 at 128^3.  The loss is quadratic in g, so central differences carry no
 truncation error; the step is large against the GMRES tolerance."""
 import numpy as np
 import pytest
@@ -82,8 +82,14 @@ def test_gradient_matches_oracle_adjoint_sphere16(prec):
     assert np.abs(got - want).max() <= 1e-8 * np.abs(want).max()
 
 
-def test_gradient_matches_central_differences_32_directions():
-    s = Solver(ki.sphere(), ki.grid(32), precision=FP64, gmres_tol=1e-12)
+@pytest.mark.parametrize("key,geom,N,prec,tol", [("sphere32", ki.sphere(), 32, FP64, 1e-12),
+                                                 ("star128_mixed", ki.star(), 128, MIXED, 1e-11)])
+def test_gradient_matches_central_differences_32_directions(key, geom, N, prec, tol):
+    """Central differences of the loss along 32 seeded directions against the
+    adjoint gradient (C5: 32 random directions).  At 128^3 the MIXED path is
+    used (a FP64 solve there takes seconds, and 64 of them are needed) with
+    GMRES to 1e-11, which keeps the solve linear to about 1e-10 relative."""
+    s = Solver(geom, ki.grid(N), precision=prec, gmres_tol=tol)
     mask, tgt = loss_parts(s)
     g0 = cuda(boundary_data(s))
 

@@ -10,7 +10,7 @@ bool slab_supported(int N) { return N == 32 || N == 64 || N == 128; }
 
 namespace {
 
-constexpr int kUpdBlocks = 1216;   // 8 x 152 SMs
+constexpr int kUpdBlocks = 304;   // 2 x 152 SMs: one wave at the kernel's register use
 
 template <int N, int MAXB>
 cudaError_t prepare_nb() {
@@ -67,8 +67,9 @@ void launch_nb(int which, const slab::SlabArgs<MAXB>& args, const SlabCg& t, int
       break;
     default: {
       const int64_t n4 = (int64_t)N * N * N / 4;
-      const unsigned blocks = (unsigned)((n4 + 255) / 256 < kUpdBlocks ? (n4 + 255) / 256 : kUpdBlocks);
-      slab::k_cg_upd<MAXB><<<dim3(blocks, nrun), 256, 0, st>>>(args, n4);
+      const int64_t per = (int64_t)slab::UPD_THREADS * slab::UPD_UNROLL;
+      const unsigned blocks = (unsigned)((n4 + per - 1) / per < kUpdBlocks ? (n4 + per - 1) / per : kUpdBlocks);
+      slab::k_cg_upd<MAXB><<<dim3(blocks, nrun), slab::UPD_THREADS, 0, st>>>(args, n4);
     }
   }
 }

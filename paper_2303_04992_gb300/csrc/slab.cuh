@@ -30,7 +30,8 @@
 //
 // Shared-memory layouts avoid bank conflicts for the access patterns of the
 // team FFT (stride 2 and runs of 8 along a line, 4 teams per warp):
-//   plane: rows of N + 1 floats (element x of row y at y (N + 1) + x),
+//   plane: element x of row y at y N + (x ^ plane_sw(y)); the plane kernel
+//   works along rows only and transposes the plane between its x and y passes,
 //   z tile: element z of line l (32 lines) at 32 z + (l ^ tile_sw(z)),
 //   exchange: in the z kernels the team's own two lines (real parts in one,
 //   imaginary parts in the other, index c at position xpi(c)); in the plane
@@ -61,8 +62,7 @@ struct Cfg {
 
 template <int N>
 struct XySmem {
-  static constexpr int RS = N + 1;   // padded plane row
-  static constexpr size_t plane = sizeof(float) * N * RS;
+  static constexpr size_t plane = sizeof(float) * N * N;
   // two planes (Z1 -> P and Q; Z3 -> P after them), the teams' exchange
   // buffers (real and imaginary arrays) and the tables
   static constexpr size_t xch = sizeof(float) * Cfg<N>::PLANE_TEAMS * ((16 * (Cfg<N>::M + 1) + 31) / 32 * 32 + 8);
@@ -74,6 +74,17 @@ struct ZSmem {
   static constexpr size_t tile = sizeof(float) * N * Cfg<N>::TILE;
   static constexpr size_t bytes = 2 * tile + sizeof(C2<float>) * 3 * N;
 };
+
+// Row swizzle of a plane: bits 0, 3 and 4 of the column index, from the row
+// index mod 16, chosen so that the rows 8w + 2t (t = 0..3; likewise the odd
+// rows) that the four teams of a warp work on map a stride-2 run and an
+// aligned run of 8 columns to disjoint banks.  The plane kernel only ever
+// works along rows (it transposes the plane between its x and y passes), so
+// a row's swizzle is fixed and an access costs one XOR.
+__device__ __forceinline__ int plane_sw(int y) {
+  const int y0 = y & 1, y1 = (y >> 1) & 1, y2 = (y >> 2) & 1, y3 = (y >> 3) & 1;
+  return (y0 ^ y1 ^ y3) | (y1 << 3) | (y2 << 4);
+}
 
 // Line swizzle of a z tile (32 lines): bits 2..4 of the line index, from
 // z mod 16, bijective on even z, odd z, z < 8 and z >= 8 of each 16; the four
@@ -89,13 +100,16 @@ __device__ __forceinline__ int tile_sw(int z) { return (((z >> 1) ^ ((z & 1) << 
 // above.
 __device__ __forceinline__ int xpi(int c) { return c ^ ((c >> 4) & 7); }
 
-// Element p of a line of a padded plane (rows of N + 1 floats): a row has
-// stride 1, a column stride N + 1; one multiply-add per access either way.
-struct Line {
-  float* base;
-  int stride;
-  __device__ __forceinline__ float& operator[](int p) const { return base[p * stride]; }
+// Row y of a plane: element x at y N + (x ^ plane_sw(y)).
+struct PlaneRow {
+  float* p;
+  int sw;
+  __device__ __forceinline__ float& operator[](int x) const { return p[x ^ sw]; }
 };
+template <int N>
+__device__ __forceinline__ PlaneRow plane_row(float* plane, int y) {
+  return {plane + y * N, plane_sw(y)};
+}
 struct TileCol {
   float* p;
   int l;
@@ -112,6 +126,7 @@ struct XLines {
   LA A;
   LB B;
   static constexpr bool in_place = true;
+  static constexpr bool blocked = true;
   __device__ __forceinline__ float& re(int c) const { return A[xpi(c)]; }
   __device__ __forceinline__ float& im(int c) const { return B[xpi(c)]; }
 };
@@ -124,6 +139,7 @@ struct XBuf {
   float* xr;
   float* xi;
   static constexpr bool in_place = false;
+  static constexpr bool blocked = false;
   static constexpr int TS = (16 * (Cfg<N>::M + 1) + 31) / 32 * 32 + 8;   // team stride, 8 banks apart
   __device__ __forceinline__ float& re(int c) const { return xr[c + c / Cfg<N>::M]; }
   __device__ __forceinline__ float& im(int c) const { return xi[c + c / Cfg<N>::M]; }
@@ -158,7 +174,7 @@ __device__ __forceinline__ void team_fft(C2<float> (&v)[16], const X& x, const C
   for (int q = 0; q < NS; ++q)
 #pragma unroll
     for (int k = 0; k < M; ++k) {
-      const int c = (NS * m + q) * M + k;
+      const int c = (X::blocked ? NS * m + q : q * M + m) * M + k;
       w2[q][k] = {x.re(c), x.im(c)};
     }
   __syncwarp();
@@ -167,7 +183,7 @@ __device__ __forceinline__ void team_fft(C2<float> (&v)[16], const X& x, const C
     dft_reg<M, INV, float>(w2[q]);
 #pragma unroll
     for (int k = 0; k < M; ++k) {
-      const int c = NS * m + q + 16 * k;
+      const int c = (X::blocked ? NS * m + q : q * M + m) + 16 * k;
       x.re(c) = w2[q][k].x;
       x.im(c) = w2[q][k].y;
     }
@@ -330,7 +346,7 @@ __device__ __forceinline__ void load_tables(C2<float>* tw, C2<float>* qN, float*
     for (int e = threadIdx.x; e < 2 * N; e += threads) s2[e] = s2g[e];
 }
 
-// Plane y-major, N^2 floats from global memory into rows of N + 1 floats.
+// Plane y-major, N^2 floats from global memory into the swizzled layout.
 template <int N, int THREADS>
 __device__ __forceinline__ void load_plane(float* P, const float* __restrict__ g) {
   constexpr int PER = N * N / THREADS;
@@ -340,8 +356,32 @@ __device__ __forceinline__ void load_plane(float* P, const float* __restrict__ g
 #pragma unroll
   for (int j = 0; j < PER; ++j) {
     const int e = threadIdx.x + j * THREADS;
-    P[(e / N) * (N + 1) + (e % N)] = t[j];
+    const int y = e / N, x = e % N;
+    P[y * N + (x ^ plane_sw(y))] = t[j];
   }
+}
+
+// In-place transpose of a swizzled plane (every thread reads its share, then
+// writes it to the mirrored position; barriers before and after).
+template <int N, int THREADS>
+__device__ __forceinline__ void transpose_plane(float* P) {
+  constexpr int PER = N * N / THREADS;
+  float t[PER];
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    const int e = threadIdx.x + j * THREADS;
+    const int y = e / N, x = e % N;
+    t[j] = P[y * N + (x ^ plane_sw(y))];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    const int e = threadIdx.x + j * THREADS;
+    const int y = e / N, x = e % N;
+    P[x * N + (y ^ plane_sw(x))] = t[j];
+  }
+  __syncthreads();
 }
 
 // ------------------------------------------------------------ the kernels
@@ -363,7 +403,7 @@ struct SlabArgs {
 // d = r + beta d; Z1 = DST-II_z d, Z3 = DCT-II_z d; sumd = sum d.  CTA: 32
 // lines along z at x = x0 .. x0 + 31, y fixed (grid N/32 x N blocks per run).
 template <int N, int MAXB>
-__global__ void __launch_bounds__(Cfg<N>::TILE_THREADS)
+__global__ void __launch_bounds__(Cfg<N>::TILE_THREADS, 4)
 k_cg_zfwd(const __grid_constant__ SlabArgs<MAXB> args, const C2<float>* __restrict__ twg,
           const C2<float>* __restrict__ qg) {
   using C = Cfg<N>;
@@ -470,30 +510,31 @@ __device__ __forceinline__ void pre_inv_rt(C2<float> (&v)[16], const LA& A, cons
   }
 }
 
-// The twelve line operations of k_cg_xy, per team (two lines each):
+// The twelve line operations of k_cg_xy, per team (two lines each), all
+// along rows; the y passes work on the transposed plane (row = x mode):
 //   0, 1   x forward of Z1: DCT-II (term 1, into P) and DST-II (term 2, into Q)
-//          of rows 2t, 2t + 1
-//   2, 3   y of term 1 on P: DST-II with its weight, DST-III (columns 2t, 2t + 1)
+//          of rows 2t, 2t + 1                          [then P, Q transposed]
+//   2, 3   y of term 1 on P: DST-II with its weight, DST-III (rows 2t, 2t + 1)
 //   4, 5   y of term 2 on Q: DCT-II with its weight, DCT-III
+//                                                  [then P, Q transposed back]
 //   6, 7   x inverse: DCT-III of P plus DST-III of Q, rows 2t, 2t + 1 -> W12
 //   (Z3 into P)
-//   8      x forward of Z3: DST-II of rows 2t, 2t + 1
-//   9, 10  y of term 3: DST-II with its weight, DST-III
+//   8      x forward of Z3: DST-II of rows 2t, 2t + 1     [then P transposed]
+//   9, 10  y of term 3: DST-II with its weight, DST-III [then P transposed back]
 //   11     x inverse: DST-III of rows 2t, 2t + 1 -> W3
-// One loop runs them all through one copy of the FFT code (a fully
-// unrolled kernel with a copy per operation does not fit the instruction
-// cache).  Barriers follow operations 1, 5, 7, 8 and 10.
+// One loop runs them all through one copy of the FFT code (a fully unrolled
+// kernel with a copy per operation does not fit the instruction cache).
 constexpr int kXyOps = 12;
 
 // The (x, y) part of the three Schur terms on plane kz = blockIdx.x of the
 // z-transformed fields of run blockIdx.y, in place: Z1 -> W12 = T1 + T2,
-// Z3 -> W3 = T3.  Plane rows of N + 1 floats.
+// Z3 -> W3 = T3.
 template <int N, int MAXB>
 __global__ void __launch_bounds__(Cfg<N>::PLANE_THREADS, 1)
 k_cg_xy(const __grid_constant__ SlabArgs<MAXB> args, const C2<float>* __restrict__ twg,
         const C2<float>* __restrict__ qg, const float* __restrict__ s2g, float inv_mu) {
   using C = Cfg<N>;
-  constexpr int T = C::PLANE_THREADS, M = C::M, TS = XBuf<N>::TS, S = N + 1;
+  constexpr int T = C::PLANE_THREADS, M = C::M, TS = XBuf<N>::TS;
   constexpr float invN = 1.0f / N;
   const int b = blockIdx.y;
   if (args.s[b]->done) return;
@@ -501,8 +542,8 @@ k_cg_xy(const __grid_constant__ SlabArgs<MAXB> args, const C2<float>* __restrict
   float* __restrict__ z3 = args.z3[b];
   extern __shared__ __align__(16) unsigned char smx[];
   float* P = reinterpret_cast<float*>(smx);
-  float* Q = P + N * S;
-  float* Xr = Q + N * S;
+  float* Q = P + N * N;
+  float* Xr = Q + N * N;
   float* Xi = Xr + C::PLANE_TEAMS * TS;
   C2<float>* tw = reinterpret_cast<C2<float>*>(Xi + C::PLANE_TEAMS * TS);
   C2<float>* qN = tw + 2 * N;
@@ -514,7 +555,7 @@ k_cg_xy(const __grid_constant__ SlabArgs<MAXB> args, const C2<float>* __restrict
   const XBuf<N> X{Xr + tm * TS, Xi + tm * TS};
   load_plane<N, T>(P, z1 + off);
   __syncthreads();   // tables and plane
-  const int l0 = 2 * tm;   // this team's pair of rows, or of columns
+  const int l0 = 2 * tm;   // this team's pair of rows
 #pragma unroll 1
   for (int op = 0; op < kXyOps; ++op) {
     if (op == 8) {
@@ -522,38 +563,34 @@ k_cg_xy(const __grid_constant__ SlabArgs<MAXB> args, const C2<float>* __restrict
       __syncthreads();
     }
     const bool inv = op == 3 || op == 5 || op == 6 || op == 7 || op == 10 || op == 11;
-    const bool col = (op >= 2 && op <= 5) || op == 9 || op == 10;
-    const int row = op == 0 || op == 6 ? l0 : (op == 1 || op == 7 ? l0 + 1 : l0);
+    const bool qplane = op == 4 || op == 5;
+    const int row = (op == 1 || op == 7) ? l0 + 1 : l0;
     int ka = 1, kb = 1, term = 0;
-    Line A, B, DA, DB;
-    if (col) {
-      float* pl = (op == 4 || op == 5) ? Q : P;
-      A = {pl + l0, S};
-      B = {pl + l0 + 1, S};
-      if (op == 4 || op == 5) ka = kb = 0;
-      term = op == 2 ? 1 : (op == 4 ? 2 : (op == 9 ? 3 : 0));
-    } else if (op <= 1) {
-      A = B = {P + row * S, 1};   // one row, DCT-II into P and DST-II into Q
+    PlaneRow A, B, DB;
+    if (op <= 1) {
+      A = B = plane_row<N>(P, row);   // one row: DCT-II into P, DST-II into Q
+      DB = plane_row<N>(Q, row);
       ka = 0;
-      kb = 1;
-    } else if (op <= 7) {
-      A = {P + row * S, 1};       // DCT-III of term 1 and DST-III of term 2
-      B = {Q + row * S, 1};
+    } else if (op == 6 || op == 7) {
+      A = plane_row<N>(P, row);       // DCT-III of term 1 and DST-III of term 2
+      B = plane_row<N>(Q, row);
+      DB = B;
       ka = 0;
-      kb = 1;
     } else {
-      A = {P + l0 * S, 1};
-      B = {P + (l0 + 1) * S, 1};
+      float* pl = qplane ? Q : P;
+      A = plane_row<N>(pl, l0);
+      B = plane_row<N>(pl, l0 + 1);
+      DB = B;
+      if (qplane) ka = kb = 0;
+      term = op == 2 ? 1 : (op == 4 ? 2 : (op == 9 ? 3 : 0));
     }
-    DA = A;
-    DB = (op <= 1) ? Line{Q + row * S, 1} : B;
     C2<float> v[16];
     if (inv) pre_inv_rt<N>(v, A, B, ka, kb, qN, m);
     else pre_fwd_rt<N>(v, A, B, ka, kb, m);
     team_fft<N, false>(v, X, tw, m);
     if (!inv) {
-      // weights of the y passes: sin^2 of the DCT axis over the sum of the
-      // three axes' sin^2, over mu; the x and z modes are fixed per line
+      // weights of the y passes (row = x mode, position = y mode): sin^2 of
+      // the DCT axis over the sum of the three axes' sin^2, over mu
       const float az = term == 3 ? s2[kz] : s2[N + kz];
       const float ax0 = s2[(term == 1 ? 0 : N) + l0], ax1 = s2[(term == 1 ? 0 : N) + l0 + 1];
       post_fwd<N>(X, qN, m, [&](int k, float va, float vb) {
@@ -565,11 +602,10 @@ k_cg_xy(const __grid_constant__ SlabArgs<MAXB> args, const C2<float>* __restrict
           va *= schur_w(n0, ax0 + ay + az, inv_mu);
           vb *= schur_w(n1, ax1 + ay + az, inv_mu);
         }
-        DA[oa] = va;
+        A[oa] = va;
         DB[ob] = vb;
       });
     } else {
-      const float sa = invN, sb = -invN;   // 1/N, and the conjugation of the imaginary part
       float* outa = nullptr;
       float* outb = nullptr;
       if (op == 6 || op == 7) outa = z1 + off + (int64_t)row * N;
@@ -577,7 +613,8 @@ k_cg_xy(const __grid_constant__ SlabArgs<MAXB> args, const C2<float>* __restrict
         outa = z3 + off + (int64_t)l0 * N;
         outb = outa + N;
       }
-      post_inv_rt<N>(X, ka, kb, sa, sb, m, [&](int o, float va, float vb) {
+      // 1/N, and the conjugation of the imaginary part
+      post_inv_rt<N>(X, ka, kb, invN, -invN, m, [&](int o, float va, float vb) {
         if (op == 6 || op == 7) outa[o] = va + vb;
         else if (op == 11) {
           outa[o] = va;
@@ -588,14 +625,19 @@ k_cg_xy(const __grid_constant__ SlabArgs<MAXB> args, const C2<float>* __restrict
         }
       });
     }
-    if (op == 1 || op == 5 || op == 7 || op == 8 || op == 10) __syncthreads();
+    if (op == 1 || op == 5 || op == 8 || op == 10) {
+      transpose_plane<N, T>(P);
+      if (op == 1 || op == 5) transpose_plane<N, T>(Q);
+    } else if (op == 7) {
+      __syncthreads();
+    }
   }
 }
 
 // q = DST-III_z W12 + DCT-III_z W3 + cdiag d; dq = d . q; alpha.  Tiles as
 // k_cg_zfwd.
 template <int N, int MAXB>
-__global__ void __launch_bounds__(Cfg<N>::TILE_THREADS)
+__global__ void __launch_bounds__(Cfg<N>::TILE_THREADS, 4)
 k_cg_zinv(const __grid_constant__ SlabArgs<MAXB> args, const C2<float>* __restrict__ twg,
           const C2<float>* __restrict__ qg) {
   using C = Cfg<N>;
@@ -662,44 +704,60 @@ k_cg_zinv(const __grid_constant__ SlabArgs<MAXB> args, const C2<float>* __restri
 }
 
 // x += alpha d; r -= alpha (q + sumd rank1); rr = r . r; beta; done once
-// rr <= stop.  Float4 vectors (n4 = N^3 / 4).
+// rr <= stop.  Float4 vectors (n4 = N^3 / 4), UPD_UNROLL float4 of each
+// vector per thread and pass with every load issued first; few blocks, so
+// that the block reductions and the last block's sum stay short.
+constexpr int UPD_THREADS = 256;
+constexpr int UPD_UNROLL = 4;
 template <int MAXB>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(UPD_THREADS, 2)
 k_cg_upd(const __grid_constant__ SlabArgs<MAXB> args, int64_t n4) {
   __shared__ double sh[32];
   __shared__ double total;
   const int b = blockIdx.y;
   CGScalars* s = args.s[b];
   if (s->done) return;
-  float* __restrict__ x = args.x[b];
-  float* __restrict__ r = args.r[b];
-  const float* __restrict__ d = args.d[b];
-  const float* __restrict__ q = args.q[b];
+  float4* __restrict__ x4 = reinterpret_cast<float4*>(args.x[b]);
+  float4* __restrict__ r4 = reinterpret_cast<float4*>(args.r[b]);
+  const float4* __restrict__ d4 = reinterpret_cast<const float4*>(args.d[b]);
+  const float4* __restrict__ q4 = reinterpret_cast<const float4*>(args.q[b]);
   double* __restrict__ partial = args.partial[b];
   const float a = float(s->alpha);
   const float c1 = float(s->sumd * s->rank1);
   CgAcc<float> acc;
-  float4* x4 = reinterpret_cast<float4*>(x);
-  float4* r4 = reinterpret_cast<float4*>(r);
-  const float4* d4 = reinterpret_cast<const float4*>(d);
-  const float4* q4 = reinterpret_cast<const float4*>(q);
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n4; e += (int64_t)gridDim.x * blockDim.x) {
-    const float4 dv = d4[e], qv = q4[e];
-    float4 rv = r4[e], xv = x4[e];
-    rv.x = rv.x - a * (qv.x + c1);
-    rv.y = rv.y - a * (qv.y + c1);
-    rv.z = rv.z - a * (qv.z + c1);
-    rv.w = rv.w - a * (qv.w + c1);
-    xv.x = xv.x + a * dv.x;
-    xv.y = xv.y + a * dv.y;
-    xv.z = xv.z + a * dv.z;
-    xv.w = xv.w + a * dv.w;
-    r4[e] = rv;
-    x4[e] = xv;
-    acc.add_prod(rv.x, rv.x);
-    acc.add_prod(rv.y, rv.y);
-    acc.add_prod(rv.z, rv.z);
-    acc.add_prod(rv.w, rv.w);
+  const int64_t stride = (int64_t)gridDim.x * UPD_THREADS;
+  for (int64_t e0 = (int64_t)blockIdx.x * UPD_THREADS + threadIdx.x; e0 < n4; e0 += stride * UPD_UNROLL) {
+    float4 dv[UPD_UNROLL], qv[UPD_UNROLL], rv[UPD_UNROLL], xv[UPD_UNROLL];
+#pragma unroll
+    for (int u = 0; u < UPD_UNROLL; ++u) {
+      const int64_t e = e0 + u * stride;
+      if (e < n4) {
+        dv[u] = d4[e];
+        qv[u] = q4[e];
+        rv[u] = r4[e];
+        xv[u] = x4[e];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < UPD_UNROLL; ++u) {
+      const int64_t e = e0 + u * stride;
+      if (e < n4) {
+        rv[u].x = rv[u].x - a * (qv[u].x + c1);
+        rv[u].y = rv[u].y - a * (qv[u].y + c1);
+        rv[u].z = rv[u].z - a * (qv[u].z + c1);
+        rv[u].w = rv[u].w - a * (qv[u].w + c1);
+        xv[u].x = xv[u].x + a * dv[u].x;
+        xv[u].y = xv[u].y + a * dv[u].y;
+        xv[u].z = xv[u].z + a * dv[u].z;
+        xv[u].w = xv[u].w + a * dv[u].w;
+        r4[e] = rv[u];
+        x4[e] = xv[u];
+        acc.add_prod(rv[u].x, rv[u].x);
+        acc.add_prod(rv[u].y, rv[u].y);
+        acc.add_prod(rv[u].z, rv[u].z);
+        acc.add_prod(rv[u].w, rv[u].w);
+      }
+    }
   }
   if (last_block_sum(acc.value(), partial, &s->ticket[1], sh, &total) && threadIdx.x == 0) {
     s->beta = (s->rr != 0.0) ? total / s->rr : 0.0;

@@ -331,7 +331,7 @@ __device__ __forceinline__ void post_inv_rt(const X& x, int ka, int kb, float sa
 // s2[a] = 4 sin^2(pi a / 2N) for the DCT modes, s2[N + a] = 4 sin^2(pi (a+1) / 2N)
 // for the DST modes; the numerator is the DCT axis's.
 __device__ __forceinline__ float schur_w(float num, float sum, float inv_mu) {
-  return num * __frcp_rn(sum) * inv_mu;
+  return __fdividef(num, sum) * inv_mu;   // sum >= 4 sin^2(pi / 2N) > 0, far from the fast path's limits
 }
 
 template <int N>

@@ -90,7 +90,7 @@ __device__ __forceinline__ int plane_sw(int y) {
 // z mod 16, bijective on even z, odd z, z < 8 and z >= 8 of each 16; the four
 // teams of a warp take lines 4w + t (bits 0, 1).  Multiples of 4 keep
 // 16-byte groups of lines together for vector copies.
-__device__ __forceinline__ int tile_sw(int z) { return (((z >> 1) ^ ((z & 1) << 2)) & 7) << 2; }
+__host__ __device__ __forceinline__ constexpr int tile_sw(int z) { return (((z >> 1) ^ ((z & 1) << 2)) & 7) << 2; }
 
 // Position along the team's two lines of logical exchange index c (the
 // team's lines double as its exchange buffer: real parts in line a,
@@ -98,7 +98,7 @@ __device__ __forceinline__ int tile_sw(int z) { return (((z >> 1) ^ ((z & 1) << 
 // exchange's three access patterns (8 consecutive indices; stride 16; the
 // natural index of the FFT output) fall on distinct banks with the swizzles
 // above.
-__device__ __forceinline__ int xpi(int c) { return c ^ ((c >> 4) & 7); }
+__host__ __device__ __forceinline__ constexpr int xpi(int c) { return c ^ ((c >> 4) & 7); }
 
 // Row y of a plane: element x at y N + (x ^ plane_sw(y)).
 struct PlaneRow {
@@ -384,6 +384,80 @@ __device__ __forceinline__ void transpose_plane(float* P) {
   __syncthreads();
 }
 
+// ------------------------------------------------- z-tile lane addressing
+// In a z tile, element z of line l sits at tl(z) ^ l with tl(z) = 32 z ^
+// tile_sw(z), and exchange index c of the team's lines at tl(xpi(c)) ^ l.  Both
+// maps are XOR-linear in the bits of their argument, so for the FFT's access
+// patterns, an index of the form (lane part) + (constant part) with disjoint
+// bits, the address is (the lane's precomputed part) ^ (a compile-time
+// constant): one XOR per access instead of the swizzle arithmetic.
+__host__ __device__ __forceinline__ constexpr int tl(int z) { return (z << 5) ^ tile_sw(z); }
+__host__ __device__ __forceinline__ constexpr int tlx(int c) { return tl(xpi(c)); }
+
+// One lane of a z-tile team: line l (the tile column), lane m < M.
+template <int N>
+struct ZLane {
+  static constexpr int M = N / 16, NS = 16 / M;
+  int m;
+  int e_m, e_2m, e_mm1, e_nm;      // tl(m), tl(2m), tl of the k-1 and N-k lane parts, each ^ l
+  int x_m, x_16m, x_nsm, x_mp, x_mh;   // tlx of m, 16 m, NS m, the partner -m mod M, m >> 1 (odd: ^ tlx(N-1))
+  __device__ __forceinline__ ZLane(int m_, int l) : m(m_) {
+    e_m = tl(m) ^ l;
+    e_2m = tl(2 * m) ^ l;
+    e_mm1 = tl(m ? m - 1 : M - 1) ^ l;   // k - 1 = (m - 1) + M r, or (M - 1) + M (r - 1) for m = 0
+    e_nm = tl(m ? M - m : 0) ^ l;        // N - k = (M - m) + M (15 - r), or M (16 - r) for m = 0
+    x_m = tlx(m) ^ l;
+    x_16m = tlx(16 * m) ^ l;
+    x_nsm = tlx(NS * m) ^ l;
+    x_mp = tlx((M - m) & (M - 1)) ^ l;
+    x_mh = tlx(m >> 1) ^ ((m & 1) ? tlx(N - 1) : 0) ^ l;
+  }
+};
+
+// The team FFT of team_fft with the exchange in the z tile's lines D (real)
+// and E (imaginary) at the lane's XOR addresses.
+template <int N, bool INV>
+__device__ __forceinline__ void zteam_fft(C2<float> (&v)[16], float* D, float* E, const ZLane<N>& L,
+                                          const C2<float>* tw) {
+  constexpr int M = ZLane<N>::M, NS = ZLane<N>::NS;
+  const int m = L.m;
+  dft_reg<16, INV, float>(v);
+  __syncwarp();
+#pragma unroll
+  for (int s = 0; s < 16; ++s) {
+    C2<float> y = v[s];
+    if (s != 0) {
+      C2<float> w = tw[2 * m * s];
+      if (INV) w.y = -w.y;
+      y = cmul(y, w);
+    }
+    const int a = L.x_m ^ tlx(s * M);
+    D[a] = y.x;
+    E[a] = y.y;
+  }
+  __syncwarp();
+  C2<float> w2[NS][M];
+#pragma unroll
+  for (int q = 0; q < NS; ++q)
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+      const int a = L.x_16m ^ tlx(q * M + k);   // c = (NS m + q) M + k = 16 m + q M + k
+      w2[q][k] = {D[a], E[a]};
+    }
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < NS; ++q) {
+    dft_reg<M, INV, float>(w2[q]);
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+      const int a = L.x_nsm ^ tlx(q + 16 * k);   // c = NS m + q + 16 k
+      D[a] = w2[q][k].x;
+      E[a] = w2[q][k].y;
+    }
+  }
+  __syncwarp();
+}
+
 // ------------------------------------------------------------ the kernels
 // The buffers of up to MAXB independent CG runs on one grid (blockIdx.y
 // selects the run): each run's blocks reduce exactly as a single run's, so a
@@ -447,16 +521,37 @@ k_cg_zfwd(const __grid_constant__ SlabArgs<MAXB> args, const C2<float>* __restri
   }
   __syncthreads();
   {
+    // DCT-II and DST-II of line tm along z in one FFT (pre: Makhoul's order,
+    // the second half negated for the DST; post: both transforms at mode k)
     const int tm = threadIdx.x / M, m = threadIdx.x % M;
-    const TileCol A{D, tm}, B{E, tm};
+    const ZLane<N> L(m, tm);
     C2<float> v[16];
-    pre_fwd_cs<N>(v, A, m);
-    const auto X = xlines(A, B);
-    team_fft<N, false>(v, X, tw, m);
-    post_fwd<N>(X, qN, m, [&](int k, float c, float sn) {
-      B[k] = c;             // DCT-II mode k -> Z3
-      A[N - 1 - k] = sn;    // DST-II mode N-1-k -> Z1
-    });
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const bool hi = r >= 8;   // n = m + M r >= N / 2: element 2(N-1-n)+1 = (2N-1) ^ 2n
+      const float a = D[L.e_2m ^ (hi ? tl(2 * N - 1) ^ tl(2 * M * r) : tl(2 * M * r))];
+      v[r] = {a, hi ? -a : a};
+    }
+    zteam_fft<N, false>(v, D, E, L, tw);
+    float oc[16], os[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const int k = m + M * r;
+      const int ak = L.x_m ^ tlx(M * r);
+      const int ac = L.x_mp ^ (m ? tlx(M * (15 - r)) : tlx(M * ((16 - r) & 15)));
+      const float zkx = D[ak], zky = E[ak], zcx = D[ac], zcy = E[ac];
+      const float vax = 0.5f * (zkx + zcx), vay = 0.5f * (zky - zcy);
+      const float vbx = 0.5f * (zky + zcy), vby = -0.5f * (zkx - zcx);
+      const C2<float> q = qN[k];
+      oc[r] = q.x * vax - q.y * vay;
+      os[r] = q.x * vbx - q.y * vby;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      E[L.e_m ^ tl(M * r)] = oc[r];                        // DCT-II mode k -> Z3
+      D[L.e_m ^ tl(N - 1) ^ tl(M * r)] = os[r];            // DST-II at N-1-k -> Z1
+    }
   }
   __syncthreads();
   for (int e4 = threadIdx.x; e4 < N * 8; e4 += T) {
@@ -669,13 +764,38 @@ k_cg_zinv(const __grid_constant__ SlabArgs<MAXB> args, const C2<float>* __restri
   }
   __syncthreads();
   {
+    // DST-III of line tm of W12 (D) plus DCT-III of line tm of W3 (E) in one
+    // inverse FFT: V_k = conj(q_k) (x_k - i x_{N-k}), the DST-III line read
+    // backwards (x_k -> D[N-1-k], x_{N-k} -> D[k-1])
     const int tm = threadIdx.x / M, m = threadIdx.x % M;
-    const TileCol A{D, tm}, B{E, tm};
+    const ZLane<N> L(m, tm);
     C2<float> v[16];
-    pre_inv_pair<N>(v, A, B, true, false, qN, m);
-    const auto X = xlines(A, B);
-    team_fft<N, true>(v, X, tw, m);
-    post_inv<N>(X, true, false, m, [&](int o, float va, float vb) { A[o] = va + vb; });
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const int k = m + M * r;
+      const bool k0 = (k == 0);
+      const float xa = D[L.e_m ^ tl(N - 1) ^ tl(M * r)];
+      const float xna = k0 ? 0.f : D[L.e_mm1 ^ (m ? tl(M * r) : (r ? tl(M * (r - 1)) : 0))];
+      const float xb = E[L.e_m ^ tl(M * r)];
+      const float xnb = k0 ? 0.f : E[L.e_nm ^ (m ? tl(M * (15 - r)) : tl(M * (16 - r)))];
+      const C2<float> q = qN[k];
+      const float vax = q.x * xa - q.y * xna, vay = -q.x * xna - q.y * xa;
+      const float vbx = q.x * xb - q.y * xnb, vby = -q.x * xnb - q.y * xb;
+      v[r] = {vax - vby, vay + vbx};
+    }
+    zteam_fft<N, true>(v, D, E, L, tw);
+    // x_{2n} = v_n, x_{2n+1} = v_{N-1-n} over N; the DST-III line negates the odd outputs
+    constexpr float invN = 1.0f / N;
+    const float sa = (m & 1) ? -invN : invN;
+    float oa[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const int a = L.x_mh ^ tlx((M / 2) * r);
+      oa[r] = D[a] * sa + E[a] * invN;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < 16; ++r) D[L.e_m ^ tl(M * r)] = oa[r];
   }
   __syncthreads();
   const float cd = float(s->cdiag);

@@ -191,6 +191,84 @@ __device__ __forceinline__ void team_fft(C2<float> (&v)[16], const X& x, const C
   __syncwarp();
 }
 
+// team_fft for the separate exchange (X::blocked false) with the output left
+// in registers: lane m returns Z[m + M j] in z[j], j = 0..15 (the radix-M
+// step's results, k = q M + m + 16 k' with j = q + NS k').  zx_store writes
+// them to the exchange at their natural index when a post-processing needs
+// a general permutation of Z.
+template <int N, bool INV, class X>
+__device__ __forceinline__ void team_fft_reg(C2<float> (&v)[16], const X& x, const C2<float>* tw, int m,
+                                             C2<float> (&z)[16]) {
+  using C = Cfg<N>;
+  constexpr int M = C::M, NS = C::NS;
+  static_assert(!X::blocked, "register output needs the interleaved stage-two order");
+  dft_reg<16, INV, float>(v);
+  __syncwarp();
+#pragma unroll
+  for (int s = 0; s < 16; ++s) {
+    C2<float> y = v[s];
+    if (s != 0) {
+      C2<float> w = tw[2 * m * s];
+      if (INV) w.y = -w.y;
+      y = cmul(y, w);
+    }
+    x.re(s * M + m) = y.x;
+    x.im(s * M + m) = y.y;
+  }
+  __syncwarp();
+  C2<float> w2[NS][M];
+#pragma unroll
+  for (int q = 0; q < NS; ++q)
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+      const int c = (q * M + m) * M + k;
+      w2[q][k] = {x.re(c), x.im(c)};
+    }
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < NS; ++q) {
+    dft_reg<M, INV, float>(w2[q]);
+#pragma unroll
+    for (int k = 0; k < M; ++k) z[q + NS * k] = w2[q][k];
+  }
+}
+
+template <int N, class X>
+__device__ __forceinline__ void zx_store(const X& x, const C2<float> (&z)[16], int m) {
+  constexpr int M = Cfg<N>::M;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    x.re(m + M * j) = z[j].x;
+    x.im(m + M * j) = z[j].y;
+  }
+  __syncwarp();
+}
+
+// Forward output from the FFT registers (team_fft_reg): Z[N - k] of mode
+// k = m + M r lies with lane (M - m) mod M of the team, register 15 - r (or
+// (16 - r) mod 16 for m = 0), and arrives by a shuffle; put(k, xa, xb) as
+// post_fwd.
+template <int N, class F>
+__device__ __forceinline__ void post_fwd_reg(const C2<float> (&z)[16], const C2<float>* qN, int m, F&& put) {
+  constexpr int M = Cfg<N>::M;
+  const int lane = threadIdx.x & 31;
+  const int partner = (lane & ~(M - 1)) | ((M - m) & (M - 1));
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    // what this lane sends: the value its partner needs, Z at register 15 - r
+    // (partner m != 0) or (16 - r) mod 16 (m = 0, its own partner)
+    const C2<float> snd = m ? z[15 - r] : z[(16 - r) & 15];
+    const float zcx = __shfl_sync(0xffffffffu, snd.x, partner);
+    const float zcy = __shfl_sync(0xffffffffu, snd.y, partner);
+    const float zkx = z[r].x, zky = z[r].y;
+    const float vax = 0.5f * (zkx + zcx), vay = 0.5f * (zky - zcy);
+    const float vbx = 0.5f * (zky + zcy), vby = -0.5f * (zkx - zcx);
+    const int k = m + M * r;
+    const C2<float> q = qN[k];
+    put(k, q.x * vax - q.y * vay, q.x * vbx - q.y * vby);
+  }
+}
+
 // Forward input of a pair of lines (DCT-II or DST-II each; DST-II negates the
 // second half of Makhoul's reordering v_n = x_{2n}, v_{N-1-n} = x_{2n+1}).
 template <int N, class LA, class LB>
@@ -679,16 +757,16 @@ k_cg_xy(const __grid_constant__ SlabArgs<MAXB> args, const C2<float>* __restrict
       if (qplane) ka = kb = 0;
       term = op == 2 ? 1 : (op == 4 ? 2 : (op == 9 ? 3 : 0));
     }
-    C2<float> v[16];
+    C2<float> v[16], zr[16];
     if (inv) pre_inv_rt<N>(v, A, B, ka, kb, qN, m);
     else pre_fwd_rt<N>(v, A, B, ka, kb, m);
-    team_fft<N, false>(v, X, tw, m);
+    team_fft_reg<N, false>(v, X, tw, m, zr);
     if (!inv) {
       // weights of the y passes (row = x mode, position = y mode): sin^2 of
       // the DCT axis over the sum of the three axes' sin^2, over mu
       const float az = term == 3 ? s2[kz] : s2[N + kz];
       const float ax0 = s2[(term == 1 ? 0 : N) + l0], ax1 = s2[(term == 1 ? 0 : N) + l0 + 1];
-      post_fwd<N>(X, qN, m, [&](int k, float va, float vb) {
+      post_fwd_reg<N>(zr, qN, m, [&](int k, float va, float vb) {
         const int oa = ka ? N - 1 - k : k, ob = kb ? N - 1 - k : k;
         if (term) {
           const float ay = s2[(term == 2 ? 0 : N) + oa];
@@ -708,6 +786,7 @@ k_cg_xy(const __grid_constant__ SlabArgs<MAXB> args, const C2<float>* __restrict
         outa = z3 + off + (int64_t)l0 * N;
         outb = outa + N;
       }
+      zx_store<N>(X, zr, m);
       // 1/N, and the conjugation of the imaginary part
       post_inv_rt<N>(X, ka, kb, invN, -invN, m, [&](int o, float va, float vb) {
         if (op == 6 || op == 7) outa[o] = va + vb;

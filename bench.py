@@ -270,7 +270,8 @@ def roofline_line(kernels, kprof, N3, cg_iters, args, peak, peak_kind):
     the largest share of the step.  For the slab CG the algorithmic bytes per
     launch are the survey model's figure for the work the kernel does: k_cg_xy
     does the middle pass of the Schur apply on all three terms (6 N^3 b); the
-    whole CG iteration (four kernels) is reported beside it against 27 N^3 b."""
+    whole CG iteration (three kernels, plus each run's closing update spread
+    over its iterations) is reported beside it against 27 N^3 b."""
     dom = max(kernels, key=lambda k: kernels[k]["share_of_step"])
     kd = kernels[dom]
     line = {"bound": "hbm", "peak": peak, "unit": "GB/s", "peak_source": peak_kind,

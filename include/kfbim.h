@@ -366,10 +366,12 @@ int kfbim_profile(kfbim_ctx* ctx, int enable, double* ms64, int64_t* launches64,
 typedef enum {
   KFBIM_KCLASS_TRANSFORM_FP64 = 0,  /* one-axis transform passes, FP64 */
   KFBIM_KCLASS_TRANSFORM_FP32 = 1,  /* one-axis transform passes, FP32 (FFT or tensor core) */
-  KFBIM_KCLASS_CG_ZFWD = 2,         /* slab CG: d = r + beta d, z transforms (5 N^3 floats) */
+  KFBIM_KCLASS_CG_ZFWD = 2,         /* slab CG: the previous iteration's x, r update, d = r + beta d,
+                                       z transforms (9 N^3 floats) */
   KFBIM_KCLASS_CG_XY = 3,           /* slab CG: xy planes of the three terms (4 N^3 floats) */
-  KFBIM_KCLASS_CG_ZINV = 4,         /* slab CG: inverse z transforms, d.q (4 N^3 floats) */
-  KFBIM_KCLASS_CG_UPDATE = 5,       /* slab CG: x, r update, r.r (6 N^3 floats) */
+  KFBIM_KCLASS_CG_ZINV = 4,         /* slab CG: inverse z transforms, d.q, r.r, r.q, q.q (5 N^3 floats) */
+  KFBIM_KCLASS_CG_UPDATE = 5,       /* slab CG: the x update still pending when a run stops
+                                       (3 N^3 floats, once per CG run) */
   KFBIM_KCLASS_CG_VECTOR = 6,       /* staged CG: the three vector kernels (14 N^3 values) */
   KFBIM_KCLASS_MAC_RESIDUAL = 7,    /* MIXED refinement: FP64 MAC residual (12 N^3 doubles) */
   KFBIM_KCLASS_JUMPS = 8,           /* jump evaluation (fit rows, jump maps, jumps) */

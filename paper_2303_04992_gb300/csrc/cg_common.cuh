@@ -97,7 +97,86 @@ struct CgAcc<float> {
     add(p);
     c = __fadd_rn(c, e);
   }
+  // add another accumulator's pair (s2, c2): TwoSum of the leading words,
+  // the error and the trailing words into c
+  __device__ __forceinline__ void merge(float s2, float c2) {
+    const float t = __fadd_rn(s, s2);
+    const float bp = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(s2, bp));
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(c2, err));
+  }
   __device__ __forceinline__ double value() const { return double(s) + double(c); }
 };
+
+// Grid sums of K compensated FP32 accumulators without FP64 arithmetic
+// (which runs at a small fraction of the FP32 rate on this GPU): warp
+// butterflies and the block and grid steps merge (s, c) pairs; block b
+// stores its K pairs at partial[K b + j]; the last block to finish merges
+// them in block order.  Returns true in that block, whose thread 0 holds the
+// K grid sums in out.  sh: K * 32 pairs of shared memory.
+__device__ __forceinline__ void warp_merge(CgAcc<float>& a) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float s2 = __shfl_xor_sync(0xffffffffu, a.s, o);
+    const float c2 = __shfl_xor_sync(0xffffffffu, a.c, o);
+    a.merge(s2, c2);
+  }
+}
+
+template <int K>
+__device__ __forceinline__ void block_merge(CgAcc<float> (&a)[K], float2* sh) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < K; ++j) warp_merge(a[j]);
+  if (lane == 0) {
+#pragma unroll
+    for (int j = 0; j < K; ++j) sh[32 * j + w] = make_float2(a[j].s, a[j].c);
+  }
+  __syncthreads();
+  if (w == 0) {
+    const bool in = lane < (int)(blockDim.x >> 5);
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const float2 p = in ? sh[32 * j + lane] : make_float2(0.f, 0.f);
+      a[j].s = p.x;
+      a[j].c = p.y;
+      warp_merge(a[j]);
+    }
+  }
+  __syncthreads();
+}
+
+template <int K>
+__device__ __forceinline__ bool last_block_merge(CgAcc<float> (&a)[K], float2* __restrict__ partial,
+                                                 unsigned int* ticket, float2* sh, double (&out)[K]) {
+  __shared__ bool is_last;
+  block_merge<K>(a, sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int j = 0; j < K; ++j) partial[K * blockIdx.x + j] = make_float2(a[j].s, a[j].c);
+    __threadfence();
+    const unsigned int t = atomicAdd(ticket, 1u);
+    is_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+  CgAcc<float> g[K];
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const float2 p = __ldcg(partial + K * b + j);
+      g[j].merge(p.x, p.y);
+    }
+  }
+  block_merge<K>(g, sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int j = 0; j < K; ++j) out[j] = g[j].value();
+    *ticket = 0u;
+  }
+  return true;
+}
 
 }  // namespace kfbim

@@ -69,7 +69,7 @@ struct kfbim_ctx {
   float* d_tc_mats = nullptr;
   int* d_tc_err = nullptr;
   int xf_plain = 0, xf_fused = 0;
-  // MIXED Schur CG as the four-kernel z-pencil / xy-slab iteration (slab.cuh)
+  // MIXED Schur CG as the three-kernel z-pencil / xy-slab iteration (slab.cuh)
   bool slab = false;
   // precision requested at setup (FP32 and MIXED_TF32 run as MIXED internally:
   // FP32 without the FP64 refinement sweeps, MIXED_TF32 on tensor-core passes)
@@ -126,7 +126,7 @@ struct kfbim_ctx {
   CGScalars* bcgs = nullptr;   // one per slot, contiguous
   double* bscal = nullptr;     // 8 per slot, contiguous
   double* bgh = nullptr;       // (bm + 1) per slot, contiguous (slot.gh points into it)
-  double* bpartial = nullptr;  // RED_BLOCKS reduction partials per slot (batched CG kernels)
+  double* bpartial = nullptr;  // kRunPartials reduction partials per slot (batched CG kernels)
   void* bpinned = nullptr;     // host staging of bcgs / bscal / bgh
   int bcap = 0, bm = 0;
   std::vector<int> b_cg, b_sweeps, b_isolves;   // per-slot counters of the current call
@@ -253,6 +253,9 @@ struct Tw<float> {
   static const float* s2(kfbim_ctx* c) { return c->d_s2f; }
 };
 
+// Reduction partials per batch slot: RED_BLOCKS for the staged CG kernels,
+// four per block of the slab iteration's k_cg_zinv (4 x 512 at N = 128).
+constexpr int kRunPartials = 2 * RED_BLOCKS;
 constexpr int kMaxJobs = 48;   // jobs per batched launch: 3 per instance, 16 instances
 
 template <typename Tin, typename T, typename Tout, int N, int MAXJ>
@@ -540,19 +543,26 @@ struct CgWs {
 CgWs<double> ws64(kfbim_ctx* c) { return {c->p, c->rres, c->cd, c->cq, c->q2, c->q3, c->T6}; }
 CgWs<float> ws32(kfbim_ctx* c) { return {c->fx, c->fr, c->fd, c->fq, c->fq2, c->fq3, c->fT6}; }
 
+// The slab CG of a single run on the FP32 workspace.
+SlabCg slab_run(kfbim_ctx* c, const CgWs<float>& w) {
+  const int64_t n = c->N3;
+  return {c->N, w.x, w.r, w.d, w.q, w.T6, w.T6 + n, c->d_twc32, c->d_q32, c->d_s2f, (float)(1.0 / c->mu),
+          c->cgs, c->partial};
+}
+
 // One CG iteration: q = S d (5 staged launches), then the three fused
-// scalar/vector kernels.  All of it is a no-op once cgs->done is set.
+// scalar/vector kernels; or the three slab kernels.  All of it is a no-op
+// once cgs->done is set.
 template <typename T>
 void cg_iteration(kfbim_ctx* c, const CgWs<T>& w, cudaStream_t s) {
   const int64_t n = c->N3;
   if constexpr (std::is_same<T, float>::value) {
     if (c->slab) {
-      // d = r + beta d and the z transforms; the xy planes; the inverse z
-      // transforms with d.q; the vector update with r.r (slab.cuh)
-      SlabCg a{c->N, w.x, w.r, w.d, w.q, w.T6, w.T6 + n, c->d_twc32, c->d_q32, c->d_s2f,
-               (float)(1.0 / c->mu), c->cgs, c->partial};
+      // the previous iteration's update, d = r + beta d and the z transforms;
+      // the xy planes; the inverse z transforms with d.q, r.q, q.q (slab.cuh)
+      const SlabCg a = slab_run(c, w);
       if (c->prof) {
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < 3; ++k) {
           const int at = prof_begin(c, s);
           g_launches += slab_launch(k, a, s);
           prof_end(c, s, at, KFBIM_KCLASS_CG_ZFWD + k, 1, (double)kSlabValues[k] * n * sizeof(float));
@@ -647,7 +657,7 @@ cudaGraphExec_t cg_graph(kfbim_ctx* c, const CgWs<T>& w) {
 // scalars.  With a loop graph the host reads the scalars once per run; else
 // once per kCgGraphIters iterations.
 template <typename T>
-int cg(kfbim_ctx* c, const T* b, const CgWs<T>& w, double tol, int maxit, cudaStream_t s, int* iters) {
+int cg_loop(kfbim_ctx* c, const T* b, const CgWs<T>& w, double tol, int maxit, cudaStream_t s, int* iters) {
   const int64_t n = c->N3;
   const bool graphs = c->use_graphs && !c->prof;
   cudaGraphExec_t exec = graphs ? cg_graph<T>(c, w) : nullptr;
@@ -682,6 +692,21 @@ int cg(kfbim_ctx* c, const T* b, const CgWs<T>& w, double tol, int maxit, cudaSt
     }
     launched += kCgGraphIters;
   }
+}
+
+// The CG run, and for the slab iteration the update it left pending.
+template <typename T>
+int cg(kfbim_ctx* c, const T* b, const CgWs<T>& w, double tol, int maxit, cudaStream_t s, int* iters) {
+  const int st = cg_loop<T>(c, b, w, tol, maxit, s, iters);
+  if constexpr (std::is_same<T, float>::value) {
+    if (c->slab) {
+      const int at = prof_begin(c, s);
+      g_launches += slab_cg_finish(slab_run(c, w), s);
+      prof_end(c, s, at, KFBIM_KCLASS_CG_UPDATE, 1, (double)kSlabValues[3] * c->N3 * sizeof(float));
+      check_launch();
+    }
+  }
+  return st;
 }
 
 // Solve the corrected MAC system for rhs = [f1|f2|f3|g] (FP64) -> u, p (FP64).
@@ -1467,7 +1492,7 @@ void batch_alloc(kfbim_ctx* c, int B) {
   }
   c->bcgs = dalloc<CGScalars>(c, B);
   c->bscal = dalloc<double>(c, 8 * (size_t)B);
-  c->bpartial = dalloc<double>(c, (size_t)RED_BLOCKS * B);
+  c->bpartial = dalloc<double>(c, (size_t)kRunPartials * B);
   if (c->bpinned) CK(cudaFreeHost(c->bpinned));
   c->bpinned = nullptr;
   const size_t pin = std::max({sizeof(CGScalars) * B, sizeof(double) * 8 * B,
@@ -1537,6 +1562,18 @@ void face3_batch(kfbim_ctx* c, const std::vector<int>& act, const std::vector<co
   for (int k = 1; k < 5; ++k) stage_list<float, float, float>(c, L[k], s);
 }
 
+// The slab CG runs of batch slots `slots`.
+std::vector<SlabCg> slab_batch_runs(kfbim_ctx* c, const std::vector<int>& slots) {
+  const int64_t n = c->N3;
+  std::vector<SlabCg> runs;
+  for (int b : slots) {
+    const kfbim_ctx::Slot& w = c->bs[b];
+    runs.push_back({c->N, w.x, w.r, w.d, w.q, w.T6, w.T6 + n, c->d_twc32, c->d_q32, c->d_s2f,
+                    (float)(1.0 / c->mu), &c->bcgs[b], c->bpartial + (size_t)kRunPartials * b});
+  }
+  return runs;
+}
+
 // Lockstep FP32 CG of the instances in `act` on (S + ...) x = b (b in fu[0:N3]).
 void cg_batch(kfbim_ctx* c, const std::vector<int>& act, double tol, cudaStream_t s) {
   const int64_t n = c->N3;
@@ -1577,18 +1614,13 @@ void cg_batch(kfbim_ctx* c, const std::vector<int>& act, double tol, cudaStream_
       A.q2[k] = w.q2;
       A.q3[k] = w.q3;
       A.s[k] = &c->bcgs[run[k]];
-      A.partial[k] = c->bpartial + (size_t)RED_BLOCKS * run[k];
+      A.partial[k] = c->bpartial + (size_t)kRunPartials * run[k];
     }
     const dim3 grid(RED_BLOCKS, (unsigned)run.size());
     if (c->slab) {
-      // the four slab kernels of all running instances, one launch each per
+      // the three slab kernels of all running instances, one launch each per
       // iteration (blockIdx.y = instance; the single-run arithmetic)
-      std::vector<SlabCg> runs;
-      for (int b : run) {
-        const kfbim_ctx::Slot& w = c->bs[b];
-        runs.push_back({c->N, w.x, w.r, w.d, w.q, w.T6, w.T6 + n, c->d_twc32, c->d_q32, c->d_s2f,
-                        (float)(1.0 / c->mu), &c->bcgs[b], c->bpartial + (size_t)RED_BLOCKS * b});
-      }
+      const std::vector<SlabCg> runs = slab_batch_runs(c, run);
       for (int it = 0; it < kCgGraphIters; ++it) {
         g_launches += slab_cg_iteration_batch(runs.data(), (int)runs.size(), s);
         check_launch();
@@ -1604,6 +1636,12 @@ void cg_batch(kfbim_ctx* c, const std::vector<int>& act, double tol, cudaStream_
       }
     }
     launched += kCgGraphIters;
+  }
+  if (c->slab && !act.empty()) {
+    // the update each run left pending when it stopped
+    const std::vector<SlabCg> runs = slab_batch_runs(c, act);
+    g_launches += slab_cg_finish_batch(runs.data(), (int)runs.size(), s);
+    check_launch();
   }
   for (int b : act) {
     c->cg_iters += h[b].iters;

@@ -1,4 +1,4 @@
-// Launchers of the four-kernel FP32 Schur CG iteration (slab.cuh).
+// Launchers of the three-kernel FP32 Schur CG iteration (slab.cuh).
 #include <cuda_runtime.h>
 
 #include "slab.cuh"
@@ -10,7 +10,7 @@ bool slab_supported(int N) { return N == 32 || N == 64 || N == 128; }
 
 namespace {
 
-constexpr int kUpdBlocks = 304;   // 2 x 152 SMs: one wave at the kernel's register use
+constexpr int kFinBlocks = 608;   // 4 x 152 SMs
 
 template <int N, int MAXB>
 cudaError_t prepare_nb() {
@@ -47,7 +47,8 @@ slab::SlabArgs<MAXB> make_args(const SlabCg* runs, int nrun) {
   return a;
 }
 
-// Kernel `which` of the iteration: 0 k_cg_zfwd, 1 k_cg_xy, 2 k_cg_zinv, 3 k_cg_upd.
+// Kernel `which` of the iteration: 0 k_cg_zfwd, 1 k_cg_xy, 2 k_cg_zinv; 3 is
+// k_cg_fin, the update still pending when a run stops.
 template <int N, int MAXB>
 void launch_nb(int which, const slab::SlabArgs<MAXB>& args, const SlabCg& t, int nrun, cudaStream_t st) {
   using C = slab::Cfg<N>;
@@ -67,9 +68,9 @@ void launch_nb(int which, const slab::SlabArgs<MAXB>& args, const SlabCg& t, int
       break;
     default: {
       const int64_t n4 = (int64_t)N * N * N / 4;
-      const int64_t per = (int64_t)slab::UPD_THREADS * slab::UPD_UNROLL;
-      const unsigned blocks = (unsigned)((n4 + per - 1) / per < kUpdBlocks ? (n4 + per - 1) / per : kUpdBlocks);
-      slab::k_cg_upd<MAXB><<<dim3(blocks, nrun), slab::UPD_THREADS, 0, st>>>(args, n4);
+      const int64_t need = (n4 + slab::FIN_THREADS - 1) / slab::FIN_THREADS;
+      const unsigned blocks = (unsigned)(need < kFinBlocks ? need : kFinBlocks);
+      slab::k_cg_fin<MAXB><<<dim3(blocks, nrun), slab::FIN_THREADS, 0, st>>>(args, n4);
     }
   }
 }
@@ -88,13 +89,18 @@ void schur_n(const SlabCg& a, cudaStream_t st) {
 template <int N>
 void iteration_n(const SlabCg& a, cudaStream_t st) {
   const slab::SlabArgs<1> args = make_args<1>(&a, 1);
-  for (int k = 0; k < 4; ++k) launch_nb<N, 1>(k, args, a, 1, st);
+  for (int k = 0; k < 3; ++k) launch_nb<N, 1>(k, args, a, 1, st);
 }
 
 template <int N>
 void iteration_batch_n(const SlabCg* runs, int nrun, cudaStream_t st) {
   const slab::SlabArgs<kSlabBatchMax> args = make_args<kSlabBatchMax>(runs, nrun);
-  for (int k = 0; k < 4; ++k) launch_nb<N, kSlabBatchMax>(k, args, runs[0], nrun, st);
+  for (int k = 0; k < 3; ++k) launch_nb<N, kSlabBatchMax>(k, args, runs[0], nrun, st);
+}
+
+template <int N>
+void finish_batch_n(const SlabCg* runs, int nrun, cudaStream_t st) {
+  launch_nb<N, kSlabBatchMax>(3, make_args<kSlabBatchMax>(runs, nrun), runs[0], nrun, st);
 }
 
 }  // namespace
@@ -115,7 +121,7 @@ int slab_cg_iteration(const SlabCg& a, cudaStream_t st) {
     case 32: iteration_n<32>(a, st); break;
     default: return 0;
   }
-  return 4;
+  return 3;
 }
 
 int slab_cg_iteration_batch(const SlabCg* runs, int nrun, cudaStream_t st) {
@@ -126,7 +132,20 @@ int slab_cg_iteration_batch(const SlabCg* runs, int nrun, cudaStream_t st) {
     case 32: iteration_batch_n<32>(runs, nrun, st); break;
     default: return 0;
   }
-  return 4;
+  return 3;
+}
+
+int slab_cg_finish(const SlabCg& a, cudaStream_t st) { return slab_launch(3, a, st); }
+
+int slab_cg_finish_batch(const SlabCg* runs, int nrun, cudaStream_t st) {
+  if (nrun < 1 || nrun > kSlabBatchMax) return 0;
+  switch (runs[0].N) {
+    case 128: finish_batch_n<128>(runs, nrun, st); break;
+    case 64: finish_batch_n<64>(runs, nrun, st); break;
+    case 32: finish_batch_n<32>(runs, nrun, st); break;
+    default: return 0;
+  }
+  return 1;
 }
 
 int slab_launch(int which, const SlabCg& a, cudaStream_t st) {

@@ -1,4 +1,4 @@
-// FP32 Schur-complement CG iteration in four kernels (Sec. 4.2, Eq. linearS1
+// FP32 Schur-complement CG iteration in three kernels (Sec. 4.2, Eq. linearS1
 // and items i-iii), for N = 32, 64, 128.
 //
 // The Schur operator is applied in spectral form,
@@ -11,13 +11,28 @@
 //   W12 = T1 + T2 with T1 = (C_x S_y)^-1 L1 (C_x S_y) Z1, T2 = (S_x C_y)^-1 L2 (S_x C_y) Z1,
 //   W3  = (S_x S_y)^-1 L3 (S_x S_y) Z3,
 // the weights taking the plane's z mode.  The inverse z transforms of W12
-// (DST-III) and W3 (DCT-III) are summed into q.  One CG iteration:
-//   k_cg_zfwd  d = r + beta d, Z1 = S_z d, Z3 = C_z d, sum(d)       (1 read r, d; 3 writes)
-//   k_cg_xy    W12, W3 in place of Z1, Z3                          (2 reads, 2 writes)
-//   k_cg_zinv  q = S_z^-1 W12 + C_z^-1 W3 + cdiag d, d.q, alpha     (3 reads, 1 write)
-//   k_cg_upd   x += alpha d, r -= alpha (q + rank-one), r.r, beta  (4 reads, 2 writes)
-// i.e. 17 N^3 values moved per iteration, against 28 for the transform
-// passes of Schur apply run one axis at a time plus 14 for the CG vectors.
+// (DST-III) and W3 (DCT-III) are summed into q.
+//
+// The vector update of iteration k waits for alpha_k, which is known only
+// once the reduction of d.q over the whole grid is done, so it is carried
+// into the first kernel of iteration k + 1, which touches every element
+// anyway; the next r.r (for beta and the stopping test) then comes from its
+// expansion
+//   |r - alpha q|^2 = r.r - 2 alpha r.q + alpha^2 q.q
+// with r.r, r.q and q.q summed beside d.q over the stored vectors.  r.r is
+// that of the stored r, never the previous expansion: the expansion carries
+// an absolute error of the FP32 rounding times the r.r it started from, and
+// carried on from one iteration to the next those errors would add up to
+// about 1e-7 of the first r.r, far above a stopping level of 1e-11 of it.
+// One CG iteration:
+//   k_cg_zfwd  x += alpha d, r -= alpha q (pending update), d = r + beta d,
+//              Z1 = S_z d, Z3 = C_z d, sum(d)          (4 reads, 5 writes)
+//   k_cg_xy    W12, W3 in place of Z1, Z3              (2 reads, 2 writes)
+//   k_cg_zinv  q = S_z^-1 W12 + C_z^-1 W3 + c d + rank-one; d.q, r.r, r.q,
+//              q.q; alpha, the next r.r, beta          (4 reads, 1 write)
+// i.e. 18 N^3 values moved per iteration, against 28 for the transform
+// passes of Schur apply run one axis at a time plus 14 for the CG vectors;
+// k_cg_fin applies the last pending update once the run stops.
 //
 // Transforms: the real DCT-II/DST-II (and inverses) of transforms.cuh via
 // Makhoul's reordering, two real lines per complex FFT of length N (or the
@@ -552,21 +567,25 @@ struct SlabArgs {
   double* partial[MAXB];
 };
 
-// d = r + beta d; Z1 = DST-II_z d, Z3 = DCT-II_z d; sumd = sum d.  CTA: 32
-// lines along z at x = x0 .. x0 + 31, y fixed (grid N/32 x N blocks per run).
+// The pending update x += alpha d, r -= alpha q (alpha = 0 in the first
+// iteration: nothing pending); d = r + beta d; Z1 = DST-II_z d, Z3 = DCT-II_z d;
+// sumd = sum d.  CTA: 32 lines along z at x = x0 .. x0 + 31, y fixed (grid
+// N/32 x N blocks per run).
 template <int N, int MAXB>
 __global__ void __launch_bounds__(Cfg<N>::TILE_THREADS, 4)
 k_cg_zfwd(const __grid_constant__ SlabArgs<MAXB> args, const C2<float>* __restrict__ twg,
           const C2<float>* __restrict__ qg) {
   using C = Cfg<N>;
   constexpr int T = C::TILE_THREADS, M = C::M;
-  __shared__ double sh[32];
-  __shared__ double total;
+  constexpr int PER = N * 8 / T, HALF = PER / 2;   // float4 groups of the tile per thread (4)
+  __shared__ float2 sh[32];
   const int b = blockIdx.y;
   CGScalars* s = args.s[b];
   if (s->done) return;
-  const float* __restrict__ r = args.r[b];
+  float* __restrict__ x = args.x[b];
+  float* __restrict__ r = args.r[b];
   float* __restrict__ d = args.d[b];
+  const float* __restrict__ q = args.q[b];
   float* __restrict__ z1 = args.z1[b];
   float* __restrict__ z3 = args.z3[b];
   double* __restrict__ partial = args.partial[b];
@@ -578,24 +597,53 @@ k_cg_zfwd(const __grid_constant__ SlabArgs<MAXB> args, const C2<float>* __restri
   load_tables<N>(tw, qN, nullptr, twg, qg, nullptr, T);
   const int xb = blockIdx.x % (N / C::TILE), y = blockIdx.x / (N / C::TILE);
   const int x0 = xb * C::TILE;
-  const float beta = float(s->beta);
-  CgAcc<float> acc;
-  for (int e4 = threadIdx.x; e4 < N * 8; e4 += T) {
-    const int z = e4 >> 3, c4 = (e4 & 7) * 4;
-    const int64_t g = ((int64_t)z * N + y) * N + x0 + c4;
-    const float4 rv = *reinterpret_cast<const float4*>(r + g);
-    const float4 dv = *reinterpret_cast<const float4*>(d + g);
-    float4 nv;
-    nv.x = rv.x + beta * dv.x;
-    nv.y = rv.y + beta * dv.y;
-    nv.z = rv.z + beta * dv.z;
-    nv.w = rv.w + beta * dv.w;
-    *reinterpret_cast<float4*>(d + g) = nv;
-    *reinterpret_cast<float4*>(D + z * 32 + (c4 ^ tile_sw(z))) = nv;
-    acc.add(nv.x);
-    acc.add(nv.y);
-    acc.add(nv.z);
-    acc.add(nv.w);
+  const double alpha = s->alpha;
+  const bool pending = alpha != 0.0;
+  const float a = float(alpha), beta = float(s->beta);
+  CgAcc<float> acc[1];
+#pragma unroll
+  for (int h = 0; h < PER; h += HALF) {
+    float4 rv[HALF], dv[HALF], xv[HALF], qv[HALF];
+#pragma unroll
+    for (int j = 0; j < HALF; ++j) {
+      const int e4 = threadIdx.x + (h + j) * T;
+      const int64_t g = ((int64_t)(e4 >> 3) * N + y) * N + x0 + (e4 & 7) * 4;
+      rv[j] = *reinterpret_cast<const float4*>(r + g);
+      dv[j] = *reinterpret_cast<const float4*>(d + g);
+      if (pending) {
+        xv[j] = *reinterpret_cast<const float4*>(x + g);
+        qv[j] = *reinterpret_cast<const float4*>(q + g);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < HALF; ++j) {
+      const int e4 = threadIdx.x + (h + j) * T;
+      const int z = e4 >> 3, c4 = (e4 & 7) * 4;
+      const int64_t g = ((int64_t)z * N + y) * N + x0 + c4;
+      if (pending) {
+        xv[j].x += a * dv[j].x;
+        xv[j].y += a * dv[j].y;
+        xv[j].z += a * dv[j].z;
+        xv[j].w += a * dv[j].w;
+        rv[j].x -= a * qv[j].x;
+        rv[j].y -= a * qv[j].y;
+        rv[j].z -= a * qv[j].z;
+        rv[j].w -= a * qv[j].w;
+        *reinterpret_cast<float4*>(x + g) = xv[j];
+        *reinterpret_cast<float4*>(r + g) = rv[j];
+      }
+      float4 nv;
+      nv.x = rv[j].x + beta * dv[j].x;
+      nv.y = rv[j].y + beta * dv[j].y;
+      nv.z = rv[j].z + beta * dv[j].z;
+      nv.w = rv[j].w + beta * dv[j].w;
+      *reinterpret_cast<float4*>(d + g) = nv;
+      *reinterpret_cast<float4*>(D + z * 32 + (c4 ^ tile_sw(z))) = nv;
+      acc[0].add(nv.x);
+      acc[0].add(nv.y);
+      acc[0].add(nv.z);
+      acc[0].add(nv.w);
+    }
   }
   __syncthreads();
   {
@@ -639,7 +687,9 @@ k_cg_zfwd(const __grid_constant__ SlabArgs<MAXB> args, const C2<float>* __restri
     *reinterpret_cast<float4*>(z1 + g) = *reinterpret_cast<const float4*>(D + a);
     *reinterpret_cast<float4*>(z3 + g) = *reinterpret_cast<const float4*>(E + a);
   }
-  if (last_block_sum(acc.value(), partial, &s->ticket[2], sh, &total) && threadIdx.x == 0) s->sumd = total;
+  double sum[1];
+  if (last_block_merge<1>(acc, reinterpret_cast<float2*>(partial), &s->ticket[2], sh, sum) && threadIdx.x == 0)
+    s->sumd = sum[0];
 }
 
 // Makhoul input of a forward line pair with the kinds known only at run
@@ -808,16 +858,16 @@ k_cg_xy(const __grid_constant__ SlabArgs<MAXB> args, const C2<float>* __restrict
   }
 }
 
-// q = DST-III_z W12 + DCT-III_z W3 + cdiag d; dq = d . q; alpha.  Tiles as
-// k_cg_zfwd.
+// q = DST-III_z W12 + DCT-III_z W3 + cdiag d + rank1 sumd; d.q, r.r, r.q,
+// q.q; alpha, the next r.r and beta, done once that r.r <= stop.  Tiles as k_cg_zfwd.
 template <int N, int MAXB>
 __global__ void __launch_bounds__(Cfg<N>::TILE_THREADS, 4)
 k_cg_zinv(const __grid_constant__ SlabArgs<MAXB> args, const C2<float>* __restrict__ twg,
           const C2<float>* __restrict__ qg) {
   using C = Cfg<N>;
   constexpr int T = C::TILE_THREADS, M = C::M;
-  __shared__ double sh[32];
-  __shared__ double total;
+  constexpr int PER = N * 8 / T;   // float4 groups of the tile per thread (4)
+  __shared__ float2 sh[4 * 32];
   const int b = blockIdx.y;
   CGScalars* s = args.s[b];
   if (s->done) return;
@@ -834,12 +884,23 @@ k_cg_zinv(const __grid_constant__ SlabArgs<MAXB> args, const C2<float>* __restri
   load_tables<N>(tw, qN, nullptr, twg, qg, nullptr, T);
   const int xb = blockIdx.x % (N / C::TILE), y = blockIdx.x / (N / C::TILE);
   const int x0 = xb * C::TILE;
-  for (int e4 = threadIdx.x; e4 < N * 8; e4 += T) {
-    const int z = e4 >> 3, c4 = (e4 & 7) * 4;
-    const int64_t g = ((int64_t)z * N + y) * N + x0 + c4;
-    const int a = z * 32 + (c4 ^ tile_sw(z));
-    *reinterpret_cast<float4*>(D + a) = *reinterpret_cast<const float4*>(w12 + g);
-    *reinterpret_cast<float4*>(E + a) = *reinterpret_cast<const float4*>(w3 + g);
+  {
+    float4 av[PER], bv[PER];
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const int e4 = threadIdx.x + j * T;
+      const int64_t g = ((int64_t)(e4 >> 3) * N + y) * N + x0 + (e4 & 7) * 4;
+      av[j] = *reinterpret_cast<const float4*>(w12 + g);
+      bv[j] = *reinterpret_cast<const float4*>(w3 + g);
+    }
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const int e4 = threadIdx.x + j * T;
+      const int z = e4 >> 3, c4 = (e4 & 7) * 4;
+      const int a = z * 32 + (c4 ^ tile_sw(z));
+      *reinterpret_cast<float4*>(D + a) = av[j];
+      *reinterpret_cast<float4*>(E + a) = bv[j];
+    }
   }
   __syncthreads();
   {
@@ -877,92 +938,81 @@ k_cg_zinv(const __grid_constant__ SlabArgs<MAXB> args, const C2<float>* __restri
     for (int r = 0; r < 16; ++r) D[L.e_m ^ tl(M * r)] = oa[r];
   }
   __syncthreads();
-  const float cd = float(s->cdiag);
-  CgAcc<float> acc;
-  for (int e4 = threadIdx.x; e4 < N * 8; e4 += T) {
+  // q = the three terms + c d + rank-one; d.q, r.r, r.q and q.q for alpha
+  // and the expansion of the next r.r
+  const float cd = float(s->cdiag), c1 = float(s->sumd * s->rank1);
+  const float* __restrict__ r = args.r[b];
+  float4 dv[PER], rv[PER];
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    const int e4 = threadIdx.x + j * T;
+    const int64_t g = ((int64_t)(e4 >> 3) * N + y) * N + x0 + (e4 & 7) * 4;
+    dv[j] = *reinterpret_cast<const float4*>(d + g);
+    rv[j] = *reinterpret_cast<const float4*>(r + g);
+  }
+  // d.q and r.r (alpha, the stopping test) exact to about 2^-48: every
+  // product split by FMA, all sums compensated; r.q and q.q (only in the
+  // expansion) sum the four products of a float4 by FMA first (within 3
+  // roundings of their magnitudes) and those sums compensated
+  CgAcc<float> acc[4];
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    const int e4 = threadIdx.x + j * T;
     const int z = e4 >> 3, c4 = (e4 & 7) * 4;
     const int64_t g = ((int64_t)z * N + y) * N + x0 + c4;
     const float4 t = *reinterpret_cast<const float4*>(D + z * 32 + (c4 ^ tile_sw(z)));
-    const float4 dv = *reinterpret_cast<const float4*>(d + g);
+    const float4 dw = dv[j], rw = rv[j];
     float4 qv;
-    qv.x = t.x + cd * dv.x;
-    qv.y = t.y + cd * dv.y;
-    qv.z = t.z + cd * dv.z;
-    qv.w = t.w + cd * dv.w;
+    qv.x = t.x + cd * dw.x + c1;
+    qv.y = t.y + cd * dw.y + c1;
+    qv.z = t.z + cd * dw.z + c1;
+    qv.w = t.w + cd * dw.w + c1;
     *reinterpret_cast<float4*>(q + g) = qv;
-    acc.add_prod(dv.x, qv.x);
-    acc.add_prod(dv.y, qv.y);
-    acc.add_prod(dv.z, qv.z);
-    acc.add_prod(dv.w, qv.w);
+    acc[0].add_prod(dw.x, qv.x);
+    acc[0].add_prod(dw.y, qv.y);
+    acc[0].add_prod(dw.z, qv.z);
+    acc[0].add_prod(dw.w, qv.w);
+    acc[1].add_prod(rw.x, rw.x);
+    acc[1].add_prod(rw.y, rw.y);
+    acc[1].add_prod(rw.z, rw.z);
+    acc[1].add_prod(rw.w, rw.w);
+    acc[2].add(fmaf(rw.w, qv.w, fmaf(rw.z, qv.z, fmaf(rw.y, qv.y, rw.x * qv.x))));
+    acc[3].add(fmaf(qv.w, qv.w, fmaf(qv.z, qv.z, fmaf(qv.y, qv.y, qv.x * qv.x))));
   }
-  if (last_block_sum(acc.value(), partial, &s->ticket[0], sh, &total) && threadIdx.x == 0) {
-    const double den = total + s->sumd * s->sumd * s->rank1;
-    s->dq = den;
-    s->alpha = (den != 0.0) ? s->rr / den : 0.0;
+  double sum[4];
+  if (last_block_merge<4>(acc, reinterpret_cast<float2*>(partial), &s->ticket[0], sh, sum) &&
+      threadIdx.x == 0) {
+    const double dq = sum[0], rr = sum[1];
+    const double al = (dq != 0.0) ? rr / dq : 0.0;
+    const double rr1 = rr - 2.0 * al * sum[2] + al * al * sum[3];   // |r - alpha q|^2
+    s->dq = dq;
+    s->alpha = al;
+    s->beta = (rr != 0.0) ? rr1 / rr : 0.0;
+    s->rr = rr1;
+    s->iters += 1;
+    if (!(rr1 > s->stop)) s->done = 1;
   }
 }
 
-// x += alpha d; r -= alpha (q + sumd rank1); rr = r . r; beta; done once
-// rr <= stop.  Float4 vectors (n4 = N^3 / 4), UPD_UNROLL float4 of each
-// vector per thread and pass with every load issued first; few blocks, so
-// that the block reductions and the last block's sum stay short.
-constexpr int UPD_THREADS = 256;
-constexpr int UPD_UNROLL = 4;
+// The update still pending when a run stops: x += alpha d (float4 vectors,
+// n4 = N^3 / 4; blockIdx.y = run).
+constexpr int FIN_THREADS = 256;
 template <int MAXB>
-__global__ void __launch_bounds__(UPD_THREADS, 2)
-k_cg_upd(const __grid_constant__ SlabArgs<MAXB> args, int64_t n4) {
-  __shared__ double sh[32];
-  __shared__ double total;
+__global__ void __launch_bounds__(FIN_THREADS)
+k_cg_fin(const __grid_constant__ SlabArgs<MAXB> args, int64_t n4) {
   const int b = blockIdx.y;
-  CGScalars* s = args.s[b];
-  if (s->done) return;
+  const float a = float(args.s[b]->alpha);
+  if (a == 0.f) return;
   float4* __restrict__ x4 = reinterpret_cast<float4*>(args.x[b]);
-  float4* __restrict__ r4 = reinterpret_cast<float4*>(args.r[b]);
   const float4* __restrict__ d4 = reinterpret_cast<const float4*>(args.d[b]);
-  const float4* __restrict__ q4 = reinterpret_cast<const float4*>(args.q[b]);
-  double* __restrict__ partial = args.partial[b];
-  const float a = float(s->alpha);
-  const float c1 = float(s->sumd * s->rank1);
-  CgAcc<float> acc;
-  const int64_t stride = (int64_t)gridDim.x * UPD_THREADS;
-  for (int64_t e0 = (int64_t)blockIdx.x * UPD_THREADS + threadIdx.x; e0 < n4; e0 += stride * UPD_UNROLL) {
-    float4 dv[UPD_UNROLL], qv[UPD_UNROLL], rv[UPD_UNROLL], xv[UPD_UNROLL];
-#pragma unroll
-    for (int u = 0; u < UPD_UNROLL; ++u) {
-      const int64_t e = e0 + u * stride;
-      if (e < n4) {
-        dv[u] = d4[e];
-        qv[u] = q4[e];
-        rv[u] = r4[e];
-        xv[u] = x4[e];
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < UPD_UNROLL; ++u) {
-      const int64_t e = e0 + u * stride;
-      if (e < n4) {
-        rv[u].x = rv[u].x - a * (qv[u].x + c1);
-        rv[u].y = rv[u].y - a * (qv[u].y + c1);
-        rv[u].z = rv[u].z - a * (qv[u].z + c1);
-        rv[u].w = rv[u].w - a * (qv[u].w + c1);
-        xv[u].x = xv[u].x + a * dv[u].x;
-        xv[u].y = xv[u].y + a * dv[u].y;
-        xv[u].z = xv[u].z + a * dv[u].z;
-        xv[u].w = xv[u].w + a * dv[u].w;
-        r4[e] = rv[u];
-        x4[e] = xv[u];
-        acc.add_prod(rv[u].x, rv[u].x);
-        acc.add_prod(rv[u].y, rv[u].y);
-        acc.add_prod(rv[u].z, rv[u].z);
-        acc.add_prod(rv[u].w, rv[u].w);
-      }
-    }
-  }
-  if (last_block_sum(acc.value(), partial, &s->ticket[1], sh, &total) && threadIdx.x == 0) {
-    s->beta = (s->rr != 0.0) ? total / s->rr : 0.0;
-    s->rr = total;
-    s->iters += 1;
-    if (!(s->rr > s->stop)) s->done = 1;
+  for (int64_t e = (int64_t)blockIdx.x * FIN_THREADS + threadIdx.x; e < n4; e += (int64_t)gridDim.x * FIN_THREADS) {
+    float4 xv = x4[e];
+    const float4 dv = d4[e];
+    xv.x += a * dv.x;
+    xv.y += a * dv.y;
+    xv.z += a * dv.z;
+    xv.w += a * dv.w;
+    x4[e] = xv;
   }
 }
 

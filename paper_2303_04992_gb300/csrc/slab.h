@@ -1,4 +1,4 @@
-// Host entry of the four-kernel FP32 Schur CG iteration of slab.cuh
+// Host entry of the three-kernel FP32 Schur CG iteration of slab.cuh
 // (Sec. 4.2, Eq. linearS1), compiled in its own translation unit.
 #pragma once
 
@@ -15,7 +15,8 @@ struct C2;
 // float temporaries), the FP32 transform tables (full-circle twiddles
 // exp(-2 pi i t / 2N), t < 2N; post-twiddles exp(-i pi k / 2N), k < N; the
 // eigenvalue table 4 sin^2 of the DCT (N) and DST (N) modes), 1/mu, the
-// device scalars and the reduction partials (>= 1216 doubles).
+// device scalars and the reduction partials (at least 4 (N / 32) N slots of
+// eight bytes: k_cg_zinv stores four FP32 pairs per block).
 struct SlabCg {
   int N;
   float *x, *r, *d, *q, *z1, *z3;
@@ -36,23 +37,31 @@ constexpr int kSlabBatchMax = 64;
 // shared tables too (only runs[0]'s tables, N and inv_mu are read).
 int slab_cg_iteration_batch(const SlabCg* runs, int nrun, cudaStream_t st);
 
-// Grids the four-kernel iteration covers (N = 32, 64, 128: a whole plane of
+// Grids the slab iteration covers (N = 32, 64, 128: a whole plane of
 // floats and its team exchange buffers fit in one CTA's shared memory).
 bool slab_supported(int N);
 // Raises the kernels' dynamic shared-memory limits on the current device.
 cudaError_t slab_prepare(int N);
 // Enqueues one CG iteration (a no-op on the device once s->done is set);
-// returns the number of kernels launched.
+// returns the number of kernels launched.  Each iteration leaves its own
+// vector update (x += alpha d, r -= alpha q) pending for the next one, so
+// a run that has stopped needs slab_cg_finish (or the batch form) before x
+// is read.
 int slab_cg_iteration(const SlabCg& a, cudaStream_t st);
-// One kernel of the iteration (0 k_cg_zfwd, 1 k_cg_xy, 2 k_cg_zinv,
-// 3 k_cg_upd), for per-kernel timing; returns the number launched (0 or 1).
+// x += alpha d, the update still pending when the run stopped (whether by
+// done or by an iteration cap); returns the number of kernels launched.
+int slab_cg_finish(const SlabCg& a, cudaStream_t st);
+int slab_cg_finish_batch(const SlabCg* runs, int nrun, cudaStream_t st);
+// One kernel of the iteration (0 k_cg_zfwd, 1 k_cg_xy, 2 k_cg_zinv; 3 the
+// finishing update), for per-kernel timing; returns the number launched.
 int slab_launch(int which, const SlabCg& a, cudaStream_t st);
-// Algorithmic bytes each kernel moves (FP32 values read and written):
-// 5, 4, 4 and 6 N^3 floats.
-constexpr int kSlabValues[4] = {5, 4, 4, 6};
-// The first three kernels of an iteration only: with s->beta = 0 and
-// s->done = 0 they leave d = r and q = S d (the three spectral terms plus
-// s->cdiag d, without the rank-one term) and set s->sumd, s->dq, s->alpha.
+// Algorithmic bytes each kernel moves (FP32 values read and written, with
+// an update pending): 9, 4, 5 and 3 N^3 floats.
+constexpr int kSlabValues[4] = {9, 4, 5, 3};
+// The three kernels of one iteration from a fresh run: with s->alpha = 0,
+// s->beta = 0 and s->done = 0 they leave d = r and q = S d (the three
+// spectral terms plus s->cdiag d plus s->rank1 sum(d)) and set s->sumd,
+// s->dq, s->alpha.
 int slab_schur_apply(const SlabCg& a, cudaStream_t st);
 
 }  // namespace kfbim

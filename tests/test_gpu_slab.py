@@ -1,6 +1,7 @@
-"""The four-kernel FP32 Schur CG iteration (z-pencil transforms, one CTA per
-xy plane, inverse z-pencil transforms, vector update) against the FP64
-oracle and against the one-axis staged passes it replaces.
+"""The three-kernel FP32 Schur CG iteration (z-pencil transforms after the
+previous iteration's vector update, one CTA per xy plane, inverse z-pencil
+transforms with the CG dot products) against the FP64 oracle and against the
+one-axis staged passes it replaces.
 
 * The FP32 Schur operator of the slab kernels (Sec. 4.2 item ii, the operator
   of Eq. linearS1 without its rank-one term) against the oracle's stencil form

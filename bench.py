@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--refine-tol", type=float, default=None, help="MIXED refinement tolerance")
     ap.add_argument("--inner-tol", type=float, default=None, help="MIXED inner FP32 CG tolerance")
+    ap.add_argument("--relax", type=float, default=None,
+                    help="MIXED inexact-GMRES relaxation factor (library default 0.1; 0 = off)")
     ap.add_argument("--transforms", default="auto", choices=["auto", "fft", "tensor", "staged"],
                     help="kernels of the FP32 axis passes (auto: the setup-time autotuner's choice)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (gradient) leg")
@@ -494,6 +496,8 @@ def main_kfbim(args):
         mixed_opts["refine_tol"] = args.refine_tol
     if args.inner_tol is not None:
         mixed_opts["inner_tol"] = args.inner_tol
+    if args.relax is not None:
+        mixed_opts["relax"] = args.relax
     mixed_opts["transforms"] = {"auto": 0, "fft": 1, "tensor": 2, "staged": 3}[args.transforms]
     solver = Solver(geom, grid, precision=MIXED, **mixed_opts, **pde)
     g_h, fpts_h, fgrid_h = inputs(solver, geom, grid, navier)
@@ -635,6 +639,7 @@ def main_kfbim(args):
                 "config": {"workload": args.workload, "description": desc,
                            "precision": "mixed", "l2_flush": "512 MiB write before each step",
                            "refine_tol": solver.options.refine_tol, "inner_tol": solver.options.inner_tol,
+                           "relax": solver.options.relax,
                            "n_points": solver.n_points, "n_unknowns": solver.n_primary,
                            "gmres_iters": st["gmres_iters"], "interface_solves": st["interface_solves"],
                            "cg_iters": st["cg_iters"], "refine_sweeps": st["refine_sweeps"],

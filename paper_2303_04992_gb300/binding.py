@@ -67,7 +67,7 @@ class Options(ctypes.Structure):
     _fields_ = [("mu", c_double), ("precision", c_int), ("gmres_tol", c_double),
                 ("gmres_max", c_int), ("cg_tol", c_double), ("cg_max", c_int),
                 ("refine_tol", c_double), ("refine_max", c_int), ("inner_tol", c_double),
-                ("pde", c_int), ("lam", c_double), ("transforms", c_int)]
+                ("pde", c_int), ("lam", c_double), ("transforms", c_int), ("relax", c_double)]
 
 
 class Stats(ctypes.Structure):

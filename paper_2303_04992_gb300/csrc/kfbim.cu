@@ -71,6 +71,10 @@ struct kfbim_ctx {
   int xf_plain = 0, xf_fused = 0;
   // MIXED Schur CG as the three-kernel z-pencil / xy-slab iteration (slab.cuh)
   bool slab = false;
+  // MIXED refinement tolerance of the next grid solve: opt.refine_tol, or
+  // looser inside GMRES once its residual is small (opt.relax > 0)
+  double refine_tol_now = 0.0;
+  double relax = 0.0;
   // precision requested at setup (FP32 and MIXED_TF32 run as MIXED internally:
   // FP32 without the FP64 refinement sweeps, MIXED_TF32 on tensor-core passes)
   int precision_requested = KFBIM_FP64;
@@ -130,6 +134,7 @@ struct kfbim_ctx {
   void* bpinned = nullptr;     // host staging of bcgs / bscal / bgh
   int bcap = 0, bm = 0;
   std::vector<int> b_cg, b_sweeps, b_isolves;   // per-slot counters of the current call
+  std::vector<double> b_refine_tol;              // per-slot refine_tol_now of a batched call
   // adjoint: transposed trace (by node), corrections (by jump slot) and fit
   // (by primary column) tables, built at setup; Jbar, Dbar work arrays
   bool adj_ready = false;
@@ -763,7 +768,7 @@ int grid_solve_mixed(kfbim_ctx* c, cudaStream_t s) {
       dot(c, resf, resf, 4 * N3, sc, 1.0, s);
       const double r2 = read_scalar(c, sc, s);
       if (!std::isfinite(r2)) return KFBIM_E_NONFINITE;
-      if (r2 <= c->opt.refine_tol * c->opt.refine_tol * ref2 || ref2 == 0.0) break;
+      if (r2 <= c->refine_tol_now * c->refine_tol_now * ref2 || ref2 == 0.0) break;
       if (sweep >= c->opt.refine_max) { status = KFBIM_E_NOCONV; break; }
     }
     ++c->refine_sweeps;
@@ -836,6 +841,20 @@ int apply_impl(kfbim_ctx* c, const double* phi, double* out, cudaStream_t s) {
 // with `adjoint`, GMRES on the transposed matvec.
 int adjoint_apply(kfbim_ctx* c, const double* lam, double* out, cudaStream_t s);
 
+// Inexact GMRES (relaxation of the matvec accuracy as the residual falls):
+// the grid solve of the matvec that extends the Krylov basis from a relative
+// residual res need only be accurate to relax * gmres_tol / res, because its
+// error enters the solution through a coefficient of size about res, so the
+// product stays about relax * gmres_tol however loose the matvec gets.  The
+// MIXED refinement stops at that relative residual (never above kRelaxCap,
+// never below refine_tol); relax = 0 keeps refine_tol throughout.
+constexpr double kRelaxCap = 1e-4;
+
+double relaxed_refine_tol(const kfbim_ctx* c, double res) {
+  if (!(c->relax > 0.0) || !(res > 0.0)) return c->opt.refine_tol;
+  return std::max(c->opt.refine_tol, std::min(kRelaxCap, c->relax * c->opt.gmres_tol / res));
+}
+
 int gmres(kfbim_ctx* c, const double* rhs, double* x, cudaStream_t s, int* iters, double* res_out,
           bool adjoint = false) {
   const int64_t n = c->n_prim;
@@ -859,7 +878,12 @@ int gmres(kfbim_ctx* c, const double* rhs, double* x, cudaStream_t s, int* iters
   int status = KFBIM_E_NOCONV;
   double res = 1.0;
   const int nb = 64;
+  struct ResetTol {
+    kfbim_ctx* c;
+    ~ResetTol() { c->refine_tol_now = c->opt.refine_tol; }
+  } reset_tol{c};
   for (k = 1; k <= m; ++k) {
+    c->refine_tol_now = relaxed_refine_tol(c, res);
     int st = adjoint ? adjoint_apply(c, c->V + (int64_t)(k - 1) * ld, c->gw, s)
                      : apply_impl(c, c->V + (int64_t)(k - 1) * ld, c->gw, s);
     if (st != KFBIM_OK && st != KFBIM_E_NOCONV) return st;
@@ -1697,7 +1721,8 @@ void grid_solve_batch(kfbim_ctx* c, const std::vector<int>& act, cudaStream_t s)
       std::vector<int> keep;
       for (size_t q = 0; q < live.size(); ++q) {
         const double ref = ref2[std::find(act.begin(), act.end(), live[q]) - act.begin()];
-        if (!(r2[q] <= c->opt.refine_tol * c->opt.refine_tol * ref)) keep.push_back(live[q]);
+        const double tol = c->b_refine_tol[live[q]];
+        if (!(r2[q] <= tol * tol * ref)) keep.push_back(live[q]);
       }
       live.swap(keep);
       if (live.empty() || sweep >= c->opt.refine_max) break;
@@ -1822,9 +1847,16 @@ void gmres_batch(kfbim_ctx* c, const std::vector<int>& act, const std::vector<do
   check_launch();
   std::vector<int> done_at(B, 0);
   const double* hp = static_cast<const double*>(c->bpinned);
+  struct ResetTols {
+    kfbim_ctx* c;
+    ~ResetTols() { std::fill(c->b_refine_tol.begin(), c->b_refine_tol.end(), c->opt.refine_tol); }
+  } reset_tols{c};
   for (int k = 1; k <= m && !live.empty(); ++k) {
     std::vector<const double*> phi, nul(live.size(), nullptr);
-    for (int b : live) phi.push_back(c->bs[b].V + (int64_t)(k - 1) * ld);
+    for (int b : live) {
+      phi.push_back(c->bs[b].V + (int64_t)(k - 1) * ld);
+      c->b_refine_tol[b] = relaxed_refine_tol(c, resid[b]);
+    }
     interface_batch(c, live, phi, nul, nul, s);
     for (int b : live) {
       const kfbim_ctx::Slot& w = c->bs[b];
@@ -1925,6 +1957,7 @@ void kfbim_default_options(kfbim_options* o) {
   o->pde = KFBIM_STOKES;
   o->lambda = 0.0;
   o->transforms = KFBIM_XF_AUTO;
+  o->relax = 0.1;
 }
 
 static int setup_common(const kfbim_geometry* geom, const kfbim_grid* grid, const kfbim_options* opt,
@@ -1939,6 +1972,7 @@ static int setup_common(const kfbim_geometry* geom, const kfbim_grid* grid, cons
       opt->precision < KFBIM_FP64 || opt->precision > KFBIM_MIXED_TF32)
     return KFBIM_E_INVALID;
   if (opt->precision == KFBIM_MIXED_TF32 && N != TC_N) return KFBIM_E_INVALID;
+  if (!(opt->relax >= 0.0)) return KFBIM_E_INVALID;
   if (alloc && (!alloc->alloc || !alloc->free)) return KFBIM_E_INVALID;
   if (geom->kind < KFBIM_SPHERE || geom->kind > KFBIM_CALLBACK) return KFBIM_E_INVALID;
   if (geom->kind == KFBIM_CALLBACK && (!geom->F || !geom->derivs)) return KFBIM_E_INVALID;
@@ -1963,6 +1997,8 @@ static int setup_common(const kfbim_geometry* geom, const kfbim_grid* grid, cons
   // KFBIM_CUDA_GRAPHS=0 launches the CG kernels one by one (kernel profilers
   // cannot look inside graphs with conditional nodes)
   if (const char* g = std::getenv("KFBIM_CUDA_GRAPHS")) c->use_graphs = std::strcmp(g, "0") != 0;
+  c->refine_tol_now = c->opt.refine_tol;
+  c->relax = c->opt.relax;
   if (alloc) {
     c->allocator = *alloc;
     c->custom_alloc = true;
@@ -2343,6 +2379,7 @@ int kfbim_solve_batch(kfbim_ctx* c, int B, const double* g, const double* fpts, 
     c->b_cg.assign(c->bcap, 0);
     c->b_sweeps.assign(c->bcap, 0);
     c->b_isolves.assign(c->bcap, 0);
+    c->b_refine_tol.assign(c->bcap, c->opt.refine_tol);
     const int64_t launches0 = g_launches;
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<int> all(B);

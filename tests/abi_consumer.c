@@ -154,6 +154,7 @@ int main(void) {
   if (ctx != NULL) return fail("kfbim_setup_host left *ctx set", st_bad);
 
   printf("n_points %lld\nn_primary %lld\nN %d\n", (long long)n_points, (long long)n_primary, N);
+  printf("options_size %d\nrelax %.17g\n", (int)sizeof(kfbim_options), opt.relax);
   printf("fit_nnz %lld\ncorr_rows %lld\ncorr_nnz %lld\n", (long long)fit_nnz, (long long)corr_rows,
          (long long)corr_nnz);
   printf("primary_flags %lld\nmax_distance %.3e\nomega_cells %d\n", (long long)n_flagged, dist, n_cells);

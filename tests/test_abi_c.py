@@ -4,6 +4,7 @@ library and runs its host-only entry points (no GPU).  Its output must match
 the Python binding's view of the same context and the geometry: every control
 point on the sphere, one primary flag per density unknown, and the same sphere
 given as C callbacks (CALLBACK kind) reproduces the built-in setup."""
+import ctypes
 import os
 import shutil
 import subprocess
@@ -13,7 +14,7 @@ import pytest
 
 import kfbim_inputs as ki
 from paper_2303_04992_gb300 import build
-from paper_2303_04992_gb300.binding import Solver
+from paper_2303_04992_gb300.binding import Options, Solver
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 INC = os.path.join(os.path.dirname(HERE), "include")
@@ -41,6 +42,9 @@ def test_c_consumer_matches_binding(tmp_path, compiler, std):
     s = Solver(ki.sphere(), ki.grid(32), device=False)
     fit, rows, nnz = s.table_sizes()
     assert got["N"] == 32
+    # the binding's options struct is the header's (size, and the last field's default)
+    assert got["options_size"] == ctypes.sizeof(Options)
+    assert got["relax"] == s.options.relax == 0.1
     assert got["n_points"] == s.n_points and got["n_primary"] == s.n_primary
     assert (got["fit_nnz"], got["corr_rows"], got["corr_nnz"]) == (fit, rows, nnz)
     assert got["primary_flags"] == s.n_primary

@@ -348,8 +348,10 @@ int kfbim_solve_adjoint(kfbim_ctx* ctx, const double* ubar_dev, double* gbar_dev
  * kfbim_solve on instance b up to rounding order (the same GMRES, refinement
  * and CG iteration per instance).
  * MIXED contexts run the instances in lockstep: every FFT stage is one launch
- * for all instances still iterating, and GMRES reads its host scalars once
- * per iteration for the whole batch.  FP64 contexts solve the instances one
+ * for all instances still iterating, each Schur CG of the batch (N = 32, 64,
+ * 128) is one launch of a CUDA graph whose conditional while loop runs the
+ * three slab kernels of every instance until all are done, and GMRES reads
+ * its host scalars once per iteration for the whole batch.  FP64 contexts solve the instances one
  * after another.  The first call with a larger B than before allocates the
  * per-instance workspace (about 20 N^3 doubles-worth plus the Krylov basis of
  * gmres_max + 1 vectors per instance); it is kept until kfbim_destroy.

@@ -107,6 +107,12 @@ struct kfbim_ctx {
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t cg_exec[2] = {nullptr, nullptr};
   int64_t cg_graph_kernels[2] = {0, 0};
+  // the batched slab CG of all bcap slots as one device-side while loop
+  // (captured once per batch allocation; null where conditional nodes are
+  // not available) and its kernels per trip
+  cudaGraphExec_t bcg_exec = nullptr;
+  int64_t bcg_kernels = 0;
+  bool bcg_tried = false;
   // whether cg_exec[slot] is the device-side while loop (conditional node)
   // or kCgGraphIters iterations in a row
   bool cg_loop[2] = {false, false};
@@ -1488,6 +1494,9 @@ namespace {
 
 void batch_alloc(kfbim_ctx* c, int B) {
   if (B <= c->bcap) return;
+  if (c->bcg_exec) CK(cudaGraphExecDestroy(c->bcg_exec));   // it holds the old slot scalars
+  c->bcg_exec = nullptr;
+  c->bcg_tried = false;
   const int64_t N3 = c->N3, np = std::max<int64_t>(1, c->n_prim);
   c->bm = c->opt.gmres_max;
   c->bgh = dalloc<double>(c, (size_t)B * (c->bm + 1));
@@ -1598,13 +1607,94 @@ std::vector<SlabCg> slab_batch_runs(kfbim_ctx* c, const std::vector<int>& slots)
   return runs;
 }
 
+// Slots not in the run are marked done, so that the batched kernels of all
+// slots skip them.
+__global__ void k_cg_mark_idle(CGScalars* s, int nslot, unsigned long long active) {
+  const int b = threadIdx.x;
+  if (b < nslot && !((active >> b) & 1ull)) s[b].done = 1;
+}
+
+// Device side of the batched CG loop: counts the trip (in every slot) and
+// keeps the loop going while any slot is running and the cap is not reached.
+__global__ void k_cg_cond_batch(cudaGraphConditionalHandle h, CGScalars* s, int nslot, int maxit) {
+  bool any = false;
+  int t = 0;
+  for (int b = 0; b < nslot; ++b) {
+    t = ++s[b].trips;
+    any = any || !s[b].done;
+  }
+  cudaGraphSetConditional(h, (any && t < maxit) ? 1u : 0u);
+}
+
+// The batched slab CG of all bcap slots as a conditional while loop: one
+// graph launch runs every slot's CG to its end (slots already done return
+// at once).  Captured on first use after the slot scalars are reset with
+// every slot marked done, after one untimed iteration (which then does
+// nothing but load the kernels).  Null where conditional nodes are refused.
+cudaGraphExec_t cg_batch_graph(kfbim_ctx* c, const std::vector<SlabCg>& all) {
+  if (c->bcg_tried) return c->bcg_exec;
+  c->bcg_tried = true;
+  CK(cudaStreamSynchronize(c->cap_stream));
+  const int64_t before = g_launches;
+  slab_cg_iteration_batch(all.data(), (int)all.size(), c->cap_stream);
+  CK(cudaStreamSynchronize(c->cap_stream));
+  const int64_t per_iter = g_launches - before;
+  g_launches = before;
+  cudaGraph_t graph = nullptr;
+  CK(cudaGraphCreate(&graph, 0));
+  cudaGraphConditionalHandle h{};
+  bool ok = cudaGraphConditionalHandleCreate(&h, graph, 1u, cudaGraphCondAssignDefault) == cudaSuccess;
+  cudaGraphNodeParams np{};
+  if (ok) {
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    ok = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np) == cudaSuccess;
+  }
+  if (!ok) {
+    (void)cudaGetLastError();   // a refused conditional node is not an error of this call
+    CK(cudaGraphDestroy(graph));
+    return nullptr;
+  }
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  CK(cudaStreamBeginCaptureToGraph(c->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  slab_cg_iteration_batch(all.data(), (int)all.size(), c->cap_stream);
+  k_cg_cond_batch<<<1, 1, 0, c->cap_stream>>>(h, c->bcgs, (int)all.size(), std::max(1, c->opt.cg_max));
+  CK(cudaStreamEndCapture(c->cap_stream, &body));
+  g_launches = before;
+  CK(cudaGraphInstantiate(&c->bcg_exec, graph, 0));
+  CK(cudaGraphDestroy(graph));
+  c->bcg_kernels = per_iter + 1;
+  return c->bcg_exec;
+}
+
 // Lockstep FP32 CG of the instances in `act` on (S + ...) x = b (b in fu[0:N3]).
 void cg_batch(kfbim_ctx* c, const std::vector<int>& act, double tol, cudaStream_t s) {
   const int64_t n = c->N3;
   const double rank1 = c->navier ? 0.0 : 1.0 / (c->mu * (double)n);
+  std::vector<int> slots(c->bcap);
+  for (int b = 0; b < c->bcap; ++b) slots[b] = b;
+  const std::vector<SlabCg> all = c->slab ? slab_batch_runs(c, slots) : std::vector<SlabCg>();
+  const bool graphs = c->slab && c->use_graphs && !c->prof;
+  if (graphs && !c->bcg_tried) {
+    // the capture stream's warm-up iteration must see every slot done
+    CK(cudaMemsetAsync(c->bcgs, 0, sizeof(CGScalars) * c->bcap, s));
+    k_cg_mark_idle<<<1, 64, 0, s>>>(c->bcgs, c->bcap, 0ull);
+    ++g_launches;
+    check_launch();
+    CK(cudaStreamSynchronize(s));
+    cg_batch_graph(c, all);
+  }
+  cudaGraphExec_t exec = graphs ? c->bcg_exec : nullptr;
+  unsigned long long mask = 0ull;
+  for (int b : act) mask |= 1ull << b;
+  CK(cudaMemsetAsync(c->bcgs, 0, sizeof(CGScalars) * c->bcap, s));
+  k_cg_mark_idle<<<1, 64, 0, s>>>(c->bcgs, c->bcap, mask);
+  ++g_launches;
   for (int b : act) {
     const kfbim_ctx::Slot& w = c->bs[b];
-    CK(cudaMemsetAsync(&c->bcgs[b], 0, sizeof(CGScalars), s));
     CK(cudaMemsetAsync(w.x, 0, n * sizeof(float), s));
     CK(cudaMemcpyAsync(w.r, w.fu, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(w.d, w.fu, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
@@ -1615,11 +1705,17 @@ void cg_batch(kfbim_ctx* c, const std::vector<int>& act, double tol, cudaStream_
   check_launch();
   std::vector<CGScalars> h(c->bcap);
   int launched = 0;
+  if (exec) {
+    // one graph launch: every slot's CG runs to done or to the cap
+    CK(cudaGraphLaunch(exec, s));
+    launched = c->opt.cg_max;
+  }
   while (true) {
     CK(cudaMemcpyAsync(c->bpinned, c->bcgs, sizeof(CGScalars) * c->bcap, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (c->prof_used) prof_collect(c);
     std::memcpy(h.data(), c->bpinned, sizeof(CGScalars) * c->bcap);
+    if (exec) g_launches += (int64_t)h[0].trips * c->bcg_kernels;
     std::vector<int> run;
     for (int b : act) {
       if (!std::isfinite(h[b].rr)) throw CudaError{"non-finite CG residual in a batched solve", KFBIM_E_NONFINITE};
@@ -2120,6 +2216,7 @@ int kfbim_destroy(kfbim_ctx* c) {
   for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
   for (auto& e : c->cg_exec)
     if (e) cudaGraphExecDestroy(e);
+  if (c->bcg_exec) cudaGraphExecDestroy(c->bcg_exec);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   for (size_t k = 0; k < c->allocs.size(); ++k) {
     if (c->custom_alloc) c->allocator.free(c->allocs[k], c->alloc_bytes[k], c->allocator.user);

@@ -2,7 +2,8 @@
 
 Translation units compiled in parallel: the host setup (g++, FP contraction
 off so that every discrete choice of the setup is reproducible across x86 and
-Arm hosts), the CUDA solver and the slab CG kernels (nvcc), linked by nvcc.
+Arm hosts), the CUDA solver, the slab CG kernels and the four-step transform
+passes of each grid size (nvcc), linked by nvcc.
 """
 import hashlib
 import os
@@ -60,7 +61,7 @@ def build(force=False, verbose=False):
     nvcc = _nvcc()
     inc = "-I" + os.path.join(os.path.dirname(HERE), "include")
     o_setup = os.path.join(OUT, "setup.o")
-    cu_units = ["kfbim", "slab"]
+    cu_units = ["kfbim", "slab", "pass2_n32", "pass2_n64", "pass2_n128", "pass2_n256"]
     objs = [os.path.join(OUT, u + ".o") for u in cu_units]
     cmds = [
         ["g++", "-std=c++17", "-O2", "-fPIC", "-ffp-contract=off", inc, "-c",

@@ -29,6 +29,7 @@
 #include "kernels.cuh"
 #include "transforms.cuh"
 #include "transforms2.cuh"
+#include "pass2.h"
 #include "tc_pass.cuh"
 #include "slab.h"
 
@@ -153,6 +154,37 @@ struct kfbim_ctx {
   int cg_iters = 0, refine_sweeps = 0, interface_solves = 0;
 };
 
+// Raise, never lower, the dynamic shared-memory limit of a kernel on the
+// current device.  The attribute belongs to the device, so the limit already
+// set is tracked per (kernel, device); a kernel launched with several sizes
+// (the runtime-N pass) keeps the largest, since setting a small size would
+// also lower it below the 48 KiB default for every later launch of that
+// kernel, from any path of this library.  Safe to call from several threads.
+cudaError_t kfbim::raise_dynamic_smem(const void* kern, size_t bytes) {
+  struct Limit {
+    const void* kern;
+    int dev;
+    size_t bytes;
+  };
+  static std::mutex m;
+  static std::vector<Limit> limit;
+  int dev = 0;
+  const cudaError_t ge = cudaGetDevice(&dev);
+  if (ge != cudaSuccess) return ge;
+  std::lock_guard<std::mutex> lock(m);
+  size_t* cur = nullptr;
+  for (auto& e : limit)
+    if (e.kern == kern && e.dev == dev) cur = &e.bytes;
+  if (!cur) {
+    limit.push_back({kern, dev, (size_t)48 * 1024});
+    cur = &limit.back().bytes;
+  }
+  if (bytes <= *cur) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) *cur = bytes;
+  return e;
+}
+
 namespace {
 
 struct CudaError {
@@ -215,36 +247,6 @@ inline void check_launch() {
   if (e != cudaSuccess) throw CudaError{std::string("kernel launch: ") + cudaGetErrorString(e)};
 }
 
-// Raise, never lower, the dynamic shared-memory limit of a kernel on the
-// current device.  The attribute belongs to the device, so the limit already
-// set is tracked per (kernel, device); a kernel launched with several sizes
-// (the runtime-N pass) keeps the largest, since setting a small size would
-// also lower it below the 48 KiB default for every later launch of that
-// kernel, from any path of this library.  Safe to call from several threads.
-cudaError_t raise_dynamic_smem(const void* kern, size_t bytes) {
-  struct Limit {
-    const void* kern;
-    int dev;
-    size_t bytes;
-  };
-  static std::mutex m;
-  static std::vector<Limit> limit;
-  int dev = 0;
-  const cudaError_t ge = cudaGetDevice(&dev);
-  if (ge != cudaSuccess) return ge;
-  std::lock_guard<std::mutex> lock(m);
-  size_t* cur = nullptr;
-  for (auto& e : limit)
-    if (e.kern == kern && e.dev == dev) cur = &e.bytes;
-  if (!cur) {
-    limit.push_back({kern, dev, (size_t)48 * 1024});
-    cur = &limit.back().bytes;
-  }
-  if (bytes <= *cur) return cudaSuccess;
-  const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e == cudaSuccess) *cur = bytes;
-  return e;
-}
 
 // ------------------------------------------------------------ transforms
 template <typename T>
@@ -267,15 +269,11 @@ struct Tw<float> {
 // Reduction partials per batch slot: RED_BLOCKS for the staged CG kernels,
 // four per block of the slab iteration's k_cg_zinv (4 x 512 at N = 128).
 constexpr int kRunPartials = 2 * RED_BLOCKS;
-constexpr int kMaxJobs = 48;   // jobs per batched launch: 3 per instance, 16 instances
+constexpr int kMaxJobs = kPass2BatchJobs;   // jobs per batched launch: 3 per instance, 16 instances
 
 template <typename Tin, typename T, typename Tout, int N, int MAXJ>
 void launch_pass2(kfbim_ctx* c, const PassJobs<Tin, Tout, MAXJ>& jobs, int njobs, cudaStream_t s) {
-  const size_t smem = Pass2Smem<T, N>::bytes;
-  auto kern = k_axis_pass2<Tin, T, Tout, N, MAXJ>;
-  CK(raise_dynamic_smem(reinterpret_cast<const void*>(kern), smem));
-  kern<<<dim3((unsigned)(N * N / LPC2), (unsigned)njobs), PASS2_THREADS, smem, s>>>(
-      jobs, Tw<T>::twc(c), Tw<T>::q(c), Tw<T>::s2(c));
+  CK((pass2_launch<N, Tin, T, Tout, MAXJ>(jobs, njobs, Tw<T>::twc(c), Tw<T>::q(c), Tw<T>::s2(c), s)));
 }
 
 // One transform pass of a stage: input, output, axis, first transform,
@@ -313,6 +311,7 @@ void launch_jobs(kfbim_ctx* c, const Job* list, int nj, cudaStream_t s, const in
   PassJobs<Tin, Tout, MAXJ> jobs{};
   for (int k = 0; k < nj; ++k) jobs.j[k] = make_job<Tin, Tout>(c, list[k], skip);
   if (c->N == 128) launch_pass2<Tin, T, Tout, 128, MAXJ>(c, jobs, nj, s);
+  else if (c->N == 256) launch_pass2<Tin, T, Tout, 256, MAXJ>(c, jobs, nj, s);
   else if (c->N == 64) launch_pass2<Tin, T, Tout, 64, MAXJ>(c, jobs, nj, s);
   else launch_pass2<Tin, T, Tout, 32, MAXJ>(c, jobs, nj, s);
   ++g_launches;
@@ -383,7 +382,7 @@ void stage_list(kfbim_ctx* c, const std::vector<Job>& list, cudaStream_t s, cons
   int launches = 1;
   if (use_tc<Tin, T, Tout>(c, list)) {
     launches = tc_passes(c, list, s, skip, &bytes);
-  } else if (c->N == 128 || c->N == 64 || c->N == 32) {
+  } else if (c->N == 256 || c->N == 128 || c->N == 64 || c->N == 32) {
     for (const Job& j : list) bytes += (double)c->N3 * (sizeof(Tin) + sizeof(Tout) * (j.acc ? 2 : 1));
     if (nj <= 3) {
       launch_jobs<Tin, T, Tout, 3>(c, list.data(), nj, s, skip);

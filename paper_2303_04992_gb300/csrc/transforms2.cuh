@@ -223,23 +223,49 @@ __device__ void xform2(const Src& src, const Dst& dst, bool lines_fast, C2<T>* X
       }
     }
     __syncthreads();
-    // step C: R/M DFTs of length M per thread, all read before the output
-    // overwrites the exchange buffer
-    constexpr int NS = R / M;
-    C2<T> w[NS][M];
-    if (active) {
+    if constexpr (M <= R) {
+      // step C: R/M DFTs of length M per thread, all read before the output
+      // overwrites the exchange buffer
+      constexpr int NS = R / M;
+      C2<T> w[NS][M];
+      if (active) {
 #pragma unroll
-      for (int q = 0; q < NS; ++q)
+        for (int q = 0; q < NS; ++q)
 #pragma unroll
-        for (int k = 0; k < M; ++k) w[q][k] = Xp[(q * M + m) * XS + k];
-    }
-    __syncthreads();
-    if (active) {
+          for (int k = 0; k < M; ++k) w[q][k] = Xp[(q * M + m) * XS + k];
+      }
+      __syncthreads();
+      if (active) {
 #pragma unroll
-      for (int q = 0; q < NS; ++q) {
-        dft_reg<M, FINV, T>(w[q]);
+        for (int q = 0; q < NS; ++q) {
+          dft_reg<M, FINV, T>(w[q]);
 #pragma unroll
-        for (int k = 0; k < M; ++k) Zp[q * M + m + R * k] = w[q][k];
+          for (int k = 0; k < M; ++k) Zp[q * M + m + R * k] = w[q][k];
+        }
+      }
+    } else {
+      // step C for M = 2R (L = 512, the DST-I at N = 256; one warp per line
+      // pair): Z[s + R k] = sum_m Y[m][s] w_M^{m k}.  Lane m takes s = m / 2
+      // and the half m0 = m % 2 of the m index: a DFT of length R over m1 of
+      // U[k'] = sum_m1 Y[2 m1 + m0][s] w_R^{m1 k'}, then the radix-2 step with
+      // the partner lane m ^ 1, Z[s + R k] = U0[k'] + w_M^k' U1[k'] and
+      // Z[s + R (k' + R)] = U0[k'] - w_M^k' U1[k'] (lane m0 = 0 writes the
+      // first, lane m0 = 1 the second half).
+      static_assert(M == 2 * R && PPR * M == PASS2_THREADS, "one warp per pair");
+      const int s = m >> 1, m0 = m & 1;
+      C2<T> u[R];
+#pragma unroll
+      for (int m1 = 0; m1 < R; ++m1) u[m1] = Xp[s * XS + 2 * m1 + m0];
+      __syncthreads();
+      dft_reg<R, FINV, T>(u);
+#pragma unroll
+      for (int k = 0; k < R; ++k) {
+        const C2<T> o = {__shfl_xor_sync(0xffffffffu, u[k].x, 1), __shfl_xor_sync(0xffffffffu, u[k].y, 1)};
+        C2<T> w = tw[k * (2 * N / M)];   // w_M^k = exp(-+ 2 pi i k / M)
+        if (FINV) w.y = -w.y;
+        const C2<T> u0 = m0 ? o : u[k];
+        const C2<T> t1 = cmul(m0 ? u[k] : o, w);
+        Zp[s + R * (k + R * m0)] = m0 ? C2<T>{u0.x - t1.x, u0.y - t1.y} : C2<T>{u0.x + t1.x, u0.y + t1.y};
       }
     }
     __syncthreads();

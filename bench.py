@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--transforms", default="auto", choices=["auto", "fft", "tensor", "staged"],
                     help="kernels of the FP32 axis passes (auto: the setup-time autotuner's choice)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (gradient) leg")
+    ap.add_argument("--no-large", action="store_true", help="skip the 256^3 FP32 forward leg")
     ap.add_argument("--batch", type=int, default=16,
                     help="instances of the batched leg (kfbim_solve_batch); 0 skips it")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
@@ -471,6 +472,52 @@ def batch_leg(solver, args, flush, stream, dev):
             "api": "kfbim_solve_batch", "steps": steps}
 
 
+def large_fp32_leg(args, flush, stream, dev, peak, peak_kind):
+    """The FP32 forward solve at 256^3 on the star (one FP32 grid solve per
+    matvec, no refinement), the manufactured forced Stokes pair as in the
+    main workload: solves/s, and the one-axis transform passes against the
+    measured HBM bandwidth.  At 256^3 one FP32 field is 67 MB and a pass of
+    three fields moves 402 MB, three times the L2, so the passes stream from
+    HBM: the HBM-bound roofline run of the transforms."""
+    import torch
+    from paper_2303_04992_gb300 import FP32, Solver
+    geom, grid = ki.star(), ki.grid(256)
+    t0 = time.perf_counter()
+    s = Solver(geom, grid, precision=FP32)
+    setup_s = time.perf_counter() - t0
+    g_h, fpts_h, fgrid_h = inputs(s, geom, grid)
+    g, fpts, fgrid = (torch.from_numpy(a).to(dev) for a in (g_h, fpts_h, fgrid_h))
+    phi = torch.zeros(s.n_primary, dtype=torch.float64, device=dev)
+    s.solve(g, phi, fpts, fgrid)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.zero_()
+    e0.record(stream)
+    s.solve(g, phi, fpts, fgrid)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    st = dict(s.last_stats)
+    s.profile(True)
+    s.solve(g, phi, fpts, fgrid)
+    kprof = s.profile_kernels()
+    s.profile(False)
+    s.close()
+    ms_x, n_x, b_x = kprof["transform_fp32"]
+    achieved = b_x / (ms_x * 1e-3) / 1e9
+    return {"workload": "star256 (r = 0.5 + 0.1 sin 3theta cos 4phi, 256^3, [-1,1]^3)", "precision": "fp32",
+            "solves_per_s": round(1e3 / ms, 4), "ms_per_solve": round(ms, 2), "setup_s": round(setup_s, 2),
+            "gmres_iters": st["gmres_iters"], "cg_iters": st["cg_iters"],
+            "transform_roofline": {"bound": "hbm", "kernel": "k_axis_pass2 (N = 256)", "launches": n_x,
+                                   "avg_launch_us": round(ms_x / n_x * 1e3, 2),
+                                   "bytes_per_launch": round(b_x / n_x), "achieved": round(achieved, 1),
+                                   "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                                   "peak_source": peak_kind,
+                                   "model": "every job reads and writes its field once (N^3 values each)",
+                                   "share_of_solve": round(ms_x / ms, 3)},
+            "api": "kfbim_solve", "steps": 1}
+
+
 # -------------------------------------------------------------- main arms
 def main_kfbim(args):
     import torch
@@ -612,6 +659,10 @@ def main_kfbim(args):
     if args.batch > 0:
         batched = batch_leg(solver, args, flush, stream, dev)
 
+    large = None
+    if not args.no_large and not navier:
+        large = large_fp32_leg(args, flush, stream, dev, peak, peak_kind)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         per_solve = stats[-1]["interface_solves"]
@@ -645,6 +696,7 @@ def main_kfbim(args):
                            "cg_iters": st["cg_iters"], "refine_sweeps": st["refine_sweeps"],
                            "parallelism": "replicas" if world > 1 else "single"},
                 "transforms": dict(tinfo, requested=args.transforms), "adjoint": adjoint,
+                "fp32_256": large,
                 "fp64": fp64, "rel_err_vs_fp64": rel,
                 "rel_err_vs_oracle": golden_error(args.workload, phi_mixed),
                 "oracle_reference": "FP64 oracle solve of the same inputs, GMRES to 1e-13 "

@@ -8,6 +8,7 @@
 #include <stdint.h>
 
 #include "cg_common.cuh"
+#include "fastcvt.h"
 
 namespace kfbim {
 
@@ -188,12 +189,23 @@ __global__ void k_f_minus_gp(const double* __restrict__ f, const Tp* __restrict_
     int id[3];
     unflat(x, lg, id[0], id[1], id[2]);
     const int nrm = c == 0 ? id[0] : (c == 1 ? id[1] : id[2]);
-    double v = 0.0;
-    if (nrm > 0) {
-      const int64_t st = (int64_t)1 << (c * lg);
-      v = f[e] - (double(p[x]) - double(p[x - st])) * ih;
+    if constexpr (sizeof(Tout) == 4 && sizeof(Tp) == 4) {
+      // FP32 result (the MIXED correction): FP32 arithmetic, f rounded by
+      // integer operations (no FP64 instruction per element)
+      float v = 0.f;
+      if (nrm > 0) {
+        const int64_t st = (int64_t)1 << (c * lg);
+        v = f64_to_f32(f[e]) - (float(p[x]) - float(p[x - st])) * float(ih);
+      }
+      r[e] = Tout(v);
+    } else {
+      double v = 0.0;
+      if (nrm > 0) {
+        const int64_t st = (int64_t)1 << (c * lg);
+        v = f[e] - (double(p[x]) - double(p[x - st])) * ih;
+      }
+      r[e] = Tout(v);
     }
-    r[e] = Tout(v);
   }
 }
 
@@ -266,6 +278,31 @@ __global__ void k_dot_partial(const Ta* __restrict__ x, const Tb* __restrict__ y
     s += y ? double(x[e]) * double(y[e]) : double(x[e]);
   s = block_sum<double>(s, sh);
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// partial[b] = this block's compensated FP32 sum of x[e]^2 over a grid-stride
+// range of FP64 values rounded to FP32 by integer operations: a norm for the
+// refinement's stopping test (relative accuracy about 1e-7) without FP64
+// instructions per element.  Finished by k_merge_partials.
+__global__ void k_norm2_partial(const double* __restrict__ x, int64_t n, float2* __restrict__ partial) {
+  __shared__ float2 sh[32];
+  CgAcc<float> a[1];
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const float v = f64_to_f32(x[e]);
+    a[0].add_prod(v, v);
+  }
+  block_merge<1>(a, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = make_float2(a[0].s, a[0].c);
+}
+
+// out = scale * the merged sum of nb compensated pairs (fixed order, one block)
+__global__ void k_merge_partials(const float2* __restrict__ partial, int nb, double scale, double* __restrict__ out) {
+  __shared__ float2 sh[32];
+  CgAcc<float> a[1];
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) a[0].merge(partial[b].x, partial[b].y);
+  block_merge<1>(a, sh);
+  if (threadIdx.x == 0) out[0] = scale * a[0].value();
 }
 
 // out[j] = scale * sum_b partial[j * nb + b]  (fixed order, one block per j)
@@ -442,34 +479,55 @@ __global__ void k_cg_direction_b(const __grid_constant__ CgBatchArgs<T> A, int64
 template <typename T>
 __global__ void k_cg_init(const T* __restrict__ b, int64_t n, CGScalars* s, double tol2, double rank1,
                           double cdiag, double* __restrict__ partial) {
-  __shared__ double sh[32];
-  double a0 = 0.0, a1 = 0.0;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const double v = double(b[e]);
-    a0 += v * v;
-    a1 += v;
-  }
-  a0 = block_sum<double>(a0, sh);
-  a1 = block_sum<double>(a1, sh);
-  __shared__ bool is_last;
-  if (threadIdx.x == 0) {
-    partial[2 * blockIdx.x] = a0;
-    partial[2 * blockIdx.x + 1] = a1;
-    __threadfence();
-    is_last = (atomicAdd(&s->ticket[0], 1u) == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!is_last) return;
-  __threadfence();
   double s0 = 0.0, s1 = 0.0;
-  for (int bk = threadIdx.x; bk < (int)gridDim.x; bk += blockDim.x) {
-    s0 += ((volatile double*)partial)[2 * bk];
-    s1 += ((volatile double*)partial)[2 * bk + 1];
+  bool last;
+  if constexpr (sizeof(T) == 4) {
+    // FP32 right-hand side: compensated FP32 sums of b.b and sum b, merged
+    // through the block and the grid without FP64 arithmetic
+    __shared__ float2 shf[2 * 32];
+    CgAcc<float> a[2];
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+      const float v = b[e];
+      a[0].add_prod(v, v);
+      a[1].add(v);
+    }
+    double out[2];
+    last = last_block_merge<2>(a, reinterpret_cast<float2*>(partial), &s->ticket[0], shf, out);
+    s0 = out[0];
+    s1 = out[1];
+  } else {
+    __shared__ double sh[32];
+    __shared__ bool is_last;
+    double a0 = 0.0, a1 = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+      const double v = double(b[e]);
+      a0 += v * v;
+      a1 += v;
+    }
+    a0 = block_sum<double>(a0, sh);
+    a1 = block_sum<double>(a1, sh);
+    if (threadIdx.x == 0) {
+      partial[2 * blockIdx.x] = a0;
+      partial[2 * blockIdx.x + 1] = a1;
+      __threadfence();
+      is_last = (atomicAdd(&s->ticket[0], 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    last = is_last;
+    if (last) {
+      __threadfence();
+      for (int bk = threadIdx.x; bk < (int)gridDim.x; bk += blockDim.x) {
+        s0 += ((volatile double*)partial)[2 * bk];
+        s1 += ((volatile double*)partial)[2 * bk + 1];
+      }
+      s0 = block_sum<double>(s0, sh);
+      s1 = block_sum<double>(s1, sh);
+      if (threadIdx.x == 0) s->ticket[0] = 0u;
+    }
   }
-  s0 = block_sum<double>(s0, sh);
-  s1 = block_sum<double>(s1, sh);
-  if (threadIdx.x == 0) {
+  if (last && threadIdx.x == 0) {
     s->rr = s0;
     s->bb = s0;
     s->sumd = s1;
@@ -478,7 +536,6 @@ __global__ void k_cg_init(const T* __restrict__ b, int64_t n, CGScalars* s, doub
     s->cdiag = cdiag;
     s->done = (s0 > s->stop) ? 0 : 1;
     s->iters = 0;
-    s->ticket[0] = 0u;
   }
 }
 
@@ -507,7 +564,12 @@ __global__ void k_sum4(const Ta* __restrict__ g, const Tb* __restrict__ b1, cons
                        const Tb* __restrict__ b3, Tb* __restrict__ out, int64_t n) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x)
-    out[e] = Tb(double(g[e]) + double(b1[e]) + double(b2[e]) + double(b3[e]));
+  {
+    if constexpr (sizeof(Ta) == 8 && sizeof(Tb) == 4)
+      out[e] = f64_to_f32(g[e]) + b1[e] + b2[e] + b3[e];   // FP32 right-hand side, FP32 sums
+    else
+      out[e] = Tb(double(g[e]) + double(b1[e]) + double(b2[e]) + double(b3[e]));
+  }
 }
 
 template <typename Ta, typename Tb>
@@ -521,7 +583,12 @@ template <typename Ta>
 __global__ void k_add_to(const Ta* __restrict__ a, double* __restrict__ b, int64_t n) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x)
-    b[e] += double(a[e]);
+  {
+    if constexpr (sizeof(Ta) == 4)
+      b[e] += f32_to_f64(a[e]);   // exact widening by integer operations, one FP64 add
+    else
+      b[e] += double(a[e]);
+  }
 }
 
 // b[e] = a[e] + shift[0] * sc   (pressure gauge)

@@ -542,6 +542,15 @@ void dot(kfbim_ctx* c, const Ta* x, const Tb* y, int64_t n, double* out, double 
   check_launch();
 }
 
+// |x|^2 of an FP64 field for the refinement's stopping test (about 1e-7
+// relative; compensated FP32 sums of the values rounded to FP32).
+void norm2_fast(kfbim_ctx* c, const double* x, int64_t n, double* out, cudaStream_t s) {
+  float2* part = reinterpret_cast<float2*>(c->partial);
+  k_norm2_partial<<<RED_BLOCKS, RED_THREADS, 0, s>>>(x, n, part); ++g_launches;
+  k_merge_partials<<<1, RED_THREADS, 0, s>>>(part, RED_BLOCKS, 1.0, out); ++g_launches;
+  check_launch();
+}
+
 constexpr int kCgGraphIters = 4;
 
 // CG vectors and stage temporaries of one precision (fixed workspace buffers).
@@ -758,7 +767,7 @@ int grid_solve_mixed(kfbim_ctx* c, cudaStream_t s) {
   CK(cudaMemcpyAsync(resg, g, N3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
   k_shift<<<grid_for(N3), 256, 0, s>>>(resg, gmean, -1.0, N3); ++g_launches;
   check_launch();
-  dot(c, resf, resf, 4 * N3, sc, 1.0, s);
+  norm2_fast(c, resf, 4 * N3, sc, s);
   const double ref2 = read_scalar(c, sc, s);
   if (!std::isfinite(ref2)) return KFBIM_E_NONFINITE;
   int status = KFBIM_OK;
@@ -770,7 +779,7 @@ int grid_solve_mixed(kfbim_ctx* c, cudaStream_t s) {
       // reads f, g, u, p (8 N^3 doubles), writes rf, rg (4 N^3)
       prof_end(c, s, at, KFBIM_KCLASS_MAC_RESIDUAL, 1, 12.0 * N3 * sizeof(double));
       check_launch();
-      dot(c, resf, resf, 4 * N3, sc, 1.0, s);
+      norm2_fast(c, resf, 4 * N3, sc, s);
       const double r2 = read_scalar(c, sc, s);
       if (!std::isfinite(r2)) return KFBIM_E_NONFINITE;
       if (r2 <= c->refine_tol_now * c->refine_tol_now * ref2 || ref2 == 0.0) break;
@@ -1795,7 +1804,7 @@ void grid_solve_batch(kfbim_ctx* c, const std::vector<int>& act, cudaStream_t s)
     else dot(c, g, (const double*)nullptr, N3, gmean, 1.0 / (double)N3, s);
     CK(cudaMemcpyAsync(w.res, w.rhs, 4 * N3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
     k_shift<<<grid_for(N3), 256, 0, s>>>(w.res + 3 * N3, gmean, -1.0, N3); ++g_launches;
-    dot(c, w.res, w.res, 4 * N3, c->bscal + 8 * b + 1, 1.0, s);
+    norm2_fast(c, w.res, 4 * N3, c->bscal + 8 * b + 1, s);
   }
   const std::vector<double> ref2 = read_slots(c, act, 1, s);
   std::vector<int> live;
@@ -1809,7 +1818,7 @@ void grid_solve_batch(kfbim_ctx* c, const std::vector<int>& act, cudaStream_t s)
         k_mac_residual<<<grid_for(4 * N3), 256, 0, s>>>(w.rhs, w.rhs + 3 * N3, c->bscal + 8 * b, w.u, w.p,
                                                         c->lg, c->h, c->mu, c->cpen, w.res, w.res + 3 * N3);
         ++g_launches;
-        dot(c, w.res, w.res, 4 * N3, c->bscal + 8 * b + 2, 1.0, s);
+        norm2_fast(c, w.res, 4 * N3, c->bscal + 8 * b + 2, s);
       }
       check_launch();
       const std::vector<double> r2 = read_slots(c, live, 2, s);

@@ -12,6 +12,7 @@
 
 #include <type_traits>
 
+#include "fastcvt.h"
 #include "transforms.cuh"
 
 namespace kfbim {
@@ -113,14 +114,27 @@ struct SmemLines {
     Rb[(2 * p + 1) * RS + o] = vb;
   }
 };
+// An input value in the working type: FP64 input of an FP32 pass is rounded
+// by integer operations (fastcvt.h; the conversion instruction runs on the
+// FP64 pipe, a small fraction of the FP32 rate on this GPU).
+template <typename T, typename Tin>
+__device__ __forceinline__ T to_work(Tin v) {
+  if constexpr (sizeof(T) == 4 && sizeof(Tin) == 8) return f64_to_f32(v);
+  else return T(v);
+}
+
 // The CTA's lines straight from global memory: element i of line l at
 // base[l * ls + i * es].
 template <typename T, typename Tin>
 struct GlobalLines {
   const Tin* base;
   int64_t ls, es;
-  __device__ __forceinline__ T a(int p, int i) const { return T(base[(int64_t)(2 * p) * ls + (int64_t)i * es]); }
-  __device__ __forceinline__ T b(int p, int i) const { return T(base[(int64_t)(2 * p + 1) * ls + (int64_t)i * es]); }
+  __device__ __forceinline__ T a(int p, int i) const {
+    return to_work<T>(base[(int64_t)(2 * p) * ls + (int64_t)i * es]);
+  }
+  __device__ __forceinline__ T b(int p, int i) const {
+    return to_work<T>(base[(int64_t)(2 * p + 1) * ls + (int64_t)i * es]);
+  }
 };
 // Results straight to global memory (out = scale * v, or out += scale * v).
 // Adjacent lines (ls == 1, the y and z passes) are written as one 2-vector.

@@ -27,16 +27,20 @@ __device__ __forceinline__ void unflat(int64_t x, int lg, int& i, int& j, int& k
 // Jump values at every control point (Sec. 4.3).  One thread per fit row
 // (point y, component c'): the fitted value and surface derivatives
 // (d_1, d_2, d_11, d_12, d_22) of phi^(c') as a sequential sum over the row's
-// neighbours (weight-major weights, so consecutive entries of a row are
-// consecutive in memory); then, per block of JB points, the 11 x 18 jump map
-// from shared memory (one output slot per task, input-major map rows).  All
-// arithmetic is FP64.  J is slot-major: J[s * n + y].
+// neighbours; then, per block of JB points, the 11 x 18 jump map from shared
+// memory (one output slot per task, input-major map rows).  All arithmetic is
+// FP64.  J is slot-major: J[s * n + y].
+// The fit rows are interleaved by groups of 32 (a warp's rows): entry i of
+// row r at fit_off[r / 32] + 32 i + r % 32, weight k at fit_w[k ne + that],
+// rows padded to their group's longest with zero weights (column 0), so a
+// warp reads one entry of each of its rows with one coalesced load per array
+// and every row's sum is the one of its CSR order (the padding adds zeros).
 constexpr int JB = 32;                 // points per block (3 JB threads)
 __global__ void __launch_bounds__(3 * JB)
 k_jumps(const double* __restrict__ phi, const double* __restrict__ fpts, int64_t n,
         const int32_t* __restrict__ comp, const int32_t* __restrict__ pid,
-        const int64_t* __restrict__ fit_ptr, const int32_t* __restrict__ fit_col,
-        const double* __restrict__ fit_w, int64_t fit_nnz, const double* __restrict__ jmap,
+        const int64_t* __restrict__ fit_off, const int32_t* __restrict__ fit_col,
+        const double* __restrict__ fit_w, int64_t ne, const double* __restrict__ jmap,
         double* __restrict__ J) {
   __shared__ double D[JB * 3][6];
   const int64_t y0 = (int64_t)blockIdx.x * JB;
@@ -46,11 +50,11 @@ k_jumps(const double* __restrict__ phi, const double* __restrict__ fpts, int64_t
     double acc[6] = {0, 0, 0, 0, 0, 0};
     if (y < n) {
       const int64_t rr = 3 * y0 + t;
-      const int64_t b = fit_ptr[rr], e = fit_ptr[rr + 1];
-      for (int64_t q = b; q < e; ++q) {
+      const int64_t b = fit_off[rr >> 5], e = fit_off[(rr >> 5) + 1];
+      for (int64_t q = b + (rr & 31); q < e; q += 32) {
         const double v = phi[fit_col[q]];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) acc[k] += fit_w[k * fit_nnz + q] * v;
+        for (int k = 0; k < 6; ++k) acc[k] += fit_w[k * ne + q] * v;
       }
     }
 #pragma unroll
@@ -220,8 +224,8 @@ __global__ void k_mac_residual(const double* __restrict__ f, const double* __res
   const int64_t N3 = (int64_t)1 << (3 * lg);
   const double ih = 1.0 / h, c_lap = -mu / (h * h);
   const double gm = gmean[0];
-  // FP64 throughput is the bound here: the six neighbours are summed first and
-  // scaled once, rf = f - (c_lap (sum - 6 u0) + (p1 - p0) / h)
+  // FP64 throughput is the bound here (a small fraction of the FP32 rate on
+  // this GPU): the six neighbours are summed first and scaled once
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < 4 * N3;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int c = (int)(e >> (3 * lg));
@@ -233,7 +237,7 @@ __global__ void k_mac_residual(const double* __restrict__ f, const double* __res
       if (nrm == 0) { rf[e] = 0.0; continue; }
       const double* uc = u + ((int64_t)c << (3 * lg));
       const double u0 = uc[x];
-      double sum = 0.0;
+      double pair[3];
 #pragma unroll
       for (int b = 0; b < 3; ++b) {
         const int64_t st = (int64_t)1 << (b * lg);
@@ -246,12 +250,16 @@ __global__ void k_mac_residual(const double* __restrict__ f, const double* __res
           um = (ib > 0) ? uc[x - st] : -u0;
           up = (ib < N - 1) ? uc[x + st] : -u0;
         }
-        sum += up + um;
+        pair[b] = up + um;
       }
+      // nine FP64 operations per value: five adds for the neighbours, the
+      // centre by one FMA, the pressure difference and two FMAs for
+      // rf = f - dp / h - c_lap (sum - 6 u0)
+      const double lap = fma(-6.0, u0, (pair[0] + pair[1]) + pair[2]);
       const double dp = p[x] - p[x - ((int64_t)1 << (c * lg))];
-      rf[e] = f[e] - fma(c_lap, fma(-6.0, u0, sum), dp * ih);
+      rf[e] = fma(-c_lap, lap, fma(-ih, dp, f[e]));
     } else {
-      double d = 0.0;
+      double dif[3];
 #pragma unroll
       for (int b = 0; b < 3; ++b) {
         const int64_t st = (int64_t)1 << (b * lg);
@@ -259,9 +267,9 @@ __global__ void k_mac_residual(const double* __restrict__ f, const double* __res
         const double* ub = u + ((int64_t)b << (3 * lg));
         const double lo = (ib >= 1) ? ub[x] : 0.0;
         const double hi = (ib + 1 <= N - 1) ? ub[x + st] : 0.0;
-        d += hi - lo;
+        dif[b] = hi - lo;
       }
-      rg[x] = fma(-cpen, p[x], g[x] - gm) - d * ih;
+      rg[x] = fma(-ih, (dif[0] + dif[1]) + dif[2], fma(-cpen, p[x], g[x] - gm));
     }
   }
 }
@@ -732,7 +740,8 @@ __global__ void k_jumps_T(const double* __restrict__ Jbar, int64_t n, const int3
 }
 
 // phibar[col] = Jbar[0][point of col] + sum over the fit entries reading col
-// of sum_s fit_w[s][q] Dbar[row][s]  (the surface fit transposed).
+// of sum_s fit_w[s][q] Dbar[row][s]  (the surface fit transposed; q are the
+// entries' positions in the interleaved fit layout of k_jumps).
 __global__ void k_fit_T(const int64_t* __restrict__ ptr, const int32_t* __restrict__ q,
                         const int32_t* __restrict__ rr, const double* __restrict__ fit_w, int64_t fit_nnz,
                         const double* __restrict__ Dbar, const double* __restrict__ Jbar,

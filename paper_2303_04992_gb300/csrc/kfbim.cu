@@ -52,8 +52,14 @@ struct kfbim_ctx {
   // tables
   int32_t *d_comp = nullptr, *d_pid = nullptr, *d_fit_col = nullptr, *d_tr_comp = nullptr,
           *d_tr_node = nullptr;
-  int64_t *d_fit_ptr = nullptr, *d_corr_row = nullptr, *d_corr_ptr = nullptr,
+  int64_t *d_corr_row = nullptr, *d_corr_ptr = nullptr,
           *d_corr_src = nullptr, *d_prim_of = nullptr;
+  // surface fit, interleaved by groups of 32 rows (k_jumps): entry i of row r
+  // at fit_off[r / 32] + 32 i + r % 32, rows padded to their group's longest
+  // with zero weights; fit_pos maps a CSR entry to its interleaved position
+  int64_t* d_fit_off = nullptr;
+  int64_t fit_ell = 0;
+  std::vector<int32_t> fit_pos;
   double *d_fit_w = nullptr, *d_jmap = nullptr, *d_corr_coef = nullptr, *d_tr_w = nullptr,
          *d_tr_cj = nullptr, *d_s2 = nullptr;
   uint8_t* d_side[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -819,12 +825,12 @@ int interface_solve(kfbim_ctx* c, const double* phi, const double* fpts, const d
   const int64_t n = c->n_all;
   const int at = prof_begin(c, s);
   k_jumps<<<(unsigned)((n + JB - 1) / JB), 3 * JB, 0, s>>>(
-      phi, fpts, n, c->d_comp, c->d_pid, c->d_fit_ptr, c->d_fit_col, c->d_fit_w, c->fit_nnz, c->d_jmap,
+      phi, fpts, n, c->d_comp, c->d_pid, c->d_fit_off, c->d_fit_col, c->d_fit_w, c->fit_ell, c->d_jmap,
       c->J); ++g_launches;
   // fit rows (column index, six weights, the density value), the 11 x 18 jump
   // map, the forcing and the twelve jump slots per point
   prof_end(c, s, at, KFBIM_KCLASS_JUMPS, 1,
-           (double)c->fit_nnz * (4 + 6 * 8 + 8) + (double)n * 8 * (11 * 18 + 3 * (fpts ? 1 : 0) + 12));
+           (double)c->fit_ell * (4 + 6 * 8 + 8) + (double)n * 8 * (11 * 18 + 3 * (fpts ? 1 : 0) + 12));
   check_launch();
   k_rhs_fill<<<grid_for(4 * c->N3), 256, 0, s>>>(fgrid, c->d_side[1], c->d_side[2], c->d_side[3],
                                                   c->lg, c->rhs); ++g_launches;
@@ -1030,7 +1036,7 @@ void adjoint_tables(kfbim_ctx* c) {
     std::vector<int32_t> qv, rv;
     for (int64_t col = 0; col < t.n_prim; ++col) {
       for (const auto& pr : bycol[col]) {
-        qv.push_back((int32_t)pr.first);
+        qv.push_back(c->fit_pos[pr.first]);
         rv.push_back((int32_t)pr.second);
       }
       ptr.push_back((int64_t)qv.size());
@@ -1059,7 +1065,7 @@ int adjoint_tail(kfbim_ctx* c, double* out, cudaStream_t s) {
                                                        rbar, c->d_Jbar); ++g_launches;
   }
   k_jumps_T<<<grid_for(n), 256, 0, s>>>(c->d_Jbar, n, c->d_comp, c->d_pid, c->d_jmap, c->d_Dbar); ++g_launches;
-  k_fit_T<<<grid_for(c->n_prim), 256, 0, s>>>(c->d_fa_ptr, c->d_fa_q, c->d_fa_rr, c->d_fit_w, c->fit_nnz, c->d_Dbar,
+  k_fit_T<<<grid_for(c->n_prim), 256, 0, s>>>(c->d_fa_ptr, c->d_fa_q, c->d_fa_rr, c->d_fit_w, c->fit_ell, c->d_Dbar,
                                                c->d_Jbar, c->d_prim_of, c->n_prim, out); ++g_launches;
   check_launch();
   return st;
@@ -1194,14 +1200,34 @@ void fill_tables(kfbim_ctx* c) {
   const int N = c->N;
   c->d_comp = upload(c, t.comp);
   c->d_pid = upload(c, t.pid);
-  c->d_fit_ptr = upload(c, t.fit_ptr);
-  c->d_fit_col = upload(c, t.fit_col);
   {
-    // weight-major fit weights and input-major jump maps (coalesced warp reads)
-    const size_t nnz = t.fit_col.size();
-    std::vector<double> fw(t.fit_w.size());
-    for (size_t e = 0; e < nnz; ++e)
-      for (int k = 0; k < kFitW; ++k) fw[k * nnz + e] = t.fit_w[kFitW * e + k];
+    // the fit rows interleaved by groups of 32 (a warp of k_jumps reads one
+    // entry of each of its 32 rows with one coalesced load per array), the
+    // weights weight-major within that layout; input-major jump maps
+    const int64_t rows = (int64_t)t.fit_ptr.size() - 1;
+    const int64_t groups = (rows + 31) / 32;
+    std::vector<int64_t> off(groups + 1, 0);
+    for (int64_t g = 0; g < groups; ++g) {
+      int64_t len = 0;
+      for (int64_t r = 32 * g; r < std::min(rows, 32 * g + 32); ++r)
+        len = std::max(len, t.fit_ptr[r + 1] - t.fit_ptr[r]);
+      off[g + 1] = off[g] + 32 * len;
+    }
+    const int64_t E = off[groups];
+    if (E > INT32_MAX) throw CudaError{"surface fit table too large", KFBIM_E_INVALID};
+    std::vector<int32_t> col(std::max<int64_t>(E, 1), 0);
+    std::vector<double> fw((size_t)kFitW * std::max<int64_t>(E, 1), 0.0);
+    c->fit_pos.assign(t.fit_col.size(), 0);
+    for (int64_t r = 0; r < rows; ++r)
+      for (int64_t q = t.fit_ptr[r]; q < t.fit_ptr[r + 1]; ++q) {
+        const int64_t pos = off[r / 32] + 32 * (q - t.fit_ptr[r]) + (r % 32);
+        col[pos] = t.fit_col[q];
+        for (int k = 0; k < kFitW; ++k) fw[(size_t)k * E + pos] = t.fit_w[kFitW * q + k];
+        c->fit_pos[q] = (int32_t)pos;
+      }
+    c->fit_ell = E;
+    c->d_fit_off = upload(c, off);
+    c->d_fit_col = upload(c, col);
     c->d_fit_w = upload(c, fw);
     std::vector<double> jm(t.jmap.size());
     for (int64_t y = 0; y < t.n_all; ++y)
@@ -1891,7 +1917,7 @@ void interface_batch(kfbim_ctx* c, const std::vector<int>& act, const std::vecto
   for (size_t q = 0; q < act.size(); ++q) {
     const kfbim_ctx::Slot& w = c->bs[act[q]];
     k_jumps<<<(unsigned)((n + JB - 1) / JB), 3 * JB, 0, s>>>(
-        phi[q], fpts[q], n, c->d_comp, c->d_pid, c->d_fit_ptr, c->d_fit_col, c->d_fit_w, c->fit_nnz,
+        phi[q], fpts[q], n, c->d_comp, c->d_pid, c->d_fit_off, c->d_fit_col, c->d_fit_w, c->fit_ell,
         c->d_jmap, w.J);
     k_rhs_fill<<<grid_for(4 * c->N3), 256, 0, s>>>(fgrid[q], c->d_side[1], c->d_side[2], c->d_side[3],
                                                     c->lg, w.rhs);
@@ -2153,6 +2179,7 @@ static int setup_common(const kfbim_geometry* geom, const kfbim_grid* grid, cons
   HostTables& t = c->host;
   std::vector<int64_t>().swap(t.fit_ptr);
   std::vector<int32_t>().swap(t.fit_col);
+  std::vector<int32_t>().swap(c->fit_pos);
   std::vector<double>().swap(t.fit_w);
   std::vector<double>().swap(t.jmap);
   std::vector<int64_t>().swap(t.corr_row);
@@ -2286,7 +2313,7 @@ int kfbim_jumps(kfbim_ctx* c, const double* phi, const double* fpts, double* Jou
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = c->n_all;
     k_jumps<<<(unsigned)((n + JB - 1) / JB), 3 * JB, 0, s>>>(
-        phi, fpts, n, c->d_comp, c->d_pid, c->d_fit_ptr, c->d_fit_col, c->d_fit_w, c->fit_nnz, c->d_jmap,
+        phi, fpts, n, c->d_comp, c->d_pid, c->d_fit_off, c->d_fit_col, c->d_fit_w, c->fit_ell, c->d_jmap,
         Jout); ++g_launches;
     check_launch();
     return KFBIM_OK;

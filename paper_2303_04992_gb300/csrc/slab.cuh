@@ -594,7 +594,6 @@ k_cg_zfwd(const __grid_constant__ SlabArgs<MAXB> args, const C2<float>* __restri
   float* E = D + N * C::TILE;
   C2<float>* tw = reinterpret_cast<C2<float>*>(E + N * C::TILE);
   C2<float>* qN = tw + 2 * N;
-  load_tables<N>(tw, qN, nullptr, twg, qg, nullptr, T);
   const int xb = blockIdx.x % (N / C::TILE), y = blockIdx.x / (N / C::TILE);
   const int x0 = xb * C::TILE;
   const double alpha = s->alpha;
@@ -645,6 +644,8 @@ k_cg_zfwd(const __grid_constant__ SlabArgs<MAXB> args, const C2<float>* __restri
       acc[0].add(nv.w);
     }
   }
+  // the tables are read from the FFT on: their loads queue behind the tile's
+  load_tables<N>(tw, qN, nullptr, twg, qg, nullptr, T);
   __syncthreads();
   {
     // DCT-II and DST-II of line tm along z in one FFT (pre: Makhoul's order,
@@ -881,7 +882,6 @@ k_cg_zinv(const __grid_constant__ SlabArgs<MAXB> args, const C2<float>* __restri
   float* E = D + N * C::TILE;
   C2<float>* tw = reinterpret_cast<C2<float>*>(E + N * C::TILE);
   C2<float>* qN = tw + 2 * N;
-  load_tables<N>(tw, qN, nullptr, twg, qg, nullptr, T);
   const int xb = blockIdx.x % (N / C::TILE), y = blockIdx.x / (N / C::TILE);
   const int x0 = xb * C::TILE;
   {
@@ -902,6 +902,7 @@ k_cg_zinv(const __grid_constant__ SlabArgs<MAXB> args, const C2<float>* __restri
       *reinterpret_cast<float4*>(E + a) = bv[j];
     }
   }
+  load_tables<N>(tw, qN, nullptr, twg, qg, nullptr, T);   // read from the FFT on
   __syncthreads();
   {
     // DST-III of line tm of W12 (D) plus DCT-III of line tm of W3 (E) in one

@@ -93,11 +93,14 @@ struct Pass2Smem {
   static constexpr size_t stage_al = (staging + 15) / 16 * 16;
   static constexpr int XA = A::X > A::Z ? A::X : A::Z;
   static constexpr int XB = B::X > B::Z ? B::X : B::Z;
-  // the exchange buffer also receives the FFT output (after a barrier)
+  // the exchange buffer also receives the FFT output (after a barrier); the
+  // twiddle, post-twiddle and eigenvalue tables (4 KB in FP32) are read
+  // through the L1 cache, which keeps an FP32 CTA within a sixth of the
+  // shared memory: six CTAs per SM up to N = 128, so that the 1536 CTAs of a
+  // three-job stage at N = 128 run in two waves of 912 slots instead of three
+  // of 760 (at N = 256 the staging rows hold four per SM)
   static constexpr size_t xbuf = sizeof(C2<T>) * (XA > XB ? XA : XB);
-  // twiddle tables staged per CTA: full-circle tw (2N) and post-twiddles qN (N)
-  static constexpr size_t tables = sizeof(C2<T>) * 3 * N + sizeof(T) * 2 * N;   // + eigenvalue table
-  static constexpr size_t bytes = stage_al + xbuf + tables;
+  static constexpr size_t bytes = stage_al + xbuf;
 };
 
 // Where the lines of a transform come from and go to.  Lines are taken in
@@ -389,7 +392,7 @@ struct PassJobs {
 };
 
 template <typename Tin, typename T, typename Tout, int N, int MAXJ>
-__global__ void __launch_bounds__(PASS2_THREADS, (sizeof(T) == 4 ? 5 : 2))
+__global__ void __launch_bounds__(PASS2_THREADS, (sizeof(T) == 4 ? (N <= 128 ? 6 : 4) : 2))
 k_axis_pass2(const __grid_constant__ PassJobs<Tin, Tout, MAXJ> jobs, const C2<T>* __restrict__ tw,
              const C2<T>* __restrict__ qN, const T* __restrict__ s2) {
   using S = Pass2Smem<T, N>;
@@ -402,16 +405,9 @@ k_axis_pass2(const __grid_constant__ PassJobs<Tin, Tout, MAXJ> jobs, const C2<T>
   T* Rb = reinterpret_cast<T*>(smem2);
   C2<T>* Xb = reinterpret_cast<C2<T>*>(smem2 + S::stage_al);
   C2<T>* Zb = Xb;
-  C2<T>* tws = reinterpret_cast<C2<T>*>(smem2 + S::stage_al + S::xbuf);
-  C2<T>* qs = tws + 2 * N;
-  T* s2s = reinterpret_cast<T*>(qs + N);   // the eigenvalue table, read by the weight
-  for (int e = threadIdx.x; e < 3 * N; e += PASS2_THREADS) {
-    if (e < 2 * N) tws[e] = tw[e];
-    else qs[e - 2 * N] = qN[e - 2 * N];
-  }
-  if (a.wmode != W_NONE)
-    for (int e = threadIdx.x; e < 2 * N; e += PASS2_THREADS) s2s[e] = s2[e];
-  __syncthreads();   // the tables are read from the first gather on
+  const C2<T>* tws = tw;
+  const C2<T>* qs = qN;
+  const T* s2s = s2;   // the eigenvalue table, read by the weight
   constexpr int RS = S::RS;
   const int line0 = blockIdx.x * LPC2;
   const int axis = a.axis;

@@ -3,8 +3,9 @@ configuration, and the error paths of the C ABI.
 
 * one matvec against the oracle's (FP64: <= 1e-10; MIXED: <= 1e-8);
 * the constant-density identity A phi = phi, exact at any size;
-* a full MIXED solve against the FP64 GPU solve (<= 1e-8; both solve the same
-  discrete BIE, parity-tested against the oracle at smaller N);
+* a full MIXED solve (the default relaxation of late matvecs) against the
+  FP64 GPU solve (<= 1e-8; both solve the same discrete BIE, parity-tested
+  against the oracle at smaller N);
 * NaN data -> KFBIM_E_NONFINITE; GMRES cap -> KFBIM_E_NOCONV with the last
   iterate written; bad arguments -> KFBIM_E_INVALID."""
 import numpy as np
@@ -85,8 +86,11 @@ def test_mixed_solve_matches_fp64_solve_at_128(solvers):
         out[prec] = (phi.cpu().numpy(), p.cpu().numpy(), s.last_stats)
     assert rel(out[MIXED][0], out[FP64][0]) < 1e-8
     assert rel(out[MIXED][1], out[FP64][1]) < 1e-7
-    # the inexact (refined FP32) matvec may take a few more GMRES steps near the tolerance
-    assert abs(out[MIXED][2]["gmres_iters"] - out[FP64][2]["gmres_iters"]) <= 3
+    # the inexact (refined FP32) matvec may take a few more GMRES steps near the
+    # tolerance, and the relaxed refinement of late matvecs (relax = 0.1, the
+    # default) some more: at most 15 % over the FP64 count
+    it_m, it_64 = out[MIXED][2]["gmres_iters"], out[FP64][2]["gmres_iters"]
+    assert it_64 - 3 <= it_m <= 1.15 * it_64 + 1, (it_m, it_64)
 
 
 def test_nonfinite_data_is_reported(solvers):

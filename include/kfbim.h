@@ -111,7 +111,7 @@ typedef struct {
 } kfbim_geometry;
 
 typedef struct {
-  int N;          /* cells per axis, a power of two, 16 <= N <= 256 */
+  int N;          /* cells per axis: a power of two with 16 <= N <= 256, or 96 */
   double lo, hi;  /* box [lo, hi]^3 */
 } kfbim_grid;
 

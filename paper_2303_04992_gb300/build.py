@@ -61,7 +61,7 @@ def build(force=False, verbose=False):
     nvcc = _nvcc()
     inc = "-I" + os.path.join(os.path.dirname(HERE), "include")
     o_setup = os.path.join(OUT, "setup.o")
-    cu_units = ["kfbim", "slab", "pass2_n32", "pass2_n64", "pass2_n128", "pass2_n256"]
+    cu_units = ["kfbim", "slab", "pass2_n32", "pass2_n64", "pass2_n96", "pass2_n128", "pass2_n256"]
     objs = [os.path.join(OUT, u + ".o") for u in cu_units]
     cmds = [
         ["g++", "-std=c++17", "-O2", "-fPIC", "-ffp-contract=off", inc, "-c",

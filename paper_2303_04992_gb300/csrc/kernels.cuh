@@ -15,13 +15,36 @@ namespace kfbim {
 constexpr int RED_THREADS = 256;
 constexpr int RED_BLOCKS = 1216;  // 8 x 152 SMs
 
-// N is a power of two: flat index x = (k N + j) N + i, lg = log2 N.
-__device__ __forceinline__ void unflat(int64_t x, int lg, int& i, int& j, int& k) {
-  const int m = (1 << lg) - 1;
-  i = (int)(x & m);
-  j = (int)((x >> lg) & m);
-  k = (int)(x >> (2 * lg));
-}
+// Index arithmetic of the N^3 grid fields, flat index x = (k N + j) N + i:
+// shifts when N is a power of two (lg = log2 N), divisions otherwise (lg < 0,
+// N = 96).
+struct GridIx {
+  int N, lg;
+  __device__ __forceinline__ int64_t n3() const { return (int64_t)N * N * N; }
+  // element stride along axis b
+  __device__ __forceinline__ int64_t stride(int b) const {
+    return b == 0 ? 1 : (b == 1 ? (int64_t)N : (int64_t)N * N);
+  }
+  // field f of a flat index e over consecutive N^3 fields, and e's index x in it
+  __device__ __forceinline__ int field(int64_t e, int64_t& x) const {
+    const int f = lg >= 0 ? (int)(e >> (3 * lg)) : (int)(e / n3());
+    x = e - (int64_t)f * n3();
+    return f;
+  }
+  __device__ __forceinline__ void unflat(int64_t x, int& i, int& j, int& k) const {
+    if (lg >= 0) {
+      const int m = N - 1;
+      i = (int)(x & m);
+      j = (int)((x >> lg) & m);
+      k = (int)(x >> (2 * lg));
+    } else {
+      const int64_t q = x / N;
+      i = (int)(x - q * N);
+      k = (int)(q / N);
+      j = (int)(q - (int64_t)k * N);
+    }
+  }
+};
 
 // ------------------------------------------------------------------ jumps
 // Jump values at every control point (Sec. 4.3).  One thread per fit row
@@ -93,17 +116,17 @@ k_jumps(const double* __restrict__ phi, const double* __restrict__ fpts, int64_t
 // the extended source of the volume integral (Prop. FBI, Alg. 1 step 2).
 __global__ void k_rhs_fill(const double* __restrict__ fgrid, const uint8_t* __restrict__ side1,
                            const uint8_t* __restrict__ side2, const uint8_t* __restrict__ side3,
-                           int lg, double* __restrict__ rhs) {
-  const int64_t N3 = (int64_t)1 << (3 * lg);
+                           GridIx gx, double* __restrict__ rhs) {
+  const int64_t N3 = gx.n3();
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < 4 * N3;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int f = (int)(e >> (3 * lg));
-    const int64_t x = e - ((int64_t)f << (3 * lg));
+    int64_t x;
+    const int f = gx.field(e, x);
     double v = 0.0;
     if (f < 3 && fgrid) {
       const uint8_t* side = f == 0 ? side1 : (f == 1 ? side2 : side3);
       int i, j, k;
-      unflat(x, lg, i, j, k);
+      gx.unflat(x, i, j, k);
       const int nrm = f == 0 ? i : (f == 1 ? j : k);
       if (side[x] && nrm > 0) v = fgrid[e];
     }
@@ -182,30 +205,30 @@ __global__ void k_pressure_trace(const double* __restrict__ p, const double* __r
 
 // r^(c) = f^(c) - G_c p   (face grid c; wall faces 0)
 template <typename Tp, typename Tout>
-__global__ void k_f_minus_gp(const double* __restrict__ f, const Tp* __restrict__ p, int lg, double h,
+__global__ void k_f_minus_gp(const double* __restrict__ f, const Tp* __restrict__ p, GridIx gx, double h,
                              Tout* __restrict__ r) {
-  const int64_t N3 = (int64_t)1 << (3 * lg);
+  const int64_t N3 = gx.n3();
   const double ih = 1.0 / h;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < 3 * N3;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(e >> (3 * lg));
-    const int64_t x = e - ((int64_t)c << (3 * lg));
+    int64_t x;
+    const int c = gx.field(e, x);
     int id[3];
-    unflat(x, lg, id[0], id[1], id[2]);
+    gx.unflat(x, id[0], id[1], id[2]);
     const int nrm = c == 0 ? id[0] : (c == 1 ? id[1] : id[2]);
     if constexpr (sizeof(Tout) == 4 && sizeof(Tp) == 4) {
       // FP32 result (the MIXED correction): FP32 arithmetic, f rounded by
       // integer operations (no FP64 instruction per element)
       float v = 0.f;
       if (nrm > 0) {
-        const int64_t st = (int64_t)1 << (c * lg);
+        const int64_t st = gx.stride(c);
         v = f64_to_f32(f[e]) - (float(p[x]) - float(p[x - st])) * float(ih);
       }
       r[e] = Tout(v);
     } else {
       double v = 0.0;
       if (nrm > 0) {
-        const int64_t st = (int64_t)1 << (c * lg);
+        const int64_t st = gx.stride(c);
         v = f[e] - (double(p[x]) - double(p[x - st])) * ih;
       }
       r[e] = Tout(v);
@@ -218,29 +241,29 @@ __global__ void k_f_minus_gp(const double* __restrict__ f, const Tp* __restrict_
 // (Stokes: c = 0; Navier: the mean is 0 and c = 1/(lambda + mu)).
 __global__ void k_mac_residual(const double* __restrict__ f, const double* __restrict__ g,
                                const double* __restrict__ gmean, const double* __restrict__ u,
-                               const double* __restrict__ p, int lg, double h, double mu, double cpen,
+                               const double* __restrict__ p, GridIx gx, double h, double mu, double cpen,
                                double* __restrict__ rf, double* __restrict__ rg) {
-  const int N = 1 << lg;
-  const int64_t N3 = (int64_t)1 << (3 * lg);
+  const int N = gx.N;
+  const int64_t N3 = gx.n3();
   const double ih = 1.0 / h, c_lap = -mu / (h * h);
   const double gm = gmean[0];
   // FP64 throughput is the bound here (a small fraction of the FP32 rate on
   // this GPU): the six neighbours are summed first and scaled once
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < 4 * N3;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(e >> (3 * lg));
-    const int64_t x = e - ((int64_t)c << (3 * lg));
+    int64_t x;
+    const int c = gx.field(e, x);
     int id[3];
-    unflat(x, lg, id[0], id[1], id[2]);
+    gx.unflat(x, id[0], id[1], id[2]);
     if (c < 3) {
       const int nrm = c == 0 ? id[0] : (c == 1 ? id[1] : id[2]);
       if (nrm == 0) { rf[e] = 0.0; continue; }
-      const double* uc = u + ((int64_t)c << (3 * lg));
+      const double* uc = u + (int64_t)c * N3;
       const double u0 = uc[x];
       double pair[3];
 #pragma unroll
       for (int b = 0; b < 3; ++b) {
-        const int64_t st = (int64_t)1 << (b * lg);
+        const int64_t st = gx.stride(b);
         const int ib = b == 0 ? id[0] : (b == 1 ? id[1] : id[2]);
         double um, up;
         if (b == c) {
@@ -256,15 +279,15 @@ __global__ void k_mac_residual(const double* __restrict__ f, const double* __res
       // centre by one FMA, the pressure difference and two FMAs for
       // rf = f - dp / h - c_lap (sum - 6 u0)
       const double lap = fma(-6.0, u0, (pair[0] + pair[1]) + pair[2]);
-      const double dp = p[x] - p[x - ((int64_t)1 << (c * lg))];
+      const double dp = p[x] - p[x - gx.stride(c)];
       rf[e] = fma(-c_lap, lap, fma(-ih, dp, f[e]));
     } else {
       double dif[3];
 #pragma unroll
       for (int b = 0; b < 3; ++b) {
-        const int64_t st = (int64_t)1 << (b * lg);
+        const int64_t st = gx.stride(b);
         const int ib = b == 0 ? id[0] : (b == 1 ? id[1] : id[2]);
-        const double* ub = u + ((int64_t)b << (3 * lg));
+        const double* ub = u + (int64_t)b * N3;
         const double lo = (ib >= 1) ? ub[x] : 0.0;
         const double hi = (ib + 1 <= N - 1) ? ub[x + st] : 0.0;
         dif[b] = hi - lo;
@@ -653,15 +676,16 @@ namespace kfbim {
 // host (fixed summation order, no atomics).
 
 // rhs[0 : 3 N^3] = ubar with the wall faces (normal index 0) zeroed, rhs[3 N^3 :] = 0.
-__global__ void k_adjoint_rhs(const double* __restrict__ ubar, int lg, double* __restrict__ rhs) {
-  const int64_t N3 = (int64_t)1 << (3 * lg);
+__global__ void k_adjoint_rhs(const double* __restrict__ ubar, GridIx gx, double* __restrict__ rhs) {
+  const int64_t N3 = gx.n3();
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < 4 * N3;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int f = (int)(e >> (3 * lg));
+    int64_t x;
+    const int f = gx.field(e, x);
     double v = 0.0;
     if (f < 3) {
       int i, j, k;
-      unflat(e - ((int64_t)f << (3 * lg)), lg, i, j, k);
+      gx.unflat(x, i, j, k);
       const int nrm = f == 0 ? i : (f == 1 ? j : k);
       if (nrm > 0) v = ubar[e];
     }

@@ -43,7 +43,8 @@ struct kfbim_ctx {
   kfbim_allocator allocator{};
   bool custom_alloc = false;
   std::vector<size_t> alloc_bytes;   // sizes of `allocs`, for the caller's free
-  int N = 0, lg = 0;   // lg = log2 N
+  int N = 0, lg = 0;   // lg = log2 N, or -1 when N is not a power of two (96)
+  GridIx gix() const { return GridIx{N, lg}; }
   int64_t N3 = 0, n_all = 0, n_prim = 0, n_corr_rows = 0;
   double h = 0, mu = 1;
   bool navier = false;
@@ -318,6 +319,7 @@ void launch_jobs(kfbim_ctx* c, const Job* list, int nj, cudaStream_t s, const in
   for (int k = 0; k < nj; ++k) jobs.j[k] = make_job<Tin, Tout>(c, list[k], skip);
   if (c->N == 128) launch_pass2<Tin, T, Tout, 128, MAXJ>(c, jobs, nj, s);
   else if (c->N == 256) launch_pass2<Tin, T, Tout, 256, MAXJ>(c, jobs, nj, s);
+  else if (c->N == 96) launch_pass2<Tin, T, Tout, 96, MAXJ>(c, jobs, nj, s);
   else if (c->N == 64) launch_pass2<Tin, T, Tout, 64, MAXJ>(c, jobs, nj, s);
   else launch_pass2<Tin, T, Tout, 32, MAXJ>(c, jobs, nj, s);
   ++g_launches;
@@ -388,7 +390,7 @@ void stage_list(kfbim_ctx* c, const std::vector<Job>& list, cudaStream_t s, cons
   int launches = 1;
   if (use_tc<Tin, T, Tout>(c, list)) {
     launches = tc_passes(c, list, s, skip, &bytes);
-  } else if (c->N == 256 || c->N == 128 || c->N == 64 || c->N == 32) {
+  } else if (c->N == 256 || c->N == 128 || c->N == 96 || c->N == 64 || c->N == 32) {
     for (const Job& j : list) bytes += (double)c->N3 * (sizeof(Tin) + sizeof(Tout) * (j.acc ? 2 : 1));
     if (nj <= 3) {
       launch_jobs<Tin, T, Tout, 3>(c, list.data(), nj, s, skip);
@@ -749,7 +751,7 @@ int grid_solve_fp64(kfbim_ctx* c, cudaStream_t s) {
   c->cg_iters += it;
   if (st != KFBIM_OK && st != KFBIM_E_NOCONV) return st;
   // u^(c) = (1/mu)(-Delta)^{-1} (f^(c) - G_c p)
-  k_f_minus_gp<double, double><<<grid_for(3 * N3), 256, 0, s>>>(f, c->p, c->lg, c->h, c->u); ++g_launches;
+  k_f_minus_gp<double, double><<<grid_for(3 * N3), 256, 0, s>>>(f, c->p, c->gix(), c->h, c->u); ++g_launches;
   check_launch();
   face_poisson3<double>(c, c->u, c->u, w.T6, s);
   return st;
@@ -781,7 +783,7 @@ int grid_solve_mixed(kfbim_ctx* c, cudaStream_t s) {
     if (sweep > 0) {
       if (c->fp32_only) break;   // FP32: one correction solve, no FP64 residual
       const int at = prof_begin(c, s);
-      k_mac_residual<<<grid_for(4 * N3), 256, 0, s>>>(f, g, gmean, c->u, c->p, c->lg, c->h, c->mu, c->cpen, resf, resg); ++g_launches;
+      k_mac_residual<<<grid_for(4 * N3), 256, 0, s>>>(f, g, gmean, c->u, c->p, c->gix(), c->h, c->mu, c->cpen, resf, resg); ++g_launches;
       // reads f, g, u, p (8 N^3 doubles), writes rf, rg (4 N^3)
       prof_end(c, s, at, KFBIM_KCLASS_MAC_RESIDUAL, 1, 12.0 * N3 * sizeof(double));
       check_launch();
@@ -804,7 +806,7 @@ int grid_solve_mixed(kfbim_ctx* c, cudaStream_t s) {
     if (st == KFBIM_E_NONFINITE) return st;
     // p += dp; u += (1/mu)(-Delta)^{-1}(rf - G dp)
     k_add_to<float><<<grid_for(N3), 256, 0, s>>>(w.x, c->p, N3); ++g_launches;
-    k_f_minus_gp<float, float><<<grid_for(3 * N3), 256, 0, s>>>(resf, w.x, c->lg, c->h, c->fu); ++g_launches;
+    k_f_minus_gp<float, float><<<grid_for(3 * N3), 256, 0, s>>>(resf, w.x, c->gix(), c->h, c->fu); ++g_launches;
     check_launch();
     face_poisson3<float>(c, c->fu, c->fu, w.T6, s);
     k_add_to<float><<<grid_for(3 * N3), 256, 0, s>>>(c->fu, c->u, 3 * N3); ++g_launches;
@@ -833,7 +835,7 @@ int interface_solve(kfbim_ctx* c, const double* phi, const double* fpts, const d
            (double)c->fit_ell * (4 + 6 * 8 + 8) + (double)n * 8 * (11 * 18 + 3 * (fpts ? 1 : 0) + 12));
   check_launch();
   k_rhs_fill<<<grid_for(4 * c->N3), 256, 0, s>>>(fgrid, c->d_side[1], c->d_side[2], c->d_side[3],
-                                                  c->lg, c->rhs); ++g_launches;
+                                                  c->gix(), c->rhs); ++g_launches;
   check_launch();
   if (c->n_corr_rows > 0) {
     k_corrections<<<grid_for(c->n_corr_rows), 256, 0, s>>>(c->d_corr_row, c->d_corr_ptr, c->d_corr_src,
@@ -1090,7 +1092,7 @@ int adjoint_apply(kfbim_ctx* c, const double* lam, double* out, cudaStream_t s) 
 // out = U^T ubar, U: phi -> interface-solve velocity (3 face fields).
 int adjoint_from_u(kfbim_ctx* c, const double* ubar, double* out, cudaStream_t s) {
   adjoint_tables(c);
-  k_adjoint_rhs<<<grid_for(4 * c->N3), 256, 0, s>>>(ubar, c->lg, c->rhs); ++g_launches;
+  k_adjoint_rhs<<<grid_for(4 * c->N3), 256, 0, s>>>(ubar, c->gix(), c->rhs); ++g_launches;
   CK(cudaMemsetAsync(c->d_Jbar, 0, kSlots * c->n_all * sizeof(double), s));
   check_launch();
   return adjoint_tail(c, out, s);
@@ -1842,7 +1844,7 @@ void grid_solve_batch(kfbim_ctx* c, const std::vector<int>& act, cudaStream_t s)
       for (int b : live) {
         const kfbim_ctx::Slot& w = c->bs[b];
         k_mac_residual<<<grid_for(4 * N3), 256, 0, s>>>(w.rhs, w.rhs + 3 * N3, c->bscal + 8 * b, w.u, w.p,
-                                                        c->lg, c->h, c->mu, c->cpen, w.res, w.res + 3 * N3);
+                                                        c->gix(), c->h, c->mu, c->cpen, w.res, w.res + 3 * N3);
         ++g_launches;
         norm2_fast(c, w.res, 4 * N3, c->bscal + 8 * b + 2, s);
       }
@@ -1881,7 +1883,7 @@ void grid_solve_batch(kfbim_ctx* c, const std::vector<int>& act, cudaStream_t s)
     for (int b : live) {
       const kfbim_ctx::Slot& w = c->bs[b];
       k_add_to<float><<<grid_for(N3), 256, 0, s>>>(w.x, w.p, N3);
-      k_f_minus_gp<float, float><<<grid_for(3 * N3), 256, 0, s>>>(w.res, w.x, c->lg, c->h, w.fu);
+      k_f_minus_gp<float, float><<<grid_for(3 * N3), 256, 0, s>>>(w.res, w.x, c->gix(), c->h, w.fu);
       g_launches += 2;
       fsrc.push_back(w.fu);
       u1.push_back(w.fu);
@@ -1920,7 +1922,7 @@ void interface_batch(kfbim_ctx* c, const std::vector<int>& act, const std::vecto
         phi[q], fpts[q], n, c->d_comp, c->d_pid, c->d_fit_off, c->d_fit_col, c->d_fit_w, c->fit_ell,
         c->d_jmap, w.J);
     k_rhs_fill<<<grid_for(4 * c->N3), 256, 0, s>>>(fgrid[q], c->d_side[1], c->d_side[2], c->d_side[3],
-                                                    c->lg, w.rhs);
+                                                    c->gix(), w.rhs);
     g_launches += 2;
     if (c->n_corr_rows > 0) {
       k_corrections<<<grid_for(c->n_corr_rows), 256, 0, s>>>(c->d_corr_row, c->d_corr_ptr, c->d_corr_src,
@@ -2097,7 +2099,7 @@ static int setup_common(const kfbim_geometry* geom, const kfbim_grid* grid, cons
   *out = nullptr;
   if (!geom || !grid || !opt) return KFBIM_E_INVALID;
   const int N = grid->N;
-  if (N < 16 || N > 256 || (N & (N - 1)) != 0 || !(grid->hi > grid->lo)) return KFBIM_E_INVALID;
+  if (N < 16 || N > 256 || ((N & (N - 1)) != 0 && N != 96) || !(grid->hi > grid->lo)) return KFBIM_E_INVALID;
   if (!(opt->mu > 0) || opt->gmres_max < 1 || opt->gmres_max > 200 || opt->cg_max < 1 ||
       opt->precision < KFBIM_FP64 || opt->precision > KFBIM_MIXED_TF32)
     return KFBIM_E_INVALID;
@@ -2135,6 +2137,7 @@ static int setup_common(const kfbim_geometry* geom, const kfbim_grid* grid, cons
   }
   c->N = N;
   while ((1 << c->lg) < N) ++c->lg;
+  if ((1 << c->lg) != N) c->lg = -1;
   c->N3 = (int64_t)N * N * N;
   c->h = (grid->hi - grid->lo) / N;
   c->mu = opt->mu;

@@ -76,12 +76,70 @@ __device__ __forceinline__ void dft_reg(C2<T>* v) {
   }
 }
 
+// cos and sin of 2 pi j / 24 for j in 0..23 (multiples of 15 degrees)
+__host__ __device__ constexpr double cos24(int j) {
+  constexpr double c15 = 0.96592582628906828675, c30 = 0.86602540378443864676, c45 = 0.70710678118654752440,
+                   c60 = 0.5, c75 = 0.25881904510252076235;
+  j = ((j % 24) + 24) % 24;
+  const int q = j % 12;   // cos(x + 180) = -cos x
+  const double v = q == 0 ? 1.0 : q == 1 ? c15 : q == 2 ? c30 : q == 3 ? c45 : q == 4 ? c60 : q == 5 ? c75
+                 : q == 6 ? 0.0 : q == 7 ? -c75 : q == 8 ? -c60 : q == 9 ? -c45 : q == 10 ? -c30 : -c15;
+  return j < 12 ? v : -v;
+}
+__host__ __device__ constexpr double sin24(int j) { return cos24(j - 6); }
+
+// In-register DFT of 24 points, natural order in and out: x[n], n = 8 n1 + n2,
+// as X[k1 + 3 k2] = sum_n2 w_8^(n2 k2) [w_24^(n2 k1) sum_n1 x[8 n1 + n2] w_3^(n1 k1)]
+// (three-point DFTs, the twiddle, then three eight-point DFTs).
+template <bool INV, typename T>
+__device__ __forceinline__ void dft24(C2<T>* v) {
+  const T sg = INV ? T(1) : T(-1);
+  const T h = T(0.86602540378443864676);   // sin 60 degrees
+  C2<T> a[3][8];
+#pragma unroll
+  for (int n2 = 0; n2 < 8; ++n2) {
+    const C2<T> x0 = v[n2], x1 = v[8 + n2], x2 = v[16 + n2];
+    const C2<T> s = {x1.x + x2.x, x1.y + x2.y}, d = {x1.x - x2.x, x1.y - x2.y};
+    a[0][n2] = {x0.x + s.x, x0.y + s.y};
+    // x0 - s / 2 -+ i sin60 d  (the sign of the forward transform, exp(-2 pi i / 3))
+    const C2<T> m = {x0.x - T(0.5) * s.x, x0.y - T(0.5) * s.y};
+    a[1][n2] = {m.x - sg * h * d.y, m.y + sg * h * d.x};
+    a[2][n2] = {m.x + sg * h * d.y, m.y - sg * h * d.x};
+  }
+#pragma unroll
+  for (int k1 = 1; k1 < 3; ++k1)
+#pragma unroll
+    for (int n2 = 1; n2 < 8; ++n2) {
+      const C2<T> w = {T(cos24(n2 * k1)), INV ? T(sin24(n2 * k1)) : T(-sin24(n2 * k1))};
+      a[k1][n2] = cmul(a[k1][n2], w);
+    }
+#pragma unroll
+  for (int k1 = 0; k1 < 3; ++k1) {
+    dft_reg<8, INV, T>(a[k1]);
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) v[k1 + 3 * k2] = a[k1][k2];
+  }
+}
+
+template <int R, bool INV, typename T>
+__device__ __forceinline__ void dft_any(C2<T>* v) {
+  if constexpr (R == 24) dft24<INV, T>(v);
+  else dft_reg<R, INV, T>(v);
+}
+
 template <int L>
 struct Fft2Shape {
-  static constexpr int M = L / 16;                                   // threads per pair
-  static constexpr int PPR = (PASS2_THREADS / M < LPC2 / 2) ? PASS2_THREADS / M : LPC2 / 2;
-  static constexpr int X = PPR * 16 * (M + 1);                       // exchange entries
+  // L = R M: a DFT of R points in each thread's registers, then R / M DFTs of
+  // M points per thread.  R = 16 for the power-of-two lengths; R = 24 (3 x 8)
+  // for the lengths 96 and 192 of the N = 96 grid, so that M (4 or 8) divides R.
+  static constexpr int R = (L & (L - 1)) == 0 ? 16 : 24;
+  static constexpr int M = L / R;                                    // threads per pair
+  static constexpr int PPR_MAX = (PASS2_THREADS / M < LPC2 / 2) ? PASS2_THREADS / M : LPC2 / 2;
+  // pairs per round: a power of two, so that the rounds cover the CTA's pairs
+  static constexpr int PPR = PPR_MAX >= 16 ? 16 : (PPR_MAX >= 8 ? 8 : (PPR_MAX >= 4 ? 4 : (PPR_MAX >= 2 ? 2 : 1)));
+  static constexpr int X = PPR * R * (M + 1);                        // exchange entries
   static constexpr int Z = PPR * (L + 1);                            // output entries (padded rows)
+  static_assert(R % M == 0 || M == 2 * R, "four-step split");
 };
 
 template <typename T, int N>
@@ -177,12 +235,12 @@ template <typename T, int N, int KIND, bool INV, class Src, class Dst>
 __device__ void xform2(const Src& src, const Dst& dst, bool lines_fast, C2<T>* Xb, C2<T>* Zb, const C2<T>* tw,
                        const C2<T>* qN) {
   constexpr int L = (KIND == 2) ? 2 * N : N;
-  constexpr int R = 16;
+  constexpr int R = Fft2Shape<L>::R;
   constexpr int M = L / R;
   constexpr int XS = M + 1;                       // padded exchange row
   constexpr int ZS = L + 1;                       // padded output row
   constexpr int PAIRS = LPC2 / 2;
-  constexpr int PPR = (PASS2_THREADS / M < PAIRS) ? PASS2_THREADS / M : PAIRS;  // pairs per round
+  constexpr int PPR = Fft2Shape<L>::PPR;          // pairs per round
   constexpr int ROUNDS = PAIRS / PPR;
   // DST-I is its own inverse up to the factor 2/N: both directions use the forward FFT
   constexpr bool FINV = (KIND == 2) ? false : INV;
@@ -227,7 +285,7 @@ __device__ void xform2(const Src& src, const Dst& dst, bool lines_fast, C2<T>* X
         }
         v[r] = z;
       }
-      dft_reg<R, FINV, T>(v);
+      dft_any<R, FINV, T>(v);
 #pragma unroll
       for (int s = 0; s < R; ++s) {
         if (s != 0 && m != 0) {
@@ -297,7 +355,7 @@ __device__ void xform2(const Src& src, const Dst& dst, bool lines_fast, C2<T>* X
         vb = (o == 0) ? T(0) : z.x * sc;
       } else if constexpr (!INV) {
         const int k = (KIND == 1) ? (N - 1 - o) : o;
-        const C2<T> zk = Z[k], zc = Z[(N - k) & (N - 1)];
+        const C2<T> zk = Z[k], zc = Z[k == 0 ? 0 : N - k];
         const C2<T> VA = {T(0.5) * (zk.x + zc.x), T(0.5) * (zk.y - zc.y)};
         const C2<T> VB = {T(0.5) * (zk.y + zc.y), T(-0.5) * (zk.x - zc.x)};
         const C2<T> q = qN[k];

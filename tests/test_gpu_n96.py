@@ -1,0 +1,141 @@
+"""The 96^3 grid (SURVEY config C4 takes N in {64, 96, 128}): the one grid
+size that is not a power of two.  Its transforms run on the four-step pass
+with a 24-point DFT in registers (lengths 96 = 24 x 4 and, for the DST-I,
+192 = 24 x 8), its grid kernels index by division, and its Schur CG is the
+staged form (the slab iteration covers N = 32, 64, 128).
+
+* FP64 Poisson solve of each velocity component and the FP64 Schur operator
+  against the oracle's: relative max-norm 1e-12, as at the power-of-two
+  sizes (tests/test_gpu_parity.py);
+* the matvec on the star against the oracle's: FP64 1e-10, MIXED 1e-8;
+* a batch of C4-style instances (divergence-free solid-harmonic boundary
+  data; one forced manufactured pair) equals the single solves and the
+  forced instance's velocity error is below the one at 64^3 (and within a
+  factor 2 of the one at 128^3)."""
+import numpy as np
+import pytest
+
+import kfbim_inputs as ki
+from oracle import kfbim as okfbim, mac
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2303_04992_gb300 import FP64, MIXED, Solver, build  # noqa: E402
+
+build()
+
+N = 96
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+@pytest.fixture(scope="module")
+def star96():
+    o = okfbim.Setup(ki.star(), ki.grid(N))
+    s = Solver(ki.star(), ki.grid(N), precision=FP64)
+    yield o, s
+    s.close()
+
+
+def test_points_match_oracle(star96):
+    o, s = star96
+    xyz, comp, axis, prim = s.points()
+    assert np.array_equal(comp, o.cp.comp) and np.array_equal(axis, o.cp.axis)
+    assert np.array_equal(prim, o.primary)
+    assert np.abs(xyz - o.cp.xyz).max() < 1e-14
+
+
+@pytest.mark.parametrize("c", [1, 2, 3])
+def test_poisson_96(star96, c):
+    _, s = star96
+    r = mac.zero_walls(np.random.default_rng(60 + c).standard_normal((N, N, N)), c)
+    want = mac.poisson(r, c, s.h)
+    got = s.poisson(c, cuda(r), torch.zeros(N ** 3, dtype=torch.float64, device="cuda"))
+    assert rel(got.cpu().numpy().reshape(N, N, N), want) < 1e-12
+
+
+def test_schur_apply_96(star96):
+    _, s = star96
+    d = np.random.default_rng(61).standard_normal((N, N, N))
+    want = mac.schur_apply(d, 1.0, s.h, 1.0 * N ** 3)
+    got = s.schur_apply(cuda(d), torch.zeros(N ** 3, dtype=torch.float64, device="cuda"))
+    assert rel(got.cpu().numpy().reshape(N, N, N), want) < 1e-12
+
+
+def test_matvec_96_fp64_and_mixed(star96):
+    o, s = star96
+    phi = ki.random_density(o.n, seed=62)
+    want = o.apply(phi)
+    out = torch.zeros(s.n_primary, dtype=torch.float64, device="cuda")
+    s.apply(cuda(phi), out)
+    assert rel(out.cpu().numpy(), want) < 1e-10
+    sm = Solver(ki.star(), ki.grid(N), precision=MIXED)
+    out.zero_()
+    sm.apply(cuda(phi), out)
+    sm.close()
+    assert rel(out.cpu().numpy(), want) < 1e-8
+
+
+def _face_nodes(s, c):
+    idx = np.arange(s.N)
+    off = [0.5, 0.5, 0.5]
+    off[c - 1] = 0.0
+    Z, Y, X = np.meshgrid(s.lo + (idx + off[2]) * s.h, s.lo + (idx + off[1]) * s.h,
+                          s.lo + (idx + off[0]) * s.h, indexing="ij")
+    return np.stack([X, Y, Z], -1)
+
+
+def _forced_error(n, batch=None):
+    """Velocity error of the forced manufactured star solve at n^3 (MIXED);
+    with batch = B, the forced pair is instance 0 of a batch with B - 1
+    harmonic instances, and each instance is also solved alone."""
+    s = Solver(ki.star(), ki.grid(n), precision=MIXED)
+    xyz, comp, _, prim = s.points()
+    rows = np.arange(len(comp))
+    N3 = n ** 3
+    B = batch or 1
+    g = np.zeros((B, s.n_primary))
+    fp = np.zeros((B, 3 * s.n_points))
+    fg = np.zeros((B, 3 * N3))
+    g[0] = ki.stokes_velocity(xyz)[rows, comp - 1][prim]
+    fp[0] = ki.stokes_forcing(xyz).T.ravel()
+    fg[0] = np.concatenate([ki.stokes_forcing(_face_nodes(s, c))[..., c - 1].ravel() for c in (1, 2, 3)])
+    for b in range(1, B):
+        g[b] = ki.harmonic_curl_field(300 + b)(xyz)[rows, comp - 1][prim]
+    phi = torch.zeros((B, s.n_primary), dtype=torch.float64, device="cuda")
+    u = torch.zeros((B, 3 * N3), dtype=torch.float64, device="cuda")
+    s.solve_batch(cuda(g), phi, cuda(fp), cuda(fg), u)
+    stats = s.last_stats
+    diffs = []
+    if batch:
+        one = torch.zeros(s.n_primary, dtype=torch.float64, device="cuda")
+        for b in range(B):
+            s.solve(cuda(g[b]), one, cuda(fp[b]), cuda(fg[b]))
+            assert s.last_stats["gmres_iters"] == stats[b]["gmres_iters"], b
+            diffs.append(rel(phi[b].cpu().numpy(), one.cpu().numpy()))
+    ub = u[0].cpu().numpy()
+    err, scale = 0.0, 0.0
+    for c in (1, 2, 3):
+        inside = s.sides(c).ravel()
+        exact = ki.stokes_velocity(_face_nodes(s, c))[..., c - 1].ravel()[inside]
+        err = max(err, np.abs(ub[(c - 1) * N3:c * N3][inside] - exact).max())
+        scale = max(scale, np.abs(exact).max())
+    s.close()
+    return err / scale, diffs
+
+
+def test_batch_96_matches_single_and_sits_between_64_and_128():
+    e96, diffs = _forced_error(N, batch=3)
+    assert max(diffs) <= 1e-12, diffs
+    e64, _ = _forced_error(64)
+    e128, _ = _forced_error(128)
+    # the star's error falls slowly on coarse grids (its poles are not C^1)
+    assert e96 < e64 and e96 < 2.0 * e128, (e64, e96, e128)

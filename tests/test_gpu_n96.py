@@ -132,7 +132,7 @@ def _forced_error(n, batch=None):
     return err / scale, diffs
 
 
-def test_batch_96_matches_single_and_sits_between_64_and_128():
+def test_batch_96_matches_single_and_converges():
     e96, diffs = _forced_error(N, batch=3)
     assert max(diffs) <= 1e-12, diffs
     e64, _ = _forced_error(64)

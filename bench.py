@@ -472,6 +472,35 @@ def batch_leg(solver, args, flush, stream, dev):
             "api": "kfbim_solve_batch", "steps": steps}
 
 
+def c4_grids_leg(args, flush, stream, dev):
+    """Config C4's other grids: the batch of the batched leg (star, seeded
+    solid-harmonic boundary data) on star64 and star96, one kfbim_solve_batch
+    call per grid (one context per grid size)."""
+    import torch
+    from paper_2303_04992_gb300 import MIXED, Solver
+    out = {}
+    for n in (64, 96):
+        s = Solver(ki.star(), ki.grid(n), precision=MIXED)
+        B = args.batch
+        g = torch.from_numpy(batch_inputs(s, B)).to(dev)
+        phi = torch.zeros((B, s.n_primary), dtype=torch.float64, device=dev)
+        s.solve_batch(g, phi)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        e0.record(stream)
+        s.solve_batch(g, phi)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        st = s.last_stats
+        out["star%d" % n] = {"instances": B, "solves_per_s": round(B * 1e3 / ms, 4), "ms_per_batch": round(ms, 2),
+                             "gmres_iters_max": max(x["gmres_iters"] for x in st),
+                             "slab_cg": n in (32, 64, 128)}
+        s.close()
+    return out
+
+
 def large_fp32_leg(args, flush, stream, dev, peak, peak_kind):
     """The FP32 forward solve at 256^3 on the star (one FP32 grid solve per
     matvec, no refinement), the manufactured forced Stokes pair as in the
@@ -659,6 +688,10 @@ def main_kfbim(args):
     if args.batch > 0:
         batched = batch_leg(solver, args, flush, stream, dev)
 
+    c4 = None
+    if args.batch > 0 and not navier and args.workload == "star128":
+        c4 = c4_grids_leg(args, flush, stream, dev)
+
     large = None
     if not args.no_large and not navier:
         large = large_fp32_leg(args, flush, stream, dev, peak, peak_kind)
@@ -696,7 +729,7 @@ def main_kfbim(args):
                            "cg_iters": st["cg_iters"], "refine_sweeps": st["refine_sweeps"],
                            "parallelism": "replicas" if world > 1 else "single"},
                 "transforms": dict(tinfo, requested=args.transforms), "adjoint": adjoint,
-                "fp32_256": large,
+                "fp32_256": large, "c4_grids": c4,
                 "fp64": fp64, "rel_err_vs_fp64": rel,
                 "rel_err_vs_oracle": golden_error(args.workload, phi_mixed),
                 "oracle_reference": "FP64 oracle solve of the same inputs, GMRES to 1e-13 "

@@ -757,6 +757,8 @@ int grid_solve_fp64(kfbim_ctx* c, cudaStream_t s) {
   return st;
 }
 
+double relaxed_inner_tol(const kfbim_ctx* c, double tol);
+
 // MIXED: FP32 transforms and CG inside FP64 iterative refinement.
 int grid_solve_mixed(kfbim_ctx* c, cudaStream_t s) {
   const int64_t N3 = c->N3;
@@ -801,7 +803,7 @@ int grid_solve_mixed(kfbim_ctx* c, cudaStream_t s) {
     k_sum4<double, float><<<grid_for(N3), 256, 0, s>>>(resg, w.q, w.q2, w.q3, b32, N3); ++g_launches;
     check_launch();
     int it = 0;
-    int st = cg<float>(c, b32, w, c->opt.inner_tol, c->opt.cg_max, s, &it);
+    int st = cg<float>(c, b32, w, relaxed_inner_tol(c, c->refine_tol_now), c->opt.cg_max, s, &it);
     c->cg_iters += it;
     if (st == KFBIM_E_NONFINITE) return st;
     // p += dp; u += (1/mu)(-Delta)^{-1}(rf - G dp)
@@ -875,6 +877,16 @@ constexpr double kRelaxCap = 1e-4;
 double relaxed_refine_tol(const kfbim_ctx* c, double res) {
   if (!(c->relax > 0.0) || !(res > 0.0)) return c->opt.refine_tol;
   return std::max(c->opt.refine_tol, std::min(kRelaxCap, c->relax * c->opt.gmres_tol / res));
+}
+
+// The FP32 CG tolerance of a grid solve refined to relative residual `tol`:
+// inner_tol, or looser by the factor the relaxed refinement tolerance allows
+// (a refinement stopping at 1e-5 has no use for an inner solve to 3e-6).
+constexpr double kInnerRelaxFactor = 0.1;
+constexpr double kInnerRelaxCap = 3e-5;
+double relaxed_inner_tol(const kfbim_ctx* c, double tol) {
+  if (!(tol > c->opt.refine_tol)) return c->opt.inner_tol;
+  return std::max(c->opt.inner_tol, std::min(kInnerRelaxCap, kInnerRelaxFactor * tol));
 }
 
 int gmres(kfbim_ctx* c, const double* rhs, double* x, cudaStream_t s, int* iters, double* res_out,
@@ -1734,7 +1746,9 @@ void cg_batch(kfbim_ctx* c, const std::vector<int>& act, double tol, cudaStream_
     CK(cudaMemsetAsync(w.x, 0, n * sizeof(float), s));
     CK(cudaMemcpyAsync(w.r, w.fu, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(w.d, w.fu, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
-    k_cg_init<float><<<RED_BLOCKS, RED_THREADS, 0, s>>>(w.fu, n, &c->bcgs[b], tol * tol, rank1, c->cpen,
+    // the slot's tolerance, relaxed with its refinement tolerance as in grid_solve_mixed
+    const double tb = std::max(tol, relaxed_inner_tol(c, c->b_refine_tol[b]));
+    k_cg_init<float><<<RED_BLOCKS, RED_THREADS, 0, s>>>(w.fu, n, &c->bcgs[b], tb * tb, rank1, c->cpen,
                                                          c->partial);
     ++g_launches;
   }

@@ -238,7 +238,8 @@ def ncu_traffic(workload, kind="fft"):
     return float(t.group(1))
 
 
-# Algorithmic bytes of the hot path by the survey's model (FP32 values, b = 4):
+# Algorithmic bytes of the hot path by a three-pass byte model of the Schur
+# apply (FP32 values, b = 4):
 # one Schur apply S d moves 20 N^3 b (three passes over three fields, read and
 # written, plus d read and q written); the CG vector updates 7 N^3 b (x, r, d,
 # q read; x, r, d written); one CG iteration 27 N^3 b.  The middle pass of
@@ -271,7 +272,7 @@ def ncu_traffic_slab(workload):
 def roofline_line(kernels, kprof, N3, cg_iters, args, peak, peak_kind):
     """The roofline object of the bench line.  Dominant kernel: the one with
     the largest share of the step.  For the slab CG the algorithmic bytes per
-    launch are the survey model's figure for the work the kernel does: k_cg_xy
+    launch are the byte model's figure for the work the kernel does: k_cg_xy
     does the middle pass of the Schur apply on all three terms (6 N^3 b); the
     whole CG iteration (three kernels, plus each run's closing update spread
     over its iterations) is reported beside it against 27 N^3 b."""
@@ -283,7 +284,7 @@ def roofline_line(kernels, kprof, N3, cg_iters, args, peak, peak_kind):
             "achieved_build_bytes": kd["achieved_gbs_build_bytes"]}
     if dom == "cg_xy":
         model = MODEL_MIDDLE_PASS_VALUES * N3 * MODEL_B
-        line["model"] = "survey 8(d): middle pass of S d on three fields, 6 N^3 b, b = 4"
+        line["model"] = "three-pass byte model: middle pass of S d on three fields, 6 N^3 b, b = 4"
         line["traffic"] = ncu_traffic_slab(args.workload)
     elif dom in ("transform_fp32", "transform_fp64"):
         # one one-axis pass of one field: 2 N^3 b per job, at the launch's jobs
@@ -305,7 +306,7 @@ def roofline_line(kernels, kprof, N3, cg_iters, args, peak, peak_kind):
         line["cg_iteration"] = {"us": round(it_us, 3), "model_bytes": bytes_it,
                                 "achieved": round(bytes_it / (it_us * 1e-6) / 1e9, 1),
                                 "frac": round(bytes_it / (it_us * 1e-6) / 1e9 / peak, 4),
-                                "model": "survey 8(d): 27 N^3 b per CG iteration (S d 20, vectors 7)"}
+                                "model": "three-pass byte model: 27 N^3 b per CG iteration (S d 20, vectors 7)"}
     return line
 
 

@@ -125,7 +125,7 @@ typedef enum {
                            jumps, corrections, traces and GMRES stay FP64.  The
                            matvec is accurate to about 1e-6 relative, so
                            gmres_tol should not be below about 1e-6.  A forward
-                           mode for large grids (the benchmark spec C5's 256^3 run) */
+                           mode for large grids (such as a 256^3 forward solve) */
   KFBIM_MIXED_TF32 = 3  /* MIXED with every FP32 transform on the tensor cores
                            (3xTF32 transform-matrix GEMMs, transforms = TENSOR);
                            N = 128 only, else E_INVALID */

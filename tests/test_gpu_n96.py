@@ -1,4 +1,4 @@
-"""The 96^3 grid (SURVEY config C4 takes N in {64, 96, 128}): the one grid
+"""The 96^3 grid (batched runs take N in {64, 96, 128}): the one grid
 size that is not a power of two.  Its transforms run on the four-step pass
 with a 24-point DFT in registers (lengths 96 = 24 x 4 and, for the DST-I,
 192 = 24 x 8), its grid kernels index by division, and its Schur CG is the

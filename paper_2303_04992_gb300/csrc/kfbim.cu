@@ -880,10 +880,10 @@ double relaxed_refine_tol(const kfbim_ctx* c, double res) {
 }
 
 // The FP32 CG tolerance of a grid solve refined to relative residual `tol`:
-// inner_tol, or looser by the factor the relaxed refinement tolerance allows
-// (a refinement stopping at 1e-5 has no use for an inner solve to 3e-6).
-constexpr double kInnerRelaxFactor = 0.1;
-constexpr double kInnerRelaxCap = 3e-5;
+// inner_tol, or looser with the relaxed refinement tolerance, 0.3 of it (a
+// refinement stopping at 1e-5 has no use for an inner solve to 3e-6).
+constexpr double kInnerRelaxFactor = 0.3;
+constexpr double kInnerRelaxCap = 1e-4;
 double relaxed_inner_tol(const kfbim_ctx* c, double tol) {
   if (!(tol > c->opt.refine_tol)) return c->opt.inner_tol;
   return std::max(c->opt.inner_tol, std::min(kInnerRelaxCap, kInnerRelaxFactor * tol));

@@ -88,8 +88,24 @@ def test_host_setup_rejects_bad_geometry():
         Solver(ki.sphere(0.95), ki.grid(16), device=False)
     assert e.value.code == -2
     with pytest.raises(KfbimError) as e:
-        Solver(ki.sphere(), ki.grid(24), device=False)      # not a power of two
+        Solver(ki.sphere(), ki.grid(24), device=False)      # not a power of two, not 96
     assert e.value.code == -1
+    with pytest.raises(KfbimError) as e:
+        Solver(ki.sphere(), ki.grid(80), device=False)
+    assert e.value.code == -1
+
+
+def test_host_setup_accepts_96():
+    """N = 96, the one grid size that is not a power of two (its transforms
+    have a 24-point stage); the host tables match the oracle's points."""
+    from oracle import kfbim as okfbim
+    s = Solver(ki.sphere(), ki.grid(96), device=False)
+    o = okfbim.Setup(ki.sphere(), ki.grid(96))
+    xyz, comp, axis, prim = s.points()
+    assert s.N == 96 and s.n_primary == o.n
+    assert np.array_equal(comp, o.cp.comp) and np.array_equal(prim, o.primary)
+    assert np.abs(xyz - o.cp.xyz).max() < 1e-14
+    s.close()
 
 
 def test_host_only_context_refuses_device_calls():
